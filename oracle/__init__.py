@@ -1,0 +1,170 @@
+"""FP64 CPU oracle of the simplified wall-modeled IBM stress stage (Sec. 3 of
+Liu & Stevens, arXiv:2006.03343).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the product package.
+The arithmetic lives in ``wmibm_oracle.c`` (plain C, double precision, loops in
+the paper's order); this module compiles it with gcc and marshals numpy arrays.
+
+Functions and the passages they follow:
+  classify      Sec. 3.3, node classes on the w-grid and the uv-grid
+  normals       Sec. 3.1, n = grad(phi)/|grad(phi)| (Eq. 24)
+  interp        Sec. 3.3, "2nd-order accurate interpolation" (trilinear)
+  wall_stress   Sec. 3.3, Eq. 28 and the tensor rotation tau_ij = a_im a_jn tau'_mn
+  wall_model_node  the same wall model evaluated at a single node
+  force         Eq. 2 / Eq. 18: f = -div(tau) on the staggered grid (Eqs. 15-16)
+  mask          Sec. 3.2, Eq. 27: the body velocity condition
+  adjoint       chain rule of wall_stress + force for L = <g, f>
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against closed
+forms, invariants and brute force (see the docstrings there).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wmibm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, OpenMP for the loops marked so)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.c_int64
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.orc_classify.argtypes = [_I64, _I64, _I64, _D, _D, ctypes.c_double,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+        lib.orc_normals.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    _D, _D]
+        lib.orc_interp.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   _D, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.orc_interp.restype = ctypes.c_double
+        lib.orc_wall_stress.argtypes = ([_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         _D, _D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _D, _D, _D] + [_D] * 6 + [_D])
+        lib.orc_wall_stress.restype = ctypes.c_int
+        lib.orc_wall_model_node.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _D, ctypes.c_int, _I64, _I64, _I64,
+                                            _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            _D, _D]
+        lib.orc_force.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double] + [_D] * 9
+        lib.orc_mask.argtypes = [_I64, _I64, _I64, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double]
+        if hasattr(lib, "orc_adjoint"):
+            lib.orc_adjoint.argtypes = ([_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         _D, _D, _D, _D, _D, _D, _D, _D, _D, _D])
+            lib.orc_adjoint.restype = ctypes.c_int
+        lib.orc_openmp_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "oracle takes C-contiguous float64 arrays"
+    return a.ctypes.data_as(_D)
+
+
+def _shape(grid):
+    nx, ny, nz, lx, ly, lz = grid
+    return int(nx), int(ny), int(nz), float(lx), float(ly), float(lz)
+
+
+def openmp_threads() -> int:
+    return int(_load().orc_openmp_threads())
+
+
+def classify(grid, phi_uv, phi_w, phi_b):
+    """Sec. 3.3 classes per node: 0 fluid, 1 band, 2 solid -> (cls_uv, cls_w) int8 arrays."""
+    nx, ny, nz, *_ = _shape(grid)
+    cu = np.empty(phi_uv.shape, np.int8)
+    cw = np.empty(phi_w.shape, np.int8)
+    _load().orc_classify(nx, ny, nz, _p(phi_uv), _p(phi_w), float(phi_b),
+                         cu.ctypes.data_as(ctypes.c_void_p), cw.ctypes.data_as(ctypes.c_void_p))
+    return cu, cw
+
+
+def normals(grid, phi):
+    """Sec. 3.1 unit normals on phi's own grid -> array [3, nz, ny, nx]."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    out = np.empty((3,) + phi.shape, np.float64)
+    _load().orc_normals(nx, ny, nz, lx, ly, lz, _p(phi), _p(out))
+    return out
+
+
+def interp(grid, f, is_w, x, y, z):
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    return float(_load().orc_interp(nx, ny, nz, lx, ly, lz, _p(f), int(is_w), float(x), float(y), float(z)))
+
+
+def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4):
+    """Sec. 3.3 wall stress.  tau: dict of 6 float64 arrays (txx txy tyy tzz txz tyz),
+    updated in place.  z0: float or per-cell array.  Returns stats [2, 5]:
+    rows (w-band, uv-band), columns (count, sum tau_w, sum tau_w^2, min tau_w, max U_r)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    if np.isscalar(z0):
+        z0a = np.array([float(z0)], np.float64)
+        is_field = 0
+    else:
+        z0a = np.ascontiguousarray(z0, np.float64)
+        is_field = 1
+    stats = np.zeros(10, np.float64)
+    rc = _load().orc_wall_stress(nx, ny, nz, lx, ly, lz, _p(phi_uv), _p(phi_w), _p(z0a), is_field,
+                                 float(phi_c), float(kappa), float(phi_b), _p(u), _p(v), _p(w),
+                                 _p(tau["txx"]), _p(tau["txy"]), _p(tau["tyy"]), _p(tau["tzz"]),
+                                 _p(tau["txz"]), _p(tau["tyz"]), _p(stats))
+    if rc != 0:
+        raise ValueError("oracle: z0 must satisfy 0 < z0 < phi_c")
+    return stats.reshape(2, 5)
+
+
+def wall_model_node(grid, phi, is_w, i, j, k, u, v, w, z0, phi_c, kappa=0.4):
+    """The Sec. 3.3 wall model at one node -> (tau 3x3, tau_w, |U_r|)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    t9 = np.zeros(9, np.float64)
+    tw = np.zeros(2, np.float64)
+    _load().orc_wall_model_node(nx, ny, nz, lx, ly, lz, _p(phi), int(is_w), int(i), int(j), int(k),
+                                _p(u), _p(v), _p(w), float(z0), float(phi_c), float(kappa), _p(t9), _p(tw))
+    return t9.reshape(3, 3), float(tw[0]), float(tw[1])
+
+
+def force(grid, tau):
+    """f = -div(tau) (Eq. 2, Eqs. 15-16, central differences in x and y) -> (fx, fy, fz)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    shp = tau["txx"].shape
+    fx, fy, fz = (np.empty(shp, np.float64) for _ in range(3))
+    _load().orc_force(nx, ny, nz, lx, ly, lz, _p(tau["txx"]), _p(tau["txy"]), _p(tau["tyy"]),
+                      _p(tau["tzz"]), _p(tau["txz"]), _p(tau["tyz"]), _p(fx), _p(fy), _p(fz))
+    return fx, fy, fz
+
+
+def mask(grid, phi_uv, phi_w, u, v, w, gradp=None, dt=0.0):
+    """Eq. 27 in place on (u, v, w); gradp = (dp/dx, dp/dy, dp/dz) on the velocity grids or None."""
+    nx, ny, nz, *_ = _shape(grid)
+    gx, gy, gz = gradp if gradp is not None else (None, None, None)
+    _load().orc_mask(nx, ny, nz, _p(phi_uv), _p(phi_w), _p(u), _p(v), _p(w), _p(gx), _p(gy), _p(gz), float(dt))

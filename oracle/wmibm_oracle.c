@@ -1,0 +1,445 @@
+/*
+ * FP64 CPU oracle of the simplified wall-modeled immersed boundary stress stage
+ * of Liu & Stevens, "Wall modeled immersed boundary method for high Reynolds
+ * number flow over complex terrain" (arXiv:2006.03343), Sec. 3.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file exists to check the CUDA library; it is
+ * called only by the tests, by the package smoke check and by the CPU-baseline
+ * leg of bench.py.  It shares no code, header, table or helper with the CUDA
+ * path: it works straight from the level set phi at every node it visits and
+ * never builds the precomputed band records the GPU path uses.
+ *
+ * Everything is plain double precision, plain loops, in the order the paper
+ * states the steps.  Compiled with -ffp-contract=off so that no multiply-add is
+ * fused behind the reader's back.
+ *
+ * Grid and storage (Sec. 2.4, Eq. 12 and Eqs. 15-16):
+ *   dx = lx/nx, dy = ly/ny, dz = lz/(nz-1); arrays are [k][j][i], i fastest.
+ *   uv-node (i,j,k) sits at (i dx, j dy, (k+1/2) dz); level k = nz-1 lies above
+ *   the lid and is a ghost level.  w-node (i,j,k) sits at (i dx, j dy, k dz);
+ *   k = 0 is the floor and k = nz-1 the lid.  u, v, p and the stresses
+ *   txx, txy, tyy, tzz live on uv-nodes; w, txz, tyz live on w-nodes.
+ *
+ * Readings of the paper where it is silent (each also listed in the design doc):
+ *   R1  phi_b is a free parameter with 2 phi_b in [dz, 1.5 dz) (Sec. 3.3);
+ *       the caller passes it.
+ *   R2  the velocity sample point lies at distance phi_c from the SURFACE
+ *       along n: x_c = x + (phi_c - phi(x)) n (Sec. 3.3).
+ *   R3  "2nd-order accurate interpolation" = trilinear interpolation of each
+ *       velocity component on its own staggered grid, periodic in x and y,
+ *       clamped to the physical levels in z (uv: 0..nz-2, w: 0..nz-1).
+ *   R4  grad(phi) by 2nd-order central differences on the node's own grid,
+ *       periodic in x, y, one-sided at the first and last z level; a zero
+ *       gradient gives n = (0,0,1).
+ *   R5  the rotation tau_ij = a_im a_jn tau'_mn with only tau'_13 = tau'_31 =
+ *       tau_w is carried out literally with the frame e1 = U_r/|U_r|,
+ *       e2 = n x e1, e3 = n; when U_r = 0 the stress is zero.
+ *   R6  horizontal derivatives of the stress divergence use 2nd-order central
+ *       differences (periodic) instead of the paper's pseudo-spectral ones
+ *       (Eqs. 13-14); vertical ones follow Eqs. 15-16.  f_x = f_y = 0 on the
+ *       ghost uv level, f_z = 0 on the floor and lid w levels (w = 0 there,
+ *       Eqs. 8 and 11).
+ *   R7  a per-cell roughness z0[k][j][i] serves both the uv-node and the
+ *       w-node with the same (i,j,k).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* node classes of Sec. 3.3 */
+#define ORC_FLUID 0
+#define ORC_BAND 1
+#define ORC_SOLID 2
+
+typedef struct {
+    int64_t nx, ny, nz;
+    double dx, dy, dz;
+} orc_grid;
+
+static orc_grid make_grid(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz)
+{
+    orc_grid g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.dx = lx / (double)nx;           /* Eq. 12 */
+    g.dy = ly / (double)ny;
+    g.dz = lz / (double)(nz - 1);
+    return g;
+}
+
+static int64_t at(const orc_grid *g, int64_t i, int64_t j, int64_t k)
+{
+    return (k * g->ny + j) * g->nx + i;
+}
+
+/* periodic wrap of a horizontal index */
+static int64_t wrap(int64_t i, int64_t n)
+{
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+int orc_openmp_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.3: node classification.  is_w selects the w-grid rules.            */
+/* ------------------------------------------------------------------------- */
+static int classify_node(double phi, double phi_b, int is_w)
+{
+    if (is_w) {
+        if (phi > phi_b) return ORC_FLUID;             /* fluid: phi > phi_b        */
+        if (phi >= -phi_b) return ORC_BAND;            /* band: -phi_b <= phi <= phi_b */
+        return ORC_SOLID;                              /* solid: phi < -phi_b       */
+    }
+    if (phi > 2.0 * phi_b) return ORC_FLUID;           /* fluid: phi > 2 phi_b      */
+    if (phi >= 0.0) return ORC_BAND;                   /* band: 0 <= phi <= 2 phi_b */
+    return ORC_SOLID;                                  /* solid: phi < 0            */
+}
+
+void orc_classify(int64_t nx, int64_t ny, int64_t nz, const double *phi_uv, const double *phi_w,
+                  double phi_b, int8_t *cls_uv, int8_t *cls_w)
+{
+    int64_t n = nx * ny * nz;
+    for (int64_t p = 0; p < n; ++p) {
+        cls_uv[p] = (int8_t)classify_node(phi_uv[p], phi_b, 0);
+        cls_w[p] = (int8_t)classify_node(phi_w[p], phi_b, 1);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.1: n = grad(phi) / |grad(phi)| (reading R4).                       */
+/* ------------------------------------------------------------------------- */
+static void normal_at(const orc_grid *g, const double *phi, int64_t i, int64_t j, int64_t k, double n[3])
+{
+    double gx = (phi[at(g, wrap(i + 1, g->nx), j, k)] - phi[at(g, wrap(i - 1, g->nx), j, k)]) / (2.0 * g->dx);
+    double gy = (phi[at(g, i, wrap(j + 1, g->ny), k)] - phi[at(g, i, wrap(j - 1, g->ny), k)]) / (2.0 * g->dy);
+    double gz;
+    if (k == 0)
+        gz = (phi[at(g, i, j, 1)] - phi[at(g, i, j, 0)]) / g->dz;
+    else if (k == g->nz - 1)
+        gz = (phi[at(g, i, j, k)] - phi[at(g, i, j, k - 1)]) / g->dz;
+    else
+        gz = (phi[at(g, i, j, k + 1)] - phi[at(g, i, j, k - 1)]) / (2.0 * g->dz);
+    double mag = sqrt(gx * gx + gy * gy + gz * gz);
+    if (mag <= 1e-12) {
+        n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+        return;
+    }
+    n[0] = gx / mag; n[1] = gy / mag; n[2] = gz / mag;
+}
+
+void orc_normals(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                 const double *phi, double *nrm /* [3][N] */)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    int64_t n = nx * ny * nz;
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                double v[3];
+                normal_at(&g, phi, i, j, k, v);
+                int64_t p = at(&g, i, j, k);
+                nrm[p] = v[0]; nrm[n + p] = v[1]; nrm[2 * n + p] = v[2];
+            }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reading R3: trilinear interpolation of a field on the uv-grid (is_w = 0)  */
+/* or the w-grid (is_w = 1) at the physical point (x, y, z).                 */
+/* ------------------------------------------------------------------------- */
+static double interp(const orc_grid *g, const double *f, int is_w, double x, double y, double z)
+{
+    double xi = x / g->dx;
+    double eta = y / g->dy;
+    double zeta = is_w ? z / g->dz : z / g->dz - 0.5;
+    int64_t top = is_w ? g->nz - 1 : g->nz - 2;  /* highest physical level */
+    if (zeta < 0.0) zeta = 0.0;
+    if (zeta > (double)top) zeta = (double)top;
+
+    double fi = floor(xi), fj = floor(eta), fk = floor(zeta);
+    int64_t k0 = (int64_t)fk;
+    if (k0 > top - 1) k0 = top - 1;
+    double ax = xi - fi, ay = eta - fj, az = zeta - (double)k0;
+    int64_t i0 = wrap((int64_t)fi, g->nx), i1 = wrap((int64_t)fi + 1, g->nx);
+    int64_t j0 = wrap((int64_t)fj, g->ny), j1 = wrap((int64_t)fj + 1, g->ny);
+    int64_t k1 = k0 + 1;
+
+    return (1 - ax) * (1 - ay) * (1 - az) * f[at(g, i0, j0, k0)]
+         + ax * (1 - ay) * (1 - az) * f[at(g, i1, j0, k0)]
+         + (1 - ax) * ay * (1 - az) * f[at(g, i0, j1, k0)]
+         + ax * ay * (1 - az) * f[at(g, i1, j1, k0)]
+         + (1 - ax) * (1 - ay) * az * f[at(g, i0, j0, k1)]
+         + ax * (1 - ay) * az * f[at(g, i1, j0, k1)]
+         + (1 - ax) * ay * az * f[at(g, i0, j1, k1)]
+         + ax * ay * az * f[at(g, i1, j1, k1)];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.3: the wall model at one band node.                                */
+/*   u   : velocity at distance phi_c above the surface along n (R2, R3)     */
+/*   U_r = u - (u.n) n, e1 = U_r/|U_r|, e2 = n x e1, e3 = n                  */
+/*   tau_w = -[kappa U_r / ln(phi_c/z0)]^2                  (Eq. 28)         */
+/*   tau'_13 = tau'_31 = tau_w, all other tau'_mn = 0                        */
+/*   tau_ij = a_im a_jn tau'_mn,  a_im = e_m . e_i          (rotation)       */
+/* Returns the full symmetric tensor in tau[3][3] plus tau_w and |U_r|.      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double tau[3][3];
+    double tau_w;
+    double ur;
+} orc_node_result;
+
+static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
+                          int64_t i, int64_t j, int64_t k,
+                          const double *u, const double *v, const double *w,
+                          double z0, double phi_c, double kappa, orc_node_result *out)
+{
+    double n[3];
+    normal_at(g, phi, i, j, k, n);
+
+    double x = (double)i * g->dx;
+    double y = (double)j * g->dy;
+    double z = is_w ? (double)k * g->dz : ((double)k + 0.5) * g->dz;
+    double d = phi_c - phi[at(g, i, j, k)];
+    double xc = x + d * n[0], yc = y + d * n[1], zc = z + d * n[2];
+
+    double uc[3];
+    uc[0] = interp(g, u, 0, xc, yc, zc);   /* u on the uv-grid */
+    uc[1] = interp(g, v, 0, xc, yc, zc);   /* v on the uv-grid */
+    uc[2] = interp(g, w, 1, xc, yc, zc);   /* w on the w-grid  */
+
+    double un = uc[0] * n[0] + uc[1] * n[1] + uc[2] * n[2];
+    double Ur[3] = { uc[0] - un * n[0], uc[1] - un * n[1], uc[2] - un * n[2] };
+    double ur = sqrt(Ur[0] * Ur[0] + Ur[1] * Ur[1] + Ur[2] * Ur[2]);
+
+    double lg = log(phi_c / z0);
+    double tw = -(kappa * ur / lg) * (kappa * ur / lg);
+    out->tau_w = tw;
+    out->ur = ur;
+
+    memset(out->tau, 0, sizeof(out->tau));
+    if (ur == 0.0) return;                        /* R5: no tangential velocity */
+
+    double e[3][3];                               /* e[m] = local basis vector m */
+    for (int c = 0; c < 3; ++c) e[0][c] = Ur[c] / ur;
+    e[1][0] = n[1] * e[0][2] - n[2] * e[0][1];    /* e2 = n x e1 */
+    e[1][1] = n[2] * e[0][0] - n[0] * e[0][2];
+    e[1][2] = n[0] * e[0][1] - n[1] * e[0][0];
+    for (int c = 0; c < 3; ++c) e[2][c] = n[c];
+
+    double tl[3][3] = { { 0 } };                  /* local-frame stress tau'_mn */
+    tl[0][2] = tw;
+    tl[2][0] = tw;
+
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m)
+                for (int q = 0; q < 3; ++q)
+                    s += e[m][a] * e[q][b] * tl[m][q];
+            out->tau[a][b] = s;
+        }
+}
+
+/* Kahan-compensated accumulation of the band statistics. */
+typedef struct {
+    int64_t count;
+    double sum_tw, c_tw, sum_tw2, c_tw2, min_tw, max_ur;
+} orc_stats_acc;
+
+static void kahan_add(double *sum, double *comp, double x)
+{
+    double y = x - *comp;
+    double t = *sum + y;
+    *comp = (t - *sum) - y;
+    *sum = t;
+}
+
+static void stats_add(orc_stats_acc *s, double tw, double ur)
+{
+    s->count += 1;
+    kahan_add(&s->sum_tw, &s->c_tw, tw);
+    kahan_add(&s->sum_tw2, &s->c_tw2, tw * tw);
+    if (tw < s->min_tw) s->min_tw = tw;
+    if (ur > s->max_ur) s->max_ur = ur;
+}
+
+/*
+ * One wall-stress pass (Sec. 3.3).  tau arrays are in/out: fluid values pass
+ * through, band values are replaced by the wall model, solid values are set
+ * to zero.  txz, tyz are modeled at w-band nodes; txx, txy, tyy, tzz at
+ * uv-band nodes.
+ * z0: scalar (z0_is_field = 0) or a per-cell field [k][j][i] (reading R7).
+ * stats (may be NULL): 2 x {count, sum tau_w, sum tau_w^2, min tau_w, max U_r},
+ * first for the w-band, then for the uv-band, count stored as a double.
+ * Returns 0, or -1 if some z0 does not satisfy 0 < z0 < phi_c.
+ */
+int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                    const double *phi_uv, const double *phi_w,
+                    const double *z0, int z0_is_field, double phi_c, double kappa, double phi_b,
+                    const double *u, const double *v, const double *w,
+                    double *txx, double *txy, double *tyy, double *tzz, double *txz, double *tyz,
+                    double *stats)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    int64_t n = nx * ny * nz;
+    for (int64_t p = 0; p < (z0_is_field ? n : 1); ++p)
+        if (!(z0[p] > 0.0 && z0[p] < phi_c)) return -1;
+
+    orc_stats_acc acc[2];
+    memset(acc, 0, sizeof(acc));
+
+    /* w-grid: txz, tyz */
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                int c = classify_node(phi_w[p], phi_b, 1);
+                if (c == ORC_SOLID) {
+                    txz[p] = 0.0;
+                    tyz[p] = 0.0;
+                } else if (c == ORC_BAND) {
+                    orc_node_result r;
+                    wall_model_at(&g, phi_w, 1, i, j, k, u, v, w, z0[z0_is_field ? p : 0], phi_c, kappa, &r);
+                    txz[p] = r.tau[0][2];
+                    tyz[p] = r.tau[1][2];
+                    stats_add(&acc[0], r.tau_w, r.ur);
+                }
+            }
+
+    /* uv-grid: txx, txy, tyy, tzz */
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                int c = classify_node(phi_uv[p], phi_b, 0);
+                if (c == ORC_SOLID) {
+                    txx[p] = 0.0; txy[p] = 0.0; tyy[p] = 0.0; tzz[p] = 0.0;
+                } else if (c == ORC_BAND) {
+                    orc_node_result r;
+                    wall_model_at(&g, phi_uv, 0, i, j, k, u, v, w, z0[z0_is_field ? p : 0], phi_c, kappa, &r);
+                    txx[p] = r.tau[0][0];
+                    txy[p] = r.tau[0][1];
+                    tyy[p] = r.tau[1][1];
+                    tzz[p] = r.tau[2][2];
+                    stats_add(&acc[1], r.tau_w, r.ur);
+                }
+            }
+
+    if (stats) {
+        for (int s = 0; s < 2; ++s) {
+            stats[5 * s + 0] = (double)acc[s].count;
+            stats[5 * s + 1] = acc[s].sum_tw;
+            stats[5 * s + 2] = acc[s].sum_tw2;
+            stats[5 * s + 3] = acc[s].min_tw;
+            stats[5 * s + 4] = acc[s].max_ur;
+        }
+    }
+    return 0;
+}
+
+/*
+ * The wall model evaluated at one node only (any class), for checks of single
+ * entries at sizes where a full pass is not wanted.  Writes the 3x3 tensor
+ * (row major), tau_w and |U_r|.
+ */
+void orc_wall_model_node(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                         const double *phi, int is_w, int64_t i, int64_t j, int64_t k,
+                         const double *u, const double *v, const double *w,
+                         double z0, double phi_c, double kappa, double *tau9, double *tw_ur)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    orc_node_result r;
+    wall_model_at(&g, phi, is_w, i, j, k, u, v, w, z0, phi_c, kappa, &r);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) tau9[3 * a + b] = r.tau[a][b];
+    tw_ur[0] = r.tau_w;
+    tw_ur[1] = r.ur;
+}
+
+/* Reading R3 exposed for the brute-force interpolation check. */
+double orc_interp(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                  const double *f, int is_w, double x, double y, double z)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    return interp(&g, f, is_w, x, y, z);
+}
+
+/* ------------------------------------------------------------------------- */
+/* f = -div(tau) on the staggered grid (Eq. 2, Eq. 18; reading R6).           */
+/*   f_x(uv) = -[dx txx + dy txy + (txz[k+1] - txz[k])/dz]                   */
+/*   f_y(uv) = -[dx txy + dy tyy + (tyz[k+1] - tyz[k])/dz]                   */
+/*   f_z(w)  = -[dx txz + dy tyz + (tzz[k] - tzz[k-1])/dz]                   */
+/* ------------------------------------------------------------------------- */
+void orc_force(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+               const double *txx, const double *txy, const double *tyy,
+               const double *tzz, const double *txz, const double *tyz,
+               double *fx, double *fy, double *fz)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                int64_t ip = at(&g, wrap(i + 1, nx), j, k), im = at(&g, wrap(i - 1, nx), j, k);
+                int64_t jp = at(&g, i, wrap(j + 1, ny), k), jm = at(&g, i, wrap(j - 1, ny), k);
+
+                if (k == nz - 1) {            /* ghost uv level */
+                    fx[p] = 0.0;
+                    fy[p] = 0.0;
+                } else {
+                    int64_t kp = at(&g, i, j, k + 1);
+                    double dtxx_dx = (txx[ip] - txx[im]) / (2.0 * g.dx);
+                    double dtxy_dy = (txy[jp] - txy[jm]) / (2.0 * g.dy);
+                    double dtxz_dz = (txz[kp] - txz[p]) / g.dz;                /* Eq. 16 */
+                    fx[p] = -(dtxx_dx + dtxy_dy + dtxz_dz);
+
+                    double dtxy_dx = (txy[ip] - txy[im]) / (2.0 * g.dx);
+                    double dtyy_dy = (tyy[jp] - tyy[jm]) / (2.0 * g.dy);
+                    double dtyz_dz = (tyz[kp] - tyz[p]) / g.dz;
+                    fy[p] = -(dtxy_dx + dtyy_dy + dtyz_dz);
+                }
+
+                if (k == 0 || k == nz - 1) {  /* floor and lid: w = 0 */
+                    fz[p] = 0.0;
+                } else {
+                    int64_t km = at(&g, i, j, k - 1);
+                    double dtxz_dx = (txz[ip] - txz[im]) / (2.0 * g.dx);
+                    double dtyz_dy = (tyz[jp] - tyz[jm]) / (2.0 * g.dy);
+                    double dtzz_dz = (tzz[p] - tzz[km]) / g.dz;                /* Eq. 15 */
+                    fz[p] = -(dtxz_dx + dtyz_dy + dtzz_dz);
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 3.2, Eq. 27: u*_IB = u* where phi > 0, 3 dt/2 grad p where phi <= 0. */
+/* gpx, gpy, gpz may all be NULL: then the body velocity is set to zero.      */
+/* ------------------------------------------------------------------------- */
+void orc_mask(int64_t nx, int64_t ny, int64_t nz, const double *phi_uv, const double *phi_w,
+              double *u, double *v, double *w,
+              const double *gpx, const double *gpy, const double *gpz, double dt)
+{
+    int64_t n = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; ++p) {
+        if (phi_uv[p] <= 0.0) {
+            u[p] = gpx ? 1.5 * dt * gpx[p] : 0.0;
+            v[p] = gpy ? 1.5 * dt * gpy[p] : 0.0;
+        }
+        if (phi_w[p] <= 0.0) {
+            w[p] = gpz ? 1.5 * dt * gpz[p] : 0.0;
+        }
+    }
+}
