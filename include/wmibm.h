@@ -1,0 +1,179 @@
+/*
+ * wmibm.h - C ABI of libwmibm.so, the sm_103a CUDA implementation of the
+ * per-time-step stress stage of the simplified wall-modeled immersed boundary
+ * method (Liu & Stevens, arXiv:2006.03343, Sec. 3).
+ *
+ * Grid (Sec. 2.4, Eq. 12): nx x ny x nz nodes, dx = lx/nx, dy = ly/ny,
+ * dz = lz/(nz-1).  Every field is a dense array [k][j][i] (i fastest),
+ * nx*ny*nz elements, contiguous, on the device of the handle.
+ *   uv-node (i,j,k) at (i dx, j dy, (k+1/2) dz): u, v, txx, txy, tyy, tzz, fx, fy
+ *   w-node  (i,j,k) at (i dx, j dy, k dz):       w, txz, tyz, fz
+ * The uv level k = nz-1 lies above the lid (ghost level).
+ *
+ * Stress arrays are passed as an array of 6 pointers in the order
+ *   tau[0..5] = txx, txy, tyy, tzz, txz, tyz.
+ *
+ * Conventions for every call:
+ *   - the caller owns every field buffer; the handle owns its index lists and
+ *     band records (copied/derived at init) and frees them in wmibm_destroy;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     work is enqueued on it and the call returns without waiting, except
+ *     wmibm_init, which synchronises `stream` once to read back list sizes;
+ *   - the calling thread's current CUDA device must be the handle's device;
+ *   - the return value is a status code below; on failure nothing further is
+ *     enqueued and wmibm_last_error(h) describes the problem;
+ *   - calls on one handle must not overlap on the GPU (they share the handle's
+ *     reduction scratch): use one stream per handle, or order the streams.
+ */
+#ifndef WMIBM_H
+#define WMIBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define WMIBM_OK 0
+#define WMIBM_EINVAL 1    /* invalid argument (sizes, NaN in phi, z0 >= phi_c, ...) */
+#define WMIBM_ENOMEM 2    /* device or host allocation failed */
+#define WMIBM_ECUDA 3     /* a CUDA runtime call or kernel launch failed */
+#define WMIBM_ESTATE 4    /* wrong device, or a call the handle's mode does not allow */
+#define WMIBM_ETIMEOUT 5  /* a bounded device-side wait gave up */
+
+/* element types */
+#define WMIBM_F32 0
+#define WMIBM_F64 1
+#define WMIBM_BF16 2
+
+/* list selectors for wmibm_list_size / wmibm_export_list */
+#define WMIBM_LIST_BAND_W 0      /* w-nodes with -phi_b <= phi <= phi_b      (Sec. 3.3) */
+#define WMIBM_LIST_BAND_UV 1     /* uv-nodes with 0 <= phi <= 2 phi_b        (Sec. 3.3) */
+#define WMIBM_LIST_SOLID_W 2     /* w-nodes with phi < -phi_b: txz = tyz = 0 (Sec. 3.3) */
+#define WMIBM_LIST_SOLID_UV 3    /* uv-nodes with phi < 0: txx..tzz = 0      (Sec. 3.3) */
+#define WMIBM_LIST_BODY_W 4      /* w-nodes with phi <= 0: masked w          (Sec. 3.2, Eq. 27) */
+#define WMIBM_LIST_BODY_UV 5     /* uv-nodes with phi <= 0: masked u, v      (Sec. 3.2, Eq. 27) */
+
+typedef struct wmibm_grid {
+    int32_t nx, ny, nz;     /* nodes per direction; nz >= 3 */
+    double lx, ly, lz;      /* domain lengths, > 0 */
+} wmibm_grid;
+
+typedef struct wmibm_opts {
+    double phi_b;           /* half band width; <= 0 selects dz/2 (2 phi_b = dz, Sec. 3.3) */
+    double kappa;           /* von Karman constant; <= 0 selects 0.4 (Sec. 2.2) */
+    int32_t dtype;          /* WMIBM_F32 or WMIBM_F64: type of tau, f, grad p and of the arithmetic */
+    int32_t vel_dtype;      /* storage type of u, v, w: equal to dtype, or WMIBM_BF16 when dtype is F32 */
+} wmibm_opts;
+
+/* Band statistics of one wall-stress pass, one record per band (w, then uv). */
+typedef struct wmibm_band_stats {
+    int64_t count;          /* band nodes */
+    double sum_tw;          /* sum of tau_w = -[kappa U_r / ln(phi_c/z0)]^2  (Eq. 28) */
+    double sum_tw2;         /* sum of tau_w^2 */
+    double min_tw;          /* most negative tau_w (0 for an empty band) */
+    double max_ur;          /* largest tangential speed |U_r| (0 for an empty band) */
+} wmibm_band_stats;
+
+typedef struct wmibm_handle wmibm_handle;
+
+/*
+ * wmibm_init - one-time set-up for one terrain (Sec. 3.1 and Sec. 3.3: "phi and
+ * n are computed only once"; the node classes are identified at start-up).
+ *   out      : receives the new handle
+ *   g        : grid; nx*ny*nz must be < 2^31
+ *   phi_uv   : HOST, nx*ny*nz doubles: signed distance at the uv-nodes (+ fluid, - solid)
+ *   phi_w    : HOST, nx*ny*nz doubles: signed distance at the w-nodes
+ *   z0       : HOST: one double (z0_is_field = 0) or nx*ny*nz doubles, the roughness
+ *              of cell (i,j,k), shared by uv-node and w-node (i,j,k); 0 < z0 < phi_c
+ *   phi_c    : distance above the surface at which the velocity is sampled
+ *              (Sec. 3.3, phi_c >= 2 phi_b)
+ *   opts     : NULL for defaults (F32, phi_b = dz/2, kappa = 0.4)
+ * The inputs are copied; the handle keeps no pointer to them.  On the GPU (in
+ * FP64) it classifies every node, computes n = grad(phi)/|grad(phi)| by central
+ * differences, builds ascending index lists of the band, solid and body nodes
+ * and, per band node, the interpolation stencil of x_c = x + (phi_c - phi) n
+ * and the factor kappa^2 / ln^2(phi_c/z0).
+ * Errors: EINVAL (bad sizes, non-finite phi, z0 out of range, phi_c < 2 phi_b),
+ * ENOMEM, ECUDA.  On error *out is NULL.
+ */
+int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double *phi_uv, const double *phi_w,
+               const double *z0, int32_t z0_is_field, double phi_c, const wmibm_opts *opts, void *stream);
+
+/*
+ * wmibm_wall_stress - the wall model at every band node (Sec. 3.3, Eq. 28 and
+ * the rotation tau_ij = a_im a_jn tau'_mn).
+ *   u, v, w  : DEVICE velocity fields (vel_dtype), read only
+ *   tau      : DEVICE stresses (dtype), in/out: fluid entries are left untouched,
+ *              band entries are overwritten (txz, tyz on w-band nodes; txx, txy,
+ *              tyy, tzz on uv-band nodes), solid entries are set to 0
+ *   stats    : NULL, or DEVICE-accessible wmibm_band_stats[2] (w-band, uv-band)
+ *              written by the same launch
+ * Errors: EINVAL (NULL field pointer), ESTATE, ECUDA.
+ */
+int wmibm_wall_stress(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                      wmibm_band_stats *stats, void *stream);
+
+/*
+ * wmibm_force - the forcing f = -div(tau) on the staggered grid (Eq. 2 and
+ * Eq. 18, vertical differences of Eqs. 15-16; horizontal derivatives are
+ * second-order central differences, periodic).
+ *   tau      : DEVICE, 6 stress fields (dtype), read only
+ *   fx, fy   : DEVICE uv-node fields (dtype), written everywhere; 0 on the ghost level
+ *   fz       : DEVICE w-node field (dtype), written everywhere; 0 on the floor and lid
+ * Errors: EINVAL, ESTATE, ECUDA.
+ */
+int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream);
+
+/*
+ * wmibm_mask - the immersed-boundary velocity condition (Sec. 3.2, Eq. 27):
+ * where phi <= 0 (each component on its own grid) the velocity becomes
+ * 3 dt/2 * grad p, or 0 when gradp is NULL; elsewhere it is untouched.
+ *   u, v, w  : DEVICE velocity fields (vel_dtype), in/out
+ *   gradp    : NULL, or 3 DEVICE fields (dtype): dp/dx, dp/dy on uv-nodes, dp/dz on w-nodes
+ * Errors: EINVAL, ESTATE, ECUDA.
+ */
+int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, void *stream);
+
+/*
+ * wmibm_step - wmibm_wall_stress, wmibm_force and wmibm_mask in that order on
+ * one stream: one pass of the whole per-step stress stage.
+ */
+int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
+               const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream);
+
+/* Number of entries of list `which` (WMIBM_LIST_*), or -1 for a bad argument. */
+int64_t wmibm_list_size(const wmibm_handle *h, int32_t which);
+
+/*
+ * wmibm_export_list - copy list `which` (ascending int32 node indices) into the
+ * HOST buffer dst of capacity cap entries; synchronises `stream`.
+ * Errors: EINVAL (cap too small), ECUDA.
+ */
+int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap, void *stream);
+
+/*
+ * wmibm_traffic_bytes - algorithmic bytes of one call, counted at init:
+ *   which = 0: wmibm_wall_stress (band records, each distinct velocity element
+ *              its stencils touch, band stress writes, solid index reads and
+ *              zero writes); 1: wmibm_force (6 stress reads + 3 force writes per
+ *              node); 2: wmibm_mask without grad p; 3: wmibm_mask with grad p.
+ * Returns -1 for a bad argument.
+ */
+int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which);
+
+/* Releases everything the handle owns (waits for the device). NULL is ignored. */
+void wmibm_destroy(wmibm_handle *h);
+
+/* Static text for a status code. */
+const char *wmibm_status_string(int status);
+
+/* Text of the last error on this handle (empty if none); NULL handle: last init error. */
+const char *wmibm_last_error(const wmibm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WMIBM_H */

@@ -1,0 +1,492 @@
+// One-time set-up of a terrain (Sec. 3.1 and Sec. 3.3 of Liu & Stevens,
+// arXiv:2006.03343): node classes, ascending index lists, unit normals and the
+// per-band-node interpolation records, all computed on the GPU in FP64.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace wmibm;
+
+namespace {
+
+char g_init_error[512] = "";
+
+constexpr int kChunkItems = 8;                     // nodes per thread in the list kernels
+constexpr int kChunk = kThreads * kChunkItems;     // nodes per block
+
+// ------------------------------------------------------------------------- //
+// Sec. 3.3: the six predicates, in the order of WMIBM_LIST_*.
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ void predicates(double pw, double puv, double pb, bool q[6])
+{
+    q[0] = (pw >= -pb) && (pw <= pb);            // w band:  -phi_b <= phi <= phi_b
+    q[1] = (puv >= 0.0) && (puv <= 2.0 * pb);    // uv band: 0 <= phi <= 2 phi_b
+    q[2] = pw < -pb;                             // w solid
+    q[3] = puv < 0.0;                            // uv solid
+    q[4] = pw <= 0.0;                            // w body (Eq. 27)
+    q[5] = puv <= 0.0;                           // uv body (Eq. 27)
+}
+
+__global__ void __launch_bounds__(kThreads) k_count(const double *__restrict__ phi_uv,
+                                                    const double *__restrict__ phi_w, int64_t n, double pb,
+                                                    int32_t *__restrict__ counts, int64_t nblk)
+{
+    __shared__ int warp_tot[6][kThreads / 32];
+    int c[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    for (int it = 0; it < kChunkItems; ++it) {
+        int64_t p = base + (int64_t)it * kThreads + threadIdx.x;
+        if (p < n) {
+            bool q[6];
+            predicates(phi_w[p], phi_uv[p], pb, q);
+            for (int l = 0; l < 6; ++l) c[l] += q[l] ? 1 : 0;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 0; l < 6; ++l) {
+        int v = c[l];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) warp_tot[l][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int s = 0;
+        for (int w = 0; w < kThreads / 32; ++w) s += warp_tot[threadIdx.x][w];
+        counts[threadIdx.x * nblk + blockIdx.x] = s;
+    }
+}
+
+// Stable compaction: block b writes its matches in ascending node order starting
+// at offsets[l * nblk + b] (exclusive scan of k_count's totals).
+__global__ void __launch_bounds__(kThreads) k_compact(const double *__restrict__ phi_uv,
+                                                      const double *__restrict__ phi_w, int64_t n, double pb,
+                                                      const int64_t *__restrict__ offsets, int64_t nblk,
+                                                      Lists lists)
+{
+    __shared__ int warp_tot[6][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int64_t run[6];
+    for (int l = 0; l < 6; ++l) run[l] = offsets[l * nblk + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    for (int it = 0; it < kChunkItems; ++it) {
+        int64_t p = base + (int64_t)it * kThreads + threadIdx.x;
+        bool q[6] = {false, false, false, false, false, false};
+        if (p < n) predicates(phi_w[p], phi_uv[p], pb, q);
+        unsigned bal[6];
+        for (int l = 0; l < 6; ++l) {
+            bal[l] = __ballot_sync(0xffffffffu, q[l]);
+            if (lane == 0) warp_tot[l][warp] = __popc(bal[l]);
+        }
+        __syncthreads();
+        for (int l = 0; l < 6; ++l) {
+            int before = 0, total = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                int t = warp_tot[l][w];
+                before += (w < warp) ? t : 0;
+                total += t;
+            }
+            if (q[l]) lists.p[l][run[l] + before + __popc(bal[l] & lt_mask)] = (int32_t)p;
+            run[l] += total;
+        }
+        __syncthreads();
+    }
+}
+
+struct RecParams {
+    const double *phi_uv, *phi_w, *z0;
+    int z0_is_field;
+    const int32_t *band_w, *band_uv;
+    int64_t nb_w, nb_uv;
+    int32_t nx, ny, nz;
+    double dx, dy, dz, phi_c, kappa;
+    void *rec;
+    int f64;
+};
+
+__device__ __forceinline__ int32_t wrapi(int64_t i, int32_t n)
+{
+    int64_t r = i % n;
+    return (int32_t)(r < 0 ? r + n : r);
+}
+
+// Per band node: n = grad(phi)/|grad(phi)| (Sec. 3.1, central differences,
+// one-sided at the first and last level, (0,0,1) where the gradient vanishes),
+// x_c = x + (phi_c - phi) n (Sec. 3.3), its trilinear stencil on both grids
+// (periodic in x, y; z clamped to the physical levels) and C = kappa^2/ln^2(phi_c/z0).
+__global__ void __launch_bounds__(kThreads) k_records(RecParams p)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.nb_w + p.nb_uv) return;
+    const bool is_w = t < p.nb_w;
+    const int32_t idx = is_w ? p.band_w[t] : p.band_uv[t - p.nb_w];
+    const double *phi = is_w ? p.phi_w : p.phi_uv;
+    const int64_t plane = (int64_t)p.nx * p.ny;
+    const int32_t k = (int32_t)(idx / plane);
+    const int32_t j = (int32_t)((idx - (int64_t)k * plane) / p.nx);
+    const int32_t i = (int32_t)(idx - (int64_t)k * plane - (int64_t)j * p.nx);
+
+    auto at = [&](int32_t ii, int32_t jj, int32_t kk) { return phi[((int64_t)kk * p.ny + jj) * p.nx + ii]; };
+    double gx = (at(wrapi(i + 1, p.nx), j, k) - at(wrapi(i - 1, p.nx), j, k)) / (2.0 * p.dx);
+    double gy = (at(i, wrapi(j + 1, p.ny), k) - at(i, wrapi(j - 1, p.ny), k)) / (2.0 * p.dy);
+    double gz;
+    if (k == 0)
+        gz = (at(i, j, 1) - at(i, j, 0)) / p.dz;
+    else if (k == p.nz - 1)
+        gz = (at(i, j, k) - at(i, j, k - 1)) / p.dz;
+    else
+        gz = (at(i, j, k + 1) - at(i, j, k - 1)) / (2.0 * p.dz);
+    double mag = sqrt(gx * gx + gy * gy + gz * gz);
+    double nx, ny, nz;
+    if (mag <= 1e-12) {
+        nx = 0.0; ny = 0.0; nz = 1.0;
+    } else {
+        nx = gx / mag; ny = gy / mag; nz = gz / mag;
+    }
+
+    const double d = p.phi_c - phi[idx];
+    const double xc = (double)i * p.dx + d * nx;
+    const double yc = (double)j * p.dy + d * ny;
+    const double zc = (is_w ? (double)k : (double)k + 0.5) * p.dz + d * nz;
+
+    const double xi = xc / p.dx, eta = yc / p.dy;
+    const double fi = floor(xi), fj = floor(eta);
+    const double ax = xi - fi, ay = eta - fj;
+    const int32_t i0 = wrapi((int64_t)fi, p.nx), j0 = wrapi((int64_t)fj, p.ny);
+
+    double az[2];
+    int32_t kb[2];
+    for (int g = 0; g < 2; ++g) {          // g = 0: uv-grid, g = 1: w-grid
+        double zeta = (g == 1) ? zc / p.dz : zc / p.dz - 0.5;
+        const int32_t top = (g == 1) ? p.nz - 1 : p.nz - 2;
+        zeta = fmin(fmax(zeta, 0.0), (double)top);
+        int32_t k0 = (int32_t)floor(zeta);
+        if (k0 > top - 1) k0 = top - 1;
+        kb[g] = k0;
+        az[g] = zeta - (double)k0;
+    }
+
+    const double z0 = p.z0_is_field ? p.z0[idx] : p.z0[0];
+    const double lg = log(p.phi_c / z0);
+    const double C = (p.kappa * p.kappa) / (lg * lg);
+
+    int4 ix;
+    ix.x = idx;
+    ix.y = (int32_t)(((int64_t)kb[0] * p.ny + j0) * p.nx + i0);
+    ix.z = (int32_t)(((int64_t)kb[1] * p.ny + j0) * p.nx + i0);
+    ix.w = (i0 == p.nx - 1 ? 1 : 0) | (j0 == p.ny - 1 ? 2 : 0);
+    if (p.f64) {
+        RecF64 r;
+        r.n01 = make_double2(nx, ny);
+        r.n2C = make_double2(nz, C);
+        r.fxy = make_double2(ax, ay);
+        r.fz = make_double2(az[0], az[1]);
+        r.ix = ix;
+        reinterpret_cast<RecF64 *>(p.rec)[t] = r;
+    } else {
+        RecF32 r;
+        r.nC = make_float4((float)nx, (float)ny, (float)nz, (float)C);
+        r.frac = make_float4((float)ax, (float)ay, (float)az[0], (float)az[1]);
+        r.ix = ix;
+        reinterpret_cast<RecF32 *>(p.rec)[t] = r;
+    }
+}
+
+// Marks every velocity element a band stencil reads (for the algorithmic byte count).
+__global__ void __launch_bounds__(kThreads) k_mark(const void *rec, int f64, int64_t nrec, int32_t nx, int32_t ny,
+                                                    uint8_t *mark_uv, uint8_t *mark_w)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrec) return;
+    int4 ix = f64 ? reinterpret_cast<const RecF64 *>(rec)[t].ix : reinterpret_cast<const RecF32 *>(rec)[t].ix;
+    const int64_t plane = (int64_t)nx * ny;
+    const int64_t di = (ix.w & 1) ? 1 - nx : 1;
+    const int64_t dj = (ix.w & 2) ? (int64_t)(1 - ny) * nx : nx;
+    for (int c = 0; c < 8; ++c) {
+        int64_t off = ((c & 1) ? di : 0) + ((c & 2) ? dj : 0) + ((c & 4) ? plane : 0);
+        mark_uv[ix.y + off] = 1;
+        mark_w[ix.z + off] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_marks(const uint8_t *a, const uint8_t *b, int64_t n,
+                                                           unsigned long long *out)
+{
+    unsigned long long ca = 0, cb = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        ca += a[p];
+        cb += b[p];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ca += __shfl_down_sync(0xffffffffu, ca, o);
+        cb += __shfl_down_sync(0xffffffffu, cb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, ca);
+        atomicAdd(out + 1, cb);
+    }
+}
+
+void free_handle(wmibm_handle *h)
+{
+    if (!h) return;
+    for (int l = 0; l < 6; ++l)
+        if (h->lists.p[l]) cudaFree(h->lists.p[l]);
+    if (h->rec) cudaFree(h->rec);
+    if (h->partials) cudaFree(h->partials);
+    if (h->ticket) cudaFree(h->ticket);
+    free(h);
+}
+
+}  // namespace
+
+namespace wmibm {
+
+int set_error(wmibm_handle *h, int status, const char *fmt, ...)
+{
+    char *buf = h ? h->err : g_init_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_status(wmibm_handle *h, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return WMIBM_OK;
+    return set_error(h, e == cudaErrorMemoryAllocation ? WMIBM_ENOMEM : WMIBM_ECUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+int check_device(wmibm_handle *h)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(h, e, "cudaGetDevice");
+    if (dev != h->device)
+        return set_error(h, WMIBM_ESTATE, "current device %d is not the handle's device %d", dev, h->device);
+    return WMIBM_OK;
+}
+
+}  // namespace wmibm
+
+#define TRY(expr, what)                                            \
+    do {                                                           \
+        int _st = cuda_status(nullptr, (expr), what);              \
+        if (_st != WMIBM_OK) {                                     \
+            status = _st;                                          \
+            goto fail;                                             \
+        }                                                          \
+    } while (0)
+
+extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double *phi_uv, const double *phi_w,
+                          const double *z0, int32_t z0_is_field, double phi_c, const wmibm_opts *opts,
+                          void *stream_)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    g_init_error[0] = 0;
+    if (!out) return set_error(nullptr, WMIBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !phi_uv || !phi_w || !z0) return set_error(nullptr, WMIBM_EINVAL, "NULL grid, phi or z0");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 3)
+        return set_error(nullptr, WMIBM_EINVAL, "grid %d x %d x %d: need nx, ny >= 1 and nz >= 3", g->nx, g->ny, g->nz);
+    if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0) || !isfinite(g->lx) || !isfinite(g->ly) || !isfinite(g->lz))
+        return set_error(nullptr, WMIBM_EINVAL, "domain lengths must be positive and finite");
+    const int64_t n = (int64_t)g->nx * g->ny * g->nz;
+    if (n >= ((int64_t)1 << 31) - 16) return set_error(nullptr, WMIBM_EINVAL, "grid has %lld nodes (>= 2^31)", (long long)n);
+
+    wmibm_opts o = {0.0, 0.0, WMIBM_F32, WMIBM_F32};
+    if (opts) o = *opts;
+    const double dz = g->lz / (double)(g->nz - 1);
+    if (!(o.phi_b > 0)) o.phi_b = 0.5 * dz;
+    if (!(o.kappa > 0)) o.kappa = 0.4;
+    if (o.dtype != WMIBM_F32 && o.dtype != WMIBM_F64) return set_error(nullptr, WMIBM_EINVAL, "dtype must be F32 or F64");
+    if (!(o.vel_dtype == o.dtype || (o.dtype == WMIBM_F32 && o.vel_dtype == WMIBM_BF16)))
+        return set_error(nullptr, WMIBM_EINVAL, "vel_dtype must equal dtype, or be BF16 with an F32 dtype");
+    if (!isfinite(o.phi_b) || !isfinite(o.kappa)) return set_error(nullptr, WMIBM_EINVAL, "phi_b and kappa must be finite");
+    if (!(phi_c >= 2.0 * o.phi_b) || !isfinite(phi_c))
+        return set_error(nullptr, WMIBM_EINVAL, "phi_c = %g must be finite and >= 2 phi_b = %g", phi_c, 2.0 * o.phi_b);
+    const int64_t nz0 = z0_is_field ? n : 1;
+    for (int64_t p = 0; p < nz0; ++p)
+        if (!(z0[p] > 0.0 && z0[p] < phi_c))
+            return set_error(nullptr, WMIBM_EINVAL, "z0[%lld] = %g outside (0, phi_c = %g)", (long long)p, z0[p], phi_c);
+    for (int64_t p = 0; p < n; ++p)
+        if (!isfinite(phi_uv[p]) || !isfinite(phi_w[p]))
+            return set_error(nullptr, WMIBM_EINVAL, "non-finite phi at node %lld", (long long)p);
+
+    int status = WMIBM_OK;
+    double *d_phi_uv = nullptr, *d_phi_w = nullptr, *d_z0 = nullptr;
+    int32_t *d_counts = nullptr;
+    int64_t *d_offsets = nullptr;
+    uint8_t *d_mark = nullptr;
+    unsigned long long *d_marks = nullptr;
+    const int64_t nblk = (n + kChunk - 1) / kChunk;
+    std::vector<int32_t> counts(6 * nblk);
+    std::vector<int64_t> offsets(6 * nblk);
+    unsigned long long marks[2] = {0, 0};
+
+    wmibm_handle *h = (wmibm_handle *)calloc(1, sizeof(wmibm_handle));
+    if (!h) return set_error(nullptr, WMIBM_ENOMEM, "host allocation failed");
+    TRY(cudaGetDevice(&h->device), "cudaGetDevice");
+    h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;
+    h->lx = g->lx; h->ly = g->ly; h->lz = g->lz;
+    h->dx = g->lx / (double)g->nx;
+    h->dy = g->ly / (double)g->ny;
+    h->dz = dz;
+    h->phi_b = o.phi_b; h->kappa = o.kappa; h->phi_c = phi_c;
+    h->dtype = o.dtype; h->vel_dtype = o.vel_dtype;
+    h->n = n;
+
+    TRY(cudaMalloc(&d_phi_uv, n * sizeof(double)), "cudaMalloc phi_uv");
+    TRY(cudaMalloc(&d_phi_w, n * sizeof(double)), "cudaMalloc phi_w");
+    TRY(cudaMalloc(&d_z0, nz0 * sizeof(double)), "cudaMalloc z0");
+    TRY(cudaMalloc(&d_counts, 6 * nblk * sizeof(int32_t)), "cudaMalloc counts");
+    TRY(cudaMalloc(&d_offsets, 6 * nblk * sizeof(int64_t)), "cudaMalloc offsets");
+    TRY(cudaMemcpyAsync(d_phi_uv, phi_uv, n * sizeof(double), cudaMemcpyHostToDevice, stream), "copy phi_uv");
+    TRY(cudaMemcpyAsync(d_phi_w, phi_w, n * sizeof(double), cudaMemcpyHostToDevice, stream), "copy phi_w");
+    TRY(cudaMemcpyAsync(d_z0, z0, nz0 * sizeof(double), cudaMemcpyHostToDevice, stream), "copy z0");
+
+    k_count<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_counts, nblk);
+    TRY(cudaGetLastError(), "k_count launch");
+    TRY(cudaMemcpyAsync(counts.data(), d_counts, 6 * nblk * sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
+        "copy counts");
+    TRY(cudaStreamSynchronize(stream), "k_count");
+    for (int l = 0; l < 6; ++l) {
+        int64_t s = 0;
+        for (int64_t b = 0; b < nblk; ++b) {
+            offsets[l * nblk + b] = s;
+            s += counts[l * nblk + b];
+        }
+        h->lists.n[l] = s;
+        TRY(cudaMalloc(&h->lists.p[l], std::max<int64_t>(s, 1) * sizeof(int32_t)), "cudaMalloc list");
+    }
+    TRY(cudaMemcpyAsync(d_offsets, offsets.data(), 6 * nblk * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
+        "copy offsets");
+    k_compact<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_offsets, nblk, h->lists);
+    TRY(cudaGetLastError(), "k_compact launch");
+
+    h->nrec = h->lists.n[0] + h->lists.n[1];
+    {
+        const size_t rec_size = o.dtype == WMIBM_F64 ? sizeof(RecF64) : sizeof(RecF32);
+        TRY(cudaMalloc(&h->rec, std::max<int64_t>(h->nrec, 1) * rec_size), "cudaMalloc records");
+        if (h->nrec > 0) {
+            RecParams rp;
+            rp.phi_uv = d_phi_uv; rp.phi_w = d_phi_w; rp.z0 = d_z0; rp.z0_is_field = z0_is_field ? 1 : 0;
+            rp.band_w = h->lists.p[0]; rp.band_uv = h->lists.p[1];
+            rp.nb_w = h->lists.n[0]; rp.nb_uv = h->lists.n[1];
+            rp.nx = h->nx; rp.ny = h->ny; rp.nz = h->nz;
+            rp.dx = h->dx; rp.dy = h->dy; rp.dz = h->dz; rp.phi_c = phi_c; rp.kappa = o.kappa;
+            rp.rec = h->rec; rp.f64 = o.dtype == WMIBM_F64;
+            k_records<<<(unsigned)((h->nrec + kThreads - 1) / kThreads), kThreads, 0, stream>>>(rp);
+            TRY(cudaGetLastError(), "k_records launch");
+        }
+        h->partial_blocks = std::max<int64_t>((h->nrec + kThreads - 1) / kThreads, 1);
+        TRY(cudaMalloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
+        TRY(cudaMalloc(&h->ticket, sizeof(unsigned int)), "cudaMalloc ticket");
+        TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), stream), "memset ticket");
+
+        // algorithmic bytes: distinct velocity elements read by the band stencils
+        TRY(cudaMalloc(&d_mark, 2 * n), "cudaMalloc marks");
+        TRY(cudaMalloc(&d_marks, 2 * sizeof(unsigned long long)), "cudaMalloc mark counts");
+        TRY(cudaMemsetAsync(d_mark, 0, 2 * n, stream), "memset marks");
+        TRY(cudaMemsetAsync(d_marks, 0, 2 * sizeof(unsigned long long), stream), "memset mark counts");
+        if (h->nrec > 0) {
+            k_mark<<<(unsigned)((h->nrec + kThreads - 1) / kThreads), kThreads, 0, stream>>>(
+                h->rec, o.dtype == WMIBM_F64, h->nrec, h->nx, h->ny, d_mark, d_mark + n);
+            TRY(cudaGetLastError(), "k_mark launch");
+        }
+        k_count_marks<<<1024, kThreads, 0, stream>>>(d_mark, d_mark + n, n, d_marks);
+        TRY(cudaGetLastError(), "k_count_marks launch");
+        TRY(cudaMemcpyAsync(marks, d_marks, sizeof(marks), cudaMemcpyDeviceToHost, stream), "copy mark counts");
+        TRY(cudaStreamSynchronize(stream), "init kernels");
+
+        const int64_t es = (int64_t)elem_size(o.dtype), vs = (int64_t)elem_size(o.vel_dtype);
+        const int64_t *L = h->lists.n;
+        h->traffic[0] = h->nrec * (int64_t)rec_size + (int64_t)(2 * marks[0] + marks[1]) * vs +
+                        (2 * L[0] + 4 * L[1]) * es + 4 * (L[2] + L[3]) + (2 * L[2] + 4 * L[3]) * es;
+        h->traffic[1] = 9 * n * es;
+        h->traffic[2] = 4 * (L[4] + L[5]) + (L[4] + 2 * L[5]) * vs;
+        h->traffic[3] = h->traffic[2] + (L[4] + 2 * L[5]) * es;
+    }
+
+    cudaFree(d_phi_uv);
+    cudaFree(d_phi_w);
+    cudaFree(d_z0);
+    cudaFree(d_counts);
+    cudaFree(d_offsets);
+    cudaFree(d_mark);
+    cudaFree(d_marks);
+    *out = h;
+    return WMIBM_OK;
+
+fail:
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(d_phi_uv);
+    cudaFree(d_phi_w);
+    cudaFree(d_z0);
+    cudaFree(d_counts);
+    cudaFree(d_offsets);
+    cudaFree(d_mark);
+    cudaFree(d_marks);
+    free_handle(h);
+    return status;
+}
+
+extern "C" int64_t wmibm_list_size(const wmibm_handle *h, int32_t which)
+{
+    if (!h || which < 0 || which > 5) return -1;
+    return h->lists.n[which];
+}
+
+extern "C" int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap, void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (which < 0 || which > 5) return set_error(h, WMIBM_EINVAL, "list %d does not exist", which);
+    if (!dst || cap < h->lists.n[which])
+        return set_error(h, WMIBM_EINVAL, "destination holds %lld entries, list has %lld", (long long)cap,
+                         (long long)h->lists.n[which]);
+    int st = check_device(h);
+    if (st) return st;
+    if (h->lists.n[which] == 0) return WMIBM_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, h->lists.p[which], h->lists.n[which] * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return cuda_status(h, e, "export list");
+}
+
+extern "C" int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which)
+{
+    if (!h || which < 0 || which > 3) return -1;
+    return h->traffic[which];
+}
+
+extern "C" void wmibm_destroy(wmibm_handle *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_handle(h);
+}
+
+extern "C" const char *wmibm_status_string(int status)
+{
+    switch (status) {
+    case WMIBM_OK: return "ok";
+    case WMIBM_EINVAL: return "invalid argument";
+    case WMIBM_ENOMEM: return "out of memory";
+    case WMIBM_ECUDA: return "CUDA error";
+    case WMIBM_ESTATE: return "invalid state";
+    case WMIBM_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *wmibm_last_error(const wmibm_handle *h)
+{
+    return h ? h->err : g_init_error;
+}

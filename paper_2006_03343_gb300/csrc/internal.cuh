@@ -1,0 +1,97 @@
+// Internal declarations of libwmibm: the handle, the per-band-node record and
+// small device helpers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+
+#include "wmibm.h"
+
+namespace wmibm {
+
+constexpr int kThreads = 256;          // block size of the list-driven kernels
+constexpr int kStatVals = 8;           // per band: sum tau_w, sum tau_w^2, min tau_w, max |U_r|
+
+// One band node, FP32 path (48 bytes, three 16-byte vector loads).
+//   nC   = (n_x, n_y, n_z, C) with C = kappa^2 / ln^2(phi_c / z0)
+//   frac = (a_x, a_y, a_z on the uv-grid, a_z on the w-grid): trilinear weights
+//   ix   = (node index, base corner on the uv-grid, base corner on the w-grid,
+//           wrap flags: bit 0 = the +x corner wraps to i = 0, bit 1 = the +y
+//           corner wraps to j = 0)
+struct __align__(16) RecF32 {
+    float4 nC;
+    float4 frac;
+    int4 ix;
+};
+
+// One band node, FP64 path (80 bytes), same fields.
+struct __align__(16) RecF64 {
+    double2 n01;
+    double2 n2C;
+    double2 fxy;
+    double2 fz;
+    int4 ix;
+};
+
+struct Lists {
+    int32_t *p[6];
+    int64_t n[6];
+};
+
+}  // namespace wmibm
+
+struct wmibm_handle {
+    int device;
+    int32_t nx, ny, nz;
+    double lx, ly, lz, dx, dy, dz;
+    double phi_b, kappa, phi_c;
+    int32_t dtype, vel_dtype;
+    int64_t n;
+    wmibm::Lists lists;
+    void *rec;                  // band records: w-band first, then uv-band
+    int64_t nrec;
+    void *partials;             // per-block partial band statistics (dtype)
+    unsigned int *ticket;       // last-block detection counter, kept at 0 between calls
+    int64_t partial_blocks;
+    int64_t traffic[4];
+    char err[512];
+};
+
+namespace wmibm {
+
+// ------------------------------------------------------------------------- //
+// host helpers
+// ------------------------------------------------------------------------- //
+int set_error(wmibm_handle *h, int status, const char *fmt, ...);
+int check_device(wmibm_handle *h);
+int cuda_status(wmibm_handle *h, cudaError_t e, const char *what);
+
+inline size_t elem_size(int32_t t) { return t == WMIBM_F64 ? 8 : (t == WMIBM_BF16 ? 2 : 4); }
+
+// ------------------------------------------------------------------------- //
+// device helpers
+// ------------------------------------------------------------------------- //
+template <typename V>
+__device__ __forceinline__ float load_vel_f(const V *p, int64_t i);
+template <>
+__device__ __forceinline__ float load_vel_f<float>(const float *p, int64_t i) { return __ldg(p + i); }
+template <>
+__device__ __forceinline__ float load_vel_f<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t i)
+{
+    return __bfloat162float(p[i]);
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ T load_vel(const V *p, int64_t i) { return (T)load_vel_f<V>(p, i); }
+template <>
+__device__ __forceinline__ double load_vel<double, double>(const double *p, int64_t i) { return __ldg(p + i); }
+
+template <typename V, typename T>
+__device__ __forceinline__ V to_vel(T x) { return (V)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_vel<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
+
+}  // namespace wmibm

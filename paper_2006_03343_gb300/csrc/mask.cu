@@ -1,0 +1,95 @@
+// Immersed-boundary velocity condition (Sec. 3.2, Eq. 27 of Liu & Stevens,
+// arXiv:2006.03343): u*_IB = u* where phi > 0 and 3 dt/2 grad p^{t-dt} where
+// phi <= 0; with no pressure gradient given the body velocity is set to zero.
+// Driven by the ascending body-node lists built at init, so only the body
+// nodes are touched.  Also the one-pass step entry point.
+#include "internal.cuh"
+
+using namespace wmibm;
+
+namespace {
+
+template <typename T, typename V>
+struct MaskParams {
+    V *u, *v, *w;
+    const T *gpx, *gpy, *gpz;
+    const int32_t *body_w, *body_uv;
+    int64_t nb_w, nb_uv;
+    T c;   // 3 dt / 2
+};
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) k_mask(MaskParams<T, V> p)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t < p.nb_uv) {
+        const int32_t idx = __ldg(p.body_uv + t);
+        const T a = p.gpx ? p.c * __ldg(p.gpx + idx) : T(0);
+        const T b = p.gpy ? p.c * __ldg(p.gpy + idx) : T(0);
+        p.u[idx] = to_vel<V, T>(a);
+        p.v[idx] = to_vel<V, T>(b);
+    } else if (t < p.nb_uv + p.nb_w) {
+        const int32_t idx = __ldg(p.body_w + (t - p.nb_uv));
+        const T a = p.gpz ? p.c * __ldg(p.gpz + idx) : T(0);
+        p.w[idx] = to_vel<V, T>(a);
+    }
+}
+
+template <typename T, typename V>
+int launch(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream)
+{
+    MaskParams<T, V> p;
+    p.u = (V *)u; p.v = (V *)v; p.w = (V *)w;
+    p.gpx = gradp ? (const T *)gradp[0] : nullptr;
+    p.gpy = gradp ? (const T *)gradp[1] : nullptr;
+    p.gpz = gradp ? (const T *)gradp[2] : nullptr;
+    p.body_w = h->lists.p[WMIBM_LIST_BODY_W];
+    p.body_uv = h->lists.p[WMIBM_LIST_BODY_UV];
+    p.nb_w = h->lists.n[WMIBM_LIST_BODY_W];
+    p.nb_uv = h->lists.n[WMIBM_LIST_BODY_UV];
+    p.c = (T)(1.5 * dt);
+    const int64_t total = p.nb_w + p.nb_uv;
+    if (total == 0) return WMIBM_OK;
+    k_mask<T, V><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_mask launch");
+}
+
+}  // namespace
+
+namespace wmibm {
+int wall_stress_impl(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                     wmibm_band_stats *stats, cudaStream_t stream, const void *logz0);
+int force_impl(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream, int bx,
+               int by, int kc);
+void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc);
+
+int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream)
+{
+    if (h->dtype == WMIBM_F64) return launch<double, double>(h, u, v, w, gradp, dt, stream);
+    if (h->vel_dtype == WMIBM_BF16) return launch<float, __nv_bfloat16>(h, u, v, w, gradp, dt, stream);
+    return launch<float, float>(h, u, v, w, gradp, dt, stream);
+}
+}  // namespace wmibm
+
+extern "C" int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt,
+                          void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!u || !v || !w) return set_error(h, WMIBM_EINVAL, "NULL velocity pointer");
+    if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
+        return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
+    if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
+    int st = check_device(h);
+    if (st) return st;
+    return mask_impl(h, u, v, w, gradp, dt, (cudaStream_t)stream);
+}
+
+extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
+                          void *fz, const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream)
+{
+    int st = wmibm_wall_stress(h, u, v, w, tau, stats, stream);
+    if (st) return st;
+    st = wmibm_force(h, (const void *const *)tau, fx, fy, fz, stream);
+    if (st) return st;
+    return wmibm_mask(h, u, v, w, gradp, dt, stream);
+}

@@ -1,0 +1,235 @@
+"""ctypes binding of libwmibm.so (C ABI in include/wmibm.h).
+
+Argument marshalling only: every step of the stress stage runs in the CUDA
+library.  torch supplies device memory and the current stream; fields are
+passed as raw device pointers.  If the library has not been built, loading it
+raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+F32, F64, BF16 = 0, 1, 2
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
+LIST_BAND_W, LIST_BAND_UV, LIST_SOLID_W, LIST_SOLID_UV, LIST_BODY_W, LIST_BODY_UV = range(6)
+LIST_NAMES = ("band_w", "band_uv", "solid_w", "solid_uv", "body_w", "body_uv")
+TAU_ORDER = ("txx", "txy", "tyy", "tzz", "txz", "tyz")
+DTYPE_CODES = {"f32": F32, "f64": F64, "bf16": BF16}
+
+# symbols the header declares (checked by the CPU test suite)
+EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmibm_step", "wmibm_list_size",
+            "wmibm_export_list", "wmibm_traffic_bytes", "wmibm_destroy", "wmibm_status_string",
+            "wmibm_last_error")
+
+
+class WmibmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"wmibm status {status}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("phi_b", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32)]
+
+
+STATS_DTYPE = np.dtype([("count", "<i8"), ("sum_tw", "<f8"), ("sum_tw2", "<f8"), ("min_tw", "<f8"),
+                        ("max_ur", "<f8")])
+
+_lib = None
+_VP = ctypes.c_void_p
+_PVP = ctypes.POINTER(ctypes.c_void_p)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libwmibm.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: the CUDA library must be built "
+                           "(paper_2006_03343_gb300.build.build()); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    L.wmibm_init.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Grid), _VP, _VP, _VP, ctypes.c_int32,
+                             ctypes.c_double, ctypes.POINTER(Opts), _VP]
+    L.wmibm_init.restype = ctypes.c_int
+    L.wmibm_wall_stress.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP]
+    L.wmibm_wall_stress.restype = ctypes.c_int
+    L.wmibm_force.argtypes = [_VP, _PVP, _VP, _VP, _VP, _VP]
+    L.wmibm_force.restype = ctypes.c_int
+    L.wmibm_mask.argtypes = [_VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
+    L.wmibm_mask.restype = ctypes.c_int
+    L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
+    L.wmibm_step.restype = ctypes.c_int
+    L.wmibm_list_size.argtypes = [_VP, ctypes.c_int32]
+    L.wmibm_list_size.restype = ctypes.c_int64
+    L.wmibm_export_list.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP]
+    L.wmibm_export_list.restype = ctypes.c_int
+    L.wmibm_traffic_bytes.argtypes = [_VP, ctypes.c_int32]
+    L.wmibm_traffic_bytes.restype = ctypes.c_int64
+    L.wmibm_destroy.argtypes = [_VP]
+    L.wmibm_destroy.restype = None
+    L.wmibm_status_string.argtypes = [ctypes.c_int]
+    L.wmibm_status_string.restype = ctypes.c_char_p
+    L.wmibm_last_error.argtypes = [_VP]
+    L.wmibm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _ptrs(seq) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(seq))()
+    for i, t in enumerate(seq):
+        arr[i] = None if t is None else ctypes.c_void_p(_dptr(t))
+    return arr
+
+
+def _dptr(t) -> int:
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+class Handle:
+    """One terrain on one GPU: wraps wmibm_init / wmibm_destroy and the per-step calls.
+
+    dtype: "f32" or "f64" (stress, force and arithmetic); vel_dtype: None (same as
+    dtype) or "bf16" (with f32)."""
+
+    def __init__(self, grid, phi_uv, phi_w, z0, phi_c, phi_b=0.0, dtype="f32", vel_dtype=None, kappa=0.4,
+                 stream=None):
+        import torch
+        L = load()
+        nx, ny, nz, lx, ly, lz = grid
+        self.grid = tuple(grid)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.dtype = dtype
+        self.vel_dtype = vel_dtype or dtype
+        self.torch_dtype = torch.float64 if dtype == "f64" else torch.float32
+        self.torch_vel_dtype = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[self.vel_dtype]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        phi_uv = np.ascontiguousarray(phi_uv, np.float64)
+        phi_w = np.ascontiguousarray(phi_w, np.float64)
+        if np.isscalar(z0):
+            z0a = np.array([float(z0)], np.float64)
+            is_field = 0
+        else:
+            z0a = np.ascontiguousarray(z0, np.float64)
+            is_field = 1
+        g = Grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz))
+        o = Opts(float(phi_b), float(kappa), DTYPE_CODES[dtype], DTYPE_CODES[self.vel_dtype])
+        h = ctypes.c_void_p()
+        st = L.wmibm_init(ctypes.byref(h), ctypes.byref(g), phi_uv.ctypes.data, phi_w.ctypes.data,
+                          z0a.ctypes.data, is_field, float(phi_c), ctypes.byref(o), _stream_ptr(stream))
+        if st != OK:
+            raise WmibmError(st, L.wmibm_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    @classmethod
+    def from_case(cls, case, dtype=None, vel_dtype=None, stream=None):
+        return cls(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b,
+                   dtype=dtype or case.dtype, vel_dtype=vel_dtype, stream=stream)
+
+    # ------------------------------------------------------------------ #
+    def _check(self, st):
+        if st != OK:
+            raise WmibmError(st, self._L.wmibm_last_error(self._h).decode())
+
+    def _field(self, t, vel=False):
+        want = self.torch_vel_dtype if vel else self.torch_dtype
+        if t.dtype != want or not t.is_contiguous() or tuple(t.shape) != self.shape or t.device != self.device:
+            raise ValueError(f"field must be a contiguous {want} tensor of shape {self.shape} on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+        return t
+
+    def new_stats(self):
+        import torch
+        return torch.zeros(10, dtype=torch.float64, device=self.device)
+
+    @staticmethod
+    def parse_stats(stats_tensor):
+        raw = stats_tensor.detach().cpu().numpy().tobytes()
+        return np.frombuffer(raw, dtype=STATS_DTYPE)
+
+    def wall_stress(self, u, v, w, tau: Sequence, stats=None, stream=None):
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in tau:
+            self._field(t)
+        self._check(self._L.wmibm_wall_stress(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau),
+                                              None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def force(self, tau: Sequence, f: Sequence, stream=None):
+        for t in list(tau) + list(f):
+            self._field(t)
+        self._check(self._L.wmibm_force(self._h, _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
+                                        _stream_ptr(stream)))
+
+    def mask(self, u, v, w, gradp=None, dt=0.0, stream=None):
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        if gradp is not None:
+            for t in gradp:
+                self._field(t)
+        self._check(self._L.wmibm_mask(self._h, _dptr(u), _dptr(v), _dptr(w),
+                                       None if gradp is None else _ptrs(gradp), float(dt), _stream_ptr(stream)))
+
+    def step(self, u, v, w, tau, f, gradp=None, dt=0.0, stats=None, stream=None):
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in list(tau) + list(f):
+            self._field(t)
+        self._check(self._L.wmibm_step(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau), _dptr(f[0]),
+                                       _dptr(f[1]), _dptr(f[2]), None if gradp is None else _ptrs(gradp),
+                                       float(dt), None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def list_size(self, which: int) -> int:
+        return int(self._L.wmibm_list_size(self._h, int(which)))
+
+    def export_list(self, which: int) -> np.ndarray:
+        n = self.list_size(which)
+        out = np.empty(max(n, 1), np.int32)
+        self._check(self._L.wmibm_export_list(self._h, int(which), out.ctypes.data, out.size, _stream_ptr(None)))
+        return out[:n]
+
+    def traffic_bytes(self, which: int) -> int:
+        return int(self._L.wmibm_traffic_bytes(self._h, int(which)))
+
+    @property
+    def raw(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.wmibm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
