@@ -48,6 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="few launches for ncu: no clock soak, no end-to-end leg, no CPU baseline")
     return ap.parse_args(argv)
 
 
@@ -68,16 +70,16 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(kernel_file, workload, dtype):
-    """DRAM bytes per launch of the force kernel from the committed ncu summary,
-    if that summary was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"force_{workload}_{dtype}.md")
+def profiled_traffic(workload, dtype, vel_dtype):
+    """DRAM bytes per launch of the fused stencil kernel from the committed ncu
+    summary, if that summary was taken on the current kernel sources (else None)."""
+    tag = f"{dtype}" + ("_bf16vel" if vel_dtype == "bf16" else "")
+    path = os.path.join(ROOT, "profiles", f"stencil_{workload}_{tag}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    src = open(kernel_file, "rb").read()
-    digest = hashlib.sha256(src).hexdigest()[:16]
+    digest = kernel_digest()
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_hash or not m_bytes or m_hash.group(1) != digest:
@@ -156,16 +158,19 @@ def oracle_time(case, seconds):
     tau = {k: v.copy() for k, v in case.tau.items()}
     u, v, w = case.u.copy(), case.v.copy(), case.w.copy()
     passes = 0
+    ref = None
     t0 = time.perf_counter()
     while True:
         oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, u, v, w, tau)
-        oracle.force(case.grid, tau)
+        f = oracle.force(case.grid, tau)
+        if ref is None:
+            ref = ({k: t.copy() for k, t in tau.items()}, f)
         oracle.mask(case.grid, case.phi_uv, case.phi_w, u, v, w)
         passes += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return passes * case.npoints / el / 1e9, passes, oracle.openmp_threads(), el
+    return passes * case.npoints / el / 1e9, passes, oracle.openmp_threads(), el, ref
 
 
 def run_reference(args):
@@ -204,6 +209,73 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # GPU arm
 # --------------------------------------------------------------------------- #
+KERNEL_SOURCES = ("stencil.cu", "band.cuh", "tma.cuh", "internal.cuh")
+
+
+class GpuForm:
+    """One precision form of the workload on the device: handle, fields, step."""
+
+    def __init__(self, case, dtype, vel_dtype, dev):
+        import torch
+        from paper_2006_03343_gb300 import inputs, wmibm
+        self.h = wmibm.Handle.from_case(case, dtype=dtype, vel_dtype=vel_dtype)
+        self.tdt = torch.float64 if dtype == "f64" else torch.float32
+        self.vdt = torch.bfloat16 if vel_dtype == "bf16" else self.tdt
+
+        def dev_t(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
+
+        self.u, self.v, self.w = (dev_t(x, self.vdt) for x in (case.u, case.v, case.w))
+        self.tau = [dev_t(case.tau[k], self.tdt) for k in inputs.TAU_NAMES]
+        self.f = [torch.empty(case.shape, dtype=self.tdt, device=dev) for _ in range(3)]
+        self.stats = self.h.new_stats()
+
+    def step(self, stream=None):
+        """One pass of the stage through the C ABI: wall stress, force and body mask
+        (one cooperative launch where the grid allows)."""
+        self.h.step(self.u, self.v, self.w, self.tau, self.f, None, 0.0, self.stats)
+
+    def capture(self):
+        """The step captured once as a CUDA graph (replayed in the timed loop)."""
+        import torch
+        self.step()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        torch.cuda.synchronize()
+
+    def host_result(self):
+        import torch
+        torch.cuda.synchronize()
+        return ([t.double().cpu().numpy() for t in self.tau], [t.double().cpu().numpy() for t in self.f])
+
+    def timed(self, stream, flush, steps, graph=True):
+        """Per-step device time (ms) with CUDA events on the launching stream; the L2
+        is flushed before every step, outside the events."""
+        import torch
+        events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for s in range(steps):
+            flush.zero_()
+            events[s][0].record(stream)
+            if graph:
+                self.graph.replay()
+            else:
+                self.step()
+            events[s][1].record(stream)
+        torch.cuda.synchronize()
+        return [e[0].elapsed_time(e[1]) for e in events]
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_03343_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -213,70 +285,46 @@ def run_ours(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    from paper_2006_03343_gb300 import build, inputs, wmibm
+    from paper_2006_03343_gb300 import build, inputs
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
 
     case = make_case(args)
-    h = wmibm.Handle.from_case(case, dtype=args.dtype, vel_dtype=args.vel_dtype)
-    tdt = torch.float64 if args.dtype == "f64" else torch.float32
-    vdt = torch.bfloat16 if args.vel_dtype == "bf16" else tdt
-
-    def dev_t(a, dt):
-        return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
-
-    u, v, w = (dev_t(x, vdt) for x in (case.u, case.v, case.w))
-    tau = [dev_t(case.tau[k], tdt) for k in inputs.TAU_NAMES]
-    f = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(3)]
-    stats = h.new_stats()
+    form = GpuForm(case, args.dtype, args.vel_dtype, dev)
+    h = form.h
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step(evs=None):
-        if evs is not None:
-            evs[0].record(stream)
-        h.wall_stress(u, v, w, tau, stats)
-        if evs is not None:
-            evs[1].record(stream)
-        h.force(tau, f)
-        if evs is not None:
-            evs[2].record(stream)
-        h.mask(u, v, w)
-        if evs is not None:
-            evs[3].record(stream)
+    # one pass on the pristine inputs, kept for the accuracy report
+    form.step()
+    first_tau, first_f = form.host_result()
 
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
-        step()
+        form.step()
     torch.cuda.synchronize()
+    form.capture()
 
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
     if sampler:
         sampler.start()
     # keep the GPU busy ~1 s before the timed region so the clock sampler sees load
     t_soak = time.perf_counter()
-    while time.perf_counter() - t_soak < 1.0:
+    while not args.profile and time.perf_counter() - t_soak < 1.0:
         for _ in range(20):
             flush.zero_()
-            step()
+            form.graph.replay()
         torch.cuda.synchronize()
 
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        flush.zero_()
-        step(events[s])
-    torch.cuda.synchronize()
+    step_ms = form.timed(stream, flush, args.steps, graph=True)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
+    eager_ms = form.timed(stream, flush, min(args.steps, 20), graph=False)
+    status = h.device_status()
 
-    step_ms = [e[0].elapsed_time(e[3]) for e in events]
-    ws_ms = [e[0].elapsed_time(e[1]) for e in events]
-    force_ms = [e[1].elapsed_time(e[2]) for e in events]
-    mask_ms = [e[2].elapsed_time(e[3]) for e in events]
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -284,33 +332,49 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * args.steps * case.npoints / (total_ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (force)
-    force_bytes = h.traffic_bytes(1)
-    force_avg_s = float(np.mean(force_ms)) * 1e-3
+    # roofline of the dominant (and only) kernel: the cooperative step kernel
+    step_bytes = h.traffic_bytes(4) + h.traffic_bytes(2)
+    avg_s = float(np.mean(step_ms)) * 1e-3
     peak, peak_kind = measured_peak()
-    achieved = force_bytes / force_avg_s / 1e9
-    kernel_file = os.path.join(ROOT, "paper_2006_03343_gb300", "csrc", "force.cu")
-    traffic = profiled_traffic(kernel_file, args.workload, args.dtype)
+    achieved = step_bytes / avg_s / 1e9
+    traffic = profiled_traffic(args.workload, args.dtype, args.vel_dtype)
+
+    # the plain FP64 form of the same workload, timed the same way
+    f64_form = None
+    if args.dtype == "f32" and not args.profile:
+        g64 = GpuForm(case, "f64", None, dev)
+        for _ in range(3):
+            flush.zero_()
+            g64.step()
+        g64.capture()
+        s64 = g64.timed(stream, flush, args.steps)
+        b64 = g64.h.traffic_bytes(4) + g64.h.traffic_bytes(2)
+        f64_form = {"value": args.steps * case.npoints / (sum(s64) * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": float(np.mean(s64)), "gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
+                    "device_status": g64.h.device_status()}
+        g64.h.close()
+        del g64
 
     # end to end through the public API: pinned host inputs in, forcing out
     e2e = None
-    if not args.no_e2e:
-        host_in = [torch.from_numpy(np.ascontiguousarray(x)).to(vdt).pin_memory() for x in (case.u, case.v, case.w)]
-        host_tau = [torch.from_numpy(case.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
-        host_f = [torch.empty(case.shape, dtype=tdt).pin_memory() for _ in range(3)]
-        h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
-        d2h = sum(t.numel() * t.element_size() for t in host_f) + stats.numel() * 8
+    if not args.no_e2e and not args.profile:
+        host_in = [torch.from_numpy(np.ascontiguousarray(x)).to(form.vdt).pin_memory()
+                   for x in (case.u, case.v, case.w)]
+        host_tau = [torch.from_numpy(case.tau[k]).to(form.tdt).pin_memory() for k in inputs.TAU_NAMES]
+        host_f = [torch.empty(case.shape, dtype=form.tdt).pin_memory() for _ in range(3)]
         host_stats = torch.empty(10, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
+        d2h = sum(t.numel() * t.element_size() for t in host_f) + host_stats.numel() * 8
 
         def e2e_step():
-            for d, s_ in zip((u, v, w), host_in):
+            for d, s_ in zip((form.u, form.v, form.w), host_in):
                 d.copy_(s_, non_blocking=True)
-            for d, s_ in zip(tau, host_tau):
+            for d, s_ in zip(form.tau, host_tau):
                 d.copy_(s_, non_blocking=True)
-            h.step(u, v, w, tau, f, None, 0.0, stats)
-            for d, s_ in zip(host_f, f):
+            h.step(form.u, form.v, form.w, form.tau, form.f, None, 0.0, form.stats)
+            for d, s_ in zip(host_f, form.f):
                 d.copy_(s_, non_blocking=True)
-            host_stats.copy_(stats, non_blocking=True)
+            host_stats.copy_(form.stats, non_blocking=True)
 
         for _ in range(2):
             e2e_step()
@@ -330,10 +394,12 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        gpts, passes, threads, el = oracle_time(case, args.cpu_seconds)
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        gpts, passes, threads, el, ref = oracle_time(case, args.cpu_seconds)
         cpu = {"value": gpts, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{passes} full passes of the workload ({el:.1f} s, FP64 CPU oracle)"}
+        accuracy = accuracy_report(first_tau, first_f, ref)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -341,20 +407,40 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": workload_config(args, case),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic, "kernel": "k_force",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "k_stencil (cooperative step: wall stress, grid barrier, mask + force)",
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                             "algorithmic_bytes_per_launch": force_bytes},
-                "kernels_ms": {"wall_stress": float(np.mean(ws_ms)), "force": float(np.mean(force_ms)),
-                               "mask": float(np.mean(mask_ms))},
-                "step_bytes": h.traffic_bytes(0) + force_bytes + h.traffic_bytes(2),
-                "step_gbs": (h.traffic_bytes(0) + force_bytes + h.traffic_bytes(2)) / (total_ms / args.steps * 1e-3) / 1e9,
-                "gpu_launches": 3 * args.steps,
+                             "algorithmic_bytes_per_launch": step_bytes},
+                "timing": "CUDA graph replay of one step per event pair; eager launches: %.4f ms/step"
+                          % float(np.mean(eager_ms)),
+                "gpu_launches": args.steps,
+                "device_status": status,
+                "f64_form": f64_form, "accuracy": accuracy,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line))
     h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def accuracy_report(gpu_tau, gpu_f, ref):
+    """Normwise max and RMS error of the first GPU pass against the oracle's first pass."""
+    from paper_2006_03343_gb300 import inputs
+    tau_o, f_o = ref
+    out = {}
+    worst_tau = 0.0
+    for k, g in zip(inputs.TAU_NAMES, gpu_tau):
+        r = tau_o[k]
+        worst_tau = max(worst_tau, float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300)))
+    out["tau_normwise_max"] = worst_tau
+    errs, rms = [], []
+    for g, r in zip(gpu_f, f_o):
+        errs.append(float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300)))
+        rms.append(float(np.sqrt(np.mean((g - r) ** 2)) / max(np.sqrt(np.mean(r ** 2)), 1e-300)))
+    out["f_normwise_max"] = max(errs)
+    out["f_relative_rms"] = max(rms)
+    return out
 
 
 def main(argv=None):

@@ -143,6 +143,47 @@ int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gra
 int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
                const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream);
 
+/*
+ * wmibm_wall_stress_force - wmibm_wall_stress followed by wmibm_force in one
+ * cooperative launch where the grid allows (nx a multiple of 4 for F32 or 2 for
+ * F64, ny >= 3, 16-byte aligned stress and force buffers, full x-rows that fit
+ * the shared-memory stages): the wall model runs over the whole grid, then a
+ * grid barrier, then the pipelined stencil.  Otherwise the two kernels run back
+ * to back.  Same arguments and results (band entries, solid zeros, forcing,
+ * statistics) as the two calls, up to the summation order of the statistics.
+ * wmibm_step uses the same launch and applies the body mask after the barrier.
+ */
+int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                            void *fx, void *fy, void *fz, wmibm_band_stats *stats, void *stream);
+
+/*
+ * Launch tuning of the stencil kernels (what the autotuner sets).  Zero fields
+ * mean "choose automatically".
+ */
+typedef struct wmibm_tuning {
+    int32_t force_path;       /* 0 auto, 1 bulk-copy pipeline only, 2 direct-load kernel only */
+    int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
+    int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
+    int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */
+    int32_t wall_warps;       /* fused step: warps running the wall model and the mask, 1..8 */
+    int32_t blocks_per_sm;    /* pipeline: cap on resident blocks per SM */
+    int32_t direct_bx;        /* direct-load kernel: vectors per block row */
+    int32_t direct_by;        /* direct-load kernel: rows per block */
+    int32_t direct_kc;        /* direct-load kernel: levels per thread */
+} wmibm_tuning;
+
+/* Sets / reads the tuning of handle h. EINVAL for out-of-range fields. */
+int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t);
+int wmibm_get_tuning(const wmibm_handle *h, wmibm_tuning *t);
+
+/*
+ * wmibm_device_status - reads and clears the handle's device status word, which
+ * a kernel sets when one of its bounded waits gave up (ETIMEOUT).  Synchronises
+ * `stream`.  *out receives WMIBM_OK or WMIBM_ETIMEOUT; the returned status is
+ * that of the call itself.
+ */
+int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream);
+
 /* Number of entries of list `which` (WMIBM_LIST_*), or -1 for a bad argument. */
 int64_t wmibm_list_size(const wmibm_handle *h, int32_t which);
 
@@ -158,7 +199,10 @@ int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap,
  *   which = 0: wmibm_wall_stress (band records, each distinct velocity element
  *              its stencils touch, band stress writes, solid index reads and
  *              zero writes); 1: wmibm_force (6 stress reads + 3 force writes per
- *              node); 2: wmibm_mask without grad p; 3: wmibm_mask with grad p.
+ *              node); 2: wmibm_mask without grad p; 3: wmibm_mask with grad p;
+ *              4: the fused wmibm_wall_stress_force pass (force stream, band
+ *              records and velocity elements, band and solid stress writes, run
+ *              and row tables).
  * Returns -1 for a bad argument.
  */
 int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which);

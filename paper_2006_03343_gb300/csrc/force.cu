@@ -187,10 +187,24 @@ int force_impl(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, vo
 
 void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc)
 {
-    *bx = 32;
-    *by = 8;
-    *kc = 4;
-    (void)h;
+    *bx = h->tuning.direct_bx > 0 ? h->tuning.direct_bx : 32;
+    *by = h->tuning.direct_by > 0 ? h->tuning.direct_by : 8;
+    *kc = h->tuning.direct_kc > 0 ? h->tuning.direct_kc : 4;
+}
+
+bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
+int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], const StencilConfig &c,
+                  cudaStream_t stream);
+
+// f = -div(tau): the bulk-copy pipeline where it applies, else the direct-load kernel.
+int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream)
+{
+    void *const f[3] = {fx, fy, fz};
+    StencilConfig c;
+    if (stencil_config(h, tau, f, &c)) return stencil_force(h, tau, f, c, stream);
+    int bx, by, kc;
+    force_default_tile(h, &bx, &by, &kc);
+    return force_impl(h, tau, fx, fy, fz, stream, bx, by, kc);
 }
 
 }  // namespace wmibm
@@ -203,7 +217,5 @@ extern "C" int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, 
         if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
     int st = check_device(h);
     if (st) return st;
-    int bx, by, kc;
-    force_default_tile(h, &bx, &by, &kc);
-    return force_impl(h, tau, fx, fy, fz, (cudaStream_t)stream, bx, by, kc);
+    return force_any(h, tau, fx, fy, fz, (cudaStream_t)stream);
 }

@@ -2,6 +2,7 @@
 // arXiv:2006.03343): node classes, ascending index lists, unit normals and the
 // per-band-node interpolation records, all computed on the GPU in FP64.
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -235,6 +236,8 @@ __global__ void __launch_bounds__(kThreads) k_count_marks(const uint8_t *a, cons
 void free_handle(wmibm_handle *h)
 {
     if (!h) return;
+    if (h->dev_status) cudaFree(h->dev_status);
+    if (h->grid_bar) cudaFree(h->grid_bar);
     for (int l = 0; l < 6; ++l)
         if (h->lists.p[l]) cudaFree(h->lists.p[l]);
     if (h->rec) cudaFree(h->rec);
@@ -386,7 +389,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             k_records<<<(unsigned)((h->nrec + kThreads - 1) / kThreads), kThreads, 0, stream>>>(rp);
             TRY(cudaGetLastError(), "k_records launch");
         }
-        h->partial_blocks = std::max<int64_t>((h->nrec + kThreads - 1) / kThreads, 1);
+        TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+        h->partial_blocks = std::max<int64_t>((h->nrec + kThreads - 1) / kThreads, 16 * (int64_t)h->sm_count);
         TRY(cudaMalloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
         TRY(cudaMalloc(&h->ticket, sizeof(unsigned int)), "cudaMalloc ticket");
         TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), stream), "memset ticket");
@@ -406,6 +410,37 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         TRY(cudaMemcpyAsync(marks, d_marks, sizeof(marks), cudaMemcpyDeviceToHost, stream), "copy mark counts");
         TRY(cudaStreamSynchronize(stream), "init kernels");
 
+        // levels holding band or solid nodes (first and last entry of each sorted
+        // list): stencil stages at levels [lo - 1, hi + 1] read entries the wall
+        // model writes
+        {
+            int32_t lo = INT32_MAX, hi = -1;
+            for (int l = 0; l < 4; ++l) {
+                if (h->lists.n[l] == 0) continue;
+                int32_t ends[2];
+                TRY(cudaMemcpyAsync(&ends[0], h->lists.p[l], sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
+                    "copy list head");
+                TRY(cudaMemcpyAsync(&ends[1], h->lists.p[l] + h->lists.n[l] - 1, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, stream), "copy list tail");
+                TRY(cudaStreamSynchronize(stream), "list ends");
+                const int64_t plane = (int64_t)h->nx * h->ny;
+                lo = std::min<int32_t>(lo, (int32_t)(ends[0] / plane));
+                hi = std::max<int32_t>(hi, (int32_t)(ends[1] / plane));
+            }
+            if (hi < 0) {
+                h->dirty_lo = 0;
+                h->dirty_hi = 0;
+            } else {
+                h->dirty_lo = std::max(0, lo - 1);
+                h->dirty_hi = std::min(h->nz, hi + 2);
+            }
+        }
+        TRY(cudaMalloc(&h->dev_status, sizeof(int)), "cudaMalloc status");
+        TRY(cudaMemsetAsync(h->dev_status, 0, sizeof(int), stream), "memset status");
+        TRY(cudaMalloc(&h->grid_bar, 2 * sizeof(unsigned)), "cudaMalloc grid barrier");
+        TRY(cudaMemsetAsync(h->grid_bar, 0, 2 * sizeof(unsigned), stream), "memset grid barrier");
+        TRY(cudaStreamSynchronize(stream), "init state");
+
         const int64_t es = (int64_t)elem_size(o.dtype), vs = (int64_t)elem_size(o.vel_dtype);
         const int64_t *L = h->lists.n;
         h->traffic[0] = h->nrec * (int64_t)rec_size + (int64_t)(2 * marks[0] + marks[1]) * vs +
@@ -413,6 +448,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         h->traffic[1] = 9 * n * es;
         h->traffic[2] = 4 * (L[4] + L[5]) + (L[4] + 2 * L[5]) * vs;
         h->traffic[3] = h->traffic[2] + (L[4] + 2 * L[5]) * es;
+        // fused pass: the force stream plus the wall-stress work
+        h->traffic[4] = h->traffic[1] + h->traffic[0];
     }
 
     cudaFree(d_phi_uv);
@@ -462,7 +499,7 @@ extern "C" int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, i
 
 extern "C" int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which)
 {
-    if (!h || which < 0 || which > 3) return -1;
+    if (!h || which < 0 || which > 4) return -1;
     return h->traffic[which];
 }
 
@@ -489,4 +526,45 @@ extern "C" const char *wmibm_status_string(int status)
 extern "C" const char *wmibm_last_error(const wmibm_handle *h)
 {
     return h ? h->err : g_init_error;
+}
+
+extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!t) return set_error(h, WMIBM_EINVAL, "NULL tuning");
+    if (t->force_path < 0 || t->force_path > 2) return set_error(h, WMIBM_EINVAL, "force_path must be 0, 1 or 2");
+    if (!(t->rows == 0 || t->rows == 1 || t->rows == 2 || t->rows == 4))
+        return set_error(h, WMIBM_EINVAL, "rows must be 0, 1, 2 or 4");
+    if (t->stages != 0 && (t->stages < 2 || t->stages > 8)) return set_error(h, WMIBM_EINVAL, "stages must be 2..8");
+    if (t->consumer_warps < 0 || t->consumer_warps > 12)
+        return set_error(h, WMIBM_EINVAL, "consumer_warps must be 0..12");
+    if (t->wall_warps < 0 || t->wall_warps > 8) return set_error(h, WMIBM_EINVAL, "wall_warps must be 0..8");
+    if (t->blocks_per_sm < 0 || t->direct_bx < 0 || t->direct_by < 0 || t->direct_kc < 0)
+        return set_error(h, WMIBM_EINVAL, "negative tuning field");
+    if (t->direct_bx * (t->direct_by > 0 ? t->direct_by : 1) > 1024)
+        return set_error(h, WMIBM_EINVAL, "direct-load block too large");
+    h->tuning = *t;
+    return WMIBM_OK;
+}
+
+extern "C" int wmibm_get_tuning(const wmibm_handle *h, wmibm_tuning *t)
+{
+    if (!h || !t) return WMIBM_EINVAL;
+    *t = h->tuning;
+    return WMIBM_OK;
+}
+
+extern "C" int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!out) return set_error(h, WMIBM_EINVAL, "NULL output");
+    int st = check_device(h);
+    if (st) return st;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->dev_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_status, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(h, e, "device status");
+    *out = v == 0 ? WMIBM_OK : WMIBM_ETIMEOUT;
+    return WMIBM_OK;
 }

@@ -41,6 +41,11 @@ struct Lists {
     int64_t n[6];
 };
 
+// Resolved launch shape of the pipelined stencil.
+struct StencilConfig {
+    int rows, stages, consumer_warps, wall_warps, blocks_per_sm;
+};
+
 }  // namespace wmibm
 
 struct wmibm_handle {
@@ -56,7 +61,13 @@ struct wmibm_handle {
     void *partials;             // per-block partial band statistics (dtype)
     unsigned int *ticket;       // last-block detection counter, kept at 0 between calls
     int64_t partial_blocks;
-    int64_t traffic[4];
+    int64_t traffic[5];
+    int *dev_status;            // set by kernels whose bounded waits gave up
+    unsigned *grid_bar;         // grid barrier of the fused kernel: (count, generation)
+    int occ_key[8], occ_val[8], occ_next;   // cached occupancy of stencil launch shapes
+    int32_t dirty_lo, dirty_hi; // stencil levels [lo, hi) whose stages read band or solid entries
+    int sm_count;
+    wmibm_tuning tuning;
     char err[512];
 };
 

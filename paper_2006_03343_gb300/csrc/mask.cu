@@ -62,6 +62,35 @@ int wall_stress_impl(wmibm_handle *h, const void *u, const void *v, const void *
 int force_impl(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream, int bx,
                int by, int kc);
 void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc);
+int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream);
+bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
+int stencil_fused(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
+                  wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask, double dt,
+                  const StencilConfig &c, cudaStream_t stream);
+int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream);
+
+// wall stress + force (+ mask when do_mask): one cooperative launch where the
+// pipelined stencil applies, else the separate kernels in that order.
+int wall_stress_force_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
+                           void *fz, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3],
+                           int do_mask, double dt, cudaStream_t stream)
+{
+    void *const f[3] = {fx, fy, fz};
+    StencilConfig c;
+    if (stencil_config(h, (const void *const *)tau, f, &c)) {
+        if (stats && h->nrec == 0) {
+            cudaError_t e = cudaMemsetAsync(stats, 0, 2 * sizeof(wmibm_band_stats), stream);
+            if (e != cudaSuccess) return cuda_status(h, e, "clear stats");
+            stats = nullptr;
+        }
+        return stencil_fused(h, u, v, w, (const void *const *)tau, f, stats, logz0, gradp, do_mask, dt, c, stream);
+    }
+    int st = wall_stress_impl(h, u, v, w, tau, stats, stream, logz0);
+    if (st) return st;
+    st = force_any(h, (const void *const *)tau, fx, fy, fz, stream);
+    if (st || !do_mask) return st;
+    return mask_impl(h, u, v, w, gradp, dt, stream);
+}
 
 int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream)
 {
@@ -84,12 +113,35 @@ extern "C" int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void
     return mask_impl(h, u, v, w, gradp, dt, (cudaStream_t)stream);
 }
 
+static int check_fields(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6], void *fx,
+                        void *fy, void *fz)
+{
+    if (!u || !v || !w || !tau || !fx || !fy || !fz)
+        return set_error(h, WMIBM_EINVAL, "NULL velocity, stress or force pointer");
+    for (int c = 0; c < 6; ++c)
+        if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
+    return check_device(h);
+}
+
+extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const void *v, const void *w,
+                                       void *const tau[6], void *fx, void *fy, void *fz, wmibm_band_stats *stats,
+                                       void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    int st = check_fields(h, u, v, w, tau, fx, fy, fz);
+    if (st) return st;
+    return wall_stress_force_impl(h, const_cast<void *>(u), const_cast<void *>(v), const_cast<void *>(w), tau, fx,
+                                  fy, fz, stats, nullptr, nullptr, 0, 0.0, (cudaStream_t)stream);
+}
+
 extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
                           void *fz, const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream)
 {
-    int st = wmibm_wall_stress(h, u, v, w, tau, stats, stream);
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;
-    st = wmibm_force(h, (const void *const *)tau, fx, fy, fz, stream);
-    if (st) return st;
-    return wmibm_mask(h, u, v, w, gradp, dt, stream);
+    if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
+        return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
+    if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
+    return wall_stress_force_impl(h, u, v, w, tau, fx, fy, fz, stats, nullptr, gradp, 1, dt, (cudaStream_t)stream);
 }

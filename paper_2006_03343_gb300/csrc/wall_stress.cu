@@ -1,15 +1,14 @@
-// Wall model at the band nodes (Sec. 3.3 of Liu & Stevens, arXiv:2006.03343).
+// Wall model at the band nodes (Sec. 3.3 of Liu & Stevens, arXiv:2006.03343),
+// stand-alone form.
 //
-// One thread per band node: gather the 8-corner trilinear stencils of u, v
-// (uv-grid) and w (w-grid) at x_c from the precomputed record, take the
-// tangential part U_r = u - (u.n) n, and write the rotated log-law stress
-//   tau_ij = tau_w (t_i n_j + n_i t_j),  t = U_r/|U_r|,  tau_w = -C |U_r|^2
-// which is a_im a_jn tau'_mn with tau'_13 = tau'_31 = tau_w and every other
-// tau'_mn = 0 (Eq. 28 and the rotation that follows it).  Extra blocks of the
-// same launch zero the solid-node stresses.  Band statistics are reduced per
-// warp with shuffles, per block in shared memory, and across blocks by the last
-// block to finish (fixed order, so the result is deterministic).
-#include "internal.cuh"
+// One thread per band node evaluates the model of band.cuh from the node's
+// precomputed record (trilinear stencils of u, v on the uv-grid and w on the
+// w-grid at x_c, unit normal, log-law factor) and writes its stress
+// components; extra blocks of the same launch zero the solid-node stresses.
+// Band statistics are reduced per warp with shuffles, per block in shared
+// memory, and across blocks by the last block to finish (fixed order, so the
+// result is deterministic).
+#include "band.cuh"
 
 using namespace wmibm;
 
@@ -32,115 +31,10 @@ struct WSParams {
     T log_phi_c, kappa2;
 };
 
-template <typename T>
-struct RecOf;
-template <>
-struct RecOf<float> {
-    using type = RecF32;
-};
-template <>
-struct RecOf<double> {
-    using type = RecF64;
-};
-
-struct Unpacked32 {
-    float nx, ny, nz, C, ax, ay, azu, azw;
-    int4 ix;
-};
-
-__device__ __forceinline__ void unpack(const RecF32 *r, int64_t t, float &nx, float &ny, float &nz, float &C,
-                                       float &ax, float &ay, float &azu, float &azw, int4 &ix)
-{
-    const float4 a = __ldg(&r[t].nC);
-    const float4 b = __ldg(&r[t].frac);
-    ix = __ldg(&r[t].ix);
-    nx = a.x; ny = a.y; nz = a.z; C = a.w;
-    ax = b.x; ay = b.y; azu = b.z; azw = b.w;
-}
-
-__device__ __forceinline__ void unpack(const RecF64 *r, int64_t t, double &nx, double &ny, double &nz, double &C,
-                                       double &ax, double &ay, double &azu, double &azw, int4 &ix)
-{
-    const double2 a = __ldg(&r[t].n01);
-    const double2 b = __ldg(&r[t].n2C);
-    const double2 c = __ldg(&r[t].fxy);
-    const double2 d = __ldg(&r[t].fz);
-    ix = __ldg(&r[t].ix);
-    nx = a.x; ny = a.y; nz = b.x; C = b.y;
-    ax = c.x; ay = c.y; azu = d.x; azw = d.y;
-}
-
-template <typename T>
-__device__ __forceinline__ T lerp(T a, T b, T t) { return a + t * (b - a); }
-
-template <typename V, typename T>
-__device__ __forceinline__ T trilinear(const V *f, int64_t base, int64_t di, int64_t dj, int64_t dk, T ax, T ay,
-                                       T az)
-{
-    const T c000 = load_vel<V, T>(f, base), c100 = load_vel<V, T>(f, base + di);
-    const T c010 = load_vel<V, T>(f, base + dj), c110 = load_vel<V, T>(f, base + di + dj);
-    const T c001 = load_vel<V, T>(f, base + dk), c101 = load_vel<V, T>(f, base + di + dk);
-    const T c011 = load_vel<V, T>(f, base + dj + dk), c111 = load_vel<V, T>(f, base + di + dj + dk);
-    const T c00 = lerp(c000, c100, ax), c10 = lerp(c010, c110, ax);
-    const T c01 = lerp(c001, c101, ax), c11 = lerp(c011, c111, ax);
-    return lerp(lerp(c00, c10, ay), lerp(c01, c11, ay), az);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_min(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_max(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// acc layout (kStatVals): [band][sum tau_w, sum tau_w^2, min tau_w, max U_r], band 0 = w, 1 = uv
-template <typename T>
-__device__ __forceinline__ void combine(T *dst, const T *src)
-{
-    for (int b = 0; b < 2; ++b) {
-        dst[4 * b + 0] += src[4 * b + 0];
-        dst[4 * b + 1] += src[4 * b + 1];
-        dst[4 * b + 2] = min(dst[4 * b + 2], src[4 * b + 2]);
-        dst[4 * b + 3] = max(dst[4 * b + 3], src[4 * b + 3]);
-    }
-}
-
-template <typename T>
-__device__ void block_reduce(T acc[kStatVals], T (*smem)[kStatVals])
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = 0; b < 2; ++b) {
-        acc[4 * b + 0] = warp_sum(acc[4 * b + 0]);
-        acc[4 * b + 1] = warp_sum(acc[4 * b + 1]);
-        acc[4 * b + 2] = warp_min(acc[4 * b + 2]);
-        acc[4 * b + 3] = warp_max(acc[4 * b + 3]);
-    }
-    if (lane == 0)
-        for (int s = 0; s < kStatVals; ++s) smem[warp][s] = acc[s];
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int w = 1; w < kThreads / 32; ++w) combine(acc, smem[w]);
-    __syncthreads();
-}
-
 template <typename T, typename V>
 __global__ void __launch_bounds__(kThreads) k_wall_stress(WSParams<T> p)
 {
-    using Rec = typename RecOf<T>::type;
-    __shared__ T red[kThreads / 32][kStatVals];
-    __shared__ bool last;
+    __shared__ T red[32][kStatVals];
 
     if (blockIdx.x >= p.band_blocks) {
         // solid nodes: the stress is set to zero (Sec. 3.3)
@@ -160,94 +54,28 @@ __global__ void __launch_bounds__(kThreads) k_wall_stress(WSParams<T> p)
     }
 
     T acc[kStatVals];
-    for (int b = 0; b < 2; ++b) {
-        acc[4 * b + 0] = T(0);
-        acc[4 * b + 1] = T(0);
-        acc[4 * b + 2] = T(0);     // tau_w <= 0: 0 is the identity of the min
-        acc[4 * b + 3] = T(0);     // |U_r| >= 0: 0 is the identity of the max
-    }
-
+    stats_identity(acc);
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (t < p.nb_w + p.nb_uv) {
         const bool is_w = t < p.nb_w;
-        T nx, ny, nz, C, ax, ay, azu, azw;
-        int4 ix;
-        unpack(reinterpret_cast<const Rec *>(p.rec), t, nx, ny, nz, C, ax, ay, azu, azw, ix);
-        const int64_t di = (ix.w & 1) ? 1 - p.nx : 1;
-        const int64_t dj = (ix.w & 2) ? (int64_t)(1 - p.ny) * p.nx : p.nx;
-        const V *u = reinterpret_cast<const V *>(p.u);
-        const V *v = reinterpret_cast<const V *>(p.v);
-        const V *w = reinterpret_cast<const V *>(p.w);
-        const T uc = trilinear<V, T>(u, ix.y, di, dj, p.plane, ax, ay, azu);
-        const T vc = trilinear<V, T>(v, ix.y, di, dj, p.plane, ax, ay, azu);
-        const T wc = trilinear<V, T>(w, ix.z, di, dj, p.plane, ax, ay, azw);
-        if (p.logz0) {
-            const T d = p.log_phi_c - __ldg(p.logz0 + ix.x);
-            C = p.kappa2 / (d * d);
-        }
-
-        const T un = uc * nx + vc * ny + wc * nz;
-        const T urx = uc - un * nx, ury = vc - un * ny, urz = wc - un * nz;
-        const T ur2 = urx * urx + ury * ury + urz * urz;
-        const T ur = sqrt(ur2);
-        const T s = -C * ur;                      // tau_w / |U_r|
-        const int32_t idx = ix.x;
+        const BandOut<T> o = band_model<T, V>(p.rec, t, is_w, reinterpret_cast<const V *>(p.u),
+                                              reinterpret_cast<const V *>(p.v), reinterpret_cast<const V *>(p.w),
+                                              p.nx, p.ny, p.plane, p.logz0, p.log_phi_c, p.kappa2);
         if (is_w) {
-            p.txz[idx] = s * (urx * nz + nx * urz);
-            p.tyz[idx] = s * (ury * nz + ny * urz);
+            p.txz[o.idx] = o.t0;
+            p.tyz[o.idx] = o.t1;
         } else {
-            p.txx[idx] = T(2) * s * (urx * nx);
-            p.txy[idx] = s * (urx * ny + nx * ury);
-            p.tyy[idx] = T(2) * s * (ury * ny);
-            p.tzz[idx] = T(2) * s * (urz * nz);
+            p.txx[o.idx] = o.t0;
+            p.txy[o.idx] = o.t1;
+            p.tyy[o.idx] = o.t2;
+            p.tzz[o.idx] = o.t3;
         }
-        const T tw = -C * ur2;
-        const int b = is_w ? 0 : 1;
-        acc[4 * b + 0] = tw;
-        acc[4 * b + 1] = tw * tw;
-        acc[4 * b + 2] = tw;
-        acc[4 * b + 3] = ur;
+        stats_add(acc, is_w ? 0 : 1, o.tw, o.ur);
     }
 
     if (p.stats == nullptr) return;            // uniform across the launch
-
-    block_reduce(acc, red);
-    if (threadIdx.x == 0) {
-        T *dst = p.partials + (int64_t)blockIdx.x * kStatVals;
-        for (int s = 0; s < kStatVals; ++s) dst[s] = acc[s];
-        __threadfence();
-        const unsigned prev = atomicAdd(p.ticket, 1u);
-        last = (prev == p.band_blocks - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-
-    // last band block: reduce all partials in a fixed order
-    __threadfence();
-    for (int b = 0; b < 2; ++b) {
-        acc[4 * b + 0] = T(0);
-        acc[4 * b + 1] = T(0);
-        acc[4 * b + 2] = T(0);
-        acc[4 * b + 3] = T(0);
-    }
-    for (int64_t blk = threadIdx.x; blk < p.band_blocks; blk += kThreads) {
-        T src[kStatVals];
-        for (int s = 0; s < kStatVals; ++s) src[s] = __ldcg(p.partials + blk * kStatVals + s);
-        combine(acc, src);
-    }
-    block_reduce(acc, red);
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b) {
-            wmibm_band_stats st;
-            st.count = b == 0 ? p.nb_w : p.nb_uv;
-            st.sum_tw = (double)acc[4 * b + 0];
-            st.sum_tw2 = (double)acc[4 * b + 1];
-            st.min_tw = (double)acc[4 * b + 2];
-            st.max_ur = (double)acc[4 * b + 3];
-            p.stats[b] = st;
-        }
-        *p.ticket = 0u;                         // ready for the next call
-    }
+    stats_block_reduce(acc, red);
+    stats_finish(acc, red, p.partials, p.ticket, p.band_blocks, p.stats, p.nb_w, p.nb_uv);
 }
 
 template <typename T, typename V>

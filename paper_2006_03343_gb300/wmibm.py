@@ -25,7 +25,8 @@ DTYPE_CODES = {"f32": F32, "f64": F64, "bf16": BF16}
 # symbols the header declares (checked by the CPU test suite)
 EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmibm_step", "wmibm_list_size",
             "wmibm_export_list", "wmibm_traffic_bytes", "wmibm_destroy", "wmibm_status_string",
-            "wmibm_last_error")
+            "wmibm_last_error", "wmibm_wall_stress_force", "wmibm_set_tuning", "wmibm_get_tuning",
+            "wmibm_device_status")
 
 
 class WmibmError(RuntimeError):
@@ -42,6 +43,16 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("phi_b", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("force_path", ctypes.c_int32), ("rows", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("consumer_warps", ctypes.c_int32), ("wall_warps", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("direct_bx", ctypes.c_int32), ("direct_by", ctypes.c_int32),
+                ("direct_kc", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 STATS_DTYPE = np.dtype([("count", "<i8"), ("sum_tw", "<f8"), ("sum_tw2", "<f8"), ("min_tw", "<f8"),
@@ -77,6 +88,14 @@ def load(path: Optional[str] = None):
     L.wmibm_mask.restype = ctypes.c_int
     L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
     L.wmibm_step.restype = ctypes.c_int
+    L.wmibm_wall_stress_force.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _VP, _VP]
+    L.wmibm_wall_stress_force.restype = ctypes.c_int
+    L.wmibm_set_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
+    L.wmibm_set_tuning.restype = ctypes.c_int
+    L.wmibm_get_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
+    L.wmibm_get_tuning.restype = ctypes.c_int
+    L.wmibm_device_status.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), _VP]
+    L.wmibm_device_status.restype = ctypes.c_int
     L.wmibm_list_size.argtypes = [_VP, ctypes.c_int32]
     L.wmibm_list_size.restype = ctypes.c_int64
     L.wmibm_export_list.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP]
@@ -197,6 +216,31 @@ class Handle:
                 self._field(t)
         self._check(self._L.wmibm_mask(self._h, _dptr(u), _dptr(v), _dptr(w),
                                        None if gradp is None else _ptrs(gradp), float(dt), _stream_ptr(stream)))
+
+    def wall_stress_force(self, u, v, w, tau, f, stats=None, stream=None):
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in list(tau) + list(f):
+            self._field(t)
+        self._check(self._L.wmibm_wall_stress_force(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau),
+                                                    _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
+                                                    None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def set_tuning(self, **fields):
+        t = self.get_tuning()
+        for k, v in fields.items():
+            setattr(t, k, int(v))
+        self._check(self._L.wmibm_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> Tuning:
+        t = Tuning()
+        self._check(self._L.wmibm_get_tuning(self._h, ctypes.byref(t)))
+        return t
+
+    def device_status(self, stream=None) -> int:
+        out = ctypes.c_int32(-1)
+        self._check(self._L.wmibm_device_status(self._h, ctypes.byref(out), _stream_ptr(stream)))
+        return int(out.value)
 
     def step(self, u, v, w, tau, f, gradp=None, dt=0.0, stats=None, stream=None):
         for t in (u, v, w):

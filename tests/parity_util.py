@@ -98,3 +98,17 @@ def assert_stats_close(gs, os_, dtype):
             got = gs[b][name]
             scale = max(abs(ref), 1e-30)
             assert abs(got - ref) <= tol * scale + 1e-300, (b, name, got, ref)
+
+
+def gpu_fused(handle, case, dtype, vel_dtype=None, with_stats=True):
+    """The fused wall stress + force pass through the C ABI."""
+    import torch
+    vel_dtype = vel_dtype or dtype
+    u, v, w = (to_dev(x, vel_dtype) for x in (case.u, case.v, case.w))
+    tau = [to_dev(case.tau[k], dtype) for k in inputs.TAU_NAMES]
+    f = [to_dev(np.zeros(case.shape), dtype) for _ in range(3)]
+    stats = handle.new_stats() if with_stats else None
+    handle.wall_stress_force(u, v, w, tau, f, stats)
+    torch.cuda.synchronize()
+    st = handle.parse_stats(stats) if with_stats else None
+    return ({k: to_host(t) for k, t in zip(inputs.TAU_NAMES, tau)}, tuple(to_host(t) for t in f), st)
