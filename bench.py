@@ -48,6 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tile shapes)")
+    ap.add_argument("--tuning", default="", help="explicit tile shape instead of the autotuner, e.g. "
+                    "rows=2,stages=4,consumer_warps=4,wall_warps=8")
     ap.add_argument("--profile", action="store_true",
                     help="few launches for ncu: no clock soak, no end-to-end leg, no CPU baseline")
     return ap.parse_args(argv)
@@ -209,7 +212,7 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # GPU arm
 # --------------------------------------------------------------------------- #
-KERNEL_SOURCES = ("stencil.cu", "band.cuh", "tma.cuh", "internal.cuh")
+KERNEL_SOURCES = ("stencil.cu", "band.cuh", "tma.cuh", "internal.cuh")  # the profiled kernel's sources
 
 
 class GpuForm:
@@ -230,42 +233,62 @@ class GpuForm:
         self.f = [torch.empty(case.shape, dtype=self.tdt, device=dev) for _ in range(3)]
         self.stats = self.h.new_stats()
 
-    def step(self, stream=None):
-        """One pass of the stage through the C ABI: wall stress, force and body mask
-        (one cooperative launch where the grid allows)."""
-        self.h.step(self.u, self.v, self.w, self.tau, self.f, None, 0.0, self.stats)
+        self.call = self.h.prepare_step(self.u, self.v, self.w, self.tau, self.f, self.stats)
+        self.graphs = None
+
+    def step(self, stream=None, evs=None):
+        """One pass of the stage through the C ABI: the wall-model kernel, then the
+        force + body-mask kernel (each replayed from its captured CUDA graph once
+        captured); events (if given) bracket the two launches."""
+        if evs is not None:
+            evs[0].record(stream)
+        if self.graphs:
+            self.graphs[0].replay()
+        else:
+            self.call.wall_stress()
+        if evs is not None:
+            evs[1].record(stream)
+        if self.graphs:
+            self.graphs[1].replay()
+        else:
+            self.call.force_mask()
+        if evs is not None:
+            evs[2].record(stream)
 
     def capture(self):
-        """The step captured once as a CUDA graph (replayed in the timed loop)."""
+        """Captures each of the two launches as its own CUDA graph."""
         import torch
         self.step()
         torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self.step()
+        graphs = []
+        for fn in (self.call.wall_stress, self.call.force_mask):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            graphs.append(g)
         torch.cuda.synchronize()
+        self.graphs = graphs
 
     def host_result(self):
         import torch
         torch.cuda.synchronize()
         return ([t.double().cpu().numpy() for t in self.tau], [t.double().cpu().numpy() for t in self.f])
 
-    def timed(self, stream, flush, steps, graph=True):
-        """Per-step device time (ms) with CUDA events on the launching stream; the L2
-        is flushed before every step, outside the events."""
+    def timed(self, stream, flush, steps):
+        """Per-step device times (ms) with CUDA events on the launching stream: the
+        whole step, the wall kernel and the force + mask kernel.  The L2 is
+        flushed before every step, outside the events."""
         import torch
-        events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
         torch.cuda.synchronize()
         for s in range(steps):
             flush.zero_()
-            events[s][0].record(stream)
-            if graph:
-                self.graph.replay()
-            else:
-                self.step()
-            events[s][1].record(stream)
+            self.step(stream, events[s])
         torch.cuda.synchronize()
-        return [e[0].elapsed_time(e[1]) for e in events]
+        step = [e[0].elapsed_time(e[2]) for e in events]
+        wall = [e[0].elapsed_time(e[1]) for e in events]
+        force = [e[1].elapsed_time(e[2]) for e in events]
+        return step, wall, force
 
 
 def kernel_digest():
@@ -299,10 +322,20 @@ def run_ours(args):
     form.step()
     first_tau, first_f = form.host_result()
 
+    tuned = None
+    if args.tuning:
+        fields = dict(kv.split("=") for kv in args.tuning.split(","))
+        h.set_tuning(force_path=1, **{k: int(v) for k, v in fields.items()})
+        tuned = {"tuning": h.get_tuning().as_dict(), "explicit": True}
+    elif not args.no_tune:
+        from paper_2006_03343_gb300 import autotune
+        tuned = autotune.tune(h, (form.u, form.v, form.w, form.tau, form.f, form.stats))
+
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         form.step()
     torch.cuda.synchronize()
+    eager_ms = form.timed(stream, flush, min(args.steps, 20))[0]
     form.capture()
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
@@ -313,16 +346,15 @@ def run_ours(args):
     while not args.profile and time.perf_counter() - t_soak < 1.0:
         for _ in range(20):
             flush.zero_()
-            form.graph.replay()
+            form.step()
         torch.cuda.synchronize()
 
     if world > 1:
         torch.distributed.barrier()
-    step_ms = form.timed(stream, flush, args.steps, graph=True)
+    step_ms, wall_ms, force_ms = form.timed(stream, flush, args.steps)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    eager_ms = form.timed(stream, flush, min(args.steps, 20), graph=False)
     status = h.device_status()
 
     total_ms = float(sum(step_ms))
@@ -332,25 +364,29 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * args.steps * case.npoints / (total_ms * 1e-3) / 1e9
 
-    # roofline of the dominant (and only) kernel: the cooperative step kernel
-    step_bytes = h.traffic_bytes(4) + h.traffic_bytes(2)
-    avg_s = float(np.mean(step_ms)) * 1e-3
+    # roofline of the dominant kernel: force + mask (the pipelined stencil)
+    force_bytes = h.traffic_bytes(1) + h.traffic_bytes(2)
+    step_bytes = h.traffic_bytes(0) + force_bytes
     peak, peak_kind = measured_peak()
-    achieved = step_bytes / avg_s / 1e9
+    achieved = force_bytes / (float(np.mean(force_ms)) * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload, args.dtype, args.vel_dtype)
 
     # the plain FP64 form of the same workload, timed the same way
     f64_form = None
     if args.dtype == "f32" and not args.profile:
         g64 = GpuForm(case, "f64", None, dev)
+        if not args.no_tune:
+            from paper_2006_03343_gb300 import autotune
+            autotune.tune(g64.h, (g64.u, g64.v, g64.w, g64.tau, g64.f, g64.stats))
         for _ in range(3):
             flush.zero_()
             g64.step()
         g64.capture()
-        s64 = g64.timed(stream, flush, args.steps)
-        b64 = g64.h.traffic_bytes(4) + g64.h.traffic_bytes(2)
+        s64, _, fm64 = g64.timed(stream, flush, args.steps)
+        b64 = g64.h.traffic_bytes(0) + g64.h.traffic_bytes(1) + g64.h.traffic_bytes(2)
         f64_form = {"value": args.steps * case.npoints / (sum(s64) * 1e-3) / 1e9, "unit": UNIT,
-                    "ms_per_step": float(np.mean(s64)), "gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
+                    "ms_per_step": float(np.mean(s64)), "step_gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
+                    "force_gbs": (g64.h.traffic_bytes(1) + g64.h.traffic_bytes(2)) / (float(np.mean(fm64)) * 1e-3) / 1e9,
                     "device_status": g64.h.device_status()}
         g64.h.close()
         del g64
@@ -408,12 +444,17 @@ def run_ours(args):
                 "config": workload_config(args, case),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "k_stencil (cooperative step: wall stress, grid barrier, mask + force)",
+                             "kernel": "k_stencil (pipelined force + body mask)",
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                             "algorithmic_bytes_per_launch": step_bytes},
-                "timing": "CUDA graph replay of one step per event pair; eager launches: %.4f ms/step"
-                          % float(np.mean(eager_ms)),
-                "gpu_launches": args.steps,
+                             "algorithmic_bytes_per_launch": force_bytes},
+                "kernels_ms": {"wall": float(np.mean(wall_ms)), "force_mask": float(np.mean(force_ms))},
+                "step_bytes": step_bytes,
+                "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
+                "step_frac_of_peak": step_bytes / (total_ms / args.steps * 1e-3) / 1e9 / peak,
+                "timing": "per step: CUDA events around graph replays of the wall kernel and of the force + "
+                          "mask kernel; eager launches: %.4f ms/step" % float(np.mean(eager_ms)),
+                "tuning": tuned,
+                "gpu_launches": 2 * args.steps,
                 "device_status": status,
                 "f64_form": f64_form, "accuracy": accuracy,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}

@@ -138,23 +138,31 @@ int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gra
 
 /*
  * wmibm_step - wmibm_wall_stress, wmibm_force and wmibm_mask in that order on
- * one stream: one pass of the whole per-step stress stage.
+ * one stream: one pass of the whole per-step stress stage, as two launches (the
+ * wall-model kernel, then the force + mask kernel of wmibm_force_mask launched
+ * as its programmatic dependent, which streams the levels holding no band or
+ * solid node before it waits for the wall model).
  */
 int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
                const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream);
 
 /*
- * wmibm_wall_stress_force - wmibm_wall_stress followed by wmibm_force in one
- * cooperative launch where the grid allows (nx a multiple of 4 for F32 or 2 for
- * F64, ny >= 3, 16-byte aligned stress and force buffers, full x-rows that fit
- * the shared-memory stages): the wall model runs over the whole grid, then a
- * grid barrier, then the pipelined stencil.  Otherwise the two kernels run back
- * to back.  Same arguments and results (band entries, solid zeros, forcing,
- * statistics) as the two calls, up to the summation order of the statistics.
- * wmibm_step uses the same launch and applies the body mask after the barrier.
+ * wmibm_wall_stress_force - wmibm_wall_stress followed by wmibm_force on one
+ * stream (same arguments and results as the two calls).
  */
 int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                             void *fx, void *fy, void *fz, wmibm_band_stats *stats, void *stream);
+
+/*
+ * wmibm_force_mask - wmibm_force followed by wmibm_mask, in one launch where the
+ * grid allows the pipelined stencil (nx a multiple of 4 for F32 or 2 for F64,
+ * ny >= 3, 16-byte aligned stress and force buffers, full x-rows that fit the
+ * shared-memory stages): the kernel forms f and then applies Eq. 27 to u, v, w.
+ * Otherwise the force and mask kernels run back to back.  Arguments as in
+ * wmibm_force and wmibm_mask.
+ */
+int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *u, void *v,
+                     void *w, const void *const gradp[3], double dt, void *stream);
 
 /*
  * Launch tuning of the stencil kernels (what the autotuner sets).  Zero fields
@@ -165,7 +173,7 @@ typedef struct wmibm_tuning {
     int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
     int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
     int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */
-    int32_t wall_warps;       /* fused step: warps running the wall model and the mask, 1..8 */
+    int32_t wall_warps;       /* fused step: warps per block of the wall-model kernel, 1..8 */
     int32_t blocks_per_sm;    /* pipeline: cap on resident blocks per SM */
     int32_t direct_bx;        /* direct-load kernel: vectors per block row */
     int32_t direct_by;        /* direct-load kernel: rows per block */

@@ -7,7 +7,7 @@ binding is imported lazily so that input generation works on machines without
 the library; calling into it without a built library raises.
 """
 
-__all__ = ["inputs", "wmibm"]
+__all__ = ["inputs", "wmibm", "autotune"]
 
 
 def __getattr__(name):

@@ -1,0 +1,131 @@
+"""Autotuner of the stencil launch shape.
+
+Times the fused step (wall kernel + pipelined stencil + body mask) of a handle
+over a grid of tile shapes -- rows per strip, shared-memory stages, consumer
+warps, warps of the wall kernel -- with CUDA events on the launching stream
+(L2 flushed before every timed call), keeps the fastest, applies it to the
+handle and caches it in a JSON file keyed by GPU, precision and grid size.
+
+The timed calls go through the C ABI like any other call; nothing here
+computes anything of the method.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import time
+from typing import Optional
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune", "tuning.json")
+
+ROWS = (1, 2, 4)
+STAGES = (2, 3, 4, 5, 6)
+CONSUMERS = (2, 3, 4, 6, 8)
+WALL = (4, 8)
+SMEM_LIMIT = 200 * 1024
+
+
+def cache_path() -> str:
+    return os.environ.get("WMIBM_TUNE_CACHE", DEFAULT_CACHE)
+
+
+def key_of(handle) -> str:
+    import torch
+    name = torch.cuda.get_device_name(handle.device)
+    nx, ny, nz = handle.grid[:3]
+    return f"{name}|{handle.dtype}|{handle.vel_dtype}|{nx}x{ny}x{nz}"
+
+
+def candidates(handle):
+    nx, ny, nz = (int(x) for x in handle.grid[:3])
+    es = 8 if handle.dtype == "f64" else 4
+    vec = 16 // es
+    if nx % vec != 0:
+        return [dict(force_path=2)]
+    out = []
+    for rows, stages, cons, wall in itertools.product(ROWS, STAGES, CONSUMERS, WALL):
+        if ny % rows or ny < rows + 2:
+            continue
+        if (6 * rows + 6) * nx * es * stages + 256 > SMEM_LIMIT:
+            continue
+        out.append(dict(force_path=1, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall))
+    return out
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_config(handle, fields, tuning, reps, flush):
+    import torch
+    u, v, w, tau, f, stats = fields
+    handle.set_tuning(**tuning)
+    for _ in range(2):
+        handle.step(u, v, w, tau, f, None, 0.0, stats)
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        handle.step(u, v, w, tau, f, None, 0.0, stats)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def tune(handle, fields, reps: int = 5, use_cache: bool = True, budget_s: float = 60.0,
+         verbose: bool = False) -> dict:
+    """Finds, applies and caches the fastest tile shape for `handle`.
+
+    fields = (u, v, w, tau[6], f[3], stats) device tensors of the handle's shape;
+    the step mutates them (velocity mask, band stresses), which does not change
+    the work it does.  Returns {"tuning": ..., "ms": ..., "tried": n}."""
+    import torch
+    path = cache_path()
+    key = key_of(handle)
+    cache = _load_cache(path) if use_cache else {}
+    if use_cache and key in cache:
+        handle.set_tuning(**cache[key]["tuning"])
+        return dict(cache[key], cached=True)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=handle.device)
+    best = None
+    tried = 0
+    t_start = time.perf_counter()
+    for cand in candidates(handle):
+        if time.perf_counter() - t_start > budget_s:
+            break
+        try:
+            ms = time_config(handle, fields, cand, reps, flush)
+        except Exception:
+            continue
+        tried += 1
+        if verbose:
+            print(f"  {ms * 1e3:8.1f} us  {cand}")
+        if best is None or ms < best[0]:
+            best = (ms, cand)
+    if best is None:
+        handle.set_tuning()
+        return {"tuning": {}, "ms": None, "tried": tried}
+    handle.set_tuning(**best[1])
+    result = {"tuning": best[1], "ms": best[0], "tried": tried}
+    if use_cache:
+        cache = _load_cache(path)
+        cache[key] = result
+        _save_cache(path, cache)
+    return dict(result, cached=False)

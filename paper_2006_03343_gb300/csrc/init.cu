@@ -233,11 +233,68 @@ __global__ void __launch_bounds__(kThreads) k_count_marks(const uint8_t *a, cons
     }
 }
 
+// A solid node starts a run (maximal set of consecutive nodes of one x-row) if
+// it is the first of the list, does not follow its predecessor, or begins a row.
+__device__ __forceinline__ bool run_start(const int32_t *list, int64_t t, int32_t nx)
+{
+    return t == 0 || list[t] != list[t - 1] + 1 || list[t] % nx == 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_runs_count(const int32_t *list, int64_t n, int32_t nx,
+                                                          int32_t *counts)
+{
+    __shared__ int warp_tot[kThreads / 32];
+    int c = 0;
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    for (int it = 0; it < kChunkItems; ++it) {
+        const int64_t t = base + (int64_t)it * kThreads + threadIdx.x;
+        if (t < n && run_start(list, t, nx)) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sacc = 0;
+        for (int w = 0; w < kThreads / 32; ++w) sacc += warp_tot[w];
+        counts[blockIdx.x] = sacc;
+    }
+}
+
+// Writes the runs (first node index, length) in ascending order.
+__global__ void __launch_bounds__(kThreads) k_runs_write(const int32_t *list, int64_t n, int32_t nx,
+                                                          const int64_t *offsets, int2 *runs)
+{
+    __shared__ int warp_tot[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t run = offsets[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    for (int it = 0; it < kChunkItems; ++it) {
+        const int64_t t = base + (int64_t)it * kThreads + threadIdx.x;
+        const bool q = t < n && run_start(list, t, nx);
+        const unsigned bal = __ballot_sync(0xffffffffu, q);
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            before += (w < warp) ? warp_tot[w] : 0;
+            total += warp_tot[w];
+        }
+        if (q) {
+            int32_t len = 1;
+            while (t + len < n && list[t + len] == list[t] + len && (list[t] + len) % nx != 0) ++len;
+            runs[run + before + __popc(bal & ((1u << lane) - 1u))] = make_int2(list[t], len);
+        }
+        run += total;
+        __syncthreads();
+    }
+}
+
 void free_handle(wmibm_handle *h)
 {
+    for (int g = 0; h && g < 2; ++g)
+        if (h->runs[g]) cudaFree(h->runs[g]);
     if (!h) return;
     if (h->dev_status) cudaFree(h->dev_status);
-    if (h->grid_bar) cudaFree(h->grid_bar);
     for (int l = 0; l < 6; ++l)
         if (h->lists.p[l]) cudaFree(h->lists.p[l]);
     if (h->rec) cudaFree(h->rec);
@@ -328,6 +385,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     int32_t *d_counts = nullptr;
     int64_t *d_offsets = nullptr;
     uint8_t *d_mark = nullptr;
+    int32_t *d_counts2 = nullptr;
+    int64_t *d_offsets2 = nullptr;
     unsigned long long *d_marks = nullptr;
     const int64_t nblk = (n + kChunk - 1) / kChunk;
     std::vector<int32_t> counts(6 * nblk);
@@ -435,10 +494,45 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
                 h->dirty_hi = std::min(h->nz, hi + 2);
             }
         }
+        // solid runs along x (used by the fused step to zero solid stresses)
+        for (int gsel = 0; gsel < 2; ++gsel) {
+            const int32_t *solid = h->lists.p[gsel == 0 ? WMIBM_LIST_SOLID_W : WMIBM_LIST_SOLID_UV];
+            const int64_t nsolid = h->lists.n[gsel == 0 ? WMIBM_LIST_SOLID_W : WMIBM_LIST_SOLID_UV];
+            const int64_t sblk = std::max<int64_t>((nsolid + kChunk - 1) / kChunk, 1);
+            std::vector<int32_t> rc(sblk, 0);
+            std::vector<int64_t> ro(sblk, 0);
+            TRY(cudaMalloc(&d_counts2, sblk * sizeof(int32_t)), "cudaMalloc run counts");
+            TRY(cudaMalloc(&d_offsets2, sblk * sizeof(int64_t)), "cudaMalloc run offsets");
+            TRY(cudaMemsetAsync(d_counts2, 0, sblk * sizeof(int32_t), stream), "memset run counts");
+            if (nsolid > 0) {
+                k_runs_count<<<(unsigned)sblk, kThreads, 0, stream>>>(solid, nsolid, h->nx, d_counts2);
+                TRY(cudaGetLastError(), "k_runs_count launch");
+            }
+            TRY(cudaMemcpyAsync(rc.data(), d_counts2, sblk * sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
+                "copy run counts");
+            TRY(cudaStreamSynchronize(stream), "k_runs_count");
+            int64_t nr = 0;
+            for (int64_t b = 0; b < sblk; ++b) {
+                ro[b] = nr;
+                nr += rc[b];
+            }
+            h->nruns[gsel] = nr;
+            TRY(cudaMalloc(&h->runs[gsel], std::max<int64_t>(nr, 1) * sizeof(int2)), "cudaMalloc runs");
+            TRY(cudaMemcpyAsync(d_offsets2, ro.data(), sblk * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
+                "copy run offsets");
+            if (nsolid > 0) {
+                k_runs_write<<<(unsigned)sblk, kThreads, 0, stream>>>(solid, nsolid, h->nx, d_offsets2,
+                                                                        h->runs[gsel]);
+                TRY(cudaGetLastError(), "k_runs_write launch");
+            }
+            TRY(cudaStreamSynchronize(stream), "k_runs_write");
+            cudaFree(d_counts2);
+            cudaFree(d_offsets2);
+            d_counts2 = nullptr;
+            d_offsets2 = nullptr;
+        }
         TRY(cudaMalloc(&h->dev_status, sizeof(int)), "cudaMalloc status");
         TRY(cudaMemsetAsync(h->dev_status, 0, sizeof(int), stream), "memset status");
-        TRY(cudaMalloc(&h->grid_bar, 2 * sizeof(unsigned)), "cudaMalloc grid barrier");
-        TRY(cudaMemsetAsync(h->grid_bar, 0, 2 * sizeof(unsigned), stream), "memset grid barrier");
         TRY(cudaStreamSynchronize(stream), "init state");
 
         const int64_t es = (int64_t)elem_size(o.dtype), vs = (int64_t)elem_size(o.vel_dtype);
@@ -464,6 +558,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
 
 fail:
     if (stream) cudaStreamSynchronize(stream);
+    cudaFree(d_counts2);
+    cudaFree(d_offsets2);
     cudaFree(d_phi_uv);
     cudaFree(d_phi_w);
     cudaFree(d_z0);

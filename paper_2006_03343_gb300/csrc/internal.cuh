@@ -62,8 +62,9 @@ struct wmibm_handle {
     unsigned int *ticket;       // last-block detection counter, kept at 0 between calls
     int64_t partial_blocks;
     int64_t traffic[5];
+    int2 *runs[2];              // solid runs along x (first node, length): w-grid, uv-grid
+    int64_t nruns[2];
     int *dev_status;            // set by kernels whose bounded waits gave up
-    unsigned *grid_bar;         // grid barrier of the fused kernel: (count, generation)
     int occ_key[8], occ_val[8], occ_next;   // cached occupancy of stencil launch shapes
     int32_t dirty_lo, dirty_hi; // stencil levels [lo, hi) whose stages read band or solid entries
     int sm_count;

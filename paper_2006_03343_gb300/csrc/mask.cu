@@ -64,30 +64,22 @@ int force_impl(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, vo
 void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc);
 int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream);
 bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
-int stencil_fused(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
-                  wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask, double dt,
-                  const StencilConfig &c, cudaStream_t stream);
+int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
+                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream);
 int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream);
 
-// wall stress + force (+ mask when do_mask): one cooperative launch where the
-// pipelined stencil applies, else the separate kernels in that order.
-int wall_stress_force_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
-                           void *fz, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3],
-                           int do_mask, double dt, cudaStream_t stream)
+// force, then (do_mask) the body mask: one pipelined launch where the grid
+// allows, else the direct-load force kernel followed by the mask kernel.
+int force_mask_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
+                    const void *const gradp[3], int do_mask, double dt, bool pdl, cudaStream_t stream)
 {
     void *const f[3] = {fx, fy, fz};
     StencilConfig c;
     if (stencil_config(h, (const void *const *)tau, f, &c)) {
-        if (stats && h->nrec == 0) {
-            cudaError_t e = cudaMemsetAsync(stats, 0, 2 * sizeof(wmibm_band_stats), stream);
-            if (e != cudaSuccess) return cuda_status(h, e, "clear stats");
-            stats = nullptr;
-        }
-        return stencil_fused(h, u, v, w, (const void *const *)tau, f, stats, logz0, gradp, do_mask, dt, c, stream);
+        if (do_mask) return stencil_force_mask(h, u, v, w, (const void *const *)tau, f, gradp, dt, c, pdl, stream);
+        return force_any(h, (const void *const *)tau, fx, fy, fz, stream);
     }
-    int st = wall_stress_impl(h, u, v, w, tau, stats, stream, logz0);
-    if (st) return st;
-    st = force_any(h, (const void *const *)tau, fx, fy, fz, stream);
+    int st = force_any(h, (const void *const *)tau, fx, fy, fz, stream);
     if (st || !do_mask) return st;
     return mask_impl(h, u, v, w, gradp, dt, stream);
 }
@@ -130,8 +122,22 @@ extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const voi
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;
-    return wall_stress_force_impl(h, const_cast<void *>(u), const_cast<void *>(v), const_cast<void *>(w), tau, fx,
-                                  fy, fz, stats, nullptr, nullptr, 0, 0.0, (cudaStream_t)stream);
+    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, nullptr);
+    if (st) return st;
+    return force_any(h, (const void *const *)tau, fx, fy, fz, (cudaStream_t)stream);
+}
+
+extern "C" int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *u,
+                                void *v, void *w, const void *const gradp[3], double dt, void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    int st = check_fields(h, u, v, w, const_cast<void *const *>(tau), fx, fy, fz);
+    if (st) return st;
+    if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
+        return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
+    if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
+    return force_mask_impl(h, u, v, w, const_cast<void *const *>(tau), fx, fy, fz, gradp, 1, dt, false,
+                           (cudaStream_t)stream);
 }
 
 extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
@@ -143,5 +149,7 @@ extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *cons
     if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
         return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
     if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
-    return wall_stress_force_impl(h, u, v, w, tau, fx, fy, fz, stats, nullptr, gradp, 1, dt, (cudaStream_t)stream);
+    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, nullptr);
+    if (st) return st;
+    return force_mask_impl(h, u, v, w, tau, fx, fy, fz, gradp, 1, dt, true, (cudaStream_t)stream);
 }

@@ -16,15 +16,19 @@
 // wrap inside the staged full rows, and release the stage through the "empty"
 // mbarrier.
 //
-// Fused step (cooperative launch): phase 1 spreads the wall model of Sec. 3.3
-// over every thread of the grid (band records and solid zeroing, written to
-// the caller's stress arrays, band statistics accumulated on the way); a grid
-// barrier; phase 2 applies the body mask of Eq. 27 (which may only change the
-// velocity after every band stencil has read it) and runs the stencil on the
-// completed stress field.  One launch does wall stress + force (+ mask).
+// Fused step (two kernels chained by programmatic dependent launch): the wall
+// kernel evaluates the wall model of Sec. 3.3 at every band node and zeroes the
+// solid runs (stresses written to the caller's arrays, band statistics reduced
+// on the way) and lets the stencil kernel launch at once.  The stencil kernel
+// first streams its "clean" stages, whose rows hold no band or solid node;
+// before its first "dirty" stage, and before the body mask of Eq. 27 (which may
+// change the velocity only after every band stencil has read it), it waits on
+// the grid dependency, i.e. for the wall kernel to have completed.
 //
-// Every wait (mbarrier phases, the grid barrier) is bounded: on time-out the
-// kernel records a status code in device memory and leaves its loops.
+// Every mbarrier wait is bounded: on time-out the kernel records a status code
+// in device memory and leaves its loops.
+#include <algorithm>
+
 #include "band.cuh"
 #include "tma.cuh"
 
@@ -85,14 +89,13 @@ struct StencilParams {
     void *u, *v, *w;
     const void *rec;
     int64_t nb_w, nb_uv;
-    const int32_t *solid_w, *solid_uv;
-    int64_t ns_w, ns_uv;
+    const int2 *runs_w, *runs_uv;   // solid runs along x (first node, length)
+    int64_t nr_w, nr_uv;
     int do_mask;
     const int32_t *body_w, *body_uv;
     int64_t nbody_w, nbody_uv;
     const T *gpx, *gpy, *gpz;
     T mask_c;                 // 3 dt / 2
-    unsigned *bar_count, *bar_gen;
     T *partials;
     unsigned *ticket;
     wmibm_band_stats *stats;
@@ -202,24 +205,16 @@ __device__ __forceinline__ int32_t wrapj(int32_t j, int32_t ny) { return j < 0 ?
 // ------------------------------------------------------------------------- //
 // producer: lane 0 of warp 0
 // ------------------------------------------------------------------------- //
-// Waits (bounded) until the grid barrier's generation differs from g0.
-__device__ bool wait_generation(const unsigned *gen, unsigned g0, int *status)
+// Waits until the preceding kernel of the stream (the wall kernel) has
+// completed and its writes are visible (programmatic dependent launch; without
+// a programmatic dependency the stream order already guarantees it).
+__device__ __forceinline__ void wait_wall_kernel()
 {
-    const uint64_t t0 = global_timer_ns();
-    for (uint32_t it = 0; *(volatile const unsigned *)gen == g0; ++it) {
-        __nanosleep(128);
-        if ((it & 63u) == 63u && (*(volatile int *)status != 0 || global_timer_ns() - t0 > kWaitLimitNs)) {
-            atomicExch(status, kDevStatusBarrierTimeout);
-            return false;
-        }
-    }
-    __threadfence();
-    return true;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <typename T, int TY, bool FUSED>
-__device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint64_t *empty, const Schedule &sc,
-                        unsigned g0)
+__device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint64_t *empty, const Schedule &sc)
 {
     using S_ = Slots<TY>;
     const int32_t nx = p.nx, ny = p.ny;
@@ -236,9 +231,9 @@ __device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint
             if (!mbar_wait(&empty[b], ((g / p.stages) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
         }
         if (it.dirty && !released) {
-            // the stresses written by the wall phase must be complete (grid barrier)
-            // and visible to the bulk copies (async proxy) before a dirty stage
-            if (!wait_generation(p.bar_gen, g0, p.status)) break;
+            // the stresses written by the wall kernel must be complete and visible
+            // to the bulk copies (async proxy) before a dirty stage
+            wait_wall_kernel();
             asm volatile("fence.proxy.async.global;" ::: "memory");
             released = true;
         }
@@ -401,14 +396,15 @@ __device__ void consume(const StencilParams<T> &p, const T *data, uint64_t *read
 // fused step: phase 1, grid barrier, mask
 // ------------------------------------------------------------------------- //
 
-// Phase 1: the threads of the whole grid share the band records and the solid
-// nodes in rounds; in each round a thread takes up to two band records and four
-// solid nodes, issues every independent load (records, solid indices) first,
-// then the velocity gathers, then the stores, so that each thread keeps many
-// memory requests in flight.
+// Wall phase: the participating threads of the whole grid share the band
+// records (two per thread and round, all loads issued before the stores) and
+// then the solid runs (a warp zeroes one run at a time with coalesced stores,
+// run descriptors fetched 32 at a time).
 template <typename T, typename VEL>
 __device__ void wall_phase(const StencilParams<T> &p, T *acc, int wt, int nthreads)
 {
+    // let the stencil kernel (next in the stream) launch right away
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     T *const oxx = const_cast<T *>(p.tau[0]), *const oxy = const_cast<T *>(p.tau[1]);
     T *const oyy = const_cast<T *>(p.tau[2]), *const ozz = const_cast<T *>(p.tau[3]);
     T *const oxz = const_cast<T *>(p.tau[4]), *const oyz = const_cast<T *>(p.tau[5]);
@@ -417,72 +413,62 @@ __device__ void wall_phase(const StencilParams<T> &p, T *acc, int wt, int nthrea
     const VEL *const vw = reinterpret_cast<const VEL *>(p.w);
     const int64_t plane = (int64_t)p.nx * p.ny;
     const int64_t nrec = p.nb_w + p.nb_uv;
-    const int64_t nsol = p.ns_w + p.ns_uv;
     const int64_t stride = (int64_t)gridDim.x * nthreads;
     const int64_t tid = (int64_t)blockIdx.x * nthreads + wt;
-    const int64_t rounds = max((nrec + 2 * stride - 1) / (2 * stride), (nsol + 4 * stride - 1) / (4 * stride));
 
-    for (int64_t r = 0; r < rounds; ++r) {
-        int32_t sidx[4];
-        bool sw[4], sok[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t t = tid + (4 * r + q) * stride;
-            sok[q] = t < nsol;
-            sw[q] = t < p.ns_w;
-            sidx[q] = sok[q] ? __ldg(sw[q] ? p.solid_w + t : p.solid_uv + (t - p.ns_w)) : 0;
+    auto store = [&](const BandOut<T> &o, bool is_w) {
+        if (is_w) {
+            oxz[o.idx] = o.t0;
+            oyz[o.idx] = o.t1;
+        } else {
+            oxx[o.idx] = o.t0;
+            oxy[o.idx] = o.t1;
+            oyy[o.idx] = o.t2;
+            ozz[o.idx] = o.t3;
         }
-        const int64_t t0 = tid + 2 * r * stride, t1 = t0 + stride;
+        stats_add(acc, is_w ? 0 : 1, o.tw, o.ur);
+    };
+    for (int64_t t0 = tid; t0 < nrec; t0 += 2 * stride) {
+        const int64_t t1 = t0 + stride;
         BandOut<T> a, b;
-        if (t0 < nrec)
-            a = band_model<T, VEL>(p.rec, t0, t0 < p.nb_w, vu, vv, vw, p.nx, p.ny, plane, p.logz0, p.log_phi_c,
-                                   p.kappa2);
+        a = band_model<T, VEL>(p.rec, t0, t0 < p.nb_w, vu, vv, vw, p.nx, p.ny, plane, p.logz0, p.log_phi_c,
+                               p.kappa2);
         if (t1 < nrec)
             b = band_model<T, VEL>(p.rec, t1, t1 < p.nb_w, vu, vv, vw, p.nx, p.ny, plane, p.logz0, p.log_phi_c,
                                    p.kappa2);
-        // solid nodes: the stress is set to zero (Sec. 3.3)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!sok[q]) continue;
-            if (sw[q]) {
-                oxz[sidx[q]] = T(0);
-                oyz[sidx[q]] = T(0);
-            } else {
-                oxx[sidx[q]] = T(0);
-                oxy[sidx[q]] = T(0);
-                oyy[sidx[q]] = T(0);
-                ozz[sidx[q]] = T(0);
-            }
-        }
-        auto store = [&](const BandOut<T> &o, bool is_w) {
-            if (is_w) {
-                oxz[o.idx] = o.t0;
-                oyz[o.idx] = o.t1;
-            } else {
-                oxx[o.idx] = o.t0;
-                oxy[o.idx] = o.t1;
-                oyy[o.idx] = o.t2;
-                ozz[o.idx] = o.t3;
-            }
-            stats_add(acc, is_w ? 0 : 1, o.tw, o.ur);
-        };
-        if (t0 < nrec) store(a, t0 < p.nb_w);
+        store(a, t0 < p.nb_w);
         if (t1 < nrec) store(b, t1 < p.nb_w);
     }
-}
 
-// Split-phase grid barrier of a cooperative launch (all blocks co-resident):
-// one thread per block arrives after its block's wall warps have finished;
-// the last block to arrive resets the count and advances the generation.
-// Waiters compare the generation with the value read at kernel start.
-__device__ void grid_arrive(unsigned *count, unsigned *gen)
-{
-    __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == gridDim.x - 1) {
-        *(volatile unsigned *)count = 0u;
-        __threadfence();
-        atomicAdd(gen, 1u);
+    // solid nodes: the stress is set to zero (Sec. 3.3)
+    const int lane = wt & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (nthreads / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (nthreads / 32) + (wt >> 5);
+    const int64_t nruns = p.nr_w + p.nr_uv;
+    // warp gw takes runs gw, gw + nwarps, ...: lane q fetches the descriptor of
+    // the q-th of them, then the warp zeroes them one after the other
+    for (int64_t base = gw; base < nruns; base += nwarps * 32) {
+        const int64_t t = base + (int64_t)lane * nwarps;
+        int2 run = make_int2(0, 0);
+        if (t < nruns) run = __ldg(t < p.nr_w ? p.runs_w + t : p.runs_uv + (t - p.nr_w));
+        const int nq = (int)min((int64_t)32, (nruns - base + nwarps - 1) / nwarps);
+        for (int q = 0; q < nq; ++q) {
+            const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
+            const int32_t len = __shfl_sync(0xffffffffu, run.y, q);
+            const bool is_w = base + (int64_t)q * nwarps < p.nr_w;
+            for (int32_t x = lane; x < len; x += 32) {
+                const int64_t idx = (int64_t)start + x;
+                if (is_w) {
+                    oxz[idx] = T(0);
+                    oyz[idx] = T(0);
+                } else {
+                    oxx[idx] = T(0);
+                    oxy[idx] = T(0);
+                    oyy[idx] = T(0);
+                    ozz[idx] = T(0);
+                }
+            }
+        }
     }
 }
 
@@ -504,12 +490,23 @@ __device__ void mask_phase(const StencilParams<T> &p, int64_t tid, int64_t strid
     }
 }
 
+template <typename T, typename VEL>
+__global__ void __launch_bounds__(256) k_wall(StencilParams<T> p)
+{
+    __shared__ T red[32][kStatVals];
+    T acc[kStatVals];
+    stats_identity(acc);
+    wall_phase<T, VEL>(p, acc, threadIdx.x, blockDim.x);
+    if (p.stats) {
+        stats_block_reduce(acc, red);
+        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, p.nb_w, p.nb_uv);
+    }
+}
+
 template <typename T, typename VEL, int TY, bool FUSED>
 __global__ void __launch_bounds__(512) k_stencil(StencilParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ T red[32][kStatVals];
-    __shared__ unsigned gen0;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + 8;
     T *data = reinterpret_cast<T *>(smem_raw + 256);
@@ -521,38 +518,22 @@ __global__ void __launch_bounds__(512) k_stencil(StencilParams<T> p)
             mbar_init(&empty[b], p.ncons);
         }
         fence_mbar_init();
-        if (FUSED) gen0 = *(volatile unsigned *)p.bar_gen;
     }
     __syncthreads();
-    const unsigned g0 = gen0;
     const Schedule sc = block_schedule(p.nstrips, p.nz, FUSED ? p.da : 0, FUSED ? p.db : 0);
 
-    T acc[kStatVals];
-    stats_identity(acc);
     if (warp == 0) {
-        if (lane == 0) produce<T, TY, FUSED>(p, data, full, empty, sc, g0);
+        // producer: clean stages right away (their rows are not written by the
+        // wall kernel), dirty stages once the wall kernel has completed
+        if (lane == 0) produce<T, TY, FUSED>(p, data, full, empty, sc);
         __syncwarp();
-    } else if (warp <= p.ncons) {
+    } else {
         consume<T, TY>(p, data, full, empty, sc, warp - 1, lane);
-    } else if (FUSED) {
-        // wall warps: the wall model and solid zeros over the whole grid, then the
-        // block's arrival at the grid barrier, then (after every block's wall
-        // phase, since the band stencils read the velocity) the body mask
-        const int nwt = p.nwall * 32;
-        const int wt = threadIdx.x - 32 * (1 + p.ncons);
-        wall_phase<T, VEL>(p, acc, wt, nwt);
-        asm volatile("bar.sync 1, %0;" ::"r"(nwt) : "memory");
-        if (wt == 0) grid_arrive(p.bar_count, p.bar_gen);
-        if (p.do_mask) {
-            if (wait_generation(p.bar_gen, g0, p.status))
-                mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nwt + wt, (int64_t)gridDim.x * nwt);
+        if (FUSED && p.do_mask) {
+            wait_wall_kernel();
+            const int nct = p.ncons * 32;
+            mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nct + (threadIdx.x - 32), (int64_t)gridDim.x * nct);
         }
-    }
-
-    if (FUSED && p.stats) {
-        __syncthreads();
-        stats_block_reduce(acc, red);
-        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, p.nb_w, p.nb_uv);
     }
 }
 
@@ -562,7 +543,7 @@ size_t stage_elems_for(int ty, int nx) { return (size_t)(6 * ty + 6) * nx; }
 constexpr int kMaxDynSmem = 200 * 1024;
 
 template <typename T, typename VEL, int TY, bool FUSED>
-int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cudaStream_t stream)
+int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl)
 {
     auto kern = k_stencil<T, VEL, TY, FUSED>;
     static bool attr_done = false;      // once per instantiation and process
@@ -572,7 +553,7 @@ int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cuda
         attr_done = true;
     }
     const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
-    const int threads = 32 * (1 + p.ncons + (FUSED ? p.nwall : 0));
+    const int threads = 32 * (1 + p.ncons);
     // occupancy of this shape, cached in the handle
     const int key = (FUSED ? 1 : 0) | (TY << 1) | (c.stages << 4) | (c.consumer_warps << 8) | (c.wall_warps << 12);
     int per_sm = 0;
@@ -589,20 +570,19 @@ int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cuda
     if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
     int64_t grid = (int64_t)per_sm * h->sm_count;
     if (grid > p.units) grid = p.units;
-    if (FUSED && grid > h->partial_blocks) grid = h->partial_blocks;
-    if (FUSED) {
-        // cooperative launch (all blocks co-resident, so the grid barrier can be met)
+    if (FUSED && pdl) {
+        // programmatic dependent of the wall kernel launched just before
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cuda_status(h, cudaLaunchKernelEx(&cfg, kern, p), "k_stencil cooperative launch");
+        return cuda_status(h, cudaLaunchKernelEx(&cfg, kern, p), "k_stencil launch");
     }
     kern<<<(unsigned)grid, threads, smem, stream>>>(p);
     return cuda_status(h, cudaGetLastError(), "k_stencil launch");
@@ -610,16 +590,35 @@ int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cuda
 
 bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
 
+template <typename T>
+void fill_params(wmibm_handle *h, StencilParams<T> &p, const void *const tau[6], void *const f[3], void *u, void *v,
+                 void *w, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask,
+                 double dt, const StencilConfig &c);
+
 template <typename T, typename VEL, bool FUSED>
 int launch(wmibm_handle *h, const void *const tau[6], void *const f[3], void *u, void *v, void *w,
            wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask, double dt,
-           const StencilConfig &c, cudaStream_t stream)
+           const StencilConfig &c, cudaStream_t stream, bool pdl)
 {
     StencilParams<T> p;
+    fill_params<T>(h, p, tau, f, u, v, w, stats, logz0, gradp, do_mask, dt, c);
+    switch (c.rows) {
+    case 1: return launch_ty<T, VEL, 1, FUSED>(h, p, c, stream, pdl);
+    case 2: return launch_ty<T, VEL, 2, FUSED>(h, p, c, stream, pdl);
+    case 4: return launch_ty<T, VEL, 4, FUSED>(h, p, c, stream, pdl);
+    default: return set_error(h, WMIBM_EINVAL, "stencil rows must be 1, 2 or 4");
+    }
+}
+
+template <typename T>
+void fill_params(wmibm_handle *h, StencilParams<T> &p, const void *const tau[6], void *const f[3], void *u, void *v,
+                 void *w, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask,
+                 double dt, const StencilConfig &c)
+{
     for (int a = 0; a < 6; ++a) p.tau[a] = (const T *)tau[a];
     for (int a = 0; a < 3; ++a) p.f[a] = (T *)f[a];
     p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
-    p.nstrips = h->ny / c.rows;
+    p.nstrips = c.rows > 0 ? h->ny / c.rows : 0;
     p.units = (int64_t)p.nstrips * h->nz;
     p.cx = (T)(1.0 / (2.0 * h->dx));
     p.cy = (T)(1.0 / (2.0 * h->dy));
@@ -629,16 +628,16 @@ int launch(wmibm_handle *h, const void *const tau[6], void *const f[3], void *u,
     p.nwall = c.wall_warps;
     p.da = h->dirty_lo;
     p.db = h->dirty_hi;
-    p.stage_elems = (uint32_t)stage_elems_for<T>(c.rows, h->nx);
+    p.stage_elems = (uint32_t)stage_elems_for<T>(c.rows > 0 ? c.rows : 1, h->nx);
     p.status = h->dev_status;
     p.u = u; p.v = v; p.w = w;
     p.rec = h->rec;
     p.nb_w = h->lists.n[WMIBM_LIST_BAND_W];
     p.nb_uv = h->lists.n[WMIBM_LIST_BAND_UV];
-    p.solid_w = h->lists.p[WMIBM_LIST_SOLID_W];
-    p.solid_uv = h->lists.p[WMIBM_LIST_SOLID_UV];
-    p.ns_w = h->lists.n[WMIBM_LIST_SOLID_W];
-    p.ns_uv = h->lists.n[WMIBM_LIST_SOLID_UV];
+    p.runs_w = h->runs[0];
+    p.runs_uv = h->runs[1];
+    p.nr_w = h->nruns[0];
+    p.nr_uv = h->nruns[1];
     p.do_mask = do_mask;
     p.body_w = h->lists.p[WMIBM_LIST_BODY_W];
     p.body_uv = h->lists.p[WMIBM_LIST_BODY_UV];
@@ -648,20 +647,40 @@ int launch(wmibm_handle *h, const void *const tau[6], void *const f[3], void *u,
     p.gpy = gradp ? (const T *)gradp[1] : nullptr;
     p.gpz = gradp ? (const T *)gradp[2] : nullptr;
     p.mask_c = (T)(1.5 * dt);
-    p.bar_count = h->grid_bar;
-    p.bar_gen = h->grid_bar + 1;
     p.partials = (T *)h->partials;
     p.ticket = h->ticket;
     p.stats = stats;
     p.logz0 = (const T *)logz0;
     p.log_phi_c = (T)log(h->phi_c);
     p.kappa2 = (T)(h->kappa * h->kappa);
-    switch (c.rows) {
-    case 1: return launch_ty<T, VEL, 1, FUSED>(h, p, c, stream);
-    case 2: return launch_ty<T, VEL, 2, FUSED>(h, p, c, stream);
-    case 4: return launch_ty<T, VEL, 4, FUSED>(h, p, c, stream);
-    default: return set_error(h, WMIBM_EINVAL, "stencil rows must be 1, 2 or 4");
+}
+
+// The wall kernel: persistent grid sized by occupancy, wall_warps warps per block.
+template <typename T, typename VEL>
+int launch_wall(wmibm_handle *h, void *const tau[6], const void *u, const void *v, const void *w,
+                wmibm_band_stats *stats, const void *logz0, cudaStream_t stream)
+{
+    StencilParams<T> p;
+    StencilConfig c = {};
+    void *const none[3] = {nullptr, nullptr, nullptr};
+    fill_params<T>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
+                   const_cast<void *>(w), stats, logz0, nullptr, 0, 0.0, c);
+    const int wthreads = 32 * (h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 8);
+    int wper = 0;
+    const int wkey = 0x100000 | wthreads | (sizeof(T) == 8 ? 0x200000 : 0);
+    for (int q = 0; q < 8; ++q)
+        if (h->occ_key[q] == wkey) wper = h->occ_val[q];
+    if (wper == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_wall<T, VEL>, wthreads, 0);
+        if (e != cudaSuccess) return cuda_status(h, e, "wall occupancy");
+        if (wper < 1) wper = 1;
+        const int slot = h->occ_next++ & 7;
+        h->occ_key[slot] = wkey;
+        h->occ_val[slot] = wper;
     }
+    const int64_t wgrid = std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
+    k_wall<T, VEL><<<(unsigned)wgrid, wthreads, 0, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_wall launch");
 }
 
 }  // namespace
@@ -681,27 +700,26 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     for (int a = 0; a < 3; ++a)
         if (!aligned16(f[a])) return false;
     StencilConfig c;
+    auto stage_bytes_of = [&](int rows) { return (size_t)(6 * rows + 6) * h->nx * es; };
     c.rows = h->tuning.rows;
-    if (c.rows == 0) c.rows = (h->ny % 2 == 0 && h->ny >= 4) ? 2 : 1;
+    c.stages = h->tuning.stages;
+    if (c.rows == 0) {
+        // default: 2-row strips with at least 3 stages within ~110 KB of shared
+        // memory (two or three blocks per SM); 1-row strips when rows are wide
+        c.rows = (h->ny % 2 == 0 && h->ny >= 4) ? 2 : 1;
+        if (c.rows == 2 && c.stages == 0 && 3 * stage_bytes_of(2) > 110 * 1024) c.rows = 1;
+    }
     if (!(c.rows == 1 || c.rows == 2 || c.rows == 4)) return false;
     if (h->ny % c.rows != 0 || h->ny < c.rows + 2) return false;
-    size_t stage_bytes = (size_t)(6 * c.rows + 6) * h->nx * es;
-    if (h->tuning.rows == 0) {
-        // wide rows: fall back to shorter strips while 2 stages do not fit
-        while (c.rows > 1 && 2 * stage_bytes > 150 * 1024) {
-            c.rows /= 2;
-            stage_bytes = (size_t)(6 * c.rows + 6) * h->nx * es;
-        }
-    }
-    c.stages = h->tuning.stages;
+    const size_t stage_bytes = stage_bytes_of(c.rows);
     if (c.stages == 0) {
         c.stages = 4;
-        while (c.stages > 2 && (size_t)c.stages * stage_bytes > 100 * 1024) --c.stages;
+        while (c.stages > 2 && (size_t)c.stages * stage_bytes > 110 * 1024) --c.stages;
     }
     if (c.stages < 2 || c.stages > 8) return false;
     if ((size_t)c.stages * stage_bytes + 256 > (size_t)kMaxDynSmem) return false;
     c.consumer_warps = h->tuning.consumer_warps > 0 ? h->tuning.consumer_warps : 4;
-    c.wall_warps = h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 2;
+    c.wall_warps = h->tuning.wall_warps;
     if (1 + c.consumer_warps + c.wall_warps > 16) return false;
     c.blocks_per_sm = h->tuning.blocks_per_sm;
     *out = c;
@@ -713,21 +731,36 @@ int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], c
 {
     if (h->dtype == WMIBM_F64)
         return launch<double, double, false>(h, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                                             0.0, c, stream);
+                                             0.0, c, stream, false);
     return launch<float, float, false>(h, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0, c,
-                                       stream);
+                                       stream, false);
 }
 
-// One cooperative launch: wall model + solid zeros, grid barrier, (mask,) force.
-int stencil_fused(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
-                  wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask, double dt,
-                  const StencilConfig &c, cudaStream_t stream)
+// The pipelined stencil followed, in the same launch, by the body mask (Eq. 27).
+// With pdl the launch is a programmatic dependent of the preceding kernel.
+int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
+                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream)
 {
     if (h->dtype == WMIBM_F64)
-        return launch<double, double, true>(h, tau, f, u, v, w, stats, logz0, gradp, do_mask, dt, c, stream);
+        return launch<double, double, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
     if (h->vel_dtype == WMIBM_BF16)
-        return launch<float, __nv_bfloat16, true>(h, tau, f, u, v, w, stats, logz0, gradp, do_mask, dt, c, stream);
-    return launch<float, float, true>(h, tau, f, u, v, w, stats, logz0, gradp, do_mask, dt, c, stream);
+        return launch<float, __nv_bfloat16, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
+    return launch<float, float, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
+}
+
+// The wall model at every band node and the solid zeros (persistent kernel).
+int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream)
+{
+    if (stats && h->nrec == 0) {
+        cudaError_t e = cudaMemsetAsync(stats, 0, 2 * sizeof(wmibm_band_stats), stream);
+        if (e != cudaSuccess) return cuda_status(h, e, "clear stats");
+        stats = nullptr;
+    }
+    if (h->dtype == WMIBM_F64) return launch_wall<double, double>(h, tau, u, v, w, stats, logz0, stream);
+    if (h->vel_dtype == WMIBM_BF16)
+        return launch_wall<float, __nv_bfloat16>(h, tau, u, v, w, stats, logz0, stream);
+    return launch_wall<float, float>(h, tau, u, v, w, stats, logz0, stream);
 }
 
 }  // namespace wmibm

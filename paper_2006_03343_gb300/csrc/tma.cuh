@@ -16,6 +16,10 @@ constexpr int kDevStatusBarrierTimeout = 3; // a block waited too long at the gr
 // soon as another wait of the same handle has given up (status != 0).
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
+// Suspend-time hint of a try_wait: the waiting thread sleeps until the phase
+// completes or this many nanoseconds pass, instead of spinning.
+constexpr uint32_t kSuspendHintNs = 20000;
+
 __device__ __forceinline__ uint64_t global_timer_ns()
 {
     uint64_t t;
@@ -54,10 +58,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0;
 }
@@ -71,7 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0) {
+        if ((it & 7u) == 0) {
             if (*(volatile int *)status != 0) return false;
             if (global_timer_ns() - t0 > kWaitLimitNs) {
                 atomicExch(status, code);

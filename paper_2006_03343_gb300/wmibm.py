@@ -26,7 +26,7 @@ DTYPE_CODES = {"f32": F32, "f64": F64, "bf16": BF16}
 EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmibm_step", "wmibm_list_size",
             "wmibm_export_list", "wmibm_traffic_bytes", "wmibm_destroy", "wmibm_status_string",
             "wmibm_last_error", "wmibm_wall_stress_force", "wmibm_set_tuning", "wmibm_get_tuning",
-            "wmibm_device_status")
+            "wmibm_device_status", "wmibm_force_mask")
 
 
 class WmibmError(RuntimeError):
@@ -90,6 +90,8 @@ def load(path: Optional[str] = None):
     L.wmibm_step.restype = ctypes.c_int
     L.wmibm_wall_stress_force.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _VP, _VP]
     L.wmibm_wall_stress_force.restype = ctypes.c_int
+    L.wmibm_force_mask.argtypes = [_VP, _PVP, _VP, _VP, _VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
+    L.wmibm_force_mask.restype = ctypes.c_int
     L.wmibm_set_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
     L.wmibm_set_tuning.restype = ctypes.c_int
     L.wmibm_get_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
@@ -226,8 +228,33 @@ class Handle:
                                                     _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
                                                     None if stats is None else _dptr(stats), _stream_ptr(stream)))
 
+    def force_mask(self, tau, f, u, v, w, gradp=None, dt=0.0, stream=None):
+        for t in list(tau) + list(f):
+            self._field(t)
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        if gradp is not None:
+            for t in gradp:
+                self._field(t)
+        self._check(self._L.wmibm_force_mask(self._h, _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]), _dptr(u),
+                                             _dptr(v), _dptr(w), None if gradp is None else _ptrs(gradp),
+                                             float(dt), _stream_ptr(stream)))
+
+    def prepare_step(self, u, v, w, tau, f, stats=None, gradp=None, dt=0.0):
+        """Validates the fields once and returns a PreparedStep whose calls only
+        launch (for loops and graph capture)."""
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in list(tau) + list(f):
+            self._field(t)
+        if gradp is not None:
+            for t in gradp:
+                self._field(t)
+        return PreparedStep(self, u, v, w, tau, f, stats, gradp, dt)
+
     def set_tuning(self, **fields):
-        t = self.get_tuning()
+        """Replaces the handle's tuning: the given fields, every other field 0 (automatic)."""
+        t = Tuning()
         for k, v in fields.items():
             setattr(t, k, int(v))
         self._check(self._L.wmibm_set_tuning(self._h, ctypes.byref(t)))
@@ -277,3 +304,34 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+class PreparedStep:
+    """Pre-marshalled arguments of the per-step calls of one handle and one set of
+    fields (the tensors must stay alive and in place)."""
+
+    def __init__(self, handle, u, v, w, tau, f, stats, gradp, dt):
+        self._keep = (u, v, w, tuple(tau), tuple(f), stats, gradp)
+        self.h = handle
+        self._L = handle._L
+        self._u, self._v, self._w = _dptr(u), _dptr(v), _dptr(w)
+        self._tau = _ptrs(tau)
+        self._f = (_dptr(f[0]), _dptr(f[1]), _dptr(f[2]))
+        self._stats = None if stats is None else _dptr(stats)
+        self._gradp = None if gradp is None else _ptrs(gradp)
+        self._dt = float(dt)
+
+    def wall_stress(self, stream=None):
+        self.h._check(self._L.wmibm_wall_stress(self.h._h, self._u, self._v, self._w, self._tau, self._stats,
+                                                _stream_ptr(stream)))
+
+    def force_mask(self, stream=None):
+        self.h._check(self._L.wmibm_force_mask(self.h._h, self._tau, *self._f, self._u, self._v, self._w,
+                                               self._gradp, self._dt, _stream_ptr(stream)))
+
+    def force(self, stream=None):
+        self.h._check(self._L.wmibm_force(self.h._h, self._tau, *self._f, _stream_ptr(stream)))
+
+    def step(self, stream=None):
+        self.h._check(self._L.wmibm_step(self.h._h, self._u, self._v, self._w, self._tau, *self._f, self._gradp,
+                                         self._dt, self._stats, _stream_ptr(stream)))

@@ -314,3 +314,52 @@ def test_full_size_fused_parity(wm, oracle_mod, name, dtype):
     tau_o, f_o, st_o = oracle_step(oracle_mod, case)
     _check_against_oracle(tau_g, f_g, st_g, tau_o, f_o, st_o, dtype, name)
     assert h.device_status() == wm.OK
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("with_gradp", [False, True])
+def test_force_mask_equals_force_then_mask(wm, oracle_mod, dtype, with_gradp):
+    """The one-launch force + mask against the oracle's force and Eq. 27 mask."""
+    case = inputs.hill(shape=(96, 48, 40))
+    h = wm.Handle.from_case(case, dtype=dtype)
+    rng = np.random.default_rng(12)
+    tau = {k: rounded(rng.standard_normal(case.shape), dtype) for k in inputs.TAU_NAMES}
+    gp = [rounded(rng.standard_normal(case.shape), dtype) for _ in range(3)] if with_gradp else None
+    u, v, w = (rounded(x, dtype) for x in (case.u, case.v, case.w))
+    td = [to_dev(tau[k], dtype) for k in inputs.TAU_NAMES]
+    f = [to_dev(np.zeros(case.shape), dtype) for _ in range(3)]
+    ud, vd, wd = (to_dev(x, dtype) for x in (u, v, w))
+    dt = 0.02
+    h.force_mask(td, f, ud, vd, wd, None if gp is None else [to_dev(g, dtype) for g in gp], dt)
+    ref_f = oracle_mod.force(case.grid, tau)
+    uo, vo, wo = u.copy(), v.copy(), w.copy()
+    oracle_mod.mask(case.grid, case.phi_uv, case.phi_w, uo, vo, wo, gp, dt)
+    for c in range(3):
+        assert normwise(to_host(f[c]), ref_f[c])[0] <= (1e-14 if dtype == "f64" else 2e-7)
+    for got, ref in ((ud, uo), (vd, vo), (wd, wo)):
+        assert normwise(to_host(got), ref)[0] <= (0.0 if dtype == "f64" else 2e-7)
+    assert h.device_status() == wm.OK
+
+
+def test_step_full_pass_against_oracle(wm, oracle_mod):
+    """wmibm_step (wall kernel, then force + mask in one launch) against the
+    oracle's wall stress, force and mask in that order."""
+    case = inputs.cubes(shape=(128, 64, 48))
+    h = wm.Handle.from_case(case, dtype="f32")
+    u, v, w = (to_dev(x, "f32") for x in (case.u, case.v, case.w))
+    tau = [to_dev(case.tau[k], "f32") for k in inputs.TAU_NAMES]
+    f = [to_dev(np.zeros(case.shape), "f32") for _ in range(3)]
+    stats = h.new_stats()
+    h.step(u, v, w, tau, f, None, 0.0, stats)
+    torch.cuda.synchronize()
+    tau_o, f_o, st_o = oracle_step(oracle_mod, case)
+    uo, vo, wo = case.u.copy(), case.v.copy(), case.w.copy()
+    oracle_mod.mask(case.grid, case.phi_uv, case.phi_w, uo, vo, wo)
+    for c in range(3):
+        assert normwise(to_host(f[c]), f_o[c])[0] <= TOL["f32"]
+    for k, t in zip(inputs.TAU_NAMES, tau):
+        assert normwise(to_host(t), tau_o[k])[0] <= TOL["f32"]
+    for got, ref in ((u, uo), (v, vo), (w, wo)):
+        assert normwise(to_host(got), ref)[0] <= TOL["f32"]
+    assert_stats_close(h.parse_stats(stats), st_o, "f32")
+    assert h.device_status() == wm.OK
