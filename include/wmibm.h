@@ -192,6 +192,28 @@ int wmibm_get_tuning(const wmibm_handle *h, wmibm_tuning *t);
  */
 int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream);
 
+/*
+ * wmibm_wall_stress_noalloc - wmibm_wall_stress without any device allocation.
+ * The paper has no counterpart: this is a deployment variant for callers that
+ * cannot allocate device memory when they make the call -- code running while a
+ * CUDA graph is being captured (cudaMalloc is not allowed there), plug-ins
+ * whose host framework owns the device memory pool, real-time loops that must
+ * not touch the allocator.  The handle itself must already exist (wmibm_init
+ * allocates).
+ *   Same arguments and results as wmibm_wall_stress (stats up to summation
+ *   order).  The kernel's reduction scratch (per-block partial statistics and a
+ *   ticket) is a static device array of 131,328 bytes that every GPU loading
+ *   the library holds until the process exits; at most 1,048,576 band nodes
+ *   (w-band + uv-band) are accepted, larger bands return EINVAL.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current: make that first call
+ *   before any stream capture.  All calls share the array and it keeps the last
+ *   call's contents (the ticket is cleared on the stream before each launch):
+ *   calls that overlap on the GPU, on any handle, race.
+ */
+int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                              wmibm_band_stats *stats, void *stream);
+
 /* Number of entries of list `which` (WMIBM_LIST_*), or -1 for a bad argument. */
 int64_t wmibm_list_size(const wmibm_handle *h, int32_t which);
 

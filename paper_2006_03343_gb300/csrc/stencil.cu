@@ -748,6 +748,35 @@ int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *c
     return launch<float, float, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
 }
 
+// The wall kernel with caller-provided reduction scratch and grid size (used by
+// the entry point whose scratch lives in a static device array).
+int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                            wmibm_band_stats *stats, void *partials, unsigned *ticket, unsigned blocks,
+                            cudaStream_t stream)
+{
+    StencilConfig c = {};
+    void *const none[3] = {nullptr, nullptr, nullptr};
+    if (h->dtype == WMIBM_F64) {
+        StencilParams<double> p;
+        fill_params<double>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
+                            const_cast<void *>(w), stats, nullptr, nullptr, 0, 0.0, c);
+        p.partials = (double *)partials;
+        p.ticket = ticket;
+        k_wall<double, double><<<blocks, 256, 0, stream>>>(p);
+    } else {
+        StencilParams<float> p;
+        fill_params<float>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
+                           const_cast<void *>(w), stats, nullptr, nullptr, 0, 0.0, c);
+        p.partials = (float *)partials;
+        p.ticket = ticket;
+        if (h->vel_dtype == WMIBM_BF16)
+            k_wall<float, __nv_bfloat16><<<blocks, 256, 0, stream>>>(p);
+        else
+            k_wall<float, float><<<blocks, 256, 0, stream>>>(p);
+    }
+    return cuda_status(h, cudaGetLastError(), "k_wall launch");
+}
+
 // The wall model at every band node and the solid zeros (persistent kernel).
 int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                wmibm_band_stats *stats, const void *logz0, cudaStream_t stream)

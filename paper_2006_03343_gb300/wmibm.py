@@ -26,7 +26,7 @@ DTYPE_CODES = {"f32": F32, "f64": F64, "bf16": BF16}
 EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmibm_step", "wmibm_list_size",
             "wmibm_export_list", "wmibm_traffic_bytes", "wmibm_destroy", "wmibm_status_string",
             "wmibm_last_error", "wmibm_wall_stress_force", "wmibm_set_tuning", "wmibm_get_tuning",
-            "wmibm_device_status", "wmibm_force_mask")
+            "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc")
 
 
 class WmibmError(RuntimeError):
@@ -90,6 +90,8 @@ def load(path: Optional[str] = None):
     L.wmibm_step.restype = ctypes.c_int
     L.wmibm_wall_stress_force.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _VP, _VP]
     L.wmibm_wall_stress_force.restype = ctypes.c_int
+    L.wmibm_wall_stress_noalloc.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP]
+    L.wmibm_wall_stress_noalloc.restype = ctypes.c_int
     L.wmibm_force_mask.argtypes = [_VP, _PVP, _VP, _VP, _VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_force_mask.restype = ctypes.c_int
     L.wmibm_set_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
@@ -203,6 +205,16 @@ class Handle:
             self._field(t)
         self._check(self._L.wmibm_wall_stress(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau),
                                               None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def wall_stress_noalloc(self, u, v, w, tau: Sequence, stats=None, stream=None):
+        """wall_stress with the kernel's reduction scratch in a static device array
+        (no device allocation; for callers that cannot allocate at call time)."""
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in tau:
+            self._field(t)
+        self._check(self._L.wmibm_wall_stress_noalloc(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau),
+                                                      None if stats is None else _dptr(stats), _stream_ptr(stream)))
 
     def force(self, tau: Sequence, f: Sequence, stream=None):
         for t in list(tau) + list(f):
