@@ -214,6 +214,56 @@ int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream);
 int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                               wmibm_band_stats *stats, void *stream);
 
+/*
+ * Batched ensembles: many terrains of uneven grid sizes stepped together.
+ * The step of a batch is the per-step stage (wmibm_step without grad p) of
+ * every member, done by two persistent launches over all members: the wall
+ * kernel over the concatenated band records and solid runs, then the
+ * pipelined force + body-mask kernel over the concatenated (member, strip,
+ * level) units.  Member descriptors (field pointers) live in device memory, so
+ * a step can be captured in a CUDA graph and replayed.
+ */
+typedef struct wmibm_batch wmibm_batch;
+
+typedef struct wmibm_member_fields {
+    void *u, *v, *w;        /* DEVICE velocity (vel_dtype), in/out (body mask) */
+    void *tau[6];           /* DEVICE stresses (dtype), in/out, 16-byte aligned */
+    void *f[3];             /* DEVICE forcing (dtype), out, 16-byte aligned */
+} wmibm_member_fields;
+
+/*
+ * wmibm_batch_create - a batch over `count` (1..256) handles of one device with
+ * the same dtype and vel_dtype.  The batch keeps the handle pointers (it does
+ * not own them: destroy the batch first).  Every member must take the
+ * pipelined stencil (nx a multiple of 4 for F32 or 2 for F64, ny >= 3) with a
+ * common number of rows per strip.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA.
+ */
+int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *members, int32_t count, void *stream);
+
+/* Sets the fields of every member (HOST array of count entries); synchronises
+ * `stream` after uploading the descriptors.  Must precede wmibm_batch_step and
+ * follow any wmibm_batch_set_tuning. */
+int wmibm_batch_set_fields(wmibm_batch *b, const wmibm_member_fields *fields, void *stream);
+
+/* Tile shape of the batch launches (rows, stages, consumer_warps, blocks_per_sm used). */
+int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t);
+
+/*
+ * wmibm_batch_step - one step of every member (wall stress, force, mask).
+ *   stats : NULL, or DEVICE wmibm_band_stats[count][2] (w-band, uv-band per member)
+ * No host synchronisation; capturable in a CUDA graph.
+ */
+int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream);
+
+/* Algorithmic bytes of one batch step: which = 0 wall kernel, 1 force + mask kernel. */
+int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which);
+
+/* Total nodes of all members. */
+int64_t wmibm_batch_points(const wmibm_batch *b);
+
+const char *wmibm_batch_last_error(const wmibm_batch *b);
+void wmibm_batch_destroy(wmibm_batch *b);
+
 /* Number of entries of list `which` (WMIBM_LIST_*), or -1 for a bad argument. */
 int64_t wmibm_list_size(const wmibm_handle *h, int32_t which);
 

@@ -1,0 +1,266 @@
+// Batched ensembles: many terrains ("members") of uneven grid sizes stepped
+// by the same two persistent launches (the wall kernel over the concatenated
+// band records, then the pipelined force + mask kernel over the concatenated
+// (member, strip, level) units).  The member descriptors live in device
+// memory, so a step is graph-capturable and replays with the same fields.
+#include <stdarg.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "members.cuh"
+
+using namespace wmibm;
+
+struct wmibm_batch {
+    int device;
+    int count;
+    int32_t dtype, vel_dtype;
+    std::vector<wmibm_handle *> members;
+    void *dev_members;          // Member<T>[count]
+    double *bstats;             // [count][2][4]
+    unsigned *ticket;
+    int *status;
+    int max_nx;
+    int fields_set;
+    wmibm_tuning tuning;
+    StencilConfig cfg;
+    int64_t clean_total, dirty_total, rec_total, body_total;
+    int64_t traffic[2];
+    char err[512];
+};
+
+namespace {
+
+int berr(wmibm_batch *b, int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int bcuda(wmibm_batch *b, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return WMIBM_OK;
+    return berr(b, e == cudaErrorMemoryAllocation ? WMIBM_ENOMEM : WMIBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Tile shape shared by all members: rows dividing every ny, stages that fit the
+// widest rows.
+bool batch_config(wmibm_batch *b, StencilConfig *out)
+{
+    const size_t es = elem_size(b->dtype);
+    const int V = 16 / (int)es;
+    int rows = b->tuning.rows;
+    auto rows_ok = [&](int r) {
+        for (auto *h : b->members)
+            if (h->ny % r != 0 || h->ny < r + 2 || h->nx % V != 0 || h->nz < 3) return false;
+        return true;
+    };
+    auto stage_bytes = [&](int r) { return (size_t)(6 * r + 6) * b->max_nx * es; };
+    if (rows == 0) {
+        rows = rows_ok(2) && 3 * stage_bytes(2) <= 110 * 1024 ? 2 : 1;
+    }
+    if (!(rows == 1 || rows == 2 || rows == 4) || !rows_ok(rows)) return false;
+    int stages = b->tuning.stages;
+    if (stages == 0) {
+        stages = 4;
+        while (stages > 2 && (size_t)stages * stage_bytes(rows) > 110 * 1024) --stages;
+    }
+    if (stages < 2 || stages > 8 || (size_t)stages * stage_bytes(rows) + 256 > 200 * 1024) return false;
+    out->rows = rows;
+    out->stages = stages;
+    out->consumer_warps = b->tuning.consumer_warps > 0 ? b->tuning.consumer_warps : 4;
+    out->wall_warps = 8;
+    out->blocks_per_sm = b->tuning.blocks_per_sm;
+    return 1 + out->consumer_warps <= 16;
+}
+
+template <typename T>
+int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream_t stream)
+{
+    std::vector<Member<T>> host(b->count);
+    int64_t c_off = 0, d_off = 0, r_off = 0, body_off = 0;
+    for (int m = 0; m < b->count; ++m) {
+        wmibm_handle *h = b->members[m];
+        const wmibm_member_fields &fl = fields[m];
+        fill_member<T>(h, host[m], (const void *const *)fl.tau, fl.f, fl.u, fl.v, fl.w, nullptr, nullptr, 0.0,
+                       b->cfg.rows);
+        Member<T> &mm = host[m];
+        mm.c_off = c_off;
+        mm.d_off = d_off;
+        mm.r_off = r_off;
+        mm.body_off = body_off;
+        c_off += (int64_t)mm.nstrips * (mm.da + (mm.nz - mm.db));
+        d_off += (int64_t)mm.nstrips * (mm.db - mm.da);
+        r_off += mm.nb_w + mm.nb_uv;
+        body_off += mm.nbody_w + mm.nbody_uv;
+    }
+    b->clean_total = c_off;
+    b->dirty_total = d_off;
+    b->rec_total = r_off;
+    b->body_total = body_off;
+    cudaError_t e = cudaMemcpyAsync(b->dev_members, host.data(), sizeof(Member<T>) * b->count,
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return bcuda(b, e, "upload member descriptors");
+}
+
+template <typename T, typename VEL>
+int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
+{
+    KParams<T> p = {};
+    p.clean_total = b->clean_total;
+    p.dirty_total = b->dirty_total;
+    p.rec_total = b->rec_total;
+    p.run_total = 0;
+    p.body_total = b->body_total;
+    p.status = b->status;
+    p.do_mask = 1;
+    p.partials = nullptr;
+    p.ticket = b->ticket;
+    p.stats = stats;
+    p.bstats = b->bstats;
+    const int wall_blocks = 3 * b->members[0]->sm_count;
+    int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
+                                  wall_blocks, stream);
+    if (st) return berr(b, st, "%s", b->members[0]->err);
+    return WMIBM_OK;
+}
+
+}  // namespace
+
+extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *members, int32_t count, void *stream)
+{
+    if (!out) return WMIBM_EINVAL;
+    *out = nullptr;
+    if (!members || count < 1 || count > kMaxBatchMembers) return WMIBM_EINVAL;
+    for (int m = 0; m < count; ++m)
+        if (!members[m]) return WMIBM_EINVAL;
+    const wmibm_handle *h0 = members[0];
+    for (int m = 1; m < count; ++m)
+        if (members[m]->device != h0->device || members[m]->dtype != h0->dtype ||
+            members[m]->vel_dtype != h0->vel_dtype)
+            return WMIBM_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h0->device) return WMIBM_ESTATE;
+
+    wmibm_batch *b = new (std::nothrow) wmibm_batch();
+    if (!b) return WMIBM_ENOMEM;
+    b->device = h0->device;
+    b->count = count;
+    b->dtype = h0->dtype;
+    b->vel_dtype = h0->vel_dtype;
+    b->members.assign(members, members + count);
+    b->max_nx = 0;
+    for (auto *h : b->members) b->max_nx = std::max(b->max_nx, (int)h->nx);
+    const size_t msize = b->dtype == WMIBM_F64 ? sizeof(Member<double>) : sizeof(Member<float>);
+    cudaError_t e = cudaMalloc(&b->dev_members, msize * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->bstats, sizeof(double) * 8 * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->bstats, 0, sizeof(double) * 8 * count, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, sizeof(unsigned), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess || !batch_config(b, &b->cfg)) {
+        cudaFree(b->dev_members);
+        cudaFree(b->bstats);
+        cudaFree(b->ticket);
+        cudaFree(b->status);
+        delete b;
+        return e != cudaSuccess ? WMIBM_ECUDA : WMIBM_EINVAL;
+    }
+    int64_t wall_bytes = 0, force_bytes = 0;
+    for (auto *h : b->members) {
+        wall_bytes += h->traffic[0];
+        force_bytes += h->traffic[1] + h->traffic[2];
+    }
+    b->traffic[0] = wall_bytes;
+    b->traffic[1] = force_bytes;
+    *out = b;
+    return WMIBM_OK;
+}
+
+extern "C" int wmibm_batch_set_fields(wmibm_batch *b, const wmibm_member_fields *fields, void *stream)
+{
+    if (!b) return WMIBM_EINVAL;
+    if (!fields) return berr(b, WMIBM_EINVAL, "NULL fields");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return berr(b, WMIBM_ESTATE, "current device is not the batch's device");
+    for (int m = 0; m < b->count; ++m) {
+        const wmibm_member_fields &fl = fields[m];
+        if (!fl.u || !fl.v || !fl.w) return berr(b, WMIBM_EINVAL, "member %d: NULL velocity", m);
+        for (int a = 0; a < 6; ++a)
+            if (!fl.tau[a] || !aligned16(fl.tau[a]))
+                return berr(b, WMIBM_EINVAL, "member %d: stress %d NULL or not 16-byte aligned", m, a);
+        for (int a = 0; a < 3; ++a)
+            if (!fl.f[a] || !aligned16(fl.f[a]))
+                return berr(b, WMIBM_EINVAL, "member %d: force %d NULL or not 16-byte aligned", m, a);
+    }
+    int st = b->dtype == WMIBM_F64 ? upload_members<double>(b, fields, (cudaStream_t)stream)
+                                   : upload_members<float>(b, fields, (cudaStream_t)stream);
+    if (st == WMIBM_OK) b->fields_set = 1;
+    return st;
+}
+
+extern "C" int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t)
+{
+    if (!b || !t) return WMIBM_EINVAL;
+    wmibm_tuning old = b->tuning;
+    b->tuning = *t;
+    StencilConfig c;
+    if (!batch_config(b, &c)) {
+        b->tuning = old;
+        return berr(b, WMIBM_EINVAL, "tuning does not fit every member");
+    }
+    b->cfg = c;
+    b->fields_set = 0;       // unit offsets depend on the rows per strip: set the fields again
+    return WMIBM_OK;
+}
+
+extern "C" int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
+{
+    if (!b) return WMIBM_EINVAL;
+    if (!b->fields_set) return berr(b, WMIBM_ESTATE, "wmibm_batch_set_fields must be called first");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return berr(b, WMIBM_ESTATE, "current device is not the batch's device");
+    if (b->dtype == WMIBM_F64) return step_impl<double, double>(b, stats, (cudaStream_t)stream);
+    if (b->vel_dtype == WMIBM_BF16) return step_impl<float, __nv_bfloat16>(b, stats, (cudaStream_t)stream);
+    return step_impl<float, float>(b, stats, (cudaStream_t)stream);
+}
+
+extern "C" int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which)
+{
+    if (!b || which < 0 || which > 1) return -1;
+    return b->traffic[which];
+}
+
+extern "C" int64_t wmibm_batch_points(const wmibm_batch *b)
+{
+    if (!b) return -1;
+    int64_t n = 0;
+    for (auto *h : b->members) n += h->n;
+    return n;
+}
+
+extern "C" const char *wmibm_batch_last_error(const wmibm_batch *b) { return b ? b->err : ""; }
+
+extern "C" void wmibm_batch_destroy(wmibm_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    cudaFree(b->dev_members);
+    cudaFree(b->bstats);
+    cudaFree(b->ticket);
+    cudaFree(b->status);
+    delete b;
+}

@@ -1,0 +1,61 @@
+// Launch descriptors shared by the stencil / wall kernels (stencil.cu) and the
+// batch API (batch.cu): one Member per terrain of a launch.
+#pragma once
+
+#include "internal.cuh"
+
+namespace wmibm {
+
+// One terrain of a launch: its fields and its precomputed lists.
+template <typename T>
+struct Member {
+    const T *tau[6];              // txx txy tyy tzz txz tyz (the wall kernel writes band / solid entries)
+    T *f[3];
+    void *u, *v, *w;
+    int32_t nx, ny, nz, nstrips;
+    T cx, cy, cz;                 // 1/(2 dx), 1/(2 dy), 1/dz
+    int32_t da, db;               // dirty levels [da, db)
+    int64_t c_off, d_off;         // first index in the launch's clean / dirty unit spaces
+    const void *rec;              // band records (w-band first)
+    int64_t nb_w, nb_uv, r_off;   // band counts; first index in the record space
+    const int2 *runs_w, *runs_uv; // solid runs along x
+    int64_t nr_w, nr_uv, run_off;
+    const int32_t *body_w, *body_uv;
+    int64_t nbody_w, nbody_uv, body_off;
+    const T *gpx, *gpy, *gpz;     // body mask: 3 dt/2 grad p, or NULL
+    T mask_c;
+    const T *logz0;               // optional per-cell log z0
+    T log_phi_c, kappa2;
+};
+
+template <typename T>
+struct KParams {
+    Member<T> one;                // the member of a single-terrain launch (nmembers == 1)
+    const Member<T> *list;        // device array of members (nmembers > 1)
+    int nmembers;
+    int64_t clean_total, dirty_total, rec_total, run_total, body_total;
+    int stages, ncons;
+    uint32_t stage_elems;
+    int *status;
+    int do_mask;
+    // statistics: single terrain -> per-block partials reduced by the last block;
+    // batch -> per-member accumulators (scratch) converted by the last block
+    T *partials;
+    unsigned *ticket;
+    wmibm_band_stats *stats;
+    double *bstats;               // batch: [nmembers][2][4] (sum, sum^2, -min bits, max bits)
+};
+
+template <typename T>
+void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], void *const f[3], void *u, void *v,
+                 void *w, const void *logz0, const void *const gradp[3], double dt, int rows);
+
+template <typename T, typename VEL>
+int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
+                 const StencilConfig &c, int max_nx, int wall_blocks, cudaStream_t stream);
+
+bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
+
+constexpr int kMaxBatchMembers = 256;
+
+}  // namespace wmibm

@@ -1,53 +1,55 @@
 // Bulk-copy (TMA) pipelined stencil for f = -div(tau) (Eq. 2, Eq. 18, Eqs. 15-16
-// of Liu & Stevens, arXiv:2006.03343), and the fused per-step kernel built on it.
+// of Liu & Stevens, arXiv:2006.03343), the persistent wall-model kernel
+// (Sec. 3.3), and the body mask (Eq. 27), for one terrain or for a batch of
+// terrains ("members") of uneven grid sizes in the same launches.
 //
-// Stencil: the grid is cut into strips of TY full x-rows (j0 .. j0+TY-1) and the
-// (strip, level) units are split evenly over a persistent grid (one contiguous
-// range of units per block; a range spans at most a few strip segments).  Per
-// block, lane 0 of warp 0 is the producer: it issues 1D bulk copies of the rows
-// a stage needs into a ring of S shared-memory stages and arms the stage's
-// "full" mbarrier with the byte count.  A stage at level k holds
+// Stencil: every member's grid is cut into strips of TY full x-rows
+// (j0 .. j0+TY-1); the (member, strip, level) units are split evenly over a
+// persistent grid.  Per block, lane 0 of warp 0 is the producer: it issues 1D
+// bulk copies of the rows a stage needs into a ring of S shared-memory stages
+// and arms the stage's "full" mbarrier with the byte count.  A stage at level k
+// holds
 //   txx, tzz at k (TY rows), txy, tyy at k (TY + 2 rows: y-halo),
 //   txz at k+1 (TY rows), tyz at k+1 (TY + 2 rows)
 // and the stage before it supplies txz, tyz at k and tzz at k-1, so every
-// stress row is fetched from HBM once per strip.  A segment starts with a
-// prologue stage that holds only tzz at k-1 and txz, tyz at k.  Consumer warps
-// form f for the TY rows, with x-neighbours from warp shuffles and periodic
-// wrap inside the staged full rows, and release the stage through the "empty"
-// mbarrier.
+// stress row is fetched from HBM once per strip.  A segment (consecutive
+// levels of one strip of one member) starts with a prologue stage that holds
+// only tzz at k-1 and txz, tyz at k.  Consumer warps form f for the TY rows,
+// with x-neighbours from warp shuffles and periodic wrap inside the staged full
+// rows, and release the stage through the "empty" mbarrier.
 //
-// Fused step (two kernels chained by programmatic dependent launch): the wall
-// kernel evaluates the wall model of Sec. 3.3 at every band node and zeroes the
-// solid runs (stresses written to the caller's arrays, band statistics reduced
-// on the way) and lets the stencil kernel launch at once.  The stencil kernel
-// first streams its "clean" stages, whose rows hold no band or solid node;
-// before its first "dirty" stage, and before the body mask of Eq. 27 (which may
-// change the velocity only after every band stencil has read it), it waits on
-// the grid dependency, i.e. for the wall kernel to have completed.
+// Units are split into "clean" ones, whose stage rows hold no band or solid
+// node, and "dirty" ones; each block streams its share of clean units first.
+// The step runs the wall kernel, then the stencil kernel as its programmatic
+// dependent: before its first dirty stage, and before the body mask (which may
+// change the velocity only after every band stencil has read it), the stencil
+// kernel waits on the grid dependency.
+//
+// Wall kernel: the threads of the grid share the band records (two per thread
+// and round, every independent load issued before the stores) and the solid
+// runs (a warp zeroes one run at a time with coalesced stores).
 //
 // Every mbarrier wait is bounded: on time-out the kernel records a status code
 // in device memory and leaves its loops.
 #include <algorithm>
 
 #include "band.cuh"
+#include "members.cuh"
 #include "tma.cuh"
 
 using namespace wmibm;
 
 namespace {
 
-
 template <typename T>
 struct VecOf;
 template <>
 struct VecOf<float> {
     static constexpr int V = 4;
-    using vec = float4;
 };
 template <>
 struct VecOf<double> {
     static constexpr int V = 2;
-    using vec = double2;
 };
 
 template <typename T>
@@ -74,115 +76,178 @@ __device__ __forceinline__ void stg(double *p, const Pack<double> &x)
     *reinterpret_cast<double2 *>(p) = make_double2(x.v[0], x.v[1]);
 }
 
+// Views of a member's fields for the producer and the consumers (filled with
+// constant-offset loads, so that nothing is copied to local memory).
 template <typename T>
-struct StencilParams {
-    const T *tau[6];          // txx txy tyy tzz txz tyz
+struct ProdView {
+    const T *tau[6];
+    int32_t nx, ny, nz;
+};
+
+template <typename T>
+struct ConsView {
     T *f[3];
-    int32_t nx, ny, nz, nstrips;
-    int64_t units;            // nstrips * nz
+    int32_t nx, ny, nz;
     T cx, cy, cz;
-    int stages, ncons, nwall;
-    int32_t da, db;           // dirty levels (units whose stages depend on the wall phase)
-    uint32_t stage_elems;
-    int *status;
-    // fused step: phase 1 (wall model, solid zeros) and the body mask
-    void *u, *v, *w;
-    const void *rec;
-    int64_t nb_w, nb_uv;
-    const int2 *runs_w, *runs_uv;   // solid runs along x (first node, length)
-    int64_t nr_w, nr_uv;
-    int do_mask;
-    const int32_t *body_w, *body_uv;
-    int64_t nbody_w, nbody_uv;
-    const T *gpx, *gpy, *gpz;
-    T mask_c;                 // 3 dt / 2
-    T *partials;
-    unsigned *ticket;
-    wmibm_band_stats *stats;
-    const T *logz0;
-    T log_phi_c, kappa2;
 };
 
-// The units (strip s, level k) are split into "clean" units, whose stage rows
-// (levels k-1 .. k+1) hold no band or solid node, and "dirty" units (levels
-// [da, db)).  Clean units do not depend on the wall-model phase of the fused
-// kernel, so every block streams its share of clean units first and only then
-// its share of dirty units.
-struct Schedule {
-    int64_t c0, c1, d0, d1;   // this block's ranges in the clean and dirty unit spaces
-    int32_t nz, da, db;       // dirty levels [da, db)
-};
-
-__device__ __forceinline__ Schedule block_schedule(int32_t nstrips, int32_t nz, int32_t da, int32_t db)
+template <typename T>
+__device__ __forceinline__ void load_prod(const KParams<T> &p, int m, ProdView<T> &v)
 {
-    Schedule sc;
-    const int64_t C = (int64_t)nstrips * (da + (nz - db));
-    const int64_t D = (int64_t)nstrips * (db - da);
-    sc.c0 = C * blockIdx.x / gridDim.x;
-    sc.c1 = C * (blockIdx.x + 1) / gridDim.x;
-    sc.d0 = D * blockIdx.x / gridDim.x;
-    sc.d1 = D * (blockIdx.x + 1) / gridDim.x;
-    sc.nz = nz;
-    sc.da = da;
-    sc.db = db;
-    return sc;
+    if (p.nmembers == 1) {
+        v.tau[0] = p.one.tau[0]; v.tau[1] = p.one.tau[1]; v.tau[2] = p.one.tau[2];
+        v.tau[3] = p.one.tau[3]; v.tau[4] = p.one.tau[4]; v.tau[5] = p.one.tau[5];
+        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz;
+    } else {
+        const Member<T> *mm = p.list + m;
+        v.tau[0] = mm->tau[0]; v.tau[1] = mm->tau[1]; v.tau[2] = mm->tau[2];
+        v.tau[3] = mm->tau[3]; v.tau[4] = mm->tau[4]; v.tau[5] = mm->tau[5];
+        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz;
+    }
 }
 
-// Sequence of stages a block processes: its clean units then its dirty units,
-// cut into segments of consecutive levels of one strip; each segment starts
-// with a prologue stage followed by one main stage per level.
+template <typename T>
+__device__ __forceinline__ void load_cons(const KParams<T> &p, int m, ConsView<T> &v)
+{
+    if (p.nmembers == 1) {
+        v.f[0] = p.one.f[0]; v.f[1] = p.one.f[1]; v.f[2] = p.one.f[2];
+        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz;
+        v.cx = p.one.cx; v.cy = p.one.cy; v.cz = p.one.cz;
+    } else {
+        const Member<T> *mm = p.list + m;
+        v.f[0] = mm->f[0]; v.f[1] = mm->f[1]; v.f[2] = mm->f[2];
+        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz;
+        v.cx = mm->cx; v.cy = mm->cy; v.cz = mm->cz;
+    }
+}
+
+// Unit-space shape of member m.
+struct MemberUnits {
+    int32_t nstrips, nz, da, db;
+    int64_t c_off, d_off;
+};
+
+template <typename T>
+__device__ __forceinline__ MemberUnits load_units(const KParams<T> &p, int m)
+{
+    MemberUnits u;
+    if (p.nmembers == 1) {
+        u.nstrips = p.one.nstrips; u.nz = p.one.nz; u.da = p.one.da; u.db = p.one.db;
+        u.c_off = 0; u.d_off = 0;
+    } else {
+        const Member<T> *mm = p.list + m;
+        u.nstrips = mm->nstrips; u.nz = mm->nz; u.da = mm->da; u.db = mm->db;
+        u.c_off = mm->c_off; u.d_off = mm->d_off;
+    }
+    return u;
+}
+
+// Member holding index i of the clean (phase 0) or dirty (phase 1) unit space.
+template <typename T>
+__device__ int find_member(const KParams<T> &p, int phase, int64_t i)
+{
+    if (p.nmembers == 1) return 0;
+    int lo = 0, hi = p.nmembers - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int64_t off = phase == 0 ? p.list[mid].c_off : p.list[mid].d_off;
+        if (off <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Member holding index g of the concatenated band-record space (batch).
+template <typename T>
+__device__ int find_member_rec(const KParams<T> &p, int64_t g)
+{
+    int lo = 0, hi = p.nmembers - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.list[mid].r_off <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sequence of stages a block processes: its share of the clean units, then its
+// share of the dirty units, cut into segments of consecutive levels of one
+// strip of one member; each segment starts with a prologue stage followed by
+// one main stage per level.
+template <typename T>
 struct StageIter {
-    Schedule sc;
-    int64_t idx;
-    int phase;                // 0 clean, 1 dirty, 2 done
+    const KParams<T> *pp;
+    int64_t c1, d0, d1;           // block ranges (clean [c0, c1), dirty [d0, d1))
+    int64_t idx;                  // global index in the current phase's space
+    int phase;                    // 0 clean, 1 dirty, 2 done
+    int m;                        // member
+    MemberUnits mu;
     int32_t s, k;
-    bool prologue, done, dirty;
-    __device__ void unit(int ph, int64_t i, int32_t &s_, int32_t &k_) const
+    bool prologue, done, dirty, new_member;
+
+    __device__ void locate()
     {
-        if (ph == 0) {
-            const int32_t lc = sc.da + (sc.nz - sc.db);
-            s_ = (int32_t)(i / lc);
-            const int32_t r = (int32_t)(i - (int64_t)s_ * lc);
-            k_ = r < sc.da ? r : sc.db + (r - sc.da);
+        const int m2 = find_member(*pp, phase, idx);
+        if (m2 != m) {
+            m = m2;
+            mu = load_units(*pp, m);
+            new_member = true;
+        }
+        const int64_t li = idx - (phase == 0 ? mu.c_off : mu.d_off);
+        if (phase == 0) {
+            const int32_t lc = mu.da + (mu.nz - mu.db);
+            s = (int32_t)(li / lc);
+            const int32_t r = (int32_t)(li - (int64_t)s * lc);
+            k = r < mu.da ? r : mu.db + (r - mu.da);
         } else {
-            const int32_t ld = sc.db - sc.da;
-            s_ = (int32_t)(i / ld);
-            k_ = sc.da + (int32_t)(i - (int64_t)s_ * ld);
+            const int32_t ld = mu.db - mu.da;
+            s = (int32_t)(li / ld);
+            k = mu.da + (int32_t)(li - (int64_t)s * ld);
         }
     }
     __device__ void settle()
     {
-        while (phase < 2 && idx >= (phase == 0 ? sc.c1 : sc.d1)) {
+        while (phase < 2 && idx >= (phase == 0 ? c1 : d1)) {
             ++phase;
-            idx = sc.d0;
+            idx = d0;
         }
         done = phase >= 2;
         if (!done) {
-            unit(phase, idx, s, k);
+            locate();
             prologue = true;
             dirty = phase == 1;
         }
     }
-    __device__ void init(const Schedule &s_)
+    __device__ void init(const KParams<T> &p)
     {
-        sc = s_;
+        pp = &p;
+        const int64_t C = p.clean_total, D = p.dirty_total;
+        const int64_t c0 = C * blockIdx.x / gridDim.x;
+        c1 = C * (blockIdx.x + 1) / gridDim.x;
+        d0 = D * blockIdx.x / gridDim.x;
+        d1 = D * (blockIdx.x + 1) / gridDim.x;
+        m = -1;
         phase = 0;
-        idx = sc.c0;
+        idx = c0;
+        new_member = false;
         settle();
     }
     __device__ void next()
     {
+        new_member = false;
         if (prologue) {
             prologue = false;
             return;
         }
         ++idx;
-        if (idx < (phase == 0 ? sc.c1 : sc.d1)) {
-            int32_t s2, k2;
-            unit(phase, idx, s2, k2);
-            prologue = !(s2 == s && k2 == k + 1);
-            s = s2;
-            k = k2;
+        if (idx < (phase == 0 ? c1 : d1)) {
+            const int32_t s0 = s, k0 = k, m0 = m;
+            locate();
+            prologue = !(m == m0 && s == s0 && k == k0 + 1);
             return;
         }
         settle();
@@ -197,14 +262,8 @@ struct Slots {
     static constexpr int ZZ = 3 * TY + 4;
     static constexpr int XZ = 4 * TY + 4;
     static constexpr int YZ = 5 * TY + 4;
-    static constexpr int ROWS = 6 * TY + 6;
 };
 
-__device__ __forceinline__ int32_t wrapj(int32_t j, int32_t ny) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); }
-
-// ------------------------------------------------------------------------- //
-// producer: lane 0 of warp 0
-// ------------------------------------------------------------------------- //
 // Waits until the preceding kernel of the stream (the wall kernel) has
 // completed and its writes are visible (programmatic dependent launch; without
 // a programmatic dependency the stream order already guarantees it).
@@ -213,19 +272,19 @@ __device__ __forceinline__ void wait_wall_kernel()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <typename T, int TY, bool FUSED>
-__device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint64_t *empty, const Schedule &sc)
+// ------------------------------------------------------------------------- //
+// producer: lane 0 of warp 0
+// ------------------------------------------------------------------------- //
+template <typename T, int TY, bool STEP>
+__device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *empty)
 {
     using S_ = Slots<TY>;
-    const int32_t nx = p.nx, ny = p.ny;
-    const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
-    const int64_t plane = (int64_t)nx * ny;
-    const T *const txx = p.tau[0], *const txy = p.tau[1], *const tyy = p.tau[2];
-    const T *const tzz = p.tau[3], *const txz = p.tau[4], *const tyz = p.tau[5];
+    ProdView<T> v;
     uint32_t g = 0;
-    bool released = !FUSED;
-    StageIter it;
-    for (it.init(sc); !it.done; it.next(), ++g) {
+    bool released = !STEP;
+    StageIter<T> it;
+    for (it.init(p); !it.done; it.next(), ++g) {
+        if (it.new_member) load_prod(p, it.m, v);
         const int b = (int)(g % (uint32_t)p.stages);
         if (g >= (uint32_t)p.stages) {
             if (!mbar_wait(&empty[b], ((g / p.stages) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
@@ -237,6 +296,9 @@ __device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint
             asm volatile("fence.proxy.async.global;" ::: "memory");
             released = true;
         }
+        const int32_t nx = v.nx, ny = v.ny;
+        const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
+        const int64_t plane = (int64_t)nx * ny;
         T *st = data + (size_t)b * p.stage_elems;
         const int32_t j0 = it.s * TY;
         const int32_t k = it.k;
@@ -256,6 +318,8 @@ __device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint
                 bulk_g2s(dst, base + (int64_t)jstart * nx, (uint32_t)cnt * row_bytes, &full[b]);
             }
         };
+        const T *const txx = v.tau[0], *const txy = v.tau[1], *const tyy = v.tau[2];
+        const T *const tzz = v.tau[3], *const txz = v.tau[4], *const tyz = v.tau[5];
         if (it.prologue) {
             const uint32_t rows = (k > 0 ? TY : 0) + TY + (TY + 2);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
@@ -263,7 +327,7 @@ __device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint
             issue(txz, k, j0, TY, S_::XZ);
             issue(tyz, k, j0 - 1, TY + 2, S_::YZ);
         } else {
-            const bool up = k + 1 < p.nz;
+            const bool up = k + 1 < v.nz;
             const uint32_t rows = TY + 2 * (TY + 2) + TY + (up ? TY + (TY + 2) : 0);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
             issue(txx, k, j0, TY, S_::XX);
@@ -288,18 +352,19 @@ __device__ void produce(const StencilParams<T> &p, T *data, uint64_t *full, uint
 // consumers: f for the TY rows of a main stage
 // ------------------------------------------------------------------------- //
 template <typename T, int TY>
-__device__ void consume_level(const StencilParams<T> &p, const T *cur, const T *prv, int32_t k, int32_t j0, int cw,
-                              int lane)
+__device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, const T *prv, int32_t k, int32_t j0,
+                              int cw, int lane)
 {
     using S_ = Slots<TY>;
     constexpr int V = VecOf<T>::V;
-    const int32_t nx = p.nx;
+    const int32_t nx = cv.nx;
     const int nq = nx / V;
     const int groups = TY * nq;
-    const int64_t plane = (int64_t)nx * p.ny;
-    const bool top = (k == p.nz - 1);
+    const int64_t plane = (int64_t)nx * cv.ny;
+    const bool top = (k == cv.nz - 1);
     const bool bottom = (k == 0);
-    for (int base = cw * 32; base < groups; base += p.ncons * 32) {
+    const T cx = cv.cx, cy = cv.cy, cz = cv.cz;
+    for (int base = cw * 32; base < groups; base += ncons * 32) {
         const int gi = base + lane;
         const bool valid = gi < groups;
         const int gc = valid ? gi : groups - 1;
@@ -357,33 +422,34 @@ __device__ void consume_level(const StencilParams<T> &p, const T *cur, const T *
                 const T xxm_ = e == 0 ? xxl : xx.v[e - 1], xxp_ = e == V - 1 ? xxr : xx.v[e + 1];
                 const T xym_ = e == 0 ? xyl : xy.v[e - 1], xyp_ = e == V - 1 ? xyr : xy.v[e + 1];
                 const T xzm_ = e == 0 ? xzl : xz0.v[e - 1], xzp_ = e == V - 1 ? xzr : xz0.v[e + 1];
-                Fx.v[e] = -((xxp_ - xxm_) * p.cx + (xyp.v[e] - xym.v[e]) * p.cy + (xz1.v[e] - xz0.v[e]) * p.cz);
-                Fy.v[e] = -((xyp_ - xym_) * p.cx + (yyp.v[e] - yym.v[e]) * p.cy + (yz1.v[e] - yz0.v[e]) * p.cz);
-                const T fz = -((xzp_ - xzm_) * p.cx + (yz0p.v[e] - yz0m.v[e]) * p.cy + (zz.v[e] - zzm.v[e]) * p.cz);
+                Fx.v[e] = -((xxp_ - xxm_) * cx + (xyp.v[e] - xym.v[e]) * cy + (xz1.v[e] - xz0.v[e]) * cz);
+                Fy.v[e] = -((xyp_ - xym_) * cx + (yyp.v[e] - yym.v[e]) * cy + (yz1.v[e] - yz0.v[e]) * cz);
+                const T fz = -((xzp_ - xzm_) * cx + (yz0p.v[e] - yz0m.v[e]) * cy + (zz.v[e] - zzm.v[e]) * cz);
                 Fz.v[e] = bottom ? T(0) : fz;
             }
         }
         if (valid) {
-            stg(p.f[0] + o, Fx);
-            stg(p.f[1] + o, Fy);
-            stg(p.f[2] + o, Fz);
+            stg(cv.f[0] + o, Fx);
+            stg(cv.f[1] + o, Fy);
+            stg(cv.f[2] + o, Fz);
         }
     }
 }
 
 template <typename T, int TY>
-__device__ void consume(const StencilParams<T> &p, const T *data, uint64_t *ready, uint64_t *empty,
-                        const Schedule &sc, int cw, int lane)
+__device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane)
 {
+    ConsView<T> cv;
     uint32_t g = 0;
     int prevb = -1;
-    StageIter it;
-    for (it.init(sc); !it.done; it.next(), ++g) {
+    StageIter<T> it;
+    for (it.init(p); !it.done; it.next(), ++g) {
+        if (it.new_member) load_cons(p, it.m, cv);
         const int b = (int)(g % (uint32_t)p.stages);
-        if (!mbar_wait(&ready[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)) break;
+        if (!mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)) break;
         if (!it.prologue)
-            consume_level<T, TY>(p, data + (size_t)b * p.stage_elems, data + (size_t)prevb * p.stage_elems, it.k,
-                                 it.s * TY, cw, lane);
+            consume_level<T, TY>(cv, p.ncons, data + (size_t)b * p.stage_elems, data + (size_t)prevb * p.stage_elems,
+                                 it.k, it.s * TY, cw, lane);
         if (prevb >= 0) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[prevb]);
@@ -393,69 +459,87 @@ __device__ void consume(const StencilParams<T> &p, const T *data, uint64_t *read
 }
 
 // ------------------------------------------------------------------------- //
-// fused step: phase 1, grid barrier, mask
+// body mask (Eq. 27) over the launch's concatenated body lists
 // ------------------------------------------------------------------------- //
-
-// Wall phase: the participating threads of the whole grid share the band
-// records (two per thread and round, all loads issued before the stores) and
-// then the solid runs (a warp zeroes one run at a time with coalesced stores,
-// run descriptors fetched 32 at a time).
 template <typename T, typename VEL>
-__device__ void wall_phase(const StencilParams<T> &p, T *acc, int wt, int nthreads)
+__device__ void mask_member(const Member<T> &mm, int64_t t0, int64_t n, int64_t stride)
 {
-    // let the stencil kernel (next in the stream) launch right away
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    T *const oxx = const_cast<T *>(p.tau[0]), *const oxy = const_cast<T *>(p.tau[1]);
-    T *const oyy = const_cast<T *>(p.tau[2]), *const ozz = const_cast<T *>(p.tau[3]);
-    T *const oxz = const_cast<T *>(p.tau[4]), *const oyz = const_cast<T *>(p.tau[5]);
-    const VEL *const vu = reinterpret_cast<const VEL *>(p.u);
-    const VEL *const vv = reinterpret_cast<const VEL *>(p.v);
-    const VEL *const vw = reinterpret_cast<const VEL *>(p.w);
-    const int64_t plane = (int64_t)p.nx * p.ny;
-    const int64_t nrec = p.nb_w + p.nb_uv;
-    const int64_t stride = (int64_t)gridDim.x * nthreads;
-    const int64_t tid = (int64_t)blockIdx.x * nthreads + wt;
-
-    auto store = [&](const BandOut<T> &o, bool is_w) {
-        if (is_w) {
-            oxz[o.idx] = o.t0;
-            oyz[o.idx] = o.t1;
+    VEL *const vu = reinterpret_cast<VEL *>(mm.u);
+    VEL *const vv = reinterpret_cast<VEL *>(mm.v);
+    VEL *const vw = reinterpret_cast<VEL *>(mm.w);
+    const int64_t n_uv = mm.nbody_uv;
+    for (int64_t t = t0; t < n; t += stride) {
+        if (t < n_uv) {
+            const int32_t idx = __ldg(mm.body_uv + t);
+            vu[idx] = to_vel<VEL, T>(mm.gpx ? mm.mask_c * __ldg(mm.gpx + idx) : T(0));
+            vv[idx] = to_vel<VEL, T>(mm.gpy ? mm.mask_c * __ldg(mm.gpy + idx) : T(0));
         } else {
-            oxx[o.idx] = o.t0;
-            oxy[o.idx] = o.t1;
-            oyy[o.idx] = o.t2;
-            ozz[o.idx] = o.t3;
+            const int32_t idx = __ldg(mm.body_w + (t - n_uv));
+            vw[idx] = to_vel<VEL, T>(mm.gpz ? mm.mask_c * __ldg(mm.gpz + idx) : T(0));
         }
-        stats_add(acc, is_w ? 0 : 1, o.tw, o.ur);
-    };
-    for (int64_t t0 = tid; t0 < nrec; t0 += 2 * stride) {
-        const int64_t t1 = t0 + stride;
-        BandOut<T> a, b;
-        a = band_model<T, VEL>(p.rec, t0, t0 < p.nb_w, vu, vv, vw, p.nx, p.ny, plane, p.logz0, p.log_phi_c,
-                               p.kappa2);
-        if (t1 < nrec)
-            b = band_model<T, VEL>(p.rec, t1, t1 < p.nb_w, vu, vv, vw, p.nx, p.ny, plane, p.logz0, p.log_phi_c,
-                                   p.kappa2);
-        store(a, t0 < p.nb_w);
-        if (t1 < nrec) store(b, t1 < p.nb_w);
     }
+}
 
-    // solid nodes: the stress is set to zero (Sec. 3.3)
-    const int lane = wt & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (nthreads / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (nthreads / 32) + (wt >> 5);
-    const int64_t nruns = p.nr_w + p.nr_uv;
-    // warp gw takes runs gw, gw + nwarps, ...: lane q fetches the descriptor of
-    // the q-th of them, then the warp zeroes them one after the other
+template <typename T, typename VEL>
+__device__ void mask_phase(const KParams<T> &p, int64_t tid, int64_t stride)
+{
+    if (p.nmembers == 1) {
+        mask_member<T, VEL>(p.one, tid, p.one.nbody_uv + p.one.nbody_w, stride);
+        return;
+    }
+    for (int m = 0; m < p.nmembers; ++m) {
+        const Member<T> &mm = p.list[m];
+        // this thread's first index inside member m's slice of the concatenated space
+        int64_t first = tid - mm.body_off;
+        if (first < 0) first += ((-first + stride - 1) / stride) * stride;
+        mask_member<T, VEL>(mm, first, mm.nbody_uv + mm.nbody_w, stride);
+    }
+}
+
+// ------------------------------------------------------------------------- //
+// wall kernels
+// ------------------------------------------------------------------------- //
+template <typename T, typename VEL>
+__device__ __forceinline__ BandOut<T> band_of(const Member<T> &mm, int64_t t)
+{
+    return band_model<T, VEL>(mm.rec, t, t < mm.nb_w, reinterpret_cast<const VEL *>(mm.u),
+                              reinterpret_cast<const VEL *>(mm.v), reinterpret_cast<const VEL *>(mm.w), mm.nx, mm.ny,
+                              (int64_t)mm.nx * mm.ny, mm.logz0, mm.log_phi_c, mm.kappa2);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_band(const Member<T> &mm, const BandOut<T> &o, bool is_w)
+{
+    if (is_w) {
+        const_cast<T *>(mm.tau[4])[o.idx] = o.t0;
+        const_cast<T *>(mm.tau[5])[o.idx] = o.t1;
+    } else {
+        const_cast<T *>(mm.tau[0])[o.idx] = o.t0;
+        const_cast<T *>(mm.tau[1])[o.idx] = o.t1;
+        const_cast<T *>(mm.tau[2])[o.idx] = o.t2;
+        const_cast<T *>(mm.tau[3])[o.idx] = o.t3;
+    }
+}
+
+// Solid runs of one member, warp-cooperative: warp gw of nwarps takes runs
+// gw, gw + nwarps, ...: lane q fetches the descriptor of the q-th of them, then
+// the warp zeroes them one after the other with coalesced stores.
+template <typename T>
+__device__ void zero_runs(const Member<T> &mm, int64_t gw, int64_t nwarps, int lane)
+{
+    T *const oxx = const_cast<T *>(mm.tau[0]), *const oxy = const_cast<T *>(mm.tau[1]);
+    T *const oyy = const_cast<T *>(mm.tau[2]), *const ozz = const_cast<T *>(mm.tau[3]);
+    T *const oxz = const_cast<T *>(mm.tau[4]), *const oyz = const_cast<T *>(mm.tau[5]);
+    const int64_t nruns = mm.nr_w + mm.nr_uv;
     for (int64_t base = gw; base < nruns; base += nwarps * 32) {
         const int64_t t = base + (int64_t)lane * nwarps;
         int2 run = make_int2(0, 0);
-        if (t < nruns) run = __ldg(t < p.nr_w ? p.runs_w + t : p.runs_uv + (t - p.nr_w));
+        if (t < nruns) run = __ldg(t < mm.nr_w ? mm.runs_w + t : mm.runs_uv + (t - mm.nr_w));
         const int nq = (int)min((int64_t)32, (nruns - base + nwarps - 1) / nwarps);
         for (int q = 0; q < nq; ++q) {
             const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
             const int32_t len = __shfl_sync(0xffffffffu, run.y, q);
-            const bool is_w = base + (int64_t)q * nwarps < p.nr_w;
+            const bool is_w = base + (int64_t)q * nwarps < mm.nr_w;
             for (int32_t x = lane; x < len; x += 32) {
                 const int64_t idx = (int64_t)start + x;
                 if (is_w) {
@@ -472,39 +556,156 @@ __device__ void wall_phase(const StencilParams<T> &p, T *acc, int wt, int nthrea
     }
 }
 
-// Eq. 27: body velocity = 3 dt/2 grad p, or 0 (grid-stride over the body lists).
+// Single terrain: the grid shares the band records two per thread and round;
+// band statistics accumulate per thread, are reduced per block and then by the
+// last block.
 template <typename T, typename VEL>
-__device__ void mask_phase(const StencilParams<T> &p, int64_t tid, int64_t stride)
-{
-    VEL *const vu = reinterpret_cast<VEL *>(p.u);
-    VEL *const vv = reinterpret_cast<VEL *>(p.v);
-    VEL *const vw = reinterpret_cast<VEL *>(p.w);
-    for (int64_t t = tid; t < p.nbody_uv; t += stride) {
-        const int32_t idx = __ldg(p.body_uv + t);
-        vu[idx] = to_vel<VEL, T>(p.gpx ? p.mask_c * __ldg(p.gpx + idx) : T(0));
-        vv[idx] = to_vel<VEL, T>(p.gpy ? p.mask_c * __ldg(p.gpy + idx) : T(0));
-    }
-    for (int64_t t = tid; t < p.nbody_w; t += stride) {
-        const int32_t idx = __ldg(p.body_w + t);
-        vw[idx] = to_vel<VEL, T>(p.gpz ? p.mask_c * __ldg(p.gpz + idx) : T(0));
-    }
-}
-
-template <typename T, typename VEL>
-__global__ void __launch_bounds__(256) k_wall(StencilParams<T> p)
+__global__ void __launch_bounds__(256) k_wall(KParams<T> p)
 {
     __shared__ T red[32][kStatVals];
+    // let the stencil kernel (next in the stream) launch right away
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     T acc[kStatVals];
     stats_identity(acc);
-    wall_phase<T, VEL>(p, acc, threadIdx.x, blockDim.x);
+    const Member<T> &mm = p.one;
+    const int64_t nrec = mm.nb_w + mm.nb_uv;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t t0 = tid; t0 < nrec; t0 += 2 * stride) {
+        const int64_t t1 = t0 + stride;
+        BandOut<T> a, b;
+        a = band_of<T, VEL>(mm, t0);
+        if (t1 < nrec) b = band_of<T, VEL>(mm, t1);
+        store_band(mm, a, t0 < mm.nb_w);
+        stats_add(acc, t0 < mm.nb_w ? 0 : 1, a.tw, a.ur);
+        if (t1 < nrec) {
+            store_band(mm, b, t1 < mm.nb_w);
+            stats_add(acc, t1 < mm.nb_w ? 0 : 1, b.tw, b.ur);
+        }
+    }
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    zero_runs(mm, gw, nwarps, threadIdx.x & 31);
     if (p.stats) {
         stats_block_reduce(acc, red);
-        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, p.nb_w, p.nb_uv);
+        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, mm.nb_w, mm.nb_uv);
     }
 }
 
-template <typename T, typename VEL, int TY, bool FUSED>
-__global__ void __launch_bounds__(512) k_stencil(StencilParams<T> p)
+// Order-preserving encoding of a non-negative value for 64-bit integer atomics.
+__device__ __forceinline__ unsigned long long ordered_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x > 0.0 ? x : 0.0);
+}
+
+// Batch: block b takes a contiguous slice of the concatenated band records
+// (so that it meets few members) and accumulates per-member statistics in
+// shared memory, flushed to the batch scratch with global atomics; warps then
+// zero the solid runs of every member.  The last block converts the scratch
+// into wmibm_band_stats and clears it for the next call.
+template <typename T, typename VEL>
+__global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
+{
+    __shared__ double s_sum[kMaxBatchMembers][2][2];
+    __shared__ unsigned long long s_ext[kMaxBatchMembers][2][2];   // (-min tau_w, max |U_r|) bits
+    __shared__ int s_m0, s_m1;
+    __shared__ bool s_last;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    const int64_t R = p.rec_total;
+    const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    const bool want_stats = p.stats != nullptr;
+    if (threadIdx.x == 0) {
+        s_m0 = r0 < r1 ? find_member_rec(p, r0) : 0;
+        s_m1 = r0 < r1 ? find_member_rec(p, r1 - 1) : -1;
+    }
+    __syncthreads();
+    const int m0 = s_m0, m1 = s_m1;
+    for (int q = threadIdx.x; q < (m1 - m0 + 1) * 4; q += blockDim.x) {
+        const int mi = q >> 2, bnd = (q >> 1) & 1, c = q & 1;
+        s_sum[mi][bnd][c] = 0.0;
+        s_ext[mi][bnd][c] = 0ull;
+    }
+    __syncthreads();
+
+    auto account = [&](int mi, bool is_w, const BandOut<T> &o) {
+        if (!want_stats) return;
+        const int bnd = is_w ? 0 : 1;
+        atomicAdd(&s_sum[mi - m0][bnd][0], (double)o.tw);
+        atomicAdd(&s_sum[mi - m0][bnd][1], (double)o.tw * (double)o.tw);
+        atomicMax(&s_ext[mi - m0][bnd][0], ordered_bits(-(double)o.tw));
+        atomicMax(&s_ext[mi - m0][bnd][1], ordered_bits((double)o.ur));
+    };
+    for (int64_t g0 = r0 + threadIdx.x; g0 < r1; g0 += 2 * blockDim.x) {
+        const int64_t g1 = g0 + blockDim.x;
+        const int ma = find_member_rec(p, g0);
+        const Member<T> &A = p.list[ma];
+        const int64_t ta = g0 - A.r_off;
+        const BandOut<T> a = band_of<T, VEL>(A, ta);
+        const bool hb = g1 < r1;
+        const int mb = hb ? find_member_rec(p, g1) : ma;
+        const Member<T> &B = p.list[mb];
+        const int64_t tb = g1 - B.r_off;
+        BandOut<T> b;
+        if (hb) b = band_of<T, VEL>(B, tb);
+        store_band(A, a, ta < A.nb_w);
+        account(ma, ta < A.nb_w, a);
+        if (hb) {
+            store_band(B, b, tb < B.nb_w);
+            account(mb, tb < B.nb_w, b);
+        }
+    }
+    __syncthreads();
+    if (want_stats) {
+        for (int q = threadIdx.x; q < (m1 - m0 + 1) * 2; q += blockDim.x) {
+            const int mi = q >> 1, bnd = q & 1;
+            double *dst = p.bstats + ((int64_t)(m0 + mi) * 2 + bnd) * 4;
+            atomicAdd(dst + 0, s_sum[mi][bnd][0]);
+            atomicAdd(dst + 1, s_sum[mi][bnd][1]);
+            atomicMax(reinterpret_cast<unsigned long long *>(dst + 2), s_ext[mi][bnd][0]);
+            atomicMax(reinterpret_cast<unsigned long long *>(dst + 3), s_ext[mi][bnd][1]);
+        }
+    }
+
+    // solid runs of every member
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    for (int m = 0; m < p.nmembers; ++m) zero_runs(p.list[m], gw, nwarps, threadIdx.x & 31);
+
+    if (!want_stats) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int q = threadIdx.x; q < p.nmembers * 2; q += blockDim.x) {
+        const int m = q >> 1, bnd = q & 1;
+        double *src = p.bstats + ((int64_t)m * 2 + bnd) * 4;
+        wmibm_band_stats st;
+        st.count = bnd == 0 ? p.list[m].nb_w : p.list[m].nb_uv;
+        st.sum_tw = __ldcg(src + 0);
+        st.sum_tw2 = __ldcg(src + 1);
+        st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 2)));
+        st.max_ur = __longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 3)));
+        if (st.min_tw == 0.0) st.min_tw = 0.0;   // no -0 for an empty band
+        p.stats[q] = st;
+        src[0] = 0.0;
+        src[1] = 0.0;
+        src[2] = 0.0;
+        src[3] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *p.ticket = 0u;
+}
+
+// ------------------------------------------------------------------------- //
+// stencil kernel
+// ------------------------------------------------------------------------- //
+template <typename T, typename VEL, int TY, bool STEP>
+__global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
@@ -520,16 +721,15 @@ __global__ void __launch_bounds__(512) k_stencil(StencilParams<T> p)
         fence_mbar_init();
     }
     __syncthreads();
-    const Schedule sc = block_schedule(p.nstrips, p.nz, FUSED ? p.da : 0, FUSED ? p.db : 0);
 
     if (warp == 0) {
         // producer: clean stages right away (their rows are not written by the
         // wall kernel), dirty stages once the wall kernel has completed
-        if (lane == 0) produce<T, TY, FUSED>(p, data, full, empty, sc);
+        if (lane == 0) produce<T, TY, STEP>(p, data, full, empty);
         __syncwarp();
     } else {
-        consume<T, TY>(p, data, full, empty, sc, warp - 1, lane);
-        if (FUSED && p.do_mask) {
+        consume<T, TY>(p, data, full, empty, warp - 1, lane);
+        if (STEP && p.do_mask) {
             wait_wall_kernel();
             const int nct = p.ncons * 32;
             mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nct + (threadIdx.x - 32), (int64_t)gridDim.x * nct);
@@ -537,25 +737,25 @@ __global__ void __launch_bounds__(512) k_stencil(StencilParams<T> p)
     }
 }
 
-template <typename T>
-size_t stage_elems_for(int ty, int nx) { return (size_t)(6 * ty + 6) * nx; }
-
 constexpr int kMaxDynSmem = 200 * 1024;
 
-template <typename T, typename VEL, int TY, bool FUSED>
-int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl)
+template <typename T, typename VEL, int TY, bool STEP>
+int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl,
+                      int max_nx)
 {
-    auto kern = k_stencil<T, VEL, TY, FUSED>;
+    auto kern = k_stencil<T, VEL, TY, STEP>;
     static bool attr_done = false;      // once per instantiation and process
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return cuda_status(h, e, "stencil smem attribute");
         attr_done = true;
     }
+    p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
     const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
+    if (smem > (size_t)kMaxDynSmem) return set_error(h, WMIBM_EINVAL, "stencil stages exceed shared memory");
     const int threads = 32 * (1 + p.ncons);
     // occupancy of this shape, cached in the handle
-    const int key = (FUSED ? 1 : 0) | (TY << 1) | (c.stages << 4) | (c.consumer_warps << 8) | (c.wall_warps << 12);
+    const int key = (STEP ? 1 : 0) | (TY << 1) | (c.stages << 4) | (c.consumer_warps << 8) | (max_nx << 14);
     int per_sm = 0;
     for (int q = 0; q < 8; ++q)
         if (h->occ_key[q] == key) per_sm = h->occ_val[q];
@@ -568,9 +768,11 @@ int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cuda
         h->occ_val[slot] = per_sm;
     }
     if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
+    const int64_t units = p.clean_total + p.dirty_total;
     int64_t grid = (int64_t)per_sm * h->sm_count;
-    if (grid > p.units) grid = p.units;
-    if (FUSED && pdl) {
+    if (grid > units) grid = units;
+    if (grid < 1) return WMIBM_OK;
+    if (STEP && pdl) {
         // programmatic dependent of the wall kernel launched just before
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
@@ -588,104 +790,126 @@ int launch_ty(wmibm_handle *h, StencilParams<T> &p, const StencilConfig &c, cuda
     return cuda_status(h, cudaGetLastError(), "k_stencil launch");
 }
 
-bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
-
-template <typename T>
-void fill_params(wmibm_handle *h, StencilParams<T> &p, const void *const tau[6], void *const f[3], void *u, void *v,
-                 void *w, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask,
-                 double dt, const StencilConfig &c);
-
-template <typename T, typename VEL, bool FUSED>
-int launch(wmibm_handle *h, const void *const tau[6], void *const f[3], void *u, void *v, void *w,
-           wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask, double dt,
-           const StencilConfig &c, cudaStream_t stream, bool pdl)
+template <typename T, typename VEL, bool STEP>
+int launch_stencil(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl, int max_nx)
 {
-    StencilParams<T> p;
-    fill_params<T>(h, p, tau, f, u, v, w, stats, logz0, gradp, do_mask, dt, c);
     switch (c.rows) {
-    case 1: return launch_ty<T, VEL, 1, FUSED>(h, p, c, stream, pdl);
-    case 2: return launch_ty<T, VEL, 2, FUSED>(h, p, c, stream, pdl);
-    case 4: return launch_ty<T, VEL, 4, FUSED>(h, p, c, stream, pdl);
+    case 1: return launch_stencil_ty<T, VEL, 1, STEP>(h, p, c, stream, pdl, max_nx);
+    case 2: return launch_stencil_ty<T, VEL, 2, STEP>(h, p, c, stream, pdl, max_nx);
+    case 4: return launch_stencil_ty<T, VEL, 4, STEP>(h, p, c, stream, pdl, max_nx);
     default: return set_error(h, WMIBM_EINVAL, "stencil rows must be 1, 2 or 4");
     }
 }
 
+bool aligned16(const void *q) { return ((uintptr_t)q & 15u) == 0; }
+
 template <typename T>
-void fill_params(wmibm_handle *h, StencilParams<T> &p, const void *const tau[6], void *const f[3], void *u, void *v,
-                 void *w, wmibm_band_stats *stats, const void *logz0, const void *const gradp[3], int do_mask,
-                 double dt, const StencilConfig &c)
+void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
 {
-    for (int a = 0; a < 6; ++a) p.tau[a] = (const T *)tau[a];
-    for (int a = 0; a < 3; ++a) p.f[a] = (T *)f[a];
-    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
-    p.nstrips = c.rows > 0 ? h->ny / c.rows : 0;
-    p.units = (int64_t)p.nstrips * h->nz;
-    p.cx = (T)(1.0 / (2.0 * h->dx));
-    p.cy = (T)(1.0 / (2.0 * h->dy));
-    p.cz = (T)(1.0 / h->dz);
-    p.stages = c.stages;
-    p.ncons = c.consumer_warps;
-    p.nwall = c.wall_warps;
-    p.da = h->dirty_lo;
-    p.db = h->dirty_hi;
-    p.stage_elems = (uint32_t)stage_elems_for<T>(c.rows > 0 ? c.rows : 1, h->nx);
+    p.list = nullptr;
+    p.nmembers = 1;
+    Member<T> &m = p.one;
+    if (!step) {
+        // plain force: no preceding wall kernel, so every level is clean (the
+        // unit decoding in StageIter reads the member's dirty range)
+        m.da = 0;
+        m.db = 0;
+    }
+    p.clean_total = (int64_t)m.nstrips * (m.da + (m.nz - m.db));
+    p.dirty_total = (int64_t)m.nstrips * (m.db - m.da);
+    p.rec_total = m.nb_w + m.nb_uv;
+    p.run_total = m.nr_w + m.nr_uv;
+    p.body_total = m.nbody_w + m.nbody_uv;
+    p.stages = 2;
+    p.ncons = 1;
+    p.stage_elems = 0;
     p.status = h->dev_status;
-    p.u = u; p.v = v; p.w = w;
-    p.rec = h->rec;
-    p.nb_w = h->lists.n[WMIBM_LIST_BAND_W];
-    p.nb_uv = h->lists.n[WMIBM_LIST_BAND_UV];
-    p.runs_w = h->runs[0];
-    p.runs_uv = h->runs[1];
-    p.nr_w = h->nruns[0];
-    p.nr_uv = h->nruns[1];
-    p.do_mask = do_mask;
-    p.body_w = h->lists.p[WMIBM_LIST_BODY_W];
-    p.body_uv = h->lists.p[WMIBM_LIST_BODY_UV];
-    p.nbody_w = h->lists.n[WMIBM_LIST_BODY_W];
-    p.nbody_uv = h->lists.n[WMIBM_LIST_BODY_UV];
-    p.gpx = gradp ? (const T *)gradp[0] : nullptr;
-    p.gpy = gradp ? (const T *)gradp[1] : nullptr;
-    p.gpz = gradp ? (const T *)gradp[2] : nullptr;
-    p.mask_c = (T)(1.5 * dt);
+    p.do_mask = 0;
     p.partials = (T *)h->partials;
     p.ticket = h->ticket;
-    p.stats = stats;
-    p.logz0 = (const T *)logz0;
-    p.log_phi_c = (T)log(h->phi_c);
-    p.kappa2 = (T)(h->kappa * h->kappa);
+    p.stats = nullptr;
+    p.bstats = nullptr;
 }
 
-// The wall kernel: persistent grid sized by occupancy, wall_warps warps per block.
 template <typename T, typename VEL>
-int launch_wall(wmibm_handle *h, void *const tau[6], const void *u, const void *v, const void *w,
-                wmibm_band_stats *stats, const void *logz0, cudaStream_t stream)
+int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const void *v, const void *w,
+                       wmibm_band_stats *stats, const void *logz0, void *partials, unsigned *ticket, unsigned blocks,
+                       cudaStream_t stream)
 {
-    StencilParams<T> p;
-    StencilConfig c = {};
-    void *const none[3] = {nullptr, nullptr, nullptr};
-    fill_params<T>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
-                   const_cast<void *>(w), stats, logz0, nullptr, 0, 0.0, c);
-    const int wthreads = 32 * (h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 8);
-    int wper = 0;
-    const int wkey = 0x100000 | wthreads | (sizeof(T) == 8 ? 0x200000 : 0);
-    for (int q = 0; q < 8; ++q)
-        if (h->occ_key[q] == wkey) wper = h->occ_val[q];
-    if (wper == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_wall<T, VEL>, wthreads, 0);
-        if (e != cudaSuccess) return cuda_status(h, e, "wall occupancy");
-        if (wper < 1) wper = 1;
-        const int slot = h->occ_next++ & 7;
-        h->occ_key[slot] = wkey;
-        h->occ_val[slot] = wper;
+    KParams<T> p;
+    fill_member<T>(h, p.one, (const void *const *)tau, nullptr, const_cast<void *>(u), const_cast<void *>(v),
+                   const_cast<void *>(w), logz0, nullptr, 0.0, 0);
+    single_params<T>(h, p, false);
+    p.stats = stats;
+    if (partials) {
+        p.partials = (T *)partials;
+        p.ticket = ticket;
     }
-    const int64_t wgrid = std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
-    k_wall<T, VEL><<<(unsigned)wgrid, wthreads, 0, stream>>>(p);
+    const int wthreads = blocks ? 256 : 32 * (h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 8);
+    if (blocks == 0) {
+        int wper = 0;
+        const int wkey = 0x100000 | wthreads | (sizeof(T) == 8 ? 0x200000 : 0);
+        for (int q = 0; q < 8; ++q)
+            if (h->occ_key[q] == wkey) wper = h->occ_val[q];
+        if (wper == 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_wall<T, VEL>, wthreads, 0);
+            if (e != cudaSuccess) return cuda_status(h, e, "wall occupancy");
+            if (wper < 1) wper = 1;
+            const int slot = h->occ_next++ & 7;
+            h->occ_key[slot] = wkey;
+            h->occ_val[slot] = wper;
+        }
+        blocks = (unsigned)std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
+    }
+    k_wall<T, VEL><<<blocks, wthreads, 0, stream>>>(p);
     return cuda_status(h, cudaGetLastError(), "k_wall launch");
 }
 
 }  // namespace
 
 namespace wmibm {
+
+// Fills the member descriptor of handle h with the given fields.
+template <typename T>
+void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], void *const f[3], void *u, void *v,
+                 void *w, const void *logz0, const void *const gradp[3], double dt, int rows)
+{
+    for (int a = 0; a < 6; ++a) m.tau[a] = (const T *)tau[a];
+    for (int a = 0; a < 3; ++a) m.f[a] = f ? (T *)f[a] : nullptr;
+    m.u = u; m.v = v; m.w = w;
+    m.nx = h->nx; m.ny = h->ny; m.nz = h->nz;
+    m.nstrips = rows > 0 ? h->ny / rows : 0;
+    m.cx = (T)(1.0 / (2.0 * h->dx));
+    m.cy = (T)(1.0 / (2.0 * h->dy));
+    m.cz = (T)(1.0 / h->dz);
+    m.da = h->dirty_lo;
+    m.db = h->dirty_hi;
+    m.c_off = 0; m.d_off = 0;
+    m.rec = h->rec;
+    m.nb_w = h->lists.n[WMIBM_LIST_BAND_W];
+    m.nb_uv = h->lists.n[WMIBM_LIST_BAND_UV];
+    m.r_off = 0;
+    m.runs_w = h->runs[0]; m.runs_uv = h->runs[1];
+    m.nr_w = h->nruns[0]; m.nr_uv = h->nruns[1];
+    m.run_off = 0;
+    m.body_w = h->lists.p[WMIBM_LIST_BODY_W];
+    m.body_uv = h->lists.p[WMIBM_LIST_BODY_UV];
+    m.nbody_w = h->lists.n[WMIBM_LIST_BODY_W];
+    m.nbody_uv = h->lists.n[WMIBM_LIST_BODY_UV];
+    m.body_off = 0;
+    m.gpx = gradp ? (const T *)gradp[0] : nullptr;
+    m.gpy = gradp ? (const T *)gradp[1] : nullptr;
+    m.gpz = gradp ? (const T *)gradp[2] : nullptr;
+    m.mask_c = (T)(1.5 * dt);
+    m.logz0 = (const T *)logz0;
+    m.log_phi_c = (T)log(h->phi_c);
+    m.kappa2 = (T)(h->kappa * h->kappa);
+}
+
+template void fill_member<float>(const wmibm_handle *, Member<float> &, const void *const[6], void *const[3], void *,
+                                 void *, void *, const void *, const void *const[3], double, int);
+template void fill_member<double>(const wmibm_handle *, Member<double> &, const void *const[6], void *const[3],
+                                  void *, void *, void *, const void *, const void *const[3], double, int);
 
 // Chooses the stencil tile for this handle (or validates the one set by tuning).
 // Returns false when the pipelined path cannot take this grid / these buffers.
@@ -720,7 +944,7 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     if ((size_t)c.stages * stage_bytes + 256 > (size_t)kMaxDynSmem) return false;
     c.consumer_warps = h->tuning.consumer_warps > 0 ? h->tuning.consumer_warps : 4;
     c.wall_warps = h->tuning.wall_warps;
-    if (1 + c.consumer_warps + c.wall_warps > 16) return false;
+    if (1 + c.consumer_warps > 16) return false;
     c.blocks_per_sm = h->tuning.blocks_per_sm;
     *out = c;
     return true;
@@ -729,11 +953,20 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
 int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], const StencilConfig &c,
                   cudaStream_t stream)
 {
-    if (h->dtype == WMIBM_F64)
-        return launch<double, double, false>(h, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                                             0.0, c, stream, false);
-    return launch<float, float, false>(h, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0, c,
-                                       stream, false);
+    if (h->dtype == WMIBM_F64) {
+        KParams<double> p;
+        fill_member<double>(h, p.one, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, c.rows);
+        single_params<double>(h, p, false);
+        p.stages = c.stages;
+        p.ncons = c.consumer_warps;
+        return launch_stencil<double, double, false>(h, p, c, stream, false, h->nx);
+    }
+    KParams<float> p;
+    fill_member<float>(h, p.one, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, c.rows);
+    single_params<float>(h, p, false);
+    p.stages = c.stages;
+    p.ncons = c.consumer_warps;
+    return launch_stencil<float, float, false>(h, p, c, stream, false, h->nx);
 }
 
 // The pipelined stencil followed, in the same launch, by the body mask (Eq. 27).
@@ -741,40 +974,23 @@ int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], c
 int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
                        const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream)
 {
-    if (h->dtype == WMIBM_F64)
-        return launch<double, double, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
-    if (h->vel_dtype == WMIBM_BF16)
-        return launch<float, __nv_bfloat16, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
-    return launch<float, float, true>(h, tau, f, u, v, w, nullptr, nullptr, gradp, 1, dt, c, stream, pdl);
-}
-
-// The wall kernel with caller-provided reduction scratch and grid size (used by
-// the entry point whose scratch lives in a static device array).
-int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
-                            wmibm_band_stats *stats, void *partials, unsigned *ticket, unsigned blocks,
-                            cudaStream_t stream)
-{
-    StencilConfig c = {};
-    void *const none[3] = {nullptr, nullptr, nullptr};
     if (h->dtype == WMIBM_F64) {
-        StencilParams<double> p;
-        fill_params<double>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
-                            const_cast<void *>(w), stats, nullptr, nullptr, 0, 0.0, c);
-        p.partials = (double *)partials;
-        p.ticket = ticket;
-        k_wall<double, double><<<blocks, 256, 0, stream>>>(p);
-    } else {
-        StencilParams<float> p;
-        fill_params<float>(h, p, (const void *const *)tau, none, const_cast<void *>(u), const_cast<void *>(v),
-                           const_cast<void *>(w), stats, nullptr, nullptr, 0, 0.0, c);
-        p.partials = (float *)partials;
-        p.ticket = ticket;
-        if (h->vel_dtype == WMIBM_BF16)
-            k_wall<float, __nv_bfloat16><<<blocks, 256, 0, stream>>>(p);
-        else
-            k_wall<float, float><<<blocks, 256, 0, stream>>>(p);
+        KParams<double> p;
+        fill_member<double>(h, p.one, tau, f, u, v, w, nullptr, gradp, dt, c.rows);
+        single_params<double>(h, p, true);
+        p.stages = c.stages;
+        p.ncons = c.consumer_warps;
+        p.do_mask = 1;
+        return launch_stencil<double, double, true>(h, p, c, stream, pdl, h->nx);
     }
-    return cuda_status(h, cudaGetLastError(), "k_wall launch");
+    KParams<float> p;
+    fill_member<float>(h, p.one, tau, f, u, v, w, nullptr, gradp, dt, c.rows);
+    single_params<float>(h, p, true);
+    p.stages = c.stages;
+    p.ncons = c.consumer_warps;
+    p.do_mask = 1;
+    if (h->vel_dtype == WMIBM_BF16) return launch_stencil<float, __nv_bfloat16, true>(h, p, c, stream, pdl, h->nx);
+    return launch_stencil<float, float, true>(h, p, c, stream, pdl, h->nx);
 }
 
 // The wall model at every band node and the solid zeros (persistent kernel).
@@ -786,10 +1002,49 @@ int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, voi
         if (e != cudaSuccess) return cuda_status(h, e, "clear stats");
         stats = nullptr;
     }
-    if (h->dtype == WMIBM_F64) return launch_wall<double, double>(h, tau, u, v, w, stats, logz0, stream);
+    if (h->dtype == WMIBM_F64)
+        return launch_wall_single<double, double>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
     if (h->vel_dtype == WMIBM_BF16)
-        return launch_wall<float, __nv_bfloat16>(h, tau, u, v, w, stats, logz0, stream);
-    return launch_wall<float, float>(h, tau, u, v, w, stats, logz0, stream);
+        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
+    return launch_wall_single<float, float>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
 }
+
+// The wall kernel with caller-provided reduction scratch and grid size (used by
+// the entry point whose scratch lives in a static device array).
+int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                            wmibm_band_stats *stats, void *partials, unsigned *ticket, unsigned blocks,
+                            cudaStream_t stream)
+{
+    if (h->dtype == WMIBM_F64)
+        return launch_wall_single<double, double>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks, stream);
+    if (h->vel_dtype == WMIBM_BF16)
+        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks,
+                                                        stream);
+    return launch_wall_single<float, float>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks, stream);
+}
+
+// One batched step: the batch wall kernel, then the batch stencil (force + mask)
+// as its programmatic dependent.  tmpl carries the launch-wide fields.
+template <typename T, typename VEL>
+int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
+                 const StencilConfig &c, int max_nx, int wall_blocks, cudaStream_t stream)
+{
+    KParams<T> p = tmpl;
+    p.list = dev_members;
+    p.nmembers = nmembers;
+    p.stages = c.stages;
+    p.ncons = c.consumer_warps;
+    k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, 0, stream>>>(p);
+    int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
+    if (st) return st;
+    return launch_stencil<T, VEL, true>(h0, p, c, stream, true, max_nx);
+}
+
+template int batch_launch<float, float>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
+                                        const StencilConfig &, int, int, cudaStream_t);
+template int batch_launch<float, __nv_bfloat16>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
+                                                const StencilConfig &, int, int, cudaStream_t);
+template int batch_launch<double, double>(wmibm_handle *, const Member<double> *, int, const KParams<double> &,
+                                          const StencilConfig &, int, int, cudaStream_t);
 
 }  // namespace wmibm

@@ -26,7 +26,9 @@ DTYPE_CODES = {"f32": F32, "f64": F64, "bf16": BF16}
 EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmibm_step", "wmibm_list_size",
             "wmibm_export_list", "wmibm_traffic_bytes", "wmibm_destroy", "wmibm_status_string",
             "wmibm_last_error", "wmibm_wall_stress_force", "wmibm_set_tuning", "wmibm_get_tuning",
-            "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc")
+            "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
+            "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
+            "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy")
 
 
 class WmibmError(RuntimeError):
@@ -53,6 +55,11 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class MemberFields(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p * 6), ("f", ctypes.c_void_p * 3)]
 
 
 STATS_DTYPE = np.dtype([("count", "<i8"), ("sum_tw", "<f8"), ("sum_tw2", "<f8"), ("min_tw", "<f8"),
@@ -100,6 +107,22 @@ def load(path: Optional[str] = None):
     L.wmibm_get_tuning.restype = ctypes.c_int
     L.wmibm_device_status.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), _VP]
     L.wmibm_device_status.restype = ctypes.c_int
+    L.wmibm_batch_create.argtypes = [ctypes.POINTER(_VP), _PVP, ctypes.c_int32, _VP]
+    L.wmibm_batch_create.restype = ctypes.c_int
+    L.wmibm_batch_set_fields.argtypes = [_VP, ctypes.POINTER(MemberFields), _VP]
+    L.wmibm_batch_set_fields.restype = ctypes.c_int
+    L.wmibm_batch_set_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
+    L.wmibm_batch_set_tuning.restype = ctypes.c_int
+    L.wmibm_batch_step.argtypes = [_VP, _VP, _VP]
+    L.wmibm_batch_step.restype = ctypes.c_int
+    L.wmibm_batch_traffic_bytes.argtypes = [_VP, ctypes.c_int32]
+    L.wmibm_batch_traffic_bytes.restype = ctypes.c_int64
+    L.wmibm_batch_points.argtypes = [_VP]
+    L.wmibm_batch_points.restype = ctypes.c_int64
+    L.wmibm_batch_last_error.argtypes = [_VP]
+    L.wmibm_batch_last_error.restype = ctypes.c_char_p
+    L.wmibm_batch_destroy.argtypes = [_VP]
+    L.wmibm_batch_destroy.restype = None
     L.wmibm_list_size.argtypes = [_VP, ctypes.c_int32]
     L.wmibm_list_size.restype = ctypes.c_int64
     L.wmibm_export_list.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP]
@@ -347,3 +370,70 @@ class PreparedStep:
     def step(self, stream=None):
         self.h._check(self._L.wmibm_step(self.h._h, self._u, self._v, self._w, self._tau, *self._f, self._gradp,
                                          self._dt, self._stats, _stream_ptr(stream)))
+
+
+class Batch:
+    """Batched ensemble of handles stepped by the same persistent launches."""
+
+    def __init__(self, handles, stream=None):
+        L = load()
+        self._L = L
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.raw.value for h in self.handles])
+        b = ctypes.c_void_p()
+        st = L.wmibm_batch_create(ctypes.byref(b), arr, len(self.handles), _stream_ptr(stream))
+        if st != OK:
+            raise WmibmError(st, "wmibm_batch_create failed (mixed devices/dtypes, or a member the pipelined "
+                                 "stencil cannot take)")
+        self._b = b
+        self._keep = None
+
+    def _check(self, st):
+        if st != OK:
+            raise WmibmError(st, self._L.wmibm_batch_last_error(self._b).decode())
+
+    def set_fields(self, fields, stream=None):
+        """fields: per member (u, v, w, tau[6], f[3]) tensors on the handles' device."""
+        arr = (MemberFields * len(self.handles))()
+        for m, (h, (u, v, w, tau, f)) in enumerate(zip(self.handles, fields)):
+            for t in (u, v, w):
+                h._field(t, vel=True)
+            for t in list(tau) + list(f):
+                h._field(t)
+            arr[m].u, arr[m].v, arr[m].w = _dptr(u), _dptr(v), _dptr(w)
+            for a in range(6):
+                arr[m].tau[a] = _dptr(tau[a])
+            for a in range(3):
+                arr[m].f[a] = _dptr(f[a])
+        self._keep = fields
+        self._check(self._L.wmibm_batch_set_fields(self._b, arr, _stream_ptr(stream)))
+
+    def set_tuning(self, **fields):
+        t = Tuning()
+        for k, v in fields.items():
+            setattr(t, k, int(v))
+        self._check(self._L.wmibm_batch_set_tuning(self._b, ctypes.byref(t)))
+
+    def new_stats(self):
+        import torch
+        return torch.zeros(10 * len(self.handles), dtype=torch.float64, device=self.handles[0].device)
+
+    def step(self, stats=None, stream=None):
+        self._check(self._L.wmibm_batch_step(self._b, None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def points(self) -> int:
+        return int(self._L.wmibm_batch_points(self._b))
+
+    def traffic_bytes(self, which: int) -> int:
+        return int(self._L.wmibm_batch_traffic_bytes(self._b, int(which)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.wmibm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,135 @@
+"""Batched ensembles: members of uneven grid sizes stepped by the same two
+persistent launches give, member by member, what single-terrain steps give,
+and match the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2006_03343_gb300 import inputs
+
+from parity_util import TOL, assert_stats_close, normwise, oracle_step, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SMALL_SHAPES = ((32, 16, 20), (48, 24, 16), (64, 32, 24), (40, 20, 18))
+
+
+@pytest.fixture(scope="module")
+def wm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_03343_gb300 import build, wmibm
+    build.build()
+    wmibm.load()
+    return wmibm
+
+
+def _fields(case, dtype):
+    u, v, w = (to_dev(x, dtype) for x in (case.u, case.v, case.w))
+    tau = [to_dev(case.tau[k], dtype) for k in inputs.TAU_NAMES]
+    f = [to_dev(np.zeros(case.shape), dtype) for _ in range(3)]
+    return u, v, w, tau, f
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_equals_single_steps_and_oracle(wm, oracle_mod, dtype):
+    cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % len(SMALL_SHAPES)], dtype=dtype) for m in range(9)]
+    handles = [wm.Handle.from_case(c, dtype=dtype) for c in cases]
+    batch = wm.Batch(handles)
+    fields = [_fields(c, dtype) for c in cases]
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.step(stats)
+    torch.cuda.synchronize()
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(len(cases), 2)
+    for m, (c, h) in enumerate(zip(cases, handles)):
+        u, v, w, tau, f = _fields(c, dtype)
+        st = h.new_stats()
+        h.step(u, v, w, tau, f, None, 0.0, st)
+        torch.cuda.synchronize()
+        bu, bv, bw, btau, bf = fields[m]
+        for got, ref in zip(bf, f):
+            assert np.array_equal(to_host(got), to_host(ref)), m
+        for got, ref in zip(btau, tau):
+            assert np.array_equal(to_host(got), to_host(ref)), m
+        for got, ref in zip((bu, bv, bw), (u, v, w)):
+            assert np.array_equal(to_host(got), to_host(ref)), m
+        tau_o, f_o, st_o = oracle_step(oracle_mod, c)
+        for cc in range(3):
+            assert normwise(to_host(bf[cc]), f_o[cc])[0] <= TOL[dtype], (m, cc)
+        assert_stats_close(bstats[m], st_o, dtype)
+    assert handles[0].device_status() == wm.OK
+    batch.close()
+
+
+def test_batch_graph_replay(wm):
+    """The batch step captured once in a CUDA graph replays to the eager result."""
+    cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % 4]) for m in range(6)]
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    fields_a = [_fields(c, "f32") for c in cases]
+    batch.set_fields(fields_a)
+    batch.step()
+    torch.cuda.synchronize()
+    ref = [[to_host(t) for t in fa[4]] for fa in fields_a]
+    fields_b = [_fields(c, "f32") for c in cases]
+    batch.set_fields(fields_b)
+    stats = batch.new_stats()
+    batch.step(stats)        # warm up outside the capture
+    torch.cuda.synchronize()
+    for fb, c in zip(fields_b, cases):      # reset the inputs the step modified
+        fb[0].copy_(to_dev(c.u, "f32")); fb[1].copy_(to_dev(c.v, "f32")); fb[2].copy_(to_dev(c.w, "f32"))
+        for t, k in zip(fb[3], inputs.TAU_NAMES):
+            t.copy_(to_dev(c.tau[k], "f32"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.step(stats)
+    for fb, c in zip(fields_b, cases):
+        fb[0].copy_(to_dev(c.u, "f32")); fb[1].copy_(to_dev(c.v, "f32")); fb[2].copy_(to_dev(c.w, "f32"))
+        for t, k in zip(fb[3], inputs.TAU_NAMES):
+            t.copy_(to_dev(c.tau[k], "f32"))
+    g.replay()
+    torch.cuda.synchronize()
+    for m, fb in enumerate(fields_b):
+        for got, r in zip(fb[4], ref[m]):
+            assert np.array_equal(to_host(got), r), m
+    batch.close()
+
+
+def test_batch_tunings(wm, oracle_mod):
+    cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % 4]) for m in range(5)]
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    for tun in (dict(rows=1, stages=3, consumer_warps=2), dict(rows=2, stages=5, consumer_warps=8),
+                dict(rows=4, stages=2, consumer_warps=4, blocks_per_sm=1)):
+        batch.set_tuning(**tun)
+        fields = [_fields(c, "f32") for c in cases]
+        batch.set_fields(fields)
+        batch.step()
+        torch.cuda.synchronize()
+        for m, c in enumerate(cases):
+            tau_o, f_o, _ = oracle_step(oracle_mod, c)
+            for cc in range(3):
+                assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], (tun, m)
+    batch.close()
+
+
+def test_full_ensemble_64(wm, oracle_mod):
+    """The 64-member ensemble (grids 64^3 .. 256x128x64), sampled against the oracle."""
+    cases = inputs.ensemble(64)
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    fields = [_fields(c, "f32") for c in cases]
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.step(stats)
+    torch.cuda.synchronize()
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(64, 2)
+    for m in (0, 17, 42, 63):
+        tau_o, f_o, st_o = oracle_step(oracle_mod, cases[m])
+        for cc in range(3):
+            assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], m
+        assert_stats_close(bstats[m], st_o, "f32")
+    assert batch.points() == sum(c.npoints for c in cases)
+    batch.close()
