@@ -27,7 +27,7 @@ struct wmibm_batch {
     int fields_set;
     wmibm_tuning tuning;
     StencilConfig cfg;
-    int64_t clean_total, dirty_total, rec_total, body_total;
+    int64_t clean_total, dirty_total, rec_total, run_total, body_total;
     int64_t traffic[2];
     char err[512];
 };
@@ -86,7 +86,7 @@ template <typename T>
 int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream_t stream)
 {
     std::vector<Member<T>> host(b->count);
-    int64_t c_off = 0, d_off = 0, r_off = 0, body_off = 0;
+    int64_t c_off = 0, d_off = 0, r_off = 0, run_off = 0, body_off = 0;
     for (int m = 0; m < b->count; ++m) {
         wmibm_handle *h = b->members[m];
         const wmibm_member_fields &fl = fields[m];
@@ -96,15 +96,18 @@ int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream
         mm.c_off = c_off;
         mm.d_off = d_off;
         mm.r_off = r_off;
+        mm.run_off = run_off;
         mm.body_off = body_off;
         c_off += (int64_t)mm.nstrips * (mm.da + (mm.nz - mm.db));
         d_off += (int64_t)mm.nstrips * (mm.db - mm.da);
         r_off += mm.nb_w + mm.nb_uv;
+        run_off += mm.nr_w + mm.nr_uv;
         body_off += mm.nbody_w + mm.nbody_uv;
     }
     b->clean_total = c_off;
     b->dirty_total = d_off;
     b->rec_total = r_off;
+    b->run_total = run_off;
     b->body_total = body_off;
     cudaError_t e = cudaMemcpyAsync(b->dev_members, host.data(), sizeof(Member<T>) * b->count,
                                     cudaMemcpyHostToDevice, stream);
@@ -119,7 +122,7 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
     p.clean_total = b->clean_total;
     p.dirty_total = b->dirty_total;
     p.rec_total = b->rec_total;
-    p.run_total = 0;
+    p.run_total = b->run_total;
     p.body_total = b->body_total;
     p.status = b->status;
     p.do_mask = 1;
@@ -127,7 +130,7 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
     p.ticket = b->ticket;
     p.stats = stats;
     p.bstats = b->bstats;
-    const int wall_blocks = 3 * b->members[0]->sm_count;
+    const int wall_blocks = 0;   // one wave of resident blocks
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
                                   wall_blocks, stream);
     if (st) return berr(b, st, "%s", b->members[0]->err);

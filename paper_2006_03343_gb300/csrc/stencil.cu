@@ -159,14 +159,15 @@ __device__ int find_member(const KParams<T> &p, int phase, int64_t i)
     return lo;
 }
 
-// Member holding index g of the concatenated band-record space (batch).
+// Member holding index g of a concatenated per-member space (batch): the last
+// member whose first index (the Member field `first`) is <= g.
 template <typename T>
-__device__ int find_member_rec(const KParams<T> &p, int64_t g)
+__device__ int find_member_at(const KParams<T> &p, int64_t Member<T>::*first, int64_t g)
 {
     int lo = 0, hi = p.nmembers - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (p.list[mid].r_off <= g)
+        if (p.list[mid].*first <= g)
             lo = mid;
         else
             hi = mid - 1;
@@ -191,7 +192,11 @@ struct StageIter {
 
     __device__ void locate()
     {
-        const int m2 = find_member(*pp, phase, idx);
+        int m2 = m;
+        if (m < 0 || idx < (phase == 0 ? mu.c_off : mu.d_off) ||
+            idx >= (phase == 0 ? mu.c_off + (int64_t)mu.nstrips * (mu.da + (mu.nz - mu.db))
+                               : mu.d_off + (int64_t)mu.nstrips * (mu.db - mu.da)))
+            m2 = find_member(*pp, phase, idx);
         if (m2 != m) {
             m = m2;
             mu = load_units(*pp, m);
@@ -461,38 +466,49 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
 // ------------------------------------------------------------------------- //
 // body mask (Eq. 27) over the launch's concatenated body lists
 // ------------------------------------------------------------------------- //
-template <typename T, typename VEL>
-__device__ void mask_member(const Member<T> &mm, int64_t t0, int64_t n, int64_t stride)
+// One member's body-mask fields (constant-offset loads into registers).
+template <typename T>
+struct MaskView {
+    void *u, *v, *w;
+    const int32_t *body_uv, *body_w;
+    int64_t first, n_uv, end;     // member's slice [first, end) of the body space
+    const T *gpx, *gpy, *gpz;
+    T mask_c;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_mask(const Member<T> &mm, MaskView<T> &v)
 {
-    VEL *const vu = reinterpret_cast<VEL *>(mm.u);
-    VEL *const vv = reinterpret_cast<VEL *>(mm.v);
-    VEL *const vw = reinterpret_cast<VEL *>(mm.w);
-    const int64_t n_uv = mm.nbody_uv;
-    for (int64_t t = t0; t < n; t += stride) {
-        if (t < n_uv) {
-            const int32_t idx = __ldg(mm.body_uv + t);
-            vu[idx] = to_vel<VEL, T>(mm.gpx ? mm.mask_c * __ldg(mm.gpx + idx) : T(0));
-            vv[idx] = to_vel<VEL, T>(mm.gpy ? mm.mask_c * __ldg(mm.gpy + idx) : T(0));
-        } else {
-            const int32_t idx = __ldg(mm.body_w + (t - n_uv));
-            vw[idx] = to_vel<VEL, T>(mm.gpz ? mm.mask_c * __ldg(mm.gpz + idx) : T(0));
-        }
-    }
+    v.u = mm.u; v.v = mm.v; v.w = mm.w;
+    v.body_uv = mm.body_uv; v.body_w = mm.body_w;
+    v.first = mm.body_off;
+    v.n_uv = mm.nbody_uv;
+    v.end = mm.body_off + mm.nbody_uv + mm.nbody_w;
+    v.gpx = mm.gpx; v.gpy = mm.gpy; v.gpz = mm.gpz;
+    v.mask_c = mm.mask_c;
 }
 
+// Eq. 27 over the launch's concatenated body lists (uv-body nodes of a member
+// first, then its w-body nodes): thread tid takes indices tid, tid + stride, ...
 template <typename T, typename VEL>
 __device__ void mask_phase(const KParams<T> &p, int64_t tid, int64_t stride)
 {
-    if (p.nmembers == 1) {
-        mask_member<T, VEL>(p.one, tid, p.one.nbody_uv + p.one.nbody_w, stride);
-        return;
-    }
-    for (int m = 0; m < p.nmembers; ++m) {
-        const Member<T> &mm = p.list[m];
-        // this thread's first index inside member m's slice of the concatenated space
-        int64_t first = tid - mm.body_off;
-        if (first < 0) first += ((-first + stride - 1) / stride) * stride;
-        mask_member<T, VEL>(mm, first, mm.nbody_uv + mm.nbody_w, stride);
+    const int64_t total = p.body_total;
+    if (tid >= total) return;
+    int m = p.nmembers == 1 ? 0 : find_member_at(p, &Member<T>::body_off, tid);
+    MaskView<T> mv;
+    load_mask(p.nmembers == 1 ? p.one : p.list[m], mv);
+    for (int64_t t = tid; t < total; t += stride) {
+        while (t >= mv.end) load_mask(p.list[++m], mv);
+        const int64_t lt = t - mv.first;
+        if (lt < mv.n_uv) {
+            const int32_t idx = __ldg(mv.body_uv + lt);
+            reinterpret_cast<VEL *>(mv.u)[idx] = to_vel<VEL, T>(mv.gpx ? mv.mask_c * __ldg(mv.gpx + idx) : T(0));
+            reinterpret_cast<VEL *>(mv.v)[idx] = to_vel<VEL, T>(mv.gpy ? mv.mask_c * __ldg(mv.gpy + idx) : T(0));
+        } else {
+            const int32_t idx = __ldg(mv.body_w + (lt - mv.n_uv));
+            reinterpret_cast<VEL *>(mv.w)[idx] = to_vel<VEL, T>(mv.gpz ? mv.mask_c * __ldg(mv.gpz + idx) : T(0));
+        }
     }
 }
 
@@ -598,11 +614,108 @@ __device__ __forceinline__ unsigned long long ordered_bits(double x)
     return (unsigned long long)__double_as_longlong(x > 0.0 ? x : 0.0);
 }
 
+// One member's wall-model fields, held in registers while a thread walks its
+// records (constant-offset loads).
+template <typename T>
+struct WallRegs {
+    const void *rec;
+    const void *u, *v, *w;
+    T *txx, *txy, *tyy, *tzz, *txz, *tyz;
+    const T *logz0;
+    int64_t r_off, nb_w, plane;
+    int32_t nx, ny;
+    T log_phi_c, kappa2;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_wall(const Member<T> &mm, WallRegs<T> &r)
+{
+    r.rec = mm.rec;
+    r.u = mm.u; r.v = mm.v; r.w = mm.w;
+    r.txx = const_cast<T *>(mm.tau[0]); r.txy = const_cast<T *>(mm.tau[1]);
+    r.tyy = const_cast<T *>(mm.tau[2]); r.tzz = const_cast<T *>(mm.tau[3]);
+    r.txz = const_cast<T *>(mm.tau[4]); r.tyz = const_cast<T *>(mm.tau[5]);
+    r.logz0 = mm.logz0;
+    r.r_off = mm.r_off;
+    r.nb_w = mm.nb_w;
+    r.nx = mm.nx;
+    r.ny = mm.ny;
+    r.plane = (int64_t)mm.nx * mm.ny;
+    r.log_phi_c = mm.log_phi_c;
+    r.kappa2 = mm.kappa2;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_regs(const WallRegs<T> &r, const BandOut<T> &o, bool is_w)
+{
+    if (is_w) {
+        r.txz[o.idx] = o.t0;
+        r.tyz[o.idx] = o.t1;
+    } else {
+        r.txx[o.idx] = o.t0;
+        r.txy[o.idx] = o.t1;
+        r.tyy[o.idx] = o.t2;
+        r.tzz[o.idx] = o.t3;
+    }
+}
+
+// Solid runs of every member of a batch over the concatenated run space
+// (runs of member m at [run_off, run_off + nr_w + nr_uv), w-runs first); the
+// same warp-cooperative scheme as zero_runs.
+template <typename T>
+__device__ void zero_runs_batch(const KParams<T> &p, int64_t gw, int64_t nwarps, int lane)
+{
+    const int64_t nruns = p.run_total;
+    int cm = -1;
+    T *oxx = nullptr, *oxy = nullptr, *oyy = nullptr, *ozz = nullptr, *oxz = nullptr, *oyz = nullptr;
+    for (int64_t base = gw; base < nruns; base += nwarps * 32) {
+        const int64_t t = base + (int64_t)lane * nwarps;
+        int2 run = make_int2(0, 0);
+        int mrun = 0, wrun = 0;
+        if (t < nruns) {
+            mrun = find_member_at(p, &Member<T>::run_off, t);
+            const Member<T> &mm = p.list[mrun];
+            const int64_t lt = t - mm.run_off;
+            wrun = lt < mm.nr_w;
+            run = __ldg(wrun ? mm.runs_w + lt : mm.runs_uv + (lt - mm.nr_w));
+        }
+        const int nq = (int)min((int64_t)32, (nruns - base + nwarps - 1) / nwarps);
+        for (int q = 0; q < nq; ++q) {
+            const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
+            const int32_t len = __shfl_sync(0xffffffffu, run.y, q);
+            const int m = __shfl_sync(0xffffffffu, mrun, q);
+            const bool is_w = __shfl_sync(0xffffffffu, wrun, q) != 0;
+            if (m != cm) {
+                const Member<T> &mm = p.list[m];
+                oxx = const_cast<T *>(mm.tau[0]); oxy = const_cast<T *>(mm.tau[1]);
+                oyy = const_cast<T *>(mm.tau[2]); ozz = const_cast<T *>(mm.tau[3]);
+                oxz = const_cast<T *>(mm.tau[4]); oyz = const_cast<T *>(mm.tau[5]);
+                cm = m;
+            }
+            for (int32_t x = lane; x < len; x += 32) {
+                const int64_t idx = (int64_t)start + x;
+                if (is_w) {
+                    oxz[idx] = T(0);
+                    oyz[idx] = T(0);
+                } else {
+                    oxx[idx] = T(0);
+                    oxy[idx] = T(0);
+                    oyy[idx] = T(0);
+                    ozz[idx] = T(0);
+                }
+            }
+        }
+    }
+}
+
 // Batch: block b takes a contiguous slice of the concatenated band records
-// (so that it meets few members) and accumulates per-member statistics in
-// shared memory, flushed to the batch scratch with global atomics; warps then
-// zero the solid runs of every member.  The last block converts the scratch
-// into wmibm_band_stats and clears it for the next call.
+// (so that it meets few members); a thread walks its records in increasing
+// order, advancing the member linearly, and accumulates the band statistics of
+// the current member in registers, flushed to per-block shared accumulators
+// when the member changes and at the end (warp-reduced when the whole warp
+// holds the same member); blocks flush those to the batch scratch with global
+// atomics.  Warps then zero the solid runs of every member, and the last block
+// converts the scratch into wmibm_band_stats and clears it for the next call.
 template <typename T, typename VEL>
 __global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
 {
@@ -616,8 +729,8 @@ __global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
     const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
     const bool want_stats = p.stats != nullptr;
     if (threadIdx.x == 0) {
-        s_m0 = r0 < r1 ? find_member_rec(p, r0) : 0;
-        s_m1 = r0 < r1 ? find_member_rec(p, r1 - 1) : -1;
+        s_m0 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r0) : 0;
+        s_m1 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r1 - 1) : -1;
     }
     __syncthreads();
     const int m0 = s_m0, m1 = s_m1;
@@ -628,31 +741,73 @@ __global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
     }
     __syncthreads();
 
-    auto account = [&](int mi, bool is_w, const BandOut<T> &o) {
-        if (!want_stats) return;
-        const int bnd = is_w ? 0 : 1;
-        atomicAdd(&s_sum[mi - m0][bnd][0], (double)o.tw);
-        atomicAdd(&s_sum[mi - m0][bnd][1], (double)o.tw * (double)o.tw);
-        atomicMax(&s_ext[mi - m0][bnd][0], ordered_bits(-(double)o.tw));
-        atomicMax(&s_ext[mi - m0][bnd][1], ordered_bits((double)o.ur));
+    T acc[kStatVals];
+    stats_identity(acc);
+    int nacc = 0;
+    auto flush = [&](int mi) {   // this lane's accumulators into member mi's shared slots
+        atomicAdd(&s_sum[mi - m0][0][0], (double)acc[0]);
+        atomicAdd(&s_sum[mi - m0][0][1], (double)acc[1]);
+        atomicMax(&s_ext[mi - m0][0][0], ordered_bits(-(double)acc[2]));
+        atomicMax(&s_ext[mi - m0][0][1], ordered_bits((double)acc[3]));
+        atomicAdd(&s_sum[mi - m0][1][0], (double)acc[4]);
+        atomicAdd(&s_sum[mi - m0][1][1], (double)acc[5]);
+        atomicMax(&s_ext[mi - m0][1][0], ordered_bits(-(double)acc[6]));
+        atomicMax(&s_ext[mi - m0][1][1], ordered_bits((double)acc[7]));
+        stats_identity(acc);
+        nacc = 0;
     };
-    for (int64_t g0 = r0 + threadIdx.x; g0 < r1; g0 += 2 * blockDim.x) {
-        const int64_t g1 = g0 + blockDim.x;
-        const int ma = find_member_rec(p, g0);
-        const Member<T> &A = p.list[ma];
-        const int64_t ta = g0 - A.r_off;
-        const BandOut<T> a = band_of<T, VEL>(A, ta);
-        const bool hb = g1 < r1;
-        const int mb = hb ? find_member_rec(p, g1) : ma;
-        const Member<T> &B = p.list[mb];
-        const int64_t tb = g1 - B.r_off;
+
+    const int bd = blockDim.x;
+    int cm = m0;
+    WallRegs<T> M;
+    load_wall(p.list[cm], M);
+    int64_t r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
+    for (int64_t g = r0 + threadIdx.x; g < r1;) {
+        if (g >= r_end) {
+            if (want_stats && nacc) flush(cm);
+            do {
+                ++cm;
+                r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
+            } while (g >= r_end);
+            load_wall(p.list[cm], M);
+        }
+        const int64_t g1 = g + bd;
+        const bool two = g1 < r1 && g1 < r_end;
+        const int64_t ta = g - M.r_off, tb = g1 - M.r_off;
+        const VEL *const vu = reinterpret_cast<const VEL *>(M.u);
+        const VEL *const vv = reinterpret_cast<const VEL *>(M.v);
+        const VEL *const vw = reinterpret_cast<const VEL *>(M.w);
+        const BandOut<T> a =
+            band_model<T, VEL>(M.rec, ta, ta < M.nb_w, vu, vv, vw, M.nx, M.ny, M.plane, M.logz0, M.log_phi_c, M.kappa2);
         BandOut<T> b;
-        if (hb) b = band_of<T, VEL>(B, tb);
-        store_band(A, a, ta < A.nb_w);
-        account(ma, ta < A.nb_w, a);
-        if (hb) {
-            store_band(B, b, tb < B.nb_w);
-            account(mb, tb < B.nb_w, b);
+        if (two)
+            b = band_model<T, VEL>(M.rec, tb, tb < M.nb_w, vu, vv, vw, M.nx, M.ny, M.plane, M.logz0, M.log_phi_c,
+                                   M.kappa2);
+        store_regs(M, a, ta < M.nb_w);
+        stats_add(acc, ta < M.nb_w ? 0 : 1, a.tw, a.ur);
+        if (two) {
+            store_regs(M, b, tb < M.nb_w);
+            stats_add(acc, tb < M.nb_w ? 0 : 1, b.tw, b.ur);
+        }
+        nacc = 1;
+        g += two ? 2 * bd : bd;
+    }
+    if (want_stats) {
+        __syncwarp();
+        const int key = nacc ? cm : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (same == 0xffffffffu) {
+            if (key >= 0) {
+                for (int bnd = 0; bnd < 2; ++bnd) {
+                    acc[4 * bnd + 0] = warp_sum(acc[4 * bnd + 0]);
+                    acc[4 * bnd + 1] = warp_sum(acc[4 * bnd + 1]);
+                    acc[4 * bnd + 2] = warp_min(acc[4 * bnd + 2]);
+                    acc[4 * bnd + 3] = warp_max(acc[4 * bnd + 3]);
+                }
+                if ((threadIdx.x & 31) == 0) flush(cm);
+            }
+        } else if (nacc) {
+            flush(cm);
         }
     }
     __syncthreads();
@@ -670,7 +825,7 @@ __global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
     // solid runs of every member
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    for (int m = 0; m < p.nmembers; ++m) zero_runs(p.list[m], gw, nwarps, threadIdx.x & 31);
+    zero_runs_batch(p, gw, nwarps, threadIdx.x & 31);
 
     if (!want_stats) return;
     __syncthreads();
@@ -1034,6 +1189,16 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
     p.nmembers = nmembers;
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
+    if (wall_blocks <= 0) {
+        // one wave of resident blocks (occupancy of this instantiation, once per process)
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wall_batch<T, VEL>, 256, 0);
+            if (e != cudaSuccess) return cuda_status(h0, e, "batch wall occupancy");
+            if (per_sm < 1) per_sm = 1;
+        }
+        wall_blocks = per_sm * h0->sm_count;
+    }
     k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, 0, stream>>>(p);
     int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
     if (st) return st;
