@@ -73,6 +73,9 @@ def _load():
                                             _D, _D]
         lib.orc_force.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double] + [_D] * 9
         lib.orc_mask.argtypes = [_I64, _I64, _I64, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double]
+        lib.orc_force_adjoint.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        lib.orc_force_adjoint.restype = None
         if hasattr(lib, "orc_adjoint"):
             lib.orc_adjoint.argtypes = ([_I64, _I64, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -122,12 +125,16 @@ def interp(grid, f, is_w, x, y, z):
     return float(_load().orc_interp(nx, ny, nz, lx, ly, lz, _p(f), int(is_w), float(x), float(y), float(z)))
 
 
-def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4):
+def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4, logz0=None):
     """Sec. 3.3 wall stress.  tau: dict of 6 float64 arrays (txx txy tyy tzz txz tyz),
-    updated in place.  z0: float or per-cell array.  Returns stats [2, 5]:
+    updated in place.  z0: float or per-cell array; or logz0: per-cell ln z0 (then
+    C = kappa^2 / (ln phi_c - ln z0)^2 and z0 is ignored).  Returns stats [2, 5]:
     rows (w-band, uv-band), columns (count, sum tau_w, sum tau_w^2, min tau_w, max U_r)."""
     nx, ny, nz, lx, ly, lz = _shape(grid)
-    if np.isscalar(z0):
+    if logz0 is not None:
+        z0a = np.ascontiguousarray(logz0, np.float64)
+        is_field = 2
+    elif np.isscalar(z0):
         z0a = np.array([float(z0)], np.float64)
         is_field = 0
     else:
@@ -168,3 +175,29 @@ def mask(grid, phi_uv, phi_w, u, v, w, gradp=None, dt=0.0):
     nx, ny, nz, *_ = _shape(grid)
     gx, gy, gz = gradp if gradp is not None else (None, None, None)
     _load().orc_mask(nx, ny, nz, _p(phi_uv), _p(phi_w), _p(u), _p(v), _p(w), _p(gx), _p(gy), _p(gz), float(dt))
+
+
+def force_adjoint(grid, g):
+    """Transpose of force(): dL/dtau for L = sum(g . f), g = (gx, gy, gz) -> dict of 6 arrays."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    shp = g[0].shape
+    out = {k: np.empty(shp, np.float64) for k in ("txx", "txy", "tyy", "tzz", "txz", "tyz")}
+    _load().orc_force_adjoint(nx, ny, nz, lx, ly, lz, _p(g[0]), _p(g[1]), _p(g[2]), _p(out["txx"]),
+                              _p(out["txy"]), _p(out["tyy"]), _p(out["tzz"]), _p(out["txz"]), _p(out["tyz"]))
+    return out
+
+
+def adjoint(grid, phi_uv, phi_w, logz0, phi_c, phi_b, u, v, w, g, kappa=0.4):
+    """Hand-derived adjoint of one stage (wall stress with per-cell ln z0, then f = -div tau)
+    for L = sum(g . f) -> (du, dv, dw, dlogz0)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    shp = u.shape
+    du, dv, dw, ds = (np.empty(shp, np.float64) for _ in range(4))
+    rc = _load().orc_adjoint(nx, ny, nz, lx, ly, lz, _p(phi_uv), _p(phi_w), _p(np.ascontiguousarray(logz0)),
+                             float(phi_c), float(kappa), float(phi_b), _p(u), _p(v), _p(w),
+                             _p(g[0]), _p(g[1]), _p(g[2]), _p(du), _p(dv), _p(dw), _p(ds))
+    if rc == -1:
+        raise ValueError("oracle: every z0 = exp(logz0) must satisfy 0 < z0 < phi_c")
+    if rc != 0:
+        raise MemoryError("oracle: no scratch memory for the adjoint")
+    return du, dv, dw, ds

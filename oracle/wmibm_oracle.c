@@ -45,6 +45,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -202,7 +203,7 @@ typedef struct {
 static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
                           int64_t i, int64_t j, int64_t k,
                           const double *u, const double *v, const double *w,
-                          double z0, double phi_c, double kappa, orc_node_result *out)
+                          double lg, double phi_c, double kappa, orc_node_result *out)
 {
     double n[3];
     normal_at(g, phi, i, j, k, n);
@@ -222,7 +223,7 @@ static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
     double Ur[3] = { uc[0] - un * n[0], uc[1] - un * n[1], uc[2] - un * n[2] };
     double ur = sqrt(Ur[0] * Ur[0] + Ur[1] * Ur[1] + Ur[2] * Ur[2]);
 
-    double lg = log(phi_c / z0);
+    /* lg = ln(phi_c / z0), passed in by the caller (see roughness_log) */
     double tw = -(kappa * ur / lg) * (kappa * ur / lg);
     out->tau_w = tw;
     out->ur = ur;
@@ -249,6 +250,18 @@ static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
                     s += e[m][a] * e[q][b] * tl[m][q];
             out->tau[a][b] = s;
         }
+}
+
+/*
+ * ln(phi_c / z0) of node p.  z0_mode 0: z0[0] is one roughness for every node;
+ * 1: z0 is a per-cell field [k][j][i] (reading R7); 2: the array holds
+ * s = ln z0 per cell and the log ratio is ln(phi_c) - s (the form the adjoint
+ * differentiates, C = kappa^2 / (ln phi_c - s)^2).
+ */
+static double roughness_log(const double *z0, int z0_mode, int64_t p, double phi_c)
+{
+    if (z0_mode == 2) return log(phi_c) - z0[p];
+    return log(phi_c / z0[z0_mode ? p : 0]);
 }
 
 /* Kahan-compensated accumulation of the band statistics. */
@@ -279,7 +292,8 @@ static void stats_add(orc_stats_acc *s, double tw, double ur)
  * through, band values are replaced by the wall model, solid values are set
  * to zero.  txz, tyz are modeled at w-band nodes; txx, txy, tyy, tzz at
  * uv-band nodes.
- * z0: scalar (z0_is_field = 0) or a per-cell field [k][j][i] (reading R7).
+ * z0: scalar (z0_is_field = 0), a per-cell field [k][j][i] (reading R7,
+ * z0_is_field = 1) or a per-cell field of ln z0 (z0_is_field = 2).
  * stats (may be NULL): 2 x {count, sum tau_w, sum tau_w^2, min tau_w, max U_r},
  * first for the w-band, then for the uv-band, count stored as a double.
  * Returns 0, or -1 if some z0 does not satisfy 0 < z0 < phi_c.
@@ -293,8 +307,10 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
 {
     orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
     int64_t n = nx * ny * nz;
-    for (int64_t p = 0; p < (z0_is_field ? n : 1); ++p)
-        if (!(z0[p] > 0.0 && z0[p] < phi_c)) return -1;
+    for (int64_t p = 0; p < (z0_is_field ? n : 1); ++p) {
+        double z = z0_is_field == 2 ? exp(z0[p]) : z0[p];
+        if (!(z > 0.0 && z < phi_c)) return -1;
+    }
 
     orc_stats_acc acc[2];
     memset(acc, 0, sizeof(acc));
@@ -310,7 +326,8 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
                     tyz[p] = 0.0;
                 } else if (c == ORC_BAND) {
                     orc_node_result r;
-                    wall_model_at(&g, phi_w, 1, i, j, k, u, v, w, z0[z0_is_field ? p : 0], phi_c, kappa, &r);
+                    wall_model_at(&g, phi_w, 1, i, j, k, u, v, w, roughness_log(z0, z0_is_field, p, phi_c), phi_c,
+                                  kappa, &r);
                     txz[p] = r.tau[0][2];
                     tyz[p] = r.tau[1][2];
                     stats_add(&acc[0], r.tau_w, r.ur);
@@ -327,7 +344,8 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
                     txx[p] = 0.0; txy[p] = 0.0; tyy[p] = 0.0; tzz[p] = 0.0;
                 } else if (c == ORC_BAND) {
                     orc_node_result r;
-                    wall_model_at(&g, phi_uv, 0, i, j, k, u, v, w, z0[z0_is_field ? p : 0], phi_c, kappa, &r);
+                    wall_model_at(&g, phi_uv, 0, i, j, k, u, v, w, roughness_log(z0, z0_is_field, p, phi_c), phi_c,
+                                  kappa, &r);
                     txx[p] = r.tau[0][0];
                     txy[p] = r.tau[0][1];
                     tyy[p] = r.tau[1][1];
@@ -360,7 +378,7 @@ void orc_wall_model_node(int64_t nx, int64_t ny, int64_t nz, double lx, double l
 {
     orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
     orc_node_result r;
-    wall_model_at(&g, phi, is_w, i, j, k, u, v, w, z0, phi_c, kappa, &r);
+    wall_model_at(&g, phi, is_w, i, j, k, u, v, w, log(phi_c / z0), phi_c, kappa, &r);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) tau9[3 * a + b] = r.tau[a][b];
     tw_ur[0] = r.tau_w;
@@ -442,4 +460,207 @@ void orc_mask(int64_t nx, int64_t ny, int64_t nz, const double *phi_uv, const do
             w[p] = gpz ? 1.5 * dt * gpz[p] : 0.0;
         }
     }
+}
+
+/* ========================================================================= */
+/* Adjoint of the stage for L = sum over nodes of (gx fx + gy fy + gz fz):   */
+/* the chain rule of the forward above, derived by hand and written out      */
+/* step by step (no automatic differentiation).  The mask (Eq. 27) changes   */
+/* the velocity after the forcing is formed, so it takes no part in dL/du.   */
+/* ========================================================================= */
+
+/*
+ * Transpose of orc_force.  Every term "f[q] -= c * tau[p]" of the forward
+ * becomes "gam[p] -= c * g[q]", with the loops and coefficients of orc_force,
+ * term by term.  gam = dL/dtau for the six stress arrays.  Sequential: the
+ * scatter would race under a parallel loop.
+ */
+void orc_force_adjoint(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                       const double *gx, const double *gy, const double *gz,
+                       double *gxx, double *gxy, double *gyy, double *gzz, double *gxz, double *gyz)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    int64_t n = nx * ny * nz;
+    for (int64_t p = 0; p < n; ++p) {
+        gxx[p] = 0.0; gxy[p] = 0.0; gyy[p] = 0.0; gzz[p] = 0.0; gxz[p] = 0.0; gyz[p] = 0.0;
+    }
+    double hx = 1.0 / (2.0 * g.dx), hy = 1.0 / (2.0 * g.dy), hz = 1.0 / g.dz;
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                int64_t ip = at(&g, wrap(i + 1, nx), j, k), im = at(&g, wrap(i - 1, nx), j, k);
+                int64_t jp = at(&g, i, wrap(j + 1, ny), k), jm = at(&g, i, wrap(j - 1, ny), k);
+                if (k < nz - 1) {
+                    int64_t kp = at(&g, i, j, k + 1);
+                    /* f_x[p] = -[(txx[ip] - txx[im]) hx + (txy[jp] - txy[jm]) hy + (txz[kp] - txz[p]) hz] */
+                    gxx[ip] -= hx * gx[p]; gxx[im] += hx * gx[p];
+                    gxy[jp] -= hy * gx[p]; gxy[jm] += hy * gx[p];
+                    gxz[kp] -= hz * gx[p]; gxz[p] += hz * gx[p];
+                    /* f_y[p] = -[(txy[ip] - txy[im]) hx + (tyy[jp] - tyy[jm]) hy + (tyz[kp] - tyz[p]) hz] */
+                    gxy[ip] -= hx * gy[p]; gxy[im] += hx * gy[p];
+                    gyy[jp] -= hy * gy[p]; gyy[jm] += hy * gy[p];
+                    gyz[kp] -= hz * gy[p]; gyz[p] += hz * gy[p];
+                }
+                if (k > 0 && k < nz - 1) {
+                    int64_t km = at(&g, i, j, k - 1);
+                    /* f_z[p] = -[(txz[ip] - txz[im]) hx + (tyz[jp] - tyz[jm]) hy + (tzz[p] - tzz[km]) hz] */
+                    gxz[ip] -= hx * gz[p]; gxz[im] += hx * gz[p];
+                    gyz[jp] -= hy * gz[p]; gyz[jm] += hy * gz[p];
+                    gzz[p] -= hz * gz[p]; gzz[km] += hz * gz[p];
+                }
+            }
+}
+
+/* Transpose of interp: adds a * (trilinear weight of each corner) to df. */
+static void interp_adjoint(const orc_grid *g, double *df, int is_w, double x, double y, double z, double a)
+{
+    double xi = x / g->dx;
+    double eta = y / g->dy;
+    double zeta = is_w ? z / g->dz : z / g->dz - 0.5;
+    int64_t top = is_w ? g->nz - 1 : g->nz - 2;
+    if (zeta < 0.0) zeta = 0.0;
+    if (zeta > (double)top) zeta = (double)top;
+
+    double fi = floor(xi), fj = floor(eta), fk = floor(zeta);
+    int64_t k0 = (int64_t)fk;
+    if (k0 > top - 1) k0 = top - 1;
+    double ax = xi - fi, ay = eta - fj, az = zeta - (double)k0;
+    int64_t i0 = wrap((int64_t)fi, g->nx), i1 = wrap((int64_t)fi + 1, g->nx);
+    int64_t j0 = wrap((int64_t)fj, g->ny), j1 = wrap((int64_t)fj + 1, g->ny);
+    int64_t k1 = k0 + 1;
+
+    df[at(g, i0, j0, k0)] += (1 - ax) * (1 - ay) * (1 - az) * a;
+    df[at(g, i1, j0, k0)] += ax * (1 - ay) * (1 - az) * a;
+    df[at(g, i0, j1, k0)] += (1 - ax) * ay * (1 - az) * a;
+    df[at(g, i1, j1, k0)] += ax * ay * (1 - az) * a;
+    df[at(g, i0, j0, k1)] += (1 - ax) * (1 - ay) * az * a;
+    df[at(g, i1, j0, k1)] += ax * (1 - ay) * az * a;
+    df[at(g, i0, j1, k1)] += (1 - ax) * ay * az * a;
+    df[at(g, i1, j1, k1)] += ax * ay * az * a;
+}
+
+/*
+ * Adjoint of the wall model at one band node.  With r = U_r, rho = |r| and the
+ * closed form of the rotated stress (Sec. 3.3; the literal rotation above
+ * equals it, which the pins check)
+ *     tau_ij = -C rho (r_i n_j + n_i r_j),
+ * and G the symmetric matrix with sum_ij G_ij tau_ij = sum over the node's
+ * stored components of gam_c tau_c, the node's part of L is
+ *     L_node = -2 C rho (r . G n).
+ * With m = G n and q = r . m:
+ *     dL/dr     = -2 C (q r / rho + rho m)
+ *     dL/du_hat = P dL/dr,  P = I - n n^T    (r = P u_hat)
+ *     dL/dC     = -2 rho q.
+ * At rho = 0 the gradient is taken as zero (the stress is zero there and its
+ * derivative in r tends to zero).  The velocity part is scattered to the
+ * interpolation corners; returns dL/dC.
+ */
+static double wall_model_adjoint_at(const orc_grid *g, const double *phi, int is_w,
+                                    int64_t i, int64_t j, int64_t k,
+                                    const double *u, const double *v, const double *w,
+                                    double lg, double phi_c, double kappa, double G[3][3],
+                                    double *du, double *dv, double *dw)
+{
+    double n[3];
+    normal_at(g, phi, i, j, k, n);
+
+    double x = (double)i * g->dx;
+    double y = (double)j * g->dy;
+    double z = is_w ? (double)k * g->dz : ((double)k + 0.5) * g->dz;
+    double d = phi_c - phi[at(g, i, j, k)];
+    double xc = x + d * n[0], yc = y + d * n[1], zc = z + d * n[2];
+
+    double uc[3];
+    uc[0] = interp(g, u, 0, xc, yc, zc);
+    uc[1] = interp(g, v, 0, xc, yc, zc);
+    uc[2] = interp(g, w, 1, xc, yc, zc);
+
+    double un = uc[0] * n[0] + uc[1] * n[1] + uc[2] * n[2];
+    double r[3] = { uc[0] - un * n[0], uc[1] - un * n[1], uc[2] - un * n[2] };
+    double rho = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (rho == 0.0) return 0.0;
+
+    double C = (kappa / lg) * (kappa / lg);
+    double m[3];
+    for (int a = 0; a < 3; ++a) m[a] = G[a][0] * n[0] + G[a][1] * n[1] + G[a][2] * n[2];
+    double q = r[0] * m[0] + r[1] * m[1] + r[2] * m[2];
+
+    double dr[3];
+    for (int a = 0; a < 3; ++a) dr[a] = -2.0 * C * (q * r[a] / rho + rho * m[a]);
+    double nd = n[0] * dr[0] + n[1] * dr[1] + n[2] * dr[2];
+    double duh[3] = { dr[0] - nd * n[0], dr[1] - nd * n[1], dr[2] - nd * n[2] };
+
+    interp_adjoint(g, du, 0, xc, yc, zc, duh[0]);
+    interp_adjoint(g, dv, 0, xc, yc, zc, duh[1]);
+    interp_adjoint(g, dw, 1, xc, yc, zc, duh[2]);
+    return -2.0 * rho * q;
+}
+
+/*
+ * Gradients of L = sum(gx fx + gy fy + gz fz) for one stage with per-cell
+ * roughness s = ln z0 (C = kappa^2 / (ln phi_c - s)^2):
+ *   du, dv, dw : dL/du, dL/dv, dL/dw (u, v on the uv-grid, w on the w-grid)
+ *   dlogz0     : dL/ds per cell; cell p collects its w-band node and its
+ *                uv-band node (reading R7), dC/ds = 2 C / (ln phi_c - s).
+ * Fluid stresses pass through and solid ones are zero, so neither depends on
+ * the velocity or on s.  Returns 0, or -1 if some z0 = exp(s) is not in
+ * (0, phi_c), or -2 if scratch memory cannot be had.
+ */
+int orc_adjoint(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                const double *phi_uv, const double *phi_w, const double *logz0,
+                double phi_c, double kappa, double phi_b,
+                const double *u, const double *v, const double *w,
+                const double *gx, const double *gy, const double *gz,
+                double *du, double *dv, double *dw, double *dlogz0)
+{
+    orc_grid g = make_grid(nx, ny, nz, lx, ly, lz);
+    int64_t n = nx * ny * nz;
+    for (int64_t p = 0; p < n; ++p) {
+        double z = exp(logz0[p]);
+        if (!(z > 0.0 && z < phi_c)) return -1;
+    }
+    double *gam = (double *)malloc(sizeof(double) * 6 * (size_t)n);
+    if (!gam) return -2;
+    double *gxx = gam, *gxy = gam + n, *gyy = gam + 2 * n, *gzz = gam + 3 * n, *gxz = gam + 4 * n,
+           *gyz = gam + 5 * n;
+    orc_force_adjoint(nx, ny, nz, lx, ly, lz, gx, gy, gz, gxx, gxy, gyy, gzz, gxz, gyz);
+
+    for (int64_t p = 0; p < n; ++p) {
+        du[p] = 0.0; dv[p] = 0.0; dw[p] = 0.0; dlogz0[p] = 0.0;
+    }
+
+    /* w-band nodes: stored components txz = tau_13, tyz = tau_23 */
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                if (classify_node(phi_w[p], phi_b, 1) != ORC_BAND) continue;
+                double G[3][3] = { { 0 } };
+                G[0][2] = G[2][0] = 0.5 * gxz[p];
+                G[1][2] = G[2][1] = 0.5 * gyz[p];
+                double lg = roughness_log(logz0, 2, p, phi_c);
+                double dC = wall_model_adjoint_at(&g, phi_w, 1, i, j, k, u, v, w, lg, phi_c, kappa, G, du, dv, dw);
+                double C = (kappa / lg) * (kappa / lg);
+                dlogz0[p] += dC * 2.0 * C / lg;
+            }
+
+    /* uv-band nodes: stored components txx, txy = tau_12, tyy, tzz */
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(&g, i, j, k);
+                if (classify_node(phi_uv[p], phi_b, 0) != ORC_BAND) continue;
+                double G[3][3] = { { 0 } };
+                G[0][0] = gxx[p];
+                G[0][1] = G[1][0] = 0.5 * gxy[p];
+                G[1][1] = gyy[p];
+                G[2][2] = gzz[p];
+                double lg = roughness_log(logz0, 2, p, phi_c);
+                double dC = wall_model_adjoint_at(&g, phi_uv, 0, i, j, k, u, v, w, lg, phi_c, kappa, G, du, dv, dw);
+                double C = (kappa / lg) * (kappa / lg);
+                dlogz0[p] += dC * 2.0 * C / lg;
+            }
+    free(gam);
+    return 0;
 }
