@@ -215,6 +215,50 @@ int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const void *v, con
                               wmibm_band_stats *stats, void *stream);
 
 /*
+ * Adjoint (gradients of one stage).  The stage is the wall stress of Sec. 3.3
+ * followed by f = -div(tau) (Eqs. 15-16, Eq. 18); the paper does not
+ * differentiate it: this is the chain rule of that computation, for a scalar
+ * L = sum over nodes of (gx fx + gy fy + gz fz) with the per-cell roughness
+ * s = ln z0 as a parameter: C = kappa^2 / (ln phi_c - s)^2.
+ *
+ * wmibm_set_log_z0 - use a per-cell ln z0 field from now on.
+ *   logz0 : DEVICE, nx*ny*nz elements of dtype, [k][j][i], the log roughness of
+ *           cell (i,j,k), shared by its uv-node and w-node; every exp(s) must
+ *           lie in (0, phi_c) (not checked).  The caller keeps the buffer alive
+ *           and unchanged while the handle uses it.  NULL returns to the z0
+ *           given at init.
+ * Every later wmibm_wall_stress, wmibm_wall_stress_noalloc, wmibm_step,
+ * wmibm_wall_stress_force and batch step of this handle computes C per node
+ * from it.  The first call also builds the transpose of the band records'
+ * trilinear gathers (host sort of 16 entries per band node, then upload; it
+ * synchronizes `stream`), so make it before any stream capture.
+ * Errors: EINVAL (misaligned logz0, more than 2^27 band nodes), ESTATE,
+ * ENOMEM, ECUDA.
+ */
+int wmibm_set_log_z0(wmibm_handle *h, const void *logz0, void *stream);
+
+/*
+ * wmibm_backward - dL/du, dL/dv, dL/dw and dL/d(ln z0) of one stage.
+ *   g      : DEVICE gx, gy (uv-grid) and gz (w-grid), dtype: the weights of L
+ *   uvw    : DEVICE u, v, w (vel_dtype): the velocity the forward pass read
+ *   du, dv, dw : DEVICE out, dtype, nx*ny*nz each: written everywhere (zero
+ *            where no band stencil reaches)
+ *   dlogz0 : DEVICE out (dtype, nx*ny*nz) or NULL: per cell, the sum of the
+ *            contributions of its w-band and uv-band nodes (zero elsewhere);
+ *            with no ln z0 field set, the derivative is taken at s = ln z0 of
+ *            init
+ * The fluid stresses pass through the stage and the solid ones are zero, so
+ * neither depends on the velocity; the stress is not differentiated.  At a
+ * band node with U_r = 0 the gradient is taken as zero.  Three kernels (the
+ * per-node chain rule, then one gather per touched node in a fixed order) and
+ * no atomics: the result is deterministic.  The first call builds the transpose
+ * map if wmibm_set_log_z0 has not (synchronizing, as above).
+ * Errors: EINVAL (NULL pointer), ESTATE, ENOMEM, ECUDA.
+ */
+int wmibm_backward(wmibm_handle *h, const void *const g[3], const void *const uvw[3], void *du, void *dv, void *dw,
+                   void *dlogz0, void *stream);
+
+/*
  * Batched ensembles: many terrains of uneven grid sizes stepped together.
  * The step of a batch is the per-step stage (wmibm_step without grad p) of
  * every member, done by two persistent launches over all members: the wall

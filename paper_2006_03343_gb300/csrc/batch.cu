@@ -90,7 +90,7 @@ int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream
     for (int m = 0; m < b->count; ++m) {
         wmibm_handle *h = b->members[m];
         const wmibm_member_fields &fl = fields[m];
-        fill_member<T>(h, host[m], (const void *const *)fl.tau, fl.f, fl.u, fl.v, fl.w, nullptr, nullptr, 0.0,
+        fill_member<T>(h, host[m], (const void *const *)fl.tau, fl.f, fl.u, fl.v, fl.w, h->logz0, nullptr, 0.0,
                        b->cfg.rows);
         Member<T> &mm = host[m];
         mm.c_off = c_off;

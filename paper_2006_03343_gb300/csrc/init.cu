@@ -300,6 +300,10 @@ void free_handle(wmibm_handle *h)
     if (h->rec) cudaFree(h->rec);
     if (h->partials) cudaFree(h->partials);
     if (h->ticket) cudaFree(h->ticket);
+    if (h->adj_keys) cudaFree(h->adj_keys);
+    if (h->adj_offs) cudaFree(h->adj_offs);
+    if (h->adj_ent) cudaFree(h->adj_ent);
+    if (h->adj_grad) cudaFree(h->adj_grad);
     free(h);
 }
 

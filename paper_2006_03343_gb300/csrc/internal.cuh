@@ -69,6 +69,13 @@ struct wmibm_handle {
     int32_t dirty_lo, dirty_hi; // stencil levels [lo, hi) whose stages read band or solid entries
     int sm_count;
     wmibm_tuning tuning;
+    const void *logz0;          // per-cell ln z0 (caller-owned, dtype) set by wmibm_set_log_z0, or NULL
+    // transpose of the trilinear gathers of the band records (adjoint), built once:
+    int32_t *adj_keys;          // touched uv-grid nodes, then touched w-grid nodes (ascending in each)
+    int32_t *adj_offs;          // [adj_m[0] + adj_m[1] + 1] offsets into adj_ent
+    int32_t *adj_ent;           // record * 8 + corner (bit 0: +x, bit 1: +y, bit 2: +z)
+    int64_t adj_m[2];
+    void *adj_grad;             // per record: dL/du_hat (3) and dL/d(ln z0) (1), dtype
     char err[512];
 };
 

@@ -122,7 +122,7 @@ extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const voi
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;
-    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, nullptr);
+    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, h->logz0);
     if (st) return st;
     return force_any(h, (const void *const *)tau, fx, fy, fz, (cudaStream_t)stream);
 }
@@ -149,7 +149,7 @@ extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *cons
     if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
         return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
     if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
-    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, nullptr);
+    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, h->logz0);
     if (st) return st;
     return force_mask_impl(h, u, v, w, tau, fx, fy, fz, gradp, 1, dt, true, (cudaStream_t)stream);
 }

@@ -89,6 +89,9 @@ struct ConsView {
     T *f[3];
     int32_t nx, ny, nz;
     T cx, cy, cz;
+    // this lane's first (row, vector column) of a stage and the step between
+    // its groups (ncons * 32 groups = dr rows + dq columns), per member
+    int32_t nq, r0, q0, dr, dq;
 };
 
 template <typename T>
@@ -202,16 +205,17 @@ struct StageIter {
             mu = load_units(*pp, m);
             new_member = true;
         }
-        const int64_t li = idx - (phase == 0 ? mu.c_off : mu.d_off);
+        // member-local unit index (fits 32 bits: a member has < 2^31 units)
+        const uint32_t li = (uint32_t)(idx - (phase == 0 ? mu.c_off : mu.d_off));
         if (phase == 0) {
-            const int32_t lc = mu.da + (mu.nz - mu.db);
+            const uint32_t lc = (uint32_t)(mu.da + (mu.nz - mu.db));
             s = (int32_t)(li / lc);
-            const int32_t r = (int32_t)(li - (int64_t)s * lc);
+            const int32_t r = (int32_t)(li - (uint32_t)s * lc);
             k = r < mu.da ? r : mu.db + (r - mu.da);
         } else {
-            const int32_t ld = mu.db - mu.da;
+            const uint32_t ld = (uint32_t)(mu.db - mu.da);
             s = (int32_t)(li / ld);
-            k = mu.da + (int32_t)(li - (int64_t)s * ld);
+            k = mu.da + (int32_t)(li - (uint32_t)s * ld);
         }
     }
     __device__ void settle()
@@ -241,6 +245,10 @@ struct StageIter {
         new_member = false;
         settle();
     }
+    // Next stage: the prologue's main stage, or the next unit in the member's
+    // order (clean: levels 0 .. da-1 then db .. nz-1 of a strip; dirty: da ..
+    // db-1), found without a division; a unit that does not continue the level
+    // sequence of the same strip starts a new segment.
     __device__ void next()
     {
         new_member = false;
@@ -249,13 +257,29 @@ struct StageIter {
             return;
         }
         ++idx;
-        if (idx < (phase == 0 ? c1 : d1)) {
-            const int32_t s0 = s, k0 = k, m0 = m;
-            locate();
-            prologue = !(m == m0 && s == s0 && k == k0 + 1);
+        if (idx >= (phase == 0 ? c1 : d1)) {
+            settle();
             return;
         }
-        settle();
+        const int32_t k0 = k;
+        int32_t kn = k + 1;
+        if (phase == 0) {
+            if (kn == mu.da) kn = mu.db;
+            if (kn >= mu.nz) {
+                ++s;
+                kn = mu.da > 0 ? 0 : mu.db;
+            }
+        } else if (kn >= mu.db) {
+            ++s;
+            kn = mu.da;
+        }
+        k = kn;
+        if (s >= mu.nstrips) {
+            locate();       // the next member with units in this phase
+            prologue = true;
+            return;
+        }
+        prologue = k != k0 + 1;
     }
 };
 
@@ -363,17 +387,23 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
     using S_ = Slots<TY>;
     constexpr int V = VecOf<T>::V;
     const int32_t nx = cv.nx;
-    const int nq = nx / V;
+    const int nq = cv.nq;
     const int groups = TY * nq;
     const int64_t plane = (int64_t)nx * cv.ny;
     const bool top = (k == cv.nz - 1);
     const bool bottom = (k == 0);
     const T cx = cv.cx, cy = cv.cy, cz = cv.cz;
+    int rl = cv.r0, ql = cv.q0;
     for (int base = cw * 32; base < groups; base += ncons * 32) {
         const int gi = base + lane;
-        const bool valid = gi < groups;
-        const int gc = valid ? gi : groups - 1;
-        const int r = gc / nq, q = gc - r * nq;
+        const bool valid = rl < TY;
+        const int r = valid ? rl : TY - 1, q = valid ? ql : nq - 1;
+        ql += cv.dq;
+        rl += cv.dr;
+        if (ql >= nq) {
+            ql -= nq;
+            ++rl;
+        }
         const int i = q * V;
         const int64_t o = (int64_t)k * plane + (int64_t)(j0 + r) * nx + i;
         Pack<T> Fx, Fy, Fz;
@@ -449,7 +479,16 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
     int prevb = -1;
     StageIter<T> it;
     for (it.init(p); !it.done; it.next(), ++g) {
-        if (it.new_member) load_cons(p, it.m, cv);
+        if (it.new_member) {
+            load_cons(p, it.m, cv);
+            constexpr int V = VecOf<T>::V;
+            cv.nq = cv.nx / V;
+            const int first = cw * 32 + lane, step = p.ncons * 32;
+            cv.r0 = first / cv.nq;
+            cv.q0 = first - cv.r0 * cv.nq;
+            cv.dr = step / cv.nq;
+            cv.dq = step - cv.dr * cv.nq;
+        }
         const int b = (int)(g % (uint32_t)p.stages);
         if (!mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)) break;
         if (!it.prologue)
@@ -1171,11 +1210,12 @@ int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const
                             cudaStream_t stream)
 {
     if (h->dtype == WMIBM_F64)
-        return launch_wall_single<double, double>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks, stream);
+        return launch_wall_single<double, double>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks,
+                                                  stream);
     if (h->vel_dtype == WMIBM_BF16)
-        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks,
+        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks,
                                                         stream);
-    return launch_wall_single<float, float>(h, tau, u, v, w, stats, nullptr, partials, ticket, blocks, stream);
+    return launch_wall_single<float, float>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks, stream);
 }
 
 // One batched step: the batch wall kernel, then the batch stencil (force + mask)

@@ -28,5 +28,5 @@ extern "C" int wmibm_wall_stress(wmibm_handle *h, const void *u, const void *v, 
         if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
     int st = check_device(h);
     if (st) return st;
-    return wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, nullptr);
+    return wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, h->logz0);
 }

@@ -28,7 +28,8 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_last_error", "wmibm_wall_stress_force", "wmibm_set_tuning", "wmibm_get_tuning",
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
-            "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy")
+            "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
+            "wmibm_backward")
 
 
 class WmibmError(RuntimeError):
@@ -123,6 +124,10 @@ def load(path: Optional[str] = None):
     L.wmibm_batch_last_error.restype = ctypes.c_char_p
     L.wmibm_batch_destroy.argtypes = [_VP]
     L.wmibm_batch_destroy.restype = None
+    L.wmibm_set_log_z0.argtypes = [_VP, _VP, _VP]
+    L.wmibm_set_log_z0.restype = ctypes.c_int
+    L.wmibm_backward.argtypes = [_VP, _PVP, _PVP, _VP, _VP, _VP, _VP, _VP]
+    L.wmibm_backward.restype = ctypes.c_int
     L.wmibm_list_size.argtypes = [_VP, ctypes.c_int32]
     L.wmibm_list_size.restype = ctypes.c_int64
     L.wmibm_export_list.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP]
@@ -228,6 +233,25 @@ class Handle:
             self._field(t)
         self._check(self._L.wmibm_wall_stress(self._h, _dptr(u), _dptr(v), _dptr(w), _ptrs(tau),
                                               None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def set_log_z0(self, logz0=None, stream=None):
+        """Use a per-cell ln z0 field (device tensor of the handle's dtype, kept alive by
+        the caller) in every later forward call; None returns to the init z0.  The
+        first call builds the adjoint's transpose map (synchronizing)."""
+        if logz0 is not None:
+            self._field(logz0)
+        self._logz0 = logz0
+        self._check(self._L.wmibm_set_log_z0(self._h, None if logz0 is None else _dptr(logz0),
+                                             _stream_ptr(stream)))
+
+    def backward(self, g: Sequence, uvw: Sequence, du, dv, dw, dlogz0=None, stream=None):
+        """dL/du, dL/dv, dL/dw (and dL/d ln z0) of one stage for L = sum(g . f)."""
+        for t in list(g) + [du, dv, dw] + ([dlogz0] if dlogz0 is not None else []):
+            self._field(t)
+        for t in uvw:
+            self._field(t, vel=True)
+        self._check(self._L.wmibm_backward(self._h, _ptrs(g), _ptrs(uvw), _dptr(du), _dptr(dv), _dptr(dw),
+                                           None if dlogz0 is None else _dptr(dlogz0), _stream_ptr(stream)))
 
     def wall_stress_noalloc(self, u, v, w, tau: Sequence, stats=None, stream=None):
         """wall_stress with the kernel's reduction scratch in a static device array
