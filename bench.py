@@ -176,13 +176,25 @@ def oracle_time(case, seconds):
     return passes * case.npoints / el / 1e9, passes, oracle.openmp_threads(), el, ref
 
 
+def aggregate_value(local_total_ms, steps, npoints, world, device=None):
+    """Whole-job throughput (Gpts/s) of `world` ranks that each stepped `steps` times
+    over `npoints` points: all ranks' points over the slowest rank's timed total (MAX
+    over ranks).  Returns (value, max total ms)."""
+    total = float(local_total_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return world * steps * npoints / (total * 1e-3) / 1e9, total
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     case = make_case(args)
-    for _ in range(max(args.warmup, 0)):
-        pass
     per_step = []
     import oracle
     oracle.build()
@@ -369,12 +381,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     status = h.device_status()
 
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * case.npoints / (total_ms * 1e-3) / 1e9
+    value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
 
     # roofline of the dominant kernel: force + mask (the pipelined stencil)
     force_bytes = h.traffic_bytes(1) + h.traffic_bytes(2)
