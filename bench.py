@@ -33,6 +33,26 @@ if ROOT not in sys.path:
 METRIC = "IBM wall-stress+forcing throughput (Gpts/s)"
 UNIT = "Gpts/s"
 L2_FLUSH_BYTES = 256 << 20
+L2_NOTE = ("flushed between steps outside the timed events: a 256 MiB write, then a 256 MiB read of another "
+           "buffer so that the write's dirty lines reach HBM before the step starts")
+
+
+class L2Flush:
+    """Between timed steps: a write of 256 MiB (twice the L2), which evicts whatever
+    the step left in L2, then a read of another 256 MiB buffer, which evicts the
+    write's dirty lines (their write-back to HBM then happens here, not inside the
+    next timed step)."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.acc = torch.zeros((), dtype=torch.float32, device=dev)
+
+    def zero_(self):
+        import torch
+        self.w.zero_()
+        torch.sum(self.r, dim=(0,), out=self.acc)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -147,15 +167,16 @@ def workload_config(args, case):
     nx, ny, nz = case.grid[:3]
     return {"workload": f"{case.name} {nx}x{ny}x{nz}", "nodes": case.npoints, "dtype": args.dtype,
             "vel_storage": args.vel_dtype or args.dtype, "phi_c": "1.5 dz", "z0": "per-cell" if not np.isscalar(
-                case.z0) else case.z0, "l2": "flushed between steps (256 MiB write, outside the timed events)"}
+                case.z0) else case.z0, "l2": L2_NOTE}
 
 
 # --------------------------------------------------------------------------- #
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------- #
 def oracle_time(case, seconds):
-    """Times the oracle's wall_stress + force + mask on full copies of the workload
-    for about `seconds` (at least one pass). Returns (Gpts/s, passes, threads)."""
+    """Times the oracle's wall_stress + force (the metric's stage) on full copies of
+    the workload for about `seconds` (at least one pass). Returns (Gpts/s, passes,
+    threads, seconds, first result)."""
     import oracle
     oracle.build()
     tau = {k: v.copy() for k, v in case.tau.items()}
@@ -168,7 +189,6 @@ def oracle_time(case, seconds):
         f = oracle.force(case.grid, tau)
         if ref is None:
             ref = ({k: t.copy() for k, t in tau.items()}, f)
-        oracle.mask(case.grid, case.phi_uv, case.phi_w, u, v, w)
         passes += 1
         el = time.perf_counter() - t0
         if el >= seconds:
@@ -204,7 +224,6 @@ def run_reference(args):
         t0 = time.perf_counter()
         oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, u, v, w, tau)
         oracle.force(case.grid, tau)
-        oracle.mask(case.grid, case.phi_uv, case.phi_w, u, v, w)
         if s >= args.warmup:
             per_step.append(time.perf_counter() - t0)
     total = sum(per_step)
@@ -215,7 +234,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args, case),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} full passes of the workload (FP64 CPU oracle)"},
+                             "sample": f"{args.steps} full passes of wall stress + force over the workload (FP64 CPU oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -249,37 +268,35 @@ class GpuForm:
         self.graphs = None
 
     def step(self, stream=None, evs=None):
-        """One pass of the stage through the C ABI: the wall-model kernel, then the
-        force + body-mask kernel (each replayed from its captured CUDA graph once
-        captured); events (if given) bracket the two launches."""
+        """One pass of the timed stage, wall stress + force (a1 + a2), through the C
+        ABI: a single cooperative launch (one graph replay once captured); events
+        (if given) bracket it."""
         if evs is not None:
             evs[0].record(stream)
         if self.graphs:
-            self.graphs[0].replay()
+            self.graphs["a12"].replay()
         else:
-            self.call.wall_stress()
+            self.call.wall_stress_force()
         if evs is not None:
             evs[1].record(stream)
-        if self.graphs:
-            self.graphs[1].replay()
-        else:
-            self.call.force_mask()
-        if evs is not None:
-            evs[2].record(stream)
 
     def capture(self):
-        """Captures the whole step (wall kernel, then the force + mask kernel as its
-        programmatic dependent) as one CUDA graph, and each of the two launches
-        as a graph of its own for the per-kernel split."""
+        """Captures the timed stage as one CUDA graph, and, for the per-part report,
+        the wall model alone, the force alone, the body mask alone and the whole
+        stage with the mask (a1 + a2 + a3)."""
         import torch
         self.step()
         torch.cuda.synchronize()
-        graphs = []
-        for fn in (self.call.wall_stress, self.call.force_mask, self.call.step):
+        fns = {"a12": self.call.wall_stress_force, "wall": self.call.wall_stress, "force": self.call.force,
+               "mask": lambda: self.h.mask(self.u, self.v, self.w), "step": self.call.step}
+        graphs = {}
+        for name, fn in fns.items():
+            fn()
+            torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 fn()
-            graphs.append(g)
+            graphs[name] = g
         torch.cuda.synchronize()
         self.graphs = graphs
 
@@ -289,30 +306,31 @@ class GpuForm:
         return ([t.double().cpu().numpy() for t in self.tau], [t.double().cpu().numpy() for t in self.f])
 
     def timed(self, stream, flush, steps):
-        """Per-step device times (ms) with CUDA events on the launching stream: the
-        whole step (one graph replay once captured), then, in a second pass, the
-        wall kernel and the force + mask kernel each from its own graph.  The L2
-        is flushed before every step, outside the events."""
-        import torch
-        events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
-        torch.cuda.synchronize()
-        for s in range(steps):
-            flush.zero_()
-            self.step(stream, events[s])
-        torch.cuda.synchronize()
-        step = [e[0].elapsed_time(e[2]) for e in events]
-        wall = [e[0].elapsed_time(e[1]) for e in events]
-        force = [e[1].elapsed_time(e[2]) for e in events]
-        if self.graphs:
-            whole = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
-            for s in range(steps):
-                flush.zero_()
-                whole[s][0].record(stream)
-                self.graphs[2].replay()
-                whole[s][1].record(stream)
-            torch.cuda.synchronize()
-            step = [e[0].elapsed_time(e[1]) for e in whole]
-        return step, wall, force
+        """Per-step device times (ms) of the timed stage with CUDA events on the
+        launching stream.  The L2 is flushed before every step, outside the events."""
+        return timed_run(self.step, stream, flush, steps)
+
+    def parts(self, stream, flush, steps):
+        """Per-part device times (ms), each part replayed from its own graph: the
+        wall model alone (a1), the force alone (a2), the body mask alone (a3) and
+        the stage with the mask (a1 + a2 + a3, one launch)."""
+        return {name: timed_run(self.graphs[name].replay, stream, flush, steps)
+                for name in ("wall", "force", "mask", "step")}
+
+
+def timed_run(fn, stream, flush, steps):
+    """CUDA-event times (ms) of `steps` calls of fn on `stream`, the L2 flushed
+    before each call outside the events."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        fn()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return [e[0].elapsed_time(e[1]) for e in ev]
 
 
 def kernel_digest():
@@ -340,7 +358,7 @@ def run_ours(args):
     case = make_case(args)
     form = GpuForm(case, args.dtype, args.vel_dtype, dev)
     h = form.h
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
 
     # one pass on the pristine inputs, kept for the accuracy report
     form.step()
@@ -359,7 +377,7 @@ def run_ours(args):
         flush.zero_()
         form.step()
     torch.cuda.synchronize()
-    eager_ms = form.timed(stream, flush, min(args.steps, 20))[0]
+    eager_ms = form.timed(stream, flush, min(args.steps, 20))
     form.capture()
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
@@ -375,19 +393,19 @@ def run_ours(args):
 
     if world > 1:
         torch.distributed.barrier()
-    step_ms, wall_ms, force_ms = form.timed(stream, flush, args.steps)
+    step_ms = form.timed(stream, flush, args.steps)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
+    parts = form.parts(stream, flush, args.steps)
     status = h.device_status()
 
     value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
 
-    # roofline of the dominant kernel: force + mask (the pipelined stencil)
-    force_bytes = h.traffic_bytes(1) + h.traffic_bytes(2)
-    step_bytes = h.traffic_bytes(0) + force_bytes
+    # roofline of the one kernel of the step: the stencil launch with the wall phase inside
+    step_bytes = h.traffic_bytes(4)          # wall-model bytes + 36 B/pt (FP32) of the force stream
     peak, peak_kind = measured_peak()
-    achieved = force_bytes / (float(np.mean(force_ms)) * 1e-3) / 1e9
+    achieved = step_bytes / (float(np.mean(step_ms)) * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload, args.dtype, args.vel_dtype)
 
     # the plain FP64 form of the same workload, timed the same way
@@ -401,11 +419,11 @@ def run_ours(args):
             flush.zero_()
             g64.step()
         g64.capture()
-        s64, _, fm64 = g64.timed(stream, flush, args.steps)
-        b64 = g64.h.traffic_bytes(0) + g64.h.traffic_bytes(1) + g64.h.traffic_bytes(2)
+        s64 = g64.timed(stream, flush, args.steps)
+        b64 = g64.h.traffic_bytes(4)
         f64_form = {"value": args.steps * case.npoints / (sum(s64) * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": float(np.mean(s64)), "step_gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
-                    "force_gbs": (g64.h.traffic_bytes(1) + g64.h.traffic_bytes(2)) / (float(np.mean(fm64)) * 1e-3) / 1e9,
+                    "bound": "FP64 arithmetic (GB300 FP64 rate), not HBM",
                     "device_status": g64.h.device_status()}
         g64.h.close()
         del g64
@@ -426,7 +444,7 @@ def run_ours(args):
                 d.copy_(s_, non_blocking=True)
             for d, s_ in zip(form.tau, host_tau):
                 d.copy_(s_, non_blocking=True)
-            h.step(form.u, form.v, form.w, form.tau, form.f, None, 0.0, form.stats)
+            h.wall_stress_force(form.u, form.v, form.w, form.tau, form.f, form.stats)
             for d, s_ in zip(host_f, form.f):
                 d.copy_(s_, non_blocking=True)
             host_stats.copy_(form.stats, non_blocking=True)
@@ -453,7 +471,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         gpts, passes, threads, el, ref = oracle_time(case, args.cpu_seconds)
         cpu = {"value": gpts, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{passes} full passes of the workload ({el:.1f} s, FP64 CPU oracle)"}
+               "sample": f"{passes} full passes of wall stress + force over the workload ({el:.1f} s, FP64 CPU oracle)"}
         accuracy = accuracy_report(first_tau, first_f, ref)
 
     if rank == 0:
@@ -463,18 +481,18 @@ def run_ours(args):
                 "config": workload_config(args, case),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "k_stencil (pipelined force + body mask)",
+                             "kernel": "k_stencil<fused> (wall phase + pipelined force, one cooperative launch)",
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                             "algorithmic_bytes_per_launch": force_bytes},
-                "kernels_ms": {"wall": float(np.mean(wall_ms)), "force_mask": float(np.mean(force_ms))},
-                "step_bytes": step_bytes,
-                "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
-                "step_frac_of_peak": step_bytes / (total_ms / args.steps * 1e-3) / 1e9 / peak,
-                "timing": "per step: CUDA events around one graph replay of the whole step (wall kernel, then "
-                          "the force + mask kernel as its programmatic dependent); kernels_ms from separate "
-                          "single-kernel graphs; eager launches: %.4f ms/step" % float(np.mean(eager_ms)),
+                             "algorithmic_bytes_per_launch": step_bytes},
+                "parts_ms": {"a1_wall_alone": float(np.mean(parts["wall"])),
+                             "a2_force_alone": float(np.mean(parts["force"])),
+                             "a3_mask_alone": float(np.mean(parts["mask"])),
+                             "a1_a2_a3_one_launch": float(np.mean(parts["step"]))},
+                "timing": "per step: CUDA events around one graph replay of wall stress + force (a1 + a2, one "
+                          "cooperative launch); parts_ms from graphs of each part alone; eager launches: "
+                          "%.4f ms/step" % float(np.mean(eager_ms)),
                 "tuning": tuned,
-                "gpu_launches": 2 * args.steps,
+                "gpu_launches": args.steps,
                 "device_status": status,
                 "f64_form": f64_form, "accuracy": accuracy,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
@@ -527,7 +545,7 @@ def run_ensemble(args):
     batch = wmibm.Batch(handles)
     batch.set_fields(fields)
     stats = batch.new_stats()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     for _ in range(max(args.warmup, 3)):
         batch.step(stats)
     torch.cuda.synchronize()
@@ -570,7 +588,7 @@ def run_ensemble(args):
             "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": f"ensemble of 64 random Gaussian-hill terrains, grids {shapes}",
-                       "nodes": points, "l2": "flushed between steps (256 MiB write, outside the timed events)"},
+                       "nodes": points, "l2": L2_NOTE},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "batch step (k_wall_batch + k_stencil)",
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",

@@ -108,8 +108,11 @@ int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double *phi_uv, co
  *   tau      : DEVICE stresses (dtype), in/out: fluid entries are left untouched,
  *              band entries are overwritten (txz, tyz on w-band nodes; txx, txy,
  *              tyy, tzz on uv-band nodes), solid entries are set to 0
- *   stats    : NULL, or DEVICE-accessible wmibm_band_stats[2] (w-band, uv-band)
- *              written by the same launch
+ *   stats    : NULL, or DEVICE-accessible wmibm_band_stats[2] (w-band, uv-band),
+ *              written on the stream after the wall kernel; sums are accumulated
+ *              per block in the path dtype, then across blocks in FP64 with
+ *              atomic reductions (so FP64 sums may differ in the last bits from
+ *              call to call; counts, minima and maxima are exact)
  * Errors: EINVAL (NULL field pointer), ESTATE, ECUDA.
  */
 int wmibm_wall_stress(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
@@ -138,17 +141,24 @@ int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gra
 
 /*
  * wmibm_step - wmibm_wall_stress, wmibm_force and wmibm_mask in that order on
- * one stream: one pass of the whole per-step stress stage, as two launches (the
- * wall-model kernel, then the force + mask kernel of wmibm_force_mask launched
- * as its programmatic dependent, which streams the levels holding no band or
- * solid node before it waits for the wall model).
+ * one stream: one pass of the whole per-step stress stage, with the same results
+ * as the three calls.  Where the pipelined stencil takes the grid (see
+ * wmibm_force_mask) and tuning.force_path is not 3, it is ONE cooperative launch:
+ * in every block the consumer warps first evaluate the block's share of the
+ * band nodes and solid runs while the producer streams the stencil stages that
+ * read no band or solid node; stages that do wait (bounded) until every block
+ * has finished its wall share; the body mask follows the forcing.  Otherwise
+ * it is two launches (the wall-model kernel, then the force + mask kernel as
+ * its programmatic dependent).  A cooperative launch needs all its blocks
+ * resident: it fails with ECUDA if another context holds the SMs it needs.
  */
 int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
                const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream);
 
 /*
  * wmibm_wall_stress_force - wmibm_wall_stress followed by wmibm_force on one
- * stream (same arguments and results as the two calls).
+ * stream (same arguments and results as the two calls); one cooperative launch
+ * under the same conditions as wmibm_step (without the body mask).
  */
 int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                             void *fx, void *fy, void *fz, wmibm_band_stats *stats, void *stream);
@@ -169,7 +179,9 @@ int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *
  * mean "choose automatically".
  */
 typedef struct wmibm_tuning {
-    int32_t force_path;       /* 0 auto, 1 bulk-copy pipeline only, 2 direct-load kernel only */
+    int32_t force_path;       /* 0 auto, 1 bulk-copy pipeline only, 2 direct-load kernel only,
+                                 3 bulk-copy pipeline with the wall model always in a kernel of its
+                                 own (no single-launch step) */
     int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
     int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
     int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */

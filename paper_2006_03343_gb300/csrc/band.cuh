@@ -69,23 +69,57 @@ struct BandOut {
     T tw, ur;         // tau_w and |U_r|
 };
 
-// Evaluates the wall model for record t (t < nb_w: a w-band node, else a uv-band node).
+// Inputs of the wall model at one band node: the record and the 8 corner
+// values of each velocity component (corner c: bit 0 = +x, bit 1 = +y, bit 2 = +z).
+template <typename T>
+struct BandIn {
+    T n0, n1, n2, C, ax, ay, azu, azw;
+    int32_t idx;
+    T cu[8], cv[8], cw[8];
+};
+
+// Loads record t and its 24 corner values (all loads independent of each
+// other once the record is in, so that callers can have several nodes' loads
+// in flight before any arithmetic).
 template <typename T, typename V>
-__device__ __forceinline__ BandOut<T> band_model(const void *rec, int64_t t, bool is_w, const V *u, const V *v,
-                                                 const V *w, int32_t nx, int32_t ny, int64_t plane, const T *logz0,
-                                                 T log_phi_c, T kappa2)
+__device__ __forceinline__ void band_fetch(const void *rec, int64_t t, const V *u, const V *v, const V *w,
+                                           int32_t nx, int32_t ny, int64_t plane, BandIn<T> &b)
 {
     using Rec = typename RecOf<T>::type;
-    T nxv, nyv, nzv, C, ax, ay, azu, azw;
     int4 ix;
-    unpack(reinterpret_cast<const Rec *>(rec), t, nxv, nyv, nzv, C, ax, ay, azu, azw, ix);
+    unpack(reinterpret_cast<const Rec *>(rec), t, b.n0, b.n1, b.n2, b.C, b.ax, b.ay, b.azu, b.azw, ix);
+    b.idx = ix.x;
     const int64_t di = (ix.w & 1) ? 1 - nx : 1;
     const int64_t dj = (ix.w & 2) ? (int64_t)(1 - ny) * nx : nx;
-    const T uc = trilinear<V, T>(u, ix.y, di, dj, plane, ax, ay, azu);
-    const T vc = trilinear<V, T>(v, ix.y, di, dj, plane, ax, ay, azu);
-    const T wc = trilinear<V, T>(w, ix.z, di, dj, plane, ax, ay, azw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int64_t o = ((c & 1) ? di : 0) + ((c & 2) ? dj : 0) + ((c & 4) ? plane : 0);
+        b.cu[c] = load_vel<V, T>(u, ix.y + o);
+        b.cv[c] = load_vel<V, T>(v, ix.y + o);
+        b.cw[c] = load_vel<V, T>(w, ix.z + o);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T trilinear8(const T *c, T ax, T ay, T az)
+{
+    const T c00 = lerp(c[0], c[1], ax), c10 = lerp(c[2], c[3], ax);
+    const T c01 = lerp(c[4], c[5], ax), c11 = lerp(c[6], c[7], ax);
+    return lerp(lerp(c00, c10, ay), lerp(c01, c11, ay), az);
+}
+
+// The wall model of a fetched node (t < nb_w: a w-band node, else uv-band).
+template <typename T>
+__device__ __forceinline__ BandOut<T> band_finish(const BandIn<T> &b, bool is_w, const T *logz0, T log_phi_c,
+                                                  T kappa2)
+{
+    const T nxv = b.n0, nyv = b.n1, nzv = b.n2;
+    T C = b.C;
+    const T uc = trilinear8(b.cu, b.ax, b.ay, b.azu);
+    const T vc = trilinear8(b.cv, b.ax, b.ay, b.azu);
+    const T wc = trilinear8(b.cw, b.ax, b.ay, b.azw);
     if (logz0) {
-        const T d = log_phi_c - __ldg(logz0 + ix.x);
+        const T d = log_phi_c - __ldg(logz0 + b.idx);
         C = kappa2 / (d * d);
     }
     const T un = uc * nxv + vc * nyv + wc * nzv;
@@ -94,7 +128,7 @@ __device__ __forceinline__ BandOut<T> band_model(const void *rec, int64_t t, boo
     const T ur = sqrt(ur2);
     const T s = -C * ur;
     BandOut<T> o;
-    o.idx = ix.x;
+    o.idx = b.idx;
     if (is_w) {
         o.t0 = s * (urx * nzv + nxv * urz);
         o.t1 = s * (ury * nzv + nyv * urz);
@@ -109,6 +143,17 @@ __device__ __forceinline__ BandOut<T> band_model(const void *rec, int64_t t, boo
     o.tw = -C * ur2;
     o.ur = ur;
     return o;
+}
+
+// Evaluates the wall model for record t (t < nb_w: a w-band node, else a uv-band node).
+template <typename T, typename V>
+__device__ __forceinline__ BandOut<T> band_model(const void *rec, int64_t t, bool is_w, const V *u, const V *v,
+                                                 const V *w, int32_t nx, int32_t ny, int64_t plane, const T *logz0,
+                                                 T log_phi_c, T kappa2)
+{
+    BandIn<T> b;
+    band_fetch<T, V>(rec, t, u, v, w, nx, ny, plane, b);
+    return band_finish<T>(b, is_w, logz0, log_phi_c, kappa2);
 }
 
 // ------------------------------------------------------------------------- //
@@ -223,6 +268,43 @@ __device__ void stats_finish(T acc[kStatVals], T (*smem)[kStatVals], T *partials
             stats[b] = st;
         }
         *ticket = 0u;
+    }
+}
+
+// Order-preserving encoding of a non-negative value for 64-bit integer atomics.
+__device__ __forceinline__ unsigned long long ordered_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x > 0.0 ? x : 0.0);
+}
+
+// Adds one block's reduced statistics (thread 0's acc) to the FP64 accumulator
+// sacc[8] = per band (sum tau_w, sum tau_w^2, bits of -min tau_w, bits of max
+// |U_r|) with fire-and-forget reductions (no fence, no wait).
+template <typename T>
+__device__ __forceinline__ void stats_red(const T acc[kStatVals], double *sacc)
+{
+    for (int b = 0; b < 2; ++b) {
+        atomicAdd(sacc + 4 * b + 0, (double)acc[4 * b + 0]);
+        atomicAdd(sacc + 4 * b + 1, (double)acc[4 * b + 1]);
+        atomicMax(reinterpret_cast<unsigned long long *>(sacc + 4 * b + 2), ordered_bits(-(double)acc[4 * b + 2]));
+        atomicMax(reinterpret_cast<unsigned long long *>(sacc + 4 * b + 3), ordered_bits((double)acc[4 * b + 3]));
+    }
+}
+
+// Converts the accumulator into wmibm_band_stats[2] and clears it for the next
+// call.  One thread, after every contribution is complete and visible.
+__device__ __forceinline__ void stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv)
+{
+    for (int b = 0; b < 2; ++b) {
+        wmibm_band_stats st;
+        st.count = b == 0 ? count_w : count_uv;
+        st.sum_tw = __ldcg(sacc + 4 * b + 0);
+        st.sum_tw2 = __ldcg(sacc + 4 * b + 1);
+        st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(sacc + 4 * b + 2)));
+        st.max_ur = __longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(sacc + 4 * b + 3)));
+        if (st.min_tw == 0.0) st.min_tw = 0.0;   // no -0 for an empty band
+        stats[b] = st;
+        for (int q = 0; q < 4; ++q) sacc[4 * b + q] = 0.0;
     }
 }
 

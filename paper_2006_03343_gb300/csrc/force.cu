@@ -194,14 +194,14 @@ void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc)
 
 bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
 int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], const StencilConfig &c,
-                  cudaStream_t stream);
+                  cudaStream_t stream, wmibm_band_stats *emit);
 
 // f = -div(tau): the bulk-copy pipeline where it applies, else the direct-load kernel.
 int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream)
 {
     void *const f[3] = {fx, fy, fz};
     StencilConfig c;
-    if (stencil_config(h, tau, f, &c)) return stencil_force(h, tau, f, c, stream);
+    if (stencil_config(h, tau, f, &c)) return stencil_force(h, tau, f, c, stream, nullptr);
     int bx, by, kc;
     force_default_tile(h, &bx, &by, &kc);
     return force_impl(h, tau, fx, fy, fz, stream, bx, by, kc);

@@ -300,6 +300,7 @@ void free_handle(wmibm_handle *h)
     if (h->rec) cudaFree(h->rec);
     if (h->partials) cudaFree(h->partials);
     if (h->ticket) cudaFree(h->ticket);
+    if (h->sacc) cudaFree(h->sacc);
     if (h->adj_keys) cudaFree(h->adj_keys);
     if (h->adj_offs) cudaFree(h->adj_offs);
     if (h->adj_ent) cudaFree(h->adj_ent);
@@ -455,8 +456,12 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device), "SM count");
         h->partial_blocks = std::max<int64_t>((h->nrec + kThreads - 1) / kThreads, 16 * (int64_t)h->sm_count);
         TRY(cudaMalloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
-        TRY(cudaMalloc(&h->ticket, sizeof(unsigned int)), "cudaMalloc ticket");
-        TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), stream), "memset ticket");
+        // [0] last-block ticket of the wall kernel, [1] wall-done and [2] exit counters of
+        // the fused step launch; all stay 0 between calls
+        TRY(cudaMalloc(&h->ticket, 4 * sizeof(unsigned int)), "cudaMalloc ticket");
+        TRY(cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned int), stream), "memset ticket");
+        TRY(cudaMalloc(&h->sacc, 8 * sizeof(double)), "cudaMalloc stats accumulator");
+        TRY(cudaMemsetAsync(h->sacc, 0, 8 * sizeof(double), stream), "memset stats accumulator");
 
         // algorithmic bytes: distinct velocity elements read by the band stencils
         TRY(cudaMalloc(&d_mark, 2 * n), "cudaMalloc marks");
@@ -632,7 +637,7 @@ extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
 {
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!t) return set_error(h, WMIBM_EINVAL, "NULL tuning");
-    if (t->force_path < 0 || t->force_path > 2) return set_error(h, WMIBM_EINVAL, "force_path must be 0, 1 or 2");
+    if (t->force_path < 0 || t->force_path > 3) return set_error(h, WMIBM_EINVAL, "force_path must be 0..3");
     if (!(t->rows == 0 || t->rows == 1 || t->rows == 2 || t->rows == 4))
         return set_error(h, WMIBM_EINVAL, "rows must be 0, 1, 2 or 4");
     if (t->stages != 0 && (t->stages < 2 || t->stages > 8)) return set_error(h, WMIBM_EINVAL, "stages must be 2..8");

@@ -59,7 +59,8 @@ struct wmibm_handle {
     void *rec;                  // band records: w-band first, then uv-band
     int64_t nrec;
     void *partials;             // per-block partial band statistics (dtype)
-    unsigned int *ticket;       // last-block detection counter, kept at 0 between calls
+    unsigned int *ticket;       // [4] counters kept at 0 between calls (wall-kernel ticket, fused-step counters)
+    double *sacc;               // [8] band-statistics accumulator, kept at 0 between calls
     int64_t partial_blocks;
     int64_t traffic[5];
     int2 *runs[2];              // solid runs along x (first node, length): w-grid, uv-grid

@@ -65,8 +65,56 @@ void force_default_tile(const wmibm_handle *h, int *bx, int *by, int *kc);
 int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream);
 bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
 int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
-                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream);
+                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream,
+                       wmibm_band_stats *emit);
+int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], const StencilConfig &c,
+                  cudaStream_t stream, wmibm_band_stats *emit);
+int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream, bool emit);
 int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt, cudaStream_t stream);
+int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
+                       const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
+                       const StencilConfig &c, cudaStream_t stream);
+
+// Wall stress + force (+ mask) as two launches: the wall kernel, then the
+// pipelined stencil, which converts the wall launch's statistics (block 0); where
+// the pipeline does not take the grid, the wall kernel converts them itself and
+// the direct-load force (and mask) kernels follow.
+static int two_launch_step(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
+                           void *fx, void *fy, void *fz, const void *const gradp[3], double dt, int do_mask,
+                           wmibm_band_stats *stats, cudaStream_t stream)
+{
+    void *const f[3] = {fx, fy, fz};
+    StencilConfig c;
+    if (stencil_config(h, (const void *const *)tau, f, &c)) {
+        int st = wall_model(h, u, v, w, tau, stats, h->logz0, stream, false);
+        if (st) return st;
+        if (do_mask)
+            return stencil_force_mask(h, const_cast<void *>(u), const_cast<void *>(v), const_cast<void *>(w),
+                                      (const void *const *)tau, f, gradp, dt, c, true, stream, stats);
+        return stencil_force(h, (const void *const *)tau, f, c, stream, stats);
+    }
+    int st = wall_model(h, u, v, w, tau, stats, h->logz0, stream, true);
+    if (st) return st;
+    st = force_any(h, (const void *const *)tau, fx, fy, fz, stream);
+    if (st || !do_mask) return st;
+    return mask_impl(h, const_cast<void *>(u), const_cast<void *>(v), const_cast<void *>(w), gradp, dt, stream);
+}
+
+// Wall stress + force (+ mask): one cooperative launch where the pipelined
+// stencil takes the grid and the tuning allows it; else returns 1 and does nothing.
+static int try_fused(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy, void *fz,
+                     const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
+                     cudaStream_t stream, int *done)
+{
+    *done = 0;
+    if (h->tuning.force_path == 3) return WMIBM_OK;
+    void *const f[3] = {fx, fy, fz};
+    StencilConfig c;
+    if (!stencil_config(h, (const void *const *)tau, f, &c)) return WMIBM_OK;
+    *done = 1;
+    return stencil_step_fused(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+}
 
 // force, then (do_mask) the body mask: one pipelined launch where the grid
 // allows, else the direct-load force kernel followed by the mask kernel.
@@ -76,7 +124,8 @@ int force_mask_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[
     void *const f[3] = {fx, fy, fz};
     StencilConfig c;
     if (stencil_config(h, (const void *const *)tau, f, &c)) {
-        if (do_mask) return stencil_force_mask(h, u, v, w, (const void *const *)tau, f, gradp, dt, c, pdl, stream);
+        if (do_mask)
+            return stencil_force_mask(h, u, v, w, (const void *const *)tau, f, gradp, dt, c, pdl, stream, nullptr);
         return force_any(h, (const void *const *)tau, fx, fy, fz, stream);
     }
     int st = force_any(h, (const void *const *)tau, fx, fy, fz, stream);
@@ -122,9 +171,11 @@ extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const voi
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;
-    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, h->logz0);
-    if (st) return st;
-    return force_any(h, (const void *const *)tau, fx, fy, fz, (cudaStream_t)stream);
+    int done = 0;
+    st = try_fused(h, const_cast<void *>(u), const_cast<void *>(v), const_cast<void *>(w), tau, fx, fy, fz, nullptr,
+                   0.0, 0, stats, (cudaStream_t)stream, &done);
+    if (st || done) return st;
+    return two_launch_step(h, u, v, w, tau, fx, fy, fz, nullptr, 0.0, 0, stats, (cudaStream_t)stream);
 }
 
 extern "C" int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *u,
@@ -149,7 +200,8 @@ extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *cons
     if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
         return set_error(h, WMIBM_EINVAL, "gradp given with a NULL component");
     if (!isfinite(dt)) return set_error(h, WMIBM_EINVAL, "dt must be finite");
-    st = wall_stress_impl(h, u, v, w, tau, stats, (cudaStream_t)stream, h->logz0);
-    if (st) return st;
-    return force_mask_impl(h, u, v, w, tau, fx, fy, fz, gradp, 1, dt, true, (cudaStream_t)stream);
+    int done = 0;
+    st = try_fused(h, u, v, w, tau, fx, fy, fz, gradp, dt, 1, stats, (cudaStream_t)stream, &done);
+    if (st || done) return st;
+    return two_launch_step(h, u, v, w, tau, fx, fy, fz, gradp, dt, 1, stats, (cudaStream_t)stream);
 }

@@ -44,6 +44,15 @@ struct KParams {
     unsigned *ticket;
     wmibm_band_stats *stats;
     double *bstats;               // batch: [nmembers][2][4] (sum, sum^2, -min bits, max bits)
+    // fused single-terrain step (wall phase inside the stencil launch): blocks that
+    // finished their wall share, and blocks that finished the launch (both back at 0
+    // after every launch)
+    unsigned *wall_done;
+    unsigned *exit_ticket;
+    // single terrain, statistics by reduction: the FP64 accumulator (handle-owned,
+    // kept at 0 between calls) and whether this launch converts it into stats
+    double *sacc;
+    int emit_stats;
 };
 
 template <typename T>

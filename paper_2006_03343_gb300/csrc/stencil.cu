@@ -301,27 +301,72 @@ __device__ __forceinline__ void wait_wall_kernel()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Launch modes of the stencil kernel.
+constexpr int kPlain = 0;       // force only: every unit is clean, no dependency
+constexpr int kAfterWall = 1;   // programmatic dependent of the wall kernel (dirty units, mask wait on it)
+constexpr int kFused = 2;       // the wall phase runs inside the launch (cooperative: all blocks resident)
+
+// Waits until *ctr >= target (acquire at GPU scope).  Gives up after
+// kWaitLimitNs, recording kDevStatusBarrierTimeout, or as soon as another wait
+// has given up.
+__device__ bool wait_counter(const unsigned *ctr, unsigned target, int *status)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(64);
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if ((it & 7u) == 0) {
+            if (*(volatile int *)status != 0) return false;
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
+                atomicExch(status, kDevStatusBarrierTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+// Barrier among the consumer warps only (named barrier 1).
+__device__ __forceinline__ void consumers_sync(int ncons)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(ncons * 32) : "memory");
+}
+
 // ------------------------------------------------------------------------- //
 // producer: lane 0 of warp 0
 // ------------------------------------------------------------------------- //
-template <typename T, int TY, bool STEP>
-__device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *empty)
+// Stages the producer of a fused launch issues before its block's wall share is
+// done (the rest waits, so that the wall model's gathers meet a quiet memory system).
+constexpr uint32_t kStagesBeforeWall = 1;
+
+template <typename T, int TY, int MODE>
+__device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *empty, uint64_t *wallbar)
 {
     using S_ = Slots<TY>;
     ProdView<T> v;
     uint32_t g = 0;
-    bool released = !STEP;
+    bool released = MODE == kPlain;
     StageIter<T> it;
     for (it.init(p); !it.done; it.next(), ++g) {
         if (it.new_member) load_prod(p, it.m, v);
+        if (MODE == kFused && g == kStagesBeforeWall) {
+            if (!mbar_wait(wallbar, 0u, p.status, kDevStatusBarrierTimeout)) break;
+        }
         const int b = (int)(g % (uint32_t)p.stages);
         if (g >= (uint32_t)p.stages) {
             if (!mbar_wait(&empty[b], ((g / p.stages) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
         }
         if (it.dirty && !released) {
-            // the stresses written by the wall kernel must be complete and visible
+            // the stresses written by the wall model must be complete and visible
             // to the bulk copies (async proxy) before a dirty stage
-            wait_wall_kernel();
+            if (MODE == kAfterWall) {
+                wait_wall_kernel();
+            } else if (!wait_counter(p.wall_done, gridDim.x, p.status)) {
+                break;
+            }
             asm volatile("fence.proxy.async.global;" ::: "memory");
             released = true;
         }
@@ -471,12 +516,22 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
     }
 }
 
-template <typename T, int TY>
-__device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane)
+template <typename T, typename VEL>
+__device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)[kStatVals]);
+
+template <typename T, typename VEL, int TY, int MODE>
+__device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane,
+                        T (*red)[kStatVals], uint64_t *wallbar)
 {
     ConsView<T> cv;
     uint32_t g = 0;
     int prevb = -1;
+    if (MODE == kFused) {
+        // the block's wall share first, while the memory system is quiet; then
+        // let the producer stream
+        wall_phase_fused<T, VEL>(p, cw, lane, red);
+        if (cw == 0 && lane == 0) mbar_arrive(wallbar);
+    }
     StageIter<T> it;
     for (it.init(p); !it.done; it.next(), ++g) {
         if (it.new_member) {
@@ -554,6 +609,19 @@ __device__ void mask_phase(const KParams<T> &p, int64_t tid, int64_t stride)
 // ------------------------------------------------------------------------- //
 // wall kernels
 // ------------------------------------------------------------------------- //
+template <typename T, typename VEL>
+__device__ __forceinline__ void fetch_of(const Member<T> &mm, int64_t t, BandIn<T> &b)
+{
+    band_fetch<T, VEL>(mm.rec, t, reinterpret_cast<const VEL *>(mm.u), reinterpret_cast<const VEL *>(mm.v),
+                       reinterpret_cast<const VEL *>(mm.w), mm.nx, mm.ny, (int64_t)mm.nx * mm.ny, b);
+}
+
+template <typename T>
+__device__ __forceinline__ BandOut<T> finish_of(const Member<T> &mm, const BandIn<T> &b, int64_t t)
+{
+    return band_finish<T>(b, t < mm.nb_w, mm.logz0, mm.log_phi_c, mm.kappa2);
+}
+
 template <typename T, typename VEL>
 __device__ __forceinline__ BandOut<T> band_of(const Member<T> &mm, int64_t t)
 {
@@ -641,16 +709,20 @@ __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     zero_runs(mm, gw, nwarps, threadIdx.x & 31);
-    if (p.stats) {
+    if (p.sacc) {
+        // statistics into the accumulator (a later launch converts them)
+        stats_block_reduce(acc, red);
+        if (threadIdx.x == 0) stats_red(acc, p.sacc);
+    } else if (p.stats) {
         stats_block_reduce(acc, red);
         stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, mm.nb_w, mm.nb_uv);
     }
 }
 
-// Order-preserving encoding of a non-negative value for 64-bit integer atomics.
-__device__ __forceinline__ unsigned long long ordered_bits(double x)
+// Converts the band-statistics accumulator of the preceding wall launch.
+__global__ void k_stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv)
 {
-    return (unsigned long long)__double_as_longlong(x > 0.0 ? x : 0.0);
+    if (threadIdx.x == 0) stats_emit(sacc, stats, count_w, count_uv);
 }
 
 // One member's wall-model fields, held in registers while a thread walks its
@@ -898,10 +970,77 @@ __global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
 // ------------------------------------------------------------------------- //
 // stencil kernel
 // ------------------------------------------------------------------------- //
-template <typename T, typename VEL, int TY, bool STEP>
+// Wall phase of the fused launch, run once by the consumer warps of every block
+// at its start; the producer issues only kStagesBeforeWall stages until the
+// block is done with it, so the gathers of the wall model meet a quiet memory
+// system.  The block's contiguous slice of band records (two per thread and round), its
+// share of the solid runs, then the band statistics reduced over the consumer
+// warps into the block's partial.  The block then counts itself into wall_done
+// (release); the block that completes the count reduces all partials into the
+// caller's stats.  Every consumer warp calls this exactly once, so the named
+// barriers inside always meet.
+template <typename T, typename VEL>
+__device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)[kStatVals])
+{
+    const Member<T> &mm = p.one;
+    const int nct = p.ncons * 32;
+    const int tid = cw * 32 + lane;
+    const int64_t R = mm.nb_w + mm.nb_uv;
+    const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    T acc[kStatVals];
+    stats_identity(acc);
+    for (int64_t t0 = r0 + tid; t0 < r1; t0 += 2 * nct) {
+        const int64_t t1 = t0 + nct;
+        BandOut<T> a, b;
+        if (sizeof(T) == 4) {
+            // FP32: both nodes' loads in flight before any arithmetic (the registers
+            // are there: the kernel is sized for the consumers)
+            BandIn<T> ia, ib;
+            fetch_of<T, VEL>(mm, t0, ia);
+            if (t1 < r1) fetch_of<T, VEL>(mm, t1, ib);
+            a = finish_of<T>(mm, ia, t0);
+            if (t1 < r1) b = finish_of<T>(mm, ib, t1);
+        } else {
+            a = band_of<T, VEL>(mm, t0);
+            if (t1 < r1) b = band_of<T, VEL>(mm, t1);
+        }
+        store_band(mm, a, t0 < mm.nb_w);
+        stats_add(acc, t0 < mm.nb_w ? 0 : 1, a.tw, a.ur);
+        if (t1 < r1) {
+            store_band(mm, b, t1 < mm.nb_w);
+            stats_add(acc, t1 < mm.nb_w ? 0 : 1, b.tw, b.ur);
+        }
+    }
+    zero_runs(mm, (int64_t)blockIdx.x * p.ncons + cw, (int64_t)gridDim.x * p.ncons, lane);
+    // this thread's stress writes: visible at GPU scope and ordered before the
+    // async-proxy reads that other blocks issue after acquiring wall_done
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __threadfence();
+
+    for (int q = 0; q < 2; ++q) {
+        acc[4 * q + 0] = warp_sum(acc[4 * q + 0]);
+        acc[4 * q + 1] = warp_sum(acc[4 * q + 1]);
+        acc[4 * q + 2] = warp_min(acc[4 * q + 2]);
+        acc[4 * q + 3] = warp_max(acc[4 * q + 3]);
+    }
+    if (lane == 0)
+        for (int v = 0; v < kStatVals; ++v) red[cw][v] = acc[v];
+    consumers_sync(p.ncons);
+    if (tid == 0) {
+        for (int w = 1; w < p.ncons; ++w) stats_combine(acc, red[w]);
+        if (p.stats) stats_red(acc, p.sacc);     // converted by the last block out of the launch
+        __threadfence();
+        atomicAdd(p.wall_done, 1u);
+    }
+}
+
+template <typename T, typename VEL, int TY, int MODE>
 __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ T red[16][kStatVals];
+    __shared__ uint64_t wallbar; // fused: the block's wall share is done
+    __shared__ int s_go;        // consumers: the wall model is complete (mask may run)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + 8;
     T *data = reinterpret_cast<T *>(smem_raw + 256);
@@ -912,32 +1051,66 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], p.ncons);
         }
+        mbar_init(&wallbar, 1);
         fence_mbar_init();
     }
     __syncthreads();
 
+    constexpr int kFirstConsumer = 1;
+    if (MODE != kFused && p.emit_stats && blockIdx.x == 0 && threadIdx.x == 0) {
+        // statistics of the wall launch before this one (complete: stream order,
+        // or the grid dependency of a programmatic launch)
+        if (MODE == kAfterWall) wait_wall_kernel();
+        stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+    }
     if (warp == 0) {
-        // producer: clean stages right away (their rows are not written by the
-        // wall kernel), dirty stages once the wall kernel has completed
-        if (lane == 0) produce<T, TY, STEP>(p, data, full, empty);
+        // producer: clean stages right away (their rows hold no band or solid
+        // entry), dirty stages once the wall model is complete
+        if (lane == 0) produce<T, TY, MODE>(p, data, full, empty, &wallbar);
         __syncwarp();
     } else {
-        consume<T, TY>(p, data, full, empty, warp - 1, lane);
-        if (STEP && p.do_mask) {
-            wait_wall_kernel();
+        const int cw = warp - kFirstConsumer;
+        consume<T, VEL, TY, MODE>(p, data, full, empty, cw, lane, red, &wallbar);
+        if (MODE != kPlain && p.do_mask) {
+            // the body mask may change the velocity only after every band stencil read it
+            bool go = true;
+            if (MODE == kAfterWall) {
+                wait_wall_kernel();
+            } else {
+                consumers_sync(p.ncons);
+                if (cw == 0 && lane == 0) s_go = wait_counter(p.wall_done, gridDim.x, p.status) ? 1 : 0;
+                consumers_sync(p.ncons);
+                go = s_go != 0;
+            }
             const int nct = p.ncons * 32;
-            mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nct + (threadIdx.x - 32), (int64_t)gridDim.x * nct);
+            if (go)
+                mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nct + (threadIdx.x - 32 * kFirstConsumer),
+                                   (int64_t)gridDim.x * nct);
+        }
+    }
+    if (MODE == kFused) {
+        // the last block out re-arms both counters for the next launch: every
+        // block has passed its waits on wall_done by then
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(p.exit_ticket, 1u) == gridDim.x - 1) {
+                __threadfence();
+                if (p.stats) stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+                atomicExch(p.wall_done, 0u);
+                atomicExch(p.exit_ticket, 0u);
+            }
         }
     }
 }
 
 constexpr int kMaxDynSmem = 200 * 1024;
 
-template <typename T, typename VEL, int TY, bool STEP>
+template <typename T, typename VEL, int TY, int MODE>
 int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl,
                       int max_nx)
 {
-    auto kern = k_stencil<T, VEL, TY, STEP>;
+    auto kern = k_stencil<T, VEL, TY, MODE>;
     static bool attr_done = false;      // once per instantiation and process
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
@@ -947,9 +1120,9 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
     const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
     if (smem > (size_t)kMaxDynSmem) return set_error(h, WMIBM_EINVAL, "stencil stages exceed shared memory");
-    const int threads = 32 * (1 + p.ncons);
+    const int threads = 32 * (1 + p.ncons);      // producer warp + consumer warps
     // occupancy of this shape, cached in the handle
-    const int key = (STEP ? 1 : 0) | (TY << 1) | (c.stages << 4) | (c.consumer_warps << 8) | (max_nx << 14);
+    const int key = MODE | (TY << 2) | (c.stages << 5) | (c.consumer_warps << 9) | (max_nx << 14);
     int per_sm = 0;
     for (int q = 0; q < 8; ++q)
         if (h->occ_key[q] == key) per_sm = h->occ_val[q];
@@ -965,17 +1138,25 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     const int64_t units = p.clean_total + p.dirty_total;
     int64_t grid = (int64_t)per_sm * h->sm_count;
     if (grid > units) grid = units;
+    // the fused wall phase writes one statistics partial per block
+    if (MODE == kFused && grid > h->partial_blocks) grid = h->partial_blocks;
     if (grid < 1) return WMIBM_OK;
-    if (STEP && pdl) {
-        // programmatic dependent of the wall kernel launched just before
+    if ((MODE == kAfterWall && pdl) || MODE == kFused) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        if (MODE == kFused) {
+            // blocks wait on each other's wall phase: all must be resident
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+        } else {
+            // programmatic dependent of the wall kernel launched just before
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+        }
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         return cuda_status(h, cudaLaunchKernelEx(&cfg, kern, p), "k_stencil launch");
@@ -984,13 +1165,13 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     return cuda_status(h, cudaGetLastError(), "k_stencil launch");
 }
 
-template <typename T, typename VEL, bool STEP>
+template <typename T, typename VEL, int MODE>
 int launch_stencil(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cudaStream_t stream, bool pdl, int max_nx)
 {
     switch (c.rows) {
-    case 1: return launch_stencil_ty<T, VEL, 1, STEP>(h, p, c, stream, pdl, max_nx);
-    case 2: return launch_stencil_ty<T, VEL, 2, STEP>(h, p, c, stream, pdl, max_nx);
-    case 4: return launch_stencil_ty<T, VEL, 4, STEP>(h, p, c, stream, pdl, max_nx);
+    case 1: return launch_stencil_ty<T, VEL, 1, MODE>(h, p, c, stream, pdl, max_nx);
+    case 2: return launch_stencil_ty<T, VEL, 2, MODE>(h, p, c, stream, pdl, max_nx);
+    case 4: return launch_stencil_ty<T, VEL, 4, MODE>(h, p, c, stream, pdl, max_nx);
     default: return set_error(h, WMIBM_EINVAL, "stencil rows must be 1, 2 or 4");
     }
 }
@@ -1023,12 +1204,16 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.ticket = h->ticket;
     p.stats = nullptr;
     p.bstats = nullptr;
+    p.wall_done = h->ticket + 1;
+    p.exit_ticket = h->ticket + 2;
+    p.sacc = h->sacc;
+    p.emit_stats = 0;
 }
 
 template <typename T, typename VEL>
 int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const void *v, const void *w,
                        wmibm_band_stats *stats, const void *logz0, void *partials, unsigned *ticket, unsigned blocks,
-                       cudaStream_t stream)
+                       bool emit, cudaStream_t stream)
 {
     KParams<T> p;
     fill_member<T>(h, p.one, (const void *const *)tau, nullptr, const_cast<void *>(u), const_cast<void *>(v),
@@ -1036,8 +1221,12 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
     single_params<T>(h, p, false);
     p.stats = stats;
     if (partials) {
+        // caller scratch: per-block partials and the last-block ticket
         p.partials = (T *)partials;
         p.ticket = ticket;
+        p.sacc = nullptr;
+    } else if (!stats) {
+        p.sacc = nullptr;
     }
     const int wthreads = blocks ? 256 : 32 * (h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 8);
     if (blocks == 0) {
@@ -1056,7 +1245,10 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
         blocks = (unsigned)std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
     }
     k_wall<T, VEL><<<blocks, wthreads, 0, stream>>>(p);
-    return cuda_status(h, cudaGetLastError(), "k_wall launch");
+    int st = cuda_status(h, cudaGetLastError(), "k_wall launch");
+    if (st || !p.sacc || !emit) return st;
+    k_stats_emit<<<1, 32, 0, stream>>>(p.sacc, stats, p.one.nb_w, p.one.nb_uv);
+    return cuda_status(h, cudaGetLastError(), "k_stats_emit launch");
 }
 
 }  // namespace
@@ -1144,8 +1336,9 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     return true;
 }
 
+// emit: NULL, or the stats of the wall launch just before, converted by block 0.
 int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], const StencilConfig &c,
-                  cudaStream_t stream)
+                  cudaStream_t stream, wmibm_band_stats *emit)
 {
     if (h->dtype == WMIBM_F64) {
         KParams<double> p;
@@ -1153,20 +1346,25 @@ int stencil_force(wmibm_handle *h, const void *const tau[6], void *const f[3], c
         single_params<double>(h, p, false);
         p.stages = c.stages;
         p.ncons = c.consumer_warps;
-        return launch_stencil<double, double, false>(h, p, c, stream, false, h->nx);
+        p.stats = emit;
+        p.emit_stats = emit != nullptr;
+        return launch_stencil<double, double, kPlain>(h, p, c, stream, false, h->nx);
     }
     KParams<float> p;
     fill_member<float>(h, p.one, tau, f, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, c.rows);
     single_params<float>(h, p, false);
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
-    return launch_stencil<float, float, false>(h, p, c, stream, false, h->nx);
+    p.stats = emit;
+    p.emit_stats = emit != nullptr;
+    return launch_stencil<float, float, kPlain>(h, p, c, stream, false, h->nx);
 }
 
 // The pipelined stencil followed, in the same launch, by the body mask (Eq. 27).
 // With pdl the launch is a programmatic dependent of the preceding kernel.
 int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const tau[6], void *const f[3],
-                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream)
+                       const void *const gradp[3], double dt, const StencilConfig &c, bool pdl, cudaStream_t stream,
+                       wmibm_band_stats *emit)
 {
     if (h->dtype == WMIBM_F64) {
         KParams<double> p;
@@ -1175,7 +1373,9 @@ int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *c
         p.stages = c.stages;
         p.ncons = c.consumer_warps;
         p.do_mask = 1;
-        return launch_stencil<double, double, true>(h, p, c, stream, pdl, h->nx);
+        p.stats = emit;
+        p.emit_stats = emit != nullptr;
+        return launch_stencil<double, double, kAfterWall>(h, p, c, stream, pdl, h->nx);
     }
     KParams<float> p;
     fill_member<float>(h, p.one, tau, f, u, v, w, nullptr, gradp, dt, c.rows);
@@ -1183,24 +1383,55 @@ int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *c
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
     p.do_mask = 1;
-    if (h->vel_dtype == WMIBM_BF16) return launch_stencil<float, __nv_bfloat16, true>(h, p, c, stream, pdl, h->nx);
-    return launch_stencil<float, float, true>(h, p, c, stream, pdl, h->nx);
+    p.stats = emit;
+    p.emit_stats = emit != nullptr;
+    if (h->vel_dtype == WMIBM_BF16)
+        return launch_stencil<float, __nv_bfloat16, kAfterWall>(h, p, c, stream, pdl, h->nx);
+    return launch_stencil<float, float, kAfterWall>(h, p, c, stream, pdl, h->nx);
+}
+
+template <typename T, typename VEL>
+int step_fused_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
+                    const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
+                    const StencilConfig &c, cudaStream_t stream)
+{
+    KParams<T> p;
+    fill_member<T>(h, p.one, (const void *const *)tau, f, u, v, w, h->logz0, gradp, dt, c.rows);
+    single_params<T>(h, p, true);
+    p.stages = c.stages;
+    p.ncons = c.consumer_warps;
+    p.do_mask = do_mask;
+    p.stats = stats;
+    return launch_stencil<T, VEL, kFused>(h, p, c, stream, false, h->nx);
+}
+
+// The whole stage in one cooperative launch: the wall model (Sec. 3.3) by the
+// consumer warps of every block while the producers stream the clean stages,
+// the forcing (Eq. 18) once the wall model is complete where a stage needs it,
+// and with do_mask the body mask (Eq. 27).
+int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
+                       const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
+                       const StencilConfig &c, cudaStream_t stream)
+{
+    if (h->dtype == WMIBM_F64)
+        return step_fused_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+    if (h->vel_dtype == WMIBM_BF16)
+        return step_fused_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+    return step_fused_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
 }
 
 // The wall model at every band node and the solid zeros (persistent kernel).
+// emit: convert the statistics here (a one-thread launch after the wall kernel);
+// false when the stencil launch that follows converts them.
 int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
-               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream)
+               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream, bool emit)
 {
-    if (stats && h->nrec == 0) {
-        cudaError_t e = cudaMemsetAsync(stats, 0, 2 * sizeof(wmibm_band_stats), stream);
-        if (e != cudaSuccess) return cuda_status(h, e, "clear stats");
-        stats = nullptr;
-    }
     if (h->dtype == WMIBM_F64)
-        return launch_wall_single<double, double>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
+        return launch_wall_single<double, double>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, emit, stream);
     if (h->vel_dtype == WMIBM_BF16)
-        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
-    return launch_wall_single<float, float>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, stream);
+        return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, emit,
+                                                        stream);
+    return launch_wall_single<float, float>(h, tau, u, v, w, stats, logz0, nullptr, nullptr, 0, emit, stream);
 }
 
 // The wall kernel with caller-provided reduction scratch and grid size (used by
@@ -1210,12 +1441,13 @@ int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const
                             cudaStream_t stream)
 {
     if (h->dtype == WMIBM_F64)
-        return launch_wall_single<double, double>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks,
+        return launch_wall_single<double, double>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks, true,
                                                   stream);
     if (h->vel_dtype == WMIBM_BF16)
         return launch_wall_single<float, __nv_bfloat16>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks,
-                                                        stream);
-    return launch_wall_single<float, float>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks, stream);
+                                                        true, stream);
+    return launch_wall_single<float, float>(h, tau, u, v, w, stats, h->logz0, partials, ticket, blocks, true,
+                                            stream);
 }
 
 // One batched step: the batch wall kernel, then the batch stencil (force + mask)
@@ -1242,7 +1474,7 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
     k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, 0, stream>>>(p);
     int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
     if (st) return st;
-    return launch_stencil<T, VEL, true>(h0, p, c, stream, true, max_nx);
+    return launch_stencil<T, VEL, kAfterWall>(h0, p, c, stream, true, max_nx);
 }
 
 template int batch_launch<float, float>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,

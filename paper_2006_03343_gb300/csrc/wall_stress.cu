@@ -3,19 +3,20 @@
 // stencil.cu: every thread of the grid evaluates band records (trilinear
 // stencils of u, v on the uv-grid and w on the w-grid at x_c, tangential part,
 // log law, rotated stress) and warps zero the solid runs; band statistics are
-// reduced per warp, per block and by the last block to finish.
+// reduced per warp and per block into an FP64 accumulator, which a one-thread
+// launch converts into the caller's stats.
 #include "internal.cuh"
 
 using namespace wmibm;
 
 namespace wmibm {
 int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
-               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream);
+               wmibm_band_stats *stats, const void *logz0, cudaStream_t stream, bool emit);
 
 int wall_stress_impl(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                      wmibm_band_stats *stats, cudaStream_t stream, const void *logz0)
 {
-    return wall_model(h, u, v, w, tau, stats, logz0, stream);
+    return wall_model(h, u, v, w, tau, stats, logz0, stream, true);
 }
 }  // namespace wmibm
 

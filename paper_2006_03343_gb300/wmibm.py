@@ -391,6 +391,10 @@ class PreparedStep:
     def force(self, stream=None):
         self.h._check(self._L.wmibm_force(self.h._h, self._tau, *self._f, _stream_ptr(stream)))
 
+    def wall_stress_force(self, stream=None):
+        self.h._check(self._L.wmibm_wall_stress_force(self.h._h, self._u, self._v, self._w, self._tau, *self._f,
+                                                      self._stats, _stream_ptr(stream)))
+
     def step(self, stream=None):
         self.h._check(self._L.wmibm_step(self.h._h, self._u, self._v, self._w, self._tau, *self._f, self._gradp,
                                          self._dt, self._stats, _stream_ptr(stream)))
