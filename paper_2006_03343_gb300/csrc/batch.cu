@@ -24,6 +24,8 @@ struct wmibm_batch {
     unsigned *ticket;
     int *status;
     int max_nx;
+    std::vector<int> rows;      // rows per strip of each member's stencil
+    uint32_t stage_elems;       // elements of the largest member stage
     int fields_set;
     wmibm_tuning tuning;
     StencilConfig cfg;
@@ -51,35 +53,48 @@ int bcuda(wmibm_batch *b, cudaError_t e, const char *what)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Tile shape shared by all members: rows dividing every ny, stages that fit the
-// widest rows.
-bool batch_config(wmibm_batch *b, StencilConfig *out)
+// Tile shape of the batch: the widest members take `rows` x-rows per strip
+// (tuning.rows, default 4); narrower members take proportionally more rows (at
+// most 16, dividing ny) so that every member's stage carries about the same
+// bytes.  The stages hold the largest member stage; as many as fit ~110 KB (2..4)
+// unless the tuning sets them.
+bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out, uint32_t *stage_elems)
 {
     const size_t es = elem_size(b->dtype);
     const int V = 16 / (int)es;
-    int rows = b->tuning.rows;
-    auto rows_ok = [&](int r) {
-        for (auto *h : b->members)
-            if (h->ny % r != 0 || h->ny < r + 2 || h->nx % V != 0 || h->nz < 3) return false;
-        return true;
-    };
-    auto stage_bytes = [&](int r) { return (size_t)(6 * r + 6) * b->max_nx * es; };
-    if (rows == 0) {
-        rows = rows_ok(2) && 3 * stage_bytes(2) <= 110 * 1024 ? 2 : 1;
+    const int base = b->tuning.rows > 0 ? b->tuning.rows : 4;
+    if (!(base == 1 || base == 2 || base == 4)) return false;
+    std::vector<int> rows;
+    size_t elems = 0;
+    for (auto *h : b->members) {
+        if (h->nx % V != 0 || h->nz < 3 || h->ny < 3) return false;
+        int target = (int)std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)base * b->max_nx / h->nx));
+        int ty = 0;
+        for (int t = target; t >= 1; --t)
+            if (h->ny % t == 0 && h->ny >= t + 2) {
+                ty = t;
+                break;
+            }
+        if (ty == 0) return false;
+        rows.push_back(ty);
+        elems = std::max(elems, (size_t)(6 * ty + 6) * h->nx);
     }
-    if (!(rows == 1 || rows == 2 || rows == 4) || !rows_ok(rows)) return false;
+    const size_t stage_bytes = elems * es;
     int stages = b->tuning.stages;
     if (stages == 0) {
         stages = 4;
-        while (stages > 2 && (size_t)stages * stage_bytes(rows) > 110 * 1024) --stages;
+        while (stages > 2 && (size_t)stages * stage_bytes > 110 * 1024) --stages;
     }
-    if (stages < 2 || stages > 8 || (size_t)stages * stage_bytes(rows) + 256 > 200 * 1024) return false;
-    out->rows = rows;
+    if (stages < 2 || stages > 8 || (size_t)stages * stage_bytes + 256 > 200 * 1024) return false;
+    out->rows = 0;                 // per member
     out->stages = stages;
     out->consumer_warps = b->tuning.consumer_warps > 0 ? b->tuning.consumer_warps : 4;
     out->wall_warps = 8;
     out->blocks_per_sm = b->tuning.blocks_per_sm;
-    return 1 + out->consumer_warps <= 16;
+    if (1 + out->consumer_warps > 16) return false;
+    *rows_out = rows;
+    *stage_elems = (uint32_t)elems;
+    return true;
 }
 
 template <typename T>
@@ -91,7 +106,7 @@ int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream
         wmibm_handle *h = b->members[m];
         const wmibm_member_fields &fl = fields[m];
         fill_member<T>(h, host[m], (const void *const *)fl.tau, fl.f, fl.u, fl.v, fl.w, h->logz0, nullptr, 0.0,
-                       b->cfg.rows);
+                       b->rows[m]);
         Member<T> &mm = host[m];
         mm.c_off = c_off;
         mm.d_off = d_off;
@@ -130,6 +145,7 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
     p.ticket = b->ticket;
     p.stats = stats;
     p.bstats = b->bstats;
+    p.stage_elems = b->stage_elems;
     const int wall_blocks = 0;   // one wave of resident blocks
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
                                   wall_blocks, stream);
@@ -172,7 +188,7 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, sizeof(unsigned), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
-    if (e != cudaSuccess || !batch_config(b, &b->cfg)) {
+    if (e != cudaSuccess || !batch_config(b, &b->cfg, &b->rows, &b->stage_elems)) {
         cudaFree(b->dev_members);
         cudaFree(b->bstats);
         cudaFree(b->ticket);
@@ -220,11 +236,15 @@ extern "C" int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t)
     wmibm_tuning old = b->tuning;
     b->tuning = *t;
     StencilConfig c;
-    if (!batch_config(b, &c)) {
+    std::vector<int> rows;
+    uint32_t elems = 0;
+    if (!batch_config(b, &c, &rows, &elems)) {
         b->tuning = old;
         return berr(b, WMIBM_EINVAL, "tuning does not fit every member");
     }
     b->cfg = c;
+    b->rows = rows;
+    b->stage_elems = elems;
     b->fields_set = 0;       // unit offsets depend on the rows per strip: set the fields again
     return WMIBM_OK;
 }

@@ -12,7 +12,7 @@ struct Member {
     const T *tau[6];              // txx txy tyy tzz txz tyz (the wall kernel writes band / solid entries)
     T *f[3];
     void *u, *v, *w;
-    int32_t nx, ny, nz, nstrips;
+    int32_t nx, ny, nz, nstrips, rows;   // rows: x-rows per strip of the stencil
     T cx, cy, cz;                 // 1/(2 dx), 1/(2 dy), 1/dz
     int32_t da, db;               // dirty levels [da, db)
     int64_t c_off, d_off;         // first index in the launch's clean / dirty unit spaces

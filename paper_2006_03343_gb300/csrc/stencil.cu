@@ -81,13 +81,13 @@ __device__ __forceinline__ void stg(double *p, const Pack<double> &x)
 template <typename T>
 struct ProdView {
     const T *tau[6];
-    int32_t nx, ny, nz;
+    int32_t nx, ny, nz, ty;
 };
 
 template <typename T>
 struct ConsView {
     T *f[3];
-    int32_t nx, ny, nz;
+    int32_t nx, ny, nz, ty;
     T cx, cy, cz;
     // this lane's first (row, vector column) of a stage and the step between
     // its groups (ncons * 32 groups = dr rows + dq columns), per member
@@ -100,12 +100,12 @@ __device__ __forceinline__ void load_prod(const KParams<T> &p, int m, ProdView<T
     if (p.nmembers == 1) {
         v.tau[0] = p.one.tau[0]; v.tau[1] = p.one.tau[1]; v.tau[2] = p.one.tau[2];
         v.tau[3] = p.one.tau[3]; v.tau[4] = p.one.tau[4]; v.tau[5] = p.one.tau[5];
-        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz;
+        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz; v.ty = p.one.rows;
     } else {
         const Member<T> *mm = p.list + m;
         v.tau[0] = mm->tau[0]; v.tau[1] = mm->tau[1]; v.tau[2] = mm->tau[2];
         v.tau[3] = mm->tau[3]; v.tau[4] = mm->tau[4]; v.tau[5] = mm->tau[5];
-        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz;
+        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz; v.ty = mm->rows;
     }
 }
 
@@ -114,12 +114,12 @@ __device__ __forceinline__ void load_cons(const KParams<T> &p, int m, ConsView<T
 {
     if (p.nmembers == 1) {
         v.f[0] = p.one.f[0]; v.f[1] = p.one.f[1]; v.f[2] = p.one.f[2];
-        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz;
+        v.nx = p.one.nx; v.ny = p.one.ny; v.nz = p.one.nz; v.ty = p.one.rows;
         v.cx = p.one.cx; v.cy = p.one.cy; v.cz = p.one.cz;
     } else {
         const Member<T> *mm = p.list + m;
         v.f[0] = mm->f[0]; v.f[1] = mm->f[1]; v.f[2] = mm->f[2];
-        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz;
+        v.nx = mm->nx; v.ny = mm->ny; v.nz = mm->nz; v.ty = mm->rows;
         v.cx = mm->cx; v.cy = mm->cy; v.cz = mm->cz;
     }
 }
@@ -283,14 +283,12 @@ struct StageIter {
     }
 };
 
-template <int TY>
+// First row of each stress slot in a stage of ty-row strips (compile-time
+// constants when the row count is a template argument).
 struct Slots {
-    static constexpr int XX = 0;
-    static constexpr int XY = TY;
-    static constexpr int YY = 2 * TY + 2;
-    static constexpr int ZZ = 3 * TY + 4;
-    static constexpr int XZ = 4 * TY + 4;
-    static constexpr int YZ = 5 * TY + 4;
+    int XX, XY, YY, ZZ, XZ, YZ;
+    __device__ __forceinline__ explicit Slots(int ty)
+        : XX(0), XY(ty), YY(2 * ty + 2), ZZ(3 * ty + 4), XZ(4 * ty + 4), YZ(5 * ty + 4) {}
 };
 
 // Waits until the preceding kernel of the stream (the wall kernel) has
@@ -345,7 +343,6 @@ constexpr uint32_t kStagesBeforeWall = 1;
 template <typename T, int TY, int MODE>
 __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *empty, uint64_t *wallbar)
 {
-    using S_ = Slots<TY>;
     ProdView<T> v;
     uint32_t g = 0;
     bool released = MODE == kPlain;
@@ -374,7 +371,9 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
         const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
         const int64_t plane = (int64_t)nx * ny;
         T *st = data + (size_t)b * p.stage_elems;
-        const int32_t j0 = it.s * TY;
+        const int ty = TY > 0 ? TY : v.ty;     // rows per strip (template or per member)
+        const Slots S_(ty);
+        const int32_t j0 = it.s * ty;
         const int32_t k = it.k;
         // rows [jstart, jstart + cnt) of one level (periodic in j) into consecutive
         // slot rows: one bulk copy per contiguous piece (two where the interval wraps)
@@ -395,22 +394,22 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
         const T *const txx = v.tau[0], *const txy = v.tau[1], *const tyy = v.tau[2];
         const T *const tzz = v.tau[3], *const txz = v.tau[4], *const tyz = v.tau[5];
         if (it.prologue) {
-            const uint32_t rows = (k > 0 ? TY : 0) + TY + (TY + 2);
+            const uint32_t rows = (k > 0 ? ty : 0) + ty + (ty + 2);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
-            if (k > 0) issue(tzz, k - 1, j0, TY, S_::ZZ);
-            issue(txz, k, j0, TY, S_::XZ);
-            issue(tyz, k, j0 - 1, TY + 2, S_::YZ);
+            if (k > 0) issue(tzz, k - 1, j0, ty, S_.ZZ);
+            issue(txz, k, j0, ty, S_.XZ);
+            issue(tyz, k, j0 - 1, ty + 2, S_.YZ);
         } else {
             const bool up = k + 1 < v.nz;
-            const uint32_t rows = TY + 2 * (TY + 2) + TY + (up ? TY + (TY + 2) : 0);
+            const uint32_t rows = ty + 2 * (ty + 2) + ty + (up ? ty + (ty + 2) : 0);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
-            issue(txx, k, j0, TY, S_::XX);
-            issue(txy, k, j0 - 1, TY + 2, S_::XY);
-            issue(tyy, k, j0 - 1, TY + 2, S_::YY);
-            issue(tzz, k, j0, TY, S_::ZZ);
+            issue(txx, k, j0, ty, S_.XX);
+            issue(txy, k, j0 - 1, ty + 2, S_.XY);
+            issue(tyy, k, j0 - 1, ty + 2, S_.YY);
+            issue(tzz, k, j0, ty, S_.ZZ);
             if (up) {
-                issue(txz, k + 1, j0, TY, S_::XZ);
-                issue(tyz, k + 1, j0 - 1, TY + 2, S_::YZ);
+                issue(txz, k + 1, j0, ty, S_.XZ);
+                issue(tyz, k + 1, j0 - 1, ty + 2, S_.YZ);
             }
         }
     }
@@ -429,11 +428,12 @@ template <typename T, int TY>
 __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, const T *prv, int32_t k, int32_t j0,
                               int cw, int lane)
 {
-    using S_ = Slots<TY>;
+    const int ty = TY > 0 ? TY : cv.ty;         // rows per strip (template or per member)
+    const Slots S_(ty);
     constexpr int V = VecOf<T>::V;
     const int32_t nx = cv.nx;
     const int nq = cv.nq;
-    const int groups = TY * nq;
+    const int groups = ty * nq;
     const int64_t plane = (int64_t)nx * cv.ny;
     const bool top = (k == cv.nz - 1);
     const bool bottom = (k == 0);
@@ -441,8 +441,8 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
     int rl = cv.r0, ql = cv.q0;
     for (int base = cw * 32; base < groups; base += ncons * 32) {
         const int gi = base + lane;
-        const bool valid = rl < TY;
-        const int r = valid ? rl : TY - 1, q = valid ? ql : nq - 1;
+        const bool valid = rl < ty;
+        const int r = valid ? rl : ty - 1, q = valid ? ql : nq - 1;
         ql += cv.dq;
         rl += cv.dr;
         if (ql >= nq) {
@@ -461,22 +461,22 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
         } else {
             const int im = (i == 0) ? nx - 1 : i - 1;
             const int ip = (i + V == nx) ? 0 : i + V;
-            const T *XXr = cur + (S_::XX + r) * nx;
-            const T *XYc = cur + (S_::XY + r + 1) * nx;
-            const T *XZ0 = prv + (S_::XZ + r) * nx;
+            const T *XXr = cur + (S_.XX + r) * nx;
+            const T *XYc = cur + (S_.XY + r + 1) * nx;
+            const T *XZ0 = prv + (S_.XZ + r) * nx;
             const Pack<T> xx = lds(XXr + i);
             const Pack<T> xy = lds(XYc + i);
-            const Pack<T> xym = lds(cur + (S_::XY + r) * nx + i), xyp = lds(cur + (S_::XY + r + 2) * nx + i);
-            const Pack<T> yym = lds(cur + (S_::YY + r) * nx + i), yyp = lds(cur + (S_::YY + r + 2) * nx + i);
-            const Pack<T> zz = lds(cur + (S_::ZZ + r) * nx + i);
-            const Pack<T> xz1 = lds(cur + (S_::XZ + r) * nx + i);
-            const Pack<T> yz1 = lds(cur + (S_::YZ + r + 1) * nx + i);
+            const Pack<T> xym = lds(cur + (S_.XY + r) * nx + i), xyp = lds(cur + (S_.XY + r + 2) * nx + i);
+            const Pack<T> yym = lds(cur + (S_.YY + r) * nx + i), yyp = lds(cur + (S_.YY + r + 2) * nx + i);
+            const Pack<T> zz = lds(cur + (S_.ZZ + r) * nx + i);
+            const Pack<T> xz1 = lds(cur + (S_.XZ + r) * nx + i);
+            const Pack<T> yz1 = lds(cur + (S_.YZ + r + 1) * nx + i);
             const Pack<T> xz0 = lds(XZ0 + i);
-            const Pack<T> yz0 = lds(prv + (S_::YZ + r + 1) * nx + i);
-            const Pack<T> yz0m = lds(prv + (S_::YZ + r) * nx + i), yz0p = lds(prv + (S_::YZ + r + 2) * nx + i);
+            const Pack<T> yz0 = lds(prv + (S_.YZ + r + 1) * nx + i);
+            const Pack<T> yz0m = lds(prv + (S_.YZ + r) * nx + i), yz0p = lds(prv + (S_.YZ + r + 2) * nx + i);
             Pack<T> zzm;
             if (!bottom)
-                zzm = lds(prv + (S_::ZZ + r) * nx + i);
+                zzm = lds(prv + (S_.ZZ + r) * nx + i);
             else
                 for (int e = 0; e < V; ++e) zzm.v[e] = T(0);
             // x-neighbours at the vector edges: from the adjacent lane when it holds
@@ -548,7 +548,7 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
         if (!mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)) break;
         if (!it.prologue)
             consume_level<T, TY>(cv, p.ncons, data + (size_t)b * p.stage_elems, data + (size_t)prevb * p.stage_elems,
-                                 it.k, it.s * TY, cw, lane);
+                                 it.k, it.s * (TY > 0 ? TY : cv.ty), cw, lane);
         if (prevb >= 0) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[prevb]);
@@ -731,7 +731,7 @@ template <typename T>
 struct WallRegs {
     const void *rec;
     const void *u, *v, *w;
-    T *txx, *txy, *tyy, *tzz, *txz, *tyz;
+    const Member<T> *src;         // the stress pointers are read from here at store time
     const T *logz0;
     int64_t r_off, nb_w, plane;
     int32_t nx, ny;
@@ -743,9 +743,7 @@ __device__ __forceinline__ void load_wall(const Member<T> &mm, WallRegs<T> &r)
 {
     r.rec = mm.rec;
     r.u = mm.u; r.v = mm.v; r.w = mm.w;
-    r.txx = const_cast<T *>(mm.tau[0]); r.txy = const_cast<T *>(mm.tau[1]);
-    r.tyy = const_cast<T *>(mm.tau[2]); r.tzz = const_cast<T *>(mm.tau[3]);
-    r.txz = const_cast<T *>(mm.tau[4]); r.tyz = const_cast<T *>(mm.tau[5]);
+    r.src = &mm;
     r.logz0 = mm.logz0;
     r.r_off = mm.r_off;
     r.nb_w = mm.nb_w;
@@ -759,15 +757,7 @@ __device__ __forceinline__ void load_wall(const Member<T> &mm, WallRegs<T> &r)
 template <typename T>
 __device__ __forceinline__ void store_regs(const WallRegs<T> &r, const BandOut<T> &o, bool is_w)
 {
-    if (is_w) {
-        r.txz[o.idx] = o.t0;
-        r.tyz[o.idx] = o.t1;
-    } else {
-        r.txx[o.idx] = o.t0;
-        r.txy[o.idx] = o.t1;
-        r.tyy[o.idx] = o.t2;
-        r.tzz[o.idx] = o.t3;
-    }
+    store_band(*r.src, o, is_w);
 }
 
 // Solid runs of every member of a batch over the concatenated run space
@@ -828,7 +818,7 @@ __device__ void zero_runs_batch(const KParams<T> &p, int64_t gw, int64_t nwarps,
 // atomics.  Warps then zero the solid runs of every member, and the last block
 // converts the scratch into wmibm_band_stats and clears it for the next call.
 template <typename T, typename VEL>
-__global__ void __launch_bounds__(256) k_wall_batch(KParams<T> p)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_wall_batch(KParams<T> p)
 {
     __shared__ double s_sum[kMaxBatchMembers][2][2];
     __shared__ unsigned long long s_ext[kMaxBatchMembers][2][2];   // (-min tau_w, max |U_r|) bits
@@ -1117,12 +1107,14 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
         if (e != cudaSuccess) return cuda_status(h, e, "stencil smem attribute");
         attr_done = true;
     }
-    p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
+    // TY == 0 (rows per member): the caller sets stage_elems to the largest member stage
+    if (TY > 0) p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
     const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
     if (smem > (size_t)kMaxDynSmem) return set_error(h, WMIBM_EINVAL, "stencil stages exceed shared memory");
     const int threads = 32 * (1 + p.ncons);      // producer warp + consumer warps
     // occupancy of this shape, cached in the handle
-    const int key = MODE | (TY << 2) | (c.stages << 5) | (c.consumer_warps << 9) | (max_nx << 14);
+    const int key = MODE | (TY << 2) | (c.stages << 5) | (c.consumer_warps << 9) |
+                    ((TY > 0 ? max_nx : (int)p.stage_elems) << 14);
     int per_sm = 0;
     for (int q = 0; q < 8; ++q)
         if (h->occ_key[q] == key) per_sm = h->occ_val[q];
@@ -1265,6 +1257,7 @@ void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], 
     m.u = u; m.v = v; m.w = w;
     m.nx = h->nx; m.ny = h->ny; m.nz = h->nz;
     m.nstrips = rows > 0 ? h->ny / rows : 0;
+    m.rows = rows;
     m.cx = (T)(1.0 / (2.0 * h->dx));
     m.cy = (T)(1.0 / (2.0 * h->dy));
     m.cz = (T)(1.0 / h->dz);
@@ -1474,7 +1467,7 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
     k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, 0, stream>>>(p);
     int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
     if (st) return st;
-    return launch_stencil<T, VEL, kAfterWall>(h0, p, c, stream, true, max_nx);
+    return launch_stencil_ty<T, VEL, 0, kAfterWall>(h0, p, c, stream, true, max_nx);
 }
 
 template int batch_launch<float, float>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
