@@ -311,6 +311,12 @@ int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t);
  */
 int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream);
 
+/*
+ * wmibm_batch_wall_stress_force - wall stress and force of every member (the
+ * step without the body mask); same launches, arguments and results otherwise.
+ */
+int wmibm_batch_wall_stress_force(wmibm_batch *b, wmibm_band_stats *stats, void *stream);
+
 /* Algorithmic bytes of one batch step: which = 0 wall kernel, 1 force + mask kernel. */
 int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which);
 

@@ -131,7 +131,7 @@ int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream
 }
 
 template <typename T, typename VEL>
-int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
+int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t stream)
 {
     KParams<T> p = {};
     p.clean_total = b->clean_total;
@@ -140,7 +140,7 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, cudaStream_t stream)
     p.run_total = b->run_total;
     p.body_total = b->body_total;
     p.status = b->status;
-    p.do_mask = 1;
+    p.do_mask = do_mask;
     p.partials = nullptr;
     p.ticket = b->ticket;
     p.stats = stats;
@@ -249,16 +249,27 @@ extern "C" int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t)
     return WMIBM_OK;
 }
 
-extern "C" int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
+static int batch_run(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, void *stream)
 {
     if (!b) return WMIBM_EINVAL;
     if (!b->fields_set) return berr(b, WMIBM_ESTATE, "wmibm_batch_set_fields must be called first");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
         return berr(b, WMIBM_ESTATE, "current device is not the batch's device");
-    if (b->dtype == WMIBM_F64) return step_impl<double, double>(b, stats, (cudaStream_t)stream);
-    if (b->vel_dtype == WMIBM_BF16) return step_impl<float, __nv_bfloat16>(b, stats, (cudaStream_t)stream);
-    return step_impl<float, float>(b, stats, (cudaStream_t)stream);
+    if (b->dtype == WMIBM_F64) return step_impl<double, double>(b, stats, do_mask, (cudaStream_t)stream);
+    if (b->vel_dtype == WMIBM_BF16)
+        return step_impl<float, __nv_bfloat16>(b, stats, do_mask, (cudaStream_t)stream);
+    return step_impl<float, float>(b, stats, do_mask, (cudaStream_t)stream);
+}
+
+extern "C" int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
+{
+    return batch_run(b, stats, 1, stream);
+}
+
+extern "C" int wmibm_batch_wall_stress_force(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
+{
+    return batch_run(b, stats, 0, stream);
 }
 
 extern "C" int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which)

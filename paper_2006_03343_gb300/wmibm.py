@@ -29,7 +29,7 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
-            "wmibm_backward")
+            "wmibm_backward", "wmibm_batch_wall_stress_force")
 
 
 class WmibmError(RuntimeError):
@@ -116,6 +116,8 @@ def load(path: Optional[str] = None):
     L.wmibm_batch_set_tuning.restype = ctypes.c_int
     L.wmibm_batch_step.argtypes = [_VP, _VP, _VP]
     L.wmibm_batch_step.restype = ctypes.c_int
+    L.wmibm_batch_wall_stress_force.argtypes = [_VP, _VP, _VP]
+    L.wmibm_batch_wall_stress_force.restype = ctypes.c_int
     L.wmibm_batch_traffic_bytes.argtypes = [_VP, ctypes.c_int32]
     L.wmibm_batch_traffic_bytes.restype = ctypes.c_int64
     L.wmibm_batch_points.argtypes = [_VP]
@@ -448,6 +450,11 @@ class Batch:
 
     def step(self, stats=None, stream=None):
         self._check(self._L.wmibm_batch_step(self._b, None if stats is None else _dptr(stats), _stream_ptr(stream)))
+
+    def wall_stress_force(self, stats=None, stream=None):
+        """Wall stress + force of every member (the step without the body mask)."""
+        self._check(self._L.wmibm_batch_wall_stress_force(self._b, None if stats is None else _dptr(stats),
+                                                          _stream_ptr(stream)))
 
     def points(self) -> int:
         return int(self._L.wmibm_batch_points(self._b))

@@ -133,3 +133,32 @@ def test_full_ensemble_64(wm, oracle_mod):
         assert_stats_close(bstats[m], st_o, "f32")
     assert batch.points() == sum(c.npoints for c in cases)
     batch.close()
+
+
+def test_batch_wall_stress_force_equals_single_calls(wm):
+    """The batch step without the mask: stresses and forcing equal the single-terrain
+    wall_stress_force of every member, and the velocity is left untouched."""
+    cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % len(SMALL_SHAPES)]) for m in range(7)]
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    fields = [_fields(c, "f32") for c in cases]
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.wall_stress_force(stats)
+    torch.cuda.synchronize()
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(len(cases), 2)
+    for m, (c, h) in enumerate(zip(cases, handles)):
+        u, v, w, tau, f = _fields(c, "f32")
+        st = h.new_stats()
+        h.wall_stress_force(u, v, w, tau, f, st)
+        torch.cuda.synchronize()
+        bu, bv, bw, btau, bf = fields[m]
+        for got, ref in zip(btau + bf, tau + f):
+            assert np.array_equal(to_host(got), to_host(ref)), m
+        for got, src in zip((bu, bv, bw), (c.u, c.v, c.w)):
+            assert np.array_equal(to_host(got), to_host(to_dev(src, "f32"))), m
+        single = h.parse_stats(st)
+        for bnd in range(2):
+            assert bstats[m][bnd]["count"] == single[bnd]["count"]
+            assert bstats[m][bnd]["sum_tw"] == pytest.approx(single[bnd]["sum_tw"], rel=1e-5)
+    batch.close()
