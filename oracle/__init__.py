@@ -82,6 +82,8 @@ def _load():
                                          _D, _D, _D, _D, _D, _D, _D, _D, _D, _D])
             lib.orc_adjoint.restype = ctypes.c_int
         lib.orc_openmp_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         _lib = lib
     return _lib
 
@@ -100,6 +102,11 @@ def _shape(grid):
 
 def openmp_threads() -> int:
     return int(_load().orc_openmp_threads())
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the oracle's parallel loops (for timing; results do not depend on it)."""
+    _load().orc_set_threads(int(n))
 
 
 def classify(grid, phi_uv, phi_w, phi_b):

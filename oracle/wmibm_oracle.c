@@ -92,6 +92,16 @@ int orc_openmp_threads(void)
 #endif
 }
 
+/* Sets the number of threads of the parallel loops (timing only; no effect on results). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* Sec. 3.3: node classification.  is_w selects the w-grid rules.            */
 /* ------------------------------------------------------------------------- */
