@@ -451,67 +451,82 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
         }
         const int i = q * V;
         const int64_t o = (int64_t)k * plane + (int64_t)(j0 + r) * nx + i;
-        Pack<T> Fx, Fy, Fz;
         if (top) {
-            for (int e = 0; e < V; ++e) {
-                Fx.v[e] = T(0);
-                Fy.v[e] = T(0);
-                Fz.v[e] = T(0);
+            Pack<T> z;
+            for (int e = 0; e < V; ++e) z.v[e] = T(0);
+            if (valid) {
+                stg(cv.f[0] + o, z);
+                stg(cv.f[1] + o, z);
+                stg(cv.f[2] + o, z);
             }
-        } else {
-            const int im = (i == 0) ? nx - 1 : i - 1;
-            const int ip = (i + V == nx) ? 0 : i + V;
+            continue;
+        }
+        const int im = (i == 0) ? nx - 1 : i - 1;
+        const int ip = (i + V == nx) ? 0 : i + V;
+        // x-neighbours at the vector edges: from the adjacent lane when it holds
+        // the adjacent vector of the same row, else from shared memory
+        const bool left_ok = lane > 0 && q > 0;
+        const bool right_ok = lane < 31 && q < nq - 1 && gi + 1 < groups;
+        auto x_neighbours = [&](const T *row, const Pack<T> &a, T &l, T &rr) {
+            l = __shfl_up_sync(0xffffffffu, a.v[V - 1], 1);
+            rr = __shfl_down_sync(0xffffffffu, a.v[0], 1);
+            if (!left_ok) l = row[im];
+            if (!right_ok) rr = row[ip];
+        };
+        // the three components one after the other, each with only its own
+        // operands live (fewer registers, more resident warps)
+        {
             const T *XXr = cur + (S_.XX + r) * nx;
-            const T *XYc = cur + (S_.XY + r + 1) * nx;
-            const T *XZ0 = prv + (S_.XZ + r) * nx;
             const Pack<T> xx = lds(XXr + i);
-            const Pack<T> xy = lds(XYc + i);
+            T xxl, xxr;
+            x_neighbours(XXr, xx, xxl, xxr);
             const Pack<T> xym = lds(cur + (S_.XY + r) * nx + i), xyp = lds(cur + (S_.XY + r + 2) * nx + i);
-            const Pack<T> yym = lds(cur + (S_.YY + r) * nx + i), yyp = lds(cur + (S_.YY + r + 2) * nx + i);
-            const Pack<T> zz = lds(cur + (S_.ZZ + r) * nx + i);
             const Pack<T> xz1 = lds(cur + (S_.XZ + r) * nx + i);
+            const Pack<T> xz0 = lds(prv + (S_.XZ + r) * nx + i);
+            Pack<T> Fx;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const T xxm_ = e == 0 ? xxl : xx.v[e - 1], xxp_ = e == V - 1 ? xxr : xx.v[e + 1];
+                Fx.v[e] = -((xxp_ - xxm_) * cx + (xyp.v[e] - xym.v[e]) * cy + (xz1.v[e] - xz0.v[e]) * cz);
+            }
+            if (valid) stg(cv.f[0] + o, Fx);
+        }
+        {
+            const T *XYc = cur + (S_.XY + r + 1) * nx;
+            const Pack<T> xy = lds(XYc + i);
+            T xyl, xyr;
+            x_neighbours(XYc, xy, xyl, xyr);
+            const Pack<T> yym = lds(cur + (S_.YY + r) * nx + i), yyp = lds(cur + (S_.YY + r + 2) * nx + i);
             const Pack<T> yz1 = lds(cur + (S_.YZ + r + 1) * nx + i);
-            const Pack<T> xz0 = lds(XZ0 + i);
             const Pack<T> yz0 = lds(prv + (S_.YZ + r + 1) * nx + i);
+            Pack<T> Fy;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const T xym_ = e == 0 ? xyl : xy.v[e - 1], xyp_ = e == V - 1 ? xyr : xy.v[e + 1];
+                Fy.v[e] = -((xyp_ - xym_) * cx + (yyp.v[e] - yym.v[e]) * cy + (yz1.v[e] - yz0.v[e]) * cz);
+            }
+            if (valid) stg(cv.f[1] + o, Fy);
+        }
+        {
+            const T *XZ0 = prv + (S_.XZ + r) * nx;
+            const Pack<T> xz0 = lds(XZ0 + i);
+            T xzl, xzr;
+            x_neighbours(XZ0, xz0, xzl, xzr);
             const Pack<T> yz0m = lds(prv + (S_.YZ + r) * nx + i), yz0p = lds(prv + (S_.YZ + r + 2) * nx + i);
+            const Pack<T> zz = lds(cur + (S_.ZZ + r) * nx + i);
             Pack<T> zzm;
             if (!bottom)
                 zzm = lds(prv + (S_.ZZ + r) * nx + i);
             else
                 for (int e = 0; e < V; ++e) zzm.v[e] = T(0);
-            // x-neighbours at the vector edges: from the adjacent lane when it holds
-            // the adjacent vector of the same row, else from shared memory
-            const unsigned full_mask = 0xffffffffu;
-            T xxl = __shfl_up_sync(full_mask, xx.v[V - 1], 1), xxr = __shfl_down_sync(full_mask, xx.v[0], 1);
-            T xyl = __shfl_up_sync(full_mask, xy.v[V - 1], 1), xyr = __shfl_down_sync(full_mask, xy.v[0], 1);
-            T xzl = __shfl_up_sync(full_mask, xz0.v[V - 1], 1), xzr = __shfl_down_sync(full_mask, xz0.v[0], 1);
-            const bool left_ok = lane > 0 && q > 0;
-            const bool right_ok = lane < 31 && q < nq - 1 && gi + 1 < groups;
-            if (!left_ok) {
-                xxl = XXr[im];
-                xyl = XYc[im];
-                xzl = XZ0[im];
-            }
-            if (!right_ok) {
-                xxr = XXr[ip];
-                xyr = XYc[ip];
-                xzr = XZ0[ip];
-            }
+            Pack<T> Fz;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-                const T xxm_ = e == 0 ? xxl : xx.v[e - 1], xxp_ = e == V - 1 ? xxr : xx.v[e + 1];
-                const T xym_ = e == 0 ? xyl : xy.v[e - 1], xyp_ = e == V - 1 ? xyr : xy.v[e + 1];
                 const T xzm_ = e == 0 ? xzl : xz0.v[e - 1], xzp_ = e == V - 1 ? xzr : xz0.v[e + 1];
-                Fx.v[e] = -((xxp_ - xxm_) * cx + (xyp.v[e] - xym.v[e]) * cy + (xz1.v[e] - xz0.v[e]) * cz);
-                Fy.v[e] = -((xyp_ - xym_) * cx + (yyp.v[e] - yym.v[e]) * cy + (yz1.v[e] - yz0.v[e]) * cz);
                 const T fz = -((xzp_ - xzm_) * cx + (yz0p.v[e] - yz0m.v[e]) * cy + (zz.v[e] - zzm.v[e]) * cz);
                 Fz.v[e] = bottom ? T(0) : fz;
             }
-        }
-        if (valid) {
-            stg(cv.f[0] + o, Fx);
-            stg(cv.f[1] + o, Fy);
-            stg(cv.f[2] + o, Fz);
+            if (valid) stg(cv.f[2] + o, Fz);
         }
     }
 }
@@ -609,19 +624,6 @@ __device__ void mask_phase(const KParams<T> &p, int64_t tid, int64_t stride)
 // ------------------------------------------------------------------------- //
 // wall kernels
 // ------------------------------------------------------------------------- //
-template <typename T, typename VEL>
-__device__ __forceinline__ void fetch_of(const Member<T> &mm, int64_t t, BandIn<T> &b)
-{
-    band_fetch<T, VEL>(mm.rec, t, reinterpret_cast<const VEL *>(mm.u), reinterpret_cast<const VEL *>(mm.v),
-                       reinterpret_cast<const VEL *>(mm.w), mm.nx, mm.ny, (int64_t)mm.nx * mm.ny, b);
-}
-
-template <typename T>
-__device__ __forceinline__ BandOut<T> finish_of(const Member<T> &mm, const BandIn<T> &b, int64_t t)
-{
-    return band_finish<T>(b, t < mm.nb_w, mm.logz0, mm.log_phi_c, mm.kappa2);
-}
-
 template <typename T, typename VEL>
 __device__ __forceinline__ BandOut<T> band_of(const Member<T> &mm, int64_t t)
 {
@@ -982,18 +984,8 @@ __device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)
     for (int64_t t0 = r0 + tid; t0 < r1; t0 += 2 * nct) {
         const int64_t t1 = t0 + nct;
         BandOut<T> a, b;
-        if (sizeof(T) == 4) {
-            // FP32: both nodes' loads in flight before any arithmetic (the registers
-            // are there: the kernel is sized for the consumers)
-            BandIn<T> ia, ib;
-            fetch_of<T, VEL>(mm, t0, ia);
-            if (t1 < r1) fetch_of<T, VEL>(mm, t1, ib);
-            a = finish_of<T>(mm, ia, t0);
-            if (t1 < r1) b = finish_of<T>(mm, ib, t1);
-        } else {
-            a = band_of<T, VEL>(mm, t0);
-            if (t1 < r1) b = band_of<T, VEL>(mm, t1);
-        }
+        a = band_of<T, VEL>(mm, t0);
+        if (t1 < r1) b = band_of<T, VEL>(mm, t1);
         store_band(mm, a, t0 < mm.nb_w);
         stats_add(acc, t0 < mm.nb_w ? 0 : 1, a.tw, a.ur);
         if (t1 < r1) {
