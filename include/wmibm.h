@@ -181,7 +181,9 @@ int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *
 typedef struct wmibm_tuning {
     int32_t force_path;       /* 0 auto, 1 bulk-copy pipeline only, 2 direct-load kernel only,
                                  3 bulk-copy pipeline with the wall model always in a kernel of its
-                                 own (no single-launch step) */
+                                 own (no single-launch step), 4 as 1 with the single-launch step's
+                                 wall model in dedicated blocks (one per SM) instead of a share of
+                                 every block */
     int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
     int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
     int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */

@@ -52,8 +52,10 @@ def candidates(handle):
             continue
         if (6 * rows + 6) * nx * es * stages + 256 > SMEM_LIMIT:
             continue
-        # one cooperative launch, or the wall kernel followed by the stencil
+        # one cooperative launch (wall share in every block, or dedicated wall
+        # blocks), or the wall kernel followed by the stencil
         out.append(dict(force_path=1, rows=rows, stages=stages, consumer_warps=cons))
+        out.append(dict(force_path=4, rows=rows, stages=stages, consumer_warps=cons))
         for wall in WALL_WARPS:
             out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall))
     return out

@@ -53,6 +53,10 @@ struct KParams {
     // kept at 0 between calls) and whether this launch converts it into stats
     double *sacc;
     int emit_stats;
+    // single-launch stage: 0 = every block's consumers evaluate a share of the wall
+    // model first; > 0 = blocks [0, wall_blocks) only evaluate the wall model and
+    // the others only stream the stencil; -1 = dedicated, chosen at launch
+    int wall_blocks;
 };
 
 template <typename T>

@@ -234,11 +234,14 @@ struct StageIter {
     __device__ void init(const KParams<T> &p)
     {
         pp = &p;
+        // the stencil blocks of the launch (dedicated wall blocks come first)
+        const int64_t wb = p.wall_blocks > 0 ? p.wall_blocks : 0;
+        const int64_t sb = blockIdx.x - wb, nsb = gridDim.x - wb;
         const int64_t C = p.clean_total, D = p.dirty_total;
-        const int64_t c0 = C * blockIdx.x / gridDim.x;
-        c1 = C * (blockIdx.x + 1) / gridDim.x;
-        d0 = D * blockIdx.x / gridDim.x;
-        d1 = D * (blockIdx.x + 1) / gridDim.x;
+        const int64_t c0 = C * sb / nsb;
+        c1 = C * (sb + 1) / nsb;
+        d0 = D * sb / nsb;
+        d1 = D * (sb + 1) / nsb;
         m = -1;
         phase = 0;
         idx = c0;
@@ -333,6 +336,12 @@ __device__ __forceinline__ void consumers_sync(int ncons)
     asm volatile("bar.sync 1, %0;" ::"r"(ncons * 32) : "memory");
 }
 
+// Blocks that count themselves into wall_done in a single-launch stage.
+__device__ __forceinline__ unsigned wall_target(int wall_blocks)
+{
+    return wall_blocks > 0 ? (unsigned)wall_blocks : gridDim.x;
+}
+
 // ------------------------------------------------------------------------- //
 // producer: lane 0 of warp 0
 // ------------------------------------------------------------------------- //
@@ -349,7 +358,7 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
     StageIter<T> it;
     for (it.init(p); !it.done; it.next(), ++g) {
         if (it.new_member) load_prod(p, it.m, v);
-        if (MODE == kFused && g == kStagesBeforeWall) {
+        if (MODE == kFused && p.wall_blocks == 0 && g == kStagesBeforeWall) {
             if (!mbar_wait(wallbar, 0u, p.status, kDevStatusBarrierTimeout)) break;
         }
         const int b = (int)(g % (uint32_t)p.stages);
@@ -361,7 +370,7 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
             // to the bulk copies (async proxy) before a dirty stage
             if (MODE == kAfterWall) {
                 wait_wall_kernel();
-            } else if (!wait_counter(p.wall_done, gridDim.x, p.status)) {
+            } else if (!wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status)) {
                 break;
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -532,7 +541,8 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
 }
 
 template <typename T, typename VEL>
-__device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)[kStatVals]);
+__device__ void wall_phase_fused(const KParams<T> &p, int64_t wb, int64_t nwb, int cw, int nwarps, int lane,
+                                 T (*red)[kStatVals]);
 
 template <typename T, typename VEL, int TY, int MODE>
 __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane,
@@ -541,10 +551,10 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
     ConsView<T> cv;
     uint32_t g = 0;
     int prevb = -1;
-    if (MODE == kFused) {
+    if (MODE == kFused && p.wall_blocks == 0) {
         // the block's wall share first, while the memory system is quiet; then
         // let the producer stream
-        wall_phase_fused<T, VEL>(p, cw, lane, red);
+        wall_phase_fused<T, VEL>(p, blockIdx.x, gridDim.x, cw, p.ncons, lane, red);
         if (cw == 0 && lane == 0) mbar_arrive(wallbar);
     }
     StageIter<T> it;
@@ -972,13 +982,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_wall_batch(KPar
 // caller's stats.  Every consumer warp calls this exactly once, so the named
 // barriers inside always meet.
 template <typename T, typename VEL>
-__device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)[kStatVals])
+__device__ void wall_phase_fused(const KParams<T> &p, int64_t wb, int64_t nwb, int cw, int nwarps, int lane,
+                                 T (*red)[kStatVals])
 {
     const Member<T> &mm = p.one;
-    const int nct = p.ncons * 32;
+    const int nct = nwarps * 32;
     const int tid = cw * 32 + lane;
     const int64_t R = mm.nb_w + mm.nb_uv;
-    const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    const int64_t r0 = R * wb / nwb, r1 = R * (wb + 1) / nwb;
     T acc[kStatVals];
     stats_identity(acc);
     for (int64_t t0 = r0 + tid; t0 < r1; t0 += 2 * nct) {
@@ -993,7 +1004,7 @@ __device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)
             stats_add(acc, t1 < mm.nb_w ? 0 : 1, b.tw, b.ur);
         }
     }
-    zero_runs(mm, (int64_t)blockIdx.x * p.ncons + cw, (int64_t)gridDim.x * p.ncons, lane);
+    zero_runs(mm, wb * nwarps + cw, nwb * nwarps, lane);
     // this thread's stress writes: visible at GPU scope and ordered before the
     // async-proxy reads that other blocks issue after acquiring wall_done
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1007,9 +1018,9 @@ __device__ void wall_phase_fused(const KParams<T> &p, int cw, int lane, T (*red)
     }
     if (lane == 0)
         for (int v = 0; v < kStatVals; ++v) red[cw][v] = acc[v];
-    consumers_sync(p.ncons);
+    consumers_sync(nwarps);
     if (tid == 0) {
-        for (int w = 1; w < p.ncons; ++w) stats_combine(acc, red[w]);
+        for (int w = 1; w < nwarps; ++w) stats_combine(acc, red[w]);
         if (p.stats) stats_red(acc, p.sacc);     // converted by the last block out of the launch
         __threadfence();
         atomicAdd(p.wall_done, 1u);
@@ -1045,7 +1056,10 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         if (MODE == kAfterWall) wait_wall_kernel();
         stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
     }
-    if (warp == 0) {
+    if (MODE == kFused && p.wall_blocks > 0 && (int)blockIdx.x < p.wall_blocks) {
+        // dedicated wall block: every warp evaluates the block's share of the wall model
+        wall_phase_fused<T, VEL>(p, blockIdx.x, p.wall_blocks, warp, blockDim.x >> 5, lane, red);
+    } else if (warp == 0) {
         // producer: clean stages right away (their rows hold no band or solid
         // entry), dirty stages once the wall model is complete
         if (lane == 0) produce<T, TY, MODE>(p, data, full, empty, &wallbar);
@@ -1060,14 +1074,18 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
                 wait_wall_kernel();
             } else {
                 consumers_sync(p.ncons);
-                if (cw == 0 && lane == 0) s_go = wait_counter(p.wall_done, gridDim.x, p.status) ? 1 : 0;
+                if (cw == 0 && lane == 0)
+                    s_go = wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status) ? 1 : 0;
                 consumers_sync(p.ncons);
                 go = s_go != 0;
             }
+            // over the consumer threads of the stencil blocks (dedicated wall blocks
+            // come first and take no part)
             const int nct = p.ncons * 32;
+            const int64_t wb = (MODE == kFused && p.wall_blocks > 0) ? p.wall_blocks : 0;
             if (go)
-                mask_phase<T, VEL>(p, (int64_t)blockIdx.x * nct + (threadIdx.x - 32 * kFirstConsumer),
-                                   (int64_t)gridDim.x * nct);
+                mask_phase<T, VEL>(p, ((int64_t)blockIdx.x - wb) * nct + (threadIdx.x - 32 * kFirstConsumer),
+                                   ((int64_t)gridDim.x - wb) * nct);
         }
     }
     if (MODE == kFused) {
@@ -1122,9 +1140,17 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     const int64_t units = p.clean_total + p.dirty_total;
     int64_t grid = (int64_t)per_sm * h->sm_count;
     if (grid > units) grid = units;
-    // the fused wall phase writes one statistics partial per block
-    if (MODE == kFused && grid > h->partial_blocks) grid = h->partial_blocks;
     if (grid < 1) return WMIBM_OK;
+    if (MODE == kFused && p.wall_blocks < 0) {
+        // dedicated wall blocks: one per SM when the grid has at least two blocks
+        // per SM, else a quarter of it; the grid grows by them (up to the resident
+        // limit) so that the stencil keeps its blocks
+        const int64_t resident = (int64_t)per_sm * h->sm_count;
+        int64_t wbk = grid >= 2 * (int64_t)h->sm_count ? h->sm_count : std::max<int64_t>(1, grid / 4);
+        grid = std::min<int64_t>(grid + wbk, resident);
+        if (grid - wbk < 1) wbk = grid - 1;
+        p.wall_blocks = wbk > 0 ? (int)wbk : 0;
+    }
     if ((MODE == kAfterWall && pdl) || MODE == kFused) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
@@ -1192,6 +1218,7 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.exit_ticket = h->ticket + 2;
     p.sacc = h->sacc;
     p.emit_stats = 0;
+    p.wall_blocks = 0;
 }
 
 template <typename T, typename VEL>
@@ -1378,7 +1405,7 @@ int stencil_force_mask(wmibm_handle *h, void *u, void *v, void *w, const void *c
 template <typename T, typename VEL>
 int step_fused_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
                     const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
-                    const StencilConfig &c, cudaStream_t stream)
+                    const StencilConfig &c, bool dedicated, cudaStream_t stream)
 {
     KParams<T> p;
     fill_member<T>(h, p.one, (const void *const *)tau, f, u, v, w, h->logz0, gradp, dt, c.rows);
@@ -1387,6 +1414,7 @@ int step_fused_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[
     p.ncons = c.consumer_warps;
     p.do_mask = do_mask;
     p.stats = stats;
+    p.wall_blocks = dedicated ? -1 : 0;
     return launch_stencil<T, VEL, kFused>(h, p, c, stream, false, h->nx);
 }
 
@@ -1398,11 +1426,14 @@ int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const t
                        const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
                        const StencilConfig &c, cudaStream_t stream)
 {
+    const bool dedicated = h->tuning.force_path == 4;   // dedicated wall blocks
     if (h->dtype == WMIBM_F64)
-        return step_fused_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+        return step_fused_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, dedicated,
+                                               stream);
     if (h->vel_dtype == WMIBM_BF16)
-        return step_fused_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
-    return step_fused_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+        return step_fused_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, dedicated,
+                                                     stream);
+    return step_fused_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, dedicated, stream);
 }
 
 // The wall model at every band node and the solid zeros (persistent kernel).

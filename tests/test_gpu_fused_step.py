@@ -47,10 +47,11 @@ TUNINGS = [dict(), dict(rows=1, stages=6, consumer_warps=2), dict(rows=4, stages
            dict(rows=2, stages=2, consumer_warps=1)]
 
 
+@pytest.mark.parametrize("form", [1, 4])        # wall share in every block / dedicated wall blocks
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("entry", ["step", "wall_stress_force"])
 @pytest.mark.parametrize("tuning", range(len(TUNINGS)))
-def test_single_launch_equals_two_launches(wm, dtype, entry, tuning):
+def test_single_launch_equals_two_launches(wm, dtype, entry, tuning, form):
     case = inputs.cubes(shape=(96, 48, 40))
     h = wm.Handle.from_case(case, dtype=dtype)
     gp = None
@@ -59,7 +60,7 @@ def test_single_launch_equals_two_launches(wm, dtype, entry, tuning):
         rng = np.random.default_rng(4)
         gp = [to_dev(rng.standard_normal(case.shape), dtype) for _ in range(3)]
         dt = 0.01
-    h.set_tuning(force_path=1, **TUNINGS[tuning])
+    h.set_tuning(force_path=form, **TUNINGS[tuning])
     one = _run(h, case, dtype, entry, gp, dt)
     h.set_tuning(force_path=3, **TUNINGS[tuning])
     two = _run(h, case, dtype, entry, gp, dt)
@@ -73,10 +74,12 @@ def test_single_launch_equals_two_launches(wm, dtype, entry, tuning):
     assert h.device_status() == wm.OK
 
 
-def test_single_launch_graph_replays(wm):
+@pytest.mark.parametrize("form", [1, 4])
+def test_single_launch_graph_replays(wm, form):
     """Captured once, replayed many times: every replay gives the eager result."""
     case = inputs.cubes(shape=(128, 64, 48))
     h = wm.Handle.from_case(case, dtype="f32")
+    h.set_tuning(force_path=form)
     ref = _run(h, case, "f32", "wall_stress_force")
     u, v, w, tau, f = _fields(case, "f32")
     st = h.new_stats()
@@ -100,13 +103,14 @@ def test_single_launch_graph_replays(wm):
     assert h.device_status() == wm.OK
 
 
+@pytest.mark.parametrize("form", [1, 4])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_many_small_blocks_against_oracle(wm, oracle_mod, dtype):
+def test_many_small_blocks_against_oracle(wm, oracle_mod, dtype, form):
     """One consumer warp per block on a small grid: the occupancy-sized grid is
     larger than the statistics scratch and is capped; results still match the oracle."""
     case = inputs.ridge(shape=(32, 32, 32), dtype=dtype)
     h = wm.Handle.from_case(case, dtype=dtype)
-    h.set_tuning(force_path=1, rows=1, stages=2, consumer_warps=1)
+    h.set_tuning(force_path=form, rows=1, stages=2, consumer_warps=1)
     tau_g, f_g, _, st_g = _run(h, case, dtype, "wall_stress_force")
     tau_o, f_o, st_o = oracle_step(oracle_mod, case)
     for c in range(3):
