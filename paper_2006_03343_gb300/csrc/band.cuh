@@ -82,12 +82,51 @@ struct BandIn {
 // other once the record is in, so that callers can have several nodes' loads
 // in flight before any arithmetic).
 template <typename T, typename V>
+__device__ __forceinline__ void band_gather(const int4 ix, const V *u, const V *v, const V *w, int32_t nx,
+                                            int32_t ny, int64_t plane, BandIn<T> &b);
+
+template <typename T, typename V>
 __device__ __forceinline__ void band_fetch(const void *rec, int64_t t, const V *u, const V *v, const V *w,
                                            int32_t nx, int32_t ny, int64_t plane, BandIn<T> &b)
 {
     using Rec = typename RecOf<T>::type;
     int4 ix;
     unpack(reinterpret_cast<const Rec *>(rec), t, b.n0, b.n1, b.n2, b.C, b.ax, b.ay, b.azu, b.azw, ix);
+    band_gather<T, V>(ix, u, v, w, nx, ny, plane, b);
+}
+
+// The same from a copy of the record in shared memory.
+__device__ __forceinline__ void unpack_shared(const RecF32 *r, float &nx, float &ny, float &nz, float &C, float &ax,
+                                              float &ay, float &azu, float &azw, int4 &ix)
+{
+    const float4 a = r->nC, b = r->frac;
+    ix = r->ix;
+    nx = a.x; ny = a.y; nz = a.z; C = a.w;
+    ax = b.x; ay = b.y; azu = b.z; azw = b.w;
+}
+__device__ __forceinline__ void unpack_shared(const RecF64 *r, double &nx, double &ny, double &nz, double &C,
+                                              double &ax, double &ay, double &azu, double &azw, int4 &ix)
+{
+    const double2 a = r->n01, b = r->n2C, c = r->fxy, d = r->fz;
+    ix = r->ix;
+    nx = a.x; ny = a.y; nz = b.x; C = b.y;
+    ax = c.x; ay = c.y; azu = d.x; azw = d.y;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void band_fetch_shared(const typename RecOf<T>::type *srec, const V *u, const V *v,
+                                                  const V *w, int32_t nx, int32_t ny, int64_t plane, BandIn<T> &b)
+{
+    int4 ix;
+    unpack_shared(srec, b.n0, b.n1, b.n2, b.C, b.ax, b.ay, b.azu, b.azw, ix);
+    band_gather<T, V>(ix, u, v, w, nx, ny, plane, b);
+}
+
+// The 24 corner values of the node whose record unpacked to ix.
+template <typename T, typename V>
+__device__ __forceinline__ void band_gather(const int4 ix, const V *u, const V *v, const V *w, int32_t nx,
+                                            int32_t ny, int64_t plane, BandIn<T> &b)
+{
     b.idx = ix.x;
     const int64_t di = (ix.w & 1) ? 1 - nx : 1;
     const int64_t dj = (ix.w & 2) ? (int64_t)(1 - ny) * nx : nx;

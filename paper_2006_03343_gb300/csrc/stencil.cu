@@ -425,8 +425,7 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
     if (!it.done) {
         // gave up: let the copies already issued land before the block exits
         const uint32_t first = g > (uint32_t)p.stages ? g - p.stages : 0;
-        for (uint32_t q = first; q < g; ++q)
-            mbar_wait(&full[q % p.stages], (q / p.stages) & 1u, p.status, kDevStatusFullTimeout);
+        for (uint32_t q = first; q < g; ++q) mbar_drain(&full[q % p.stages], (q / p.stages) & 1u);
     }
 }
 
@@ -830,12 +829,14 @@ __device__ void zero_runs_batch(const KParams<T> &p, int64_t gw, int64_t nwarps,
 // atomics.  Warps then zero the solid runs of every member, and the last block
 // converts the scratch into wmibm_band_stats and clears it for the next call.
 template <typename T, typename VEL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_wall_batch(KParams<T> p)
+__global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
 {
     __shared__ double s_sum[kMaxBatchMembers][2][2];
     __shared__ unsigned long long s_ext[kMaxBatchMembers][2][2];   // (-min tau_w, max |U_r|) bits
     __shared__ int s_m0, s_m1;
     __shared__ bool s_last;
+    __shared__ uint64_t rbar[2];
+    extern __shared__ __align__(128) unsigned char wb_smem[];   // record chunks
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     const int64_t R = p.rec_total;
@@ -870,41 +871,89 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_wall_batch(KPar
         nacc = 0;
     };
 
+    // The block's records arrive in shared memory a chunk ahead of use (1D bulk
+    // copies, one per member segment of the chunk; two buffers), so that only
+    // the velocity gathers remain on each record's latency path.
+    using Rec = typename RecOf<T>::type;
     const int bd = blockDim.x;
+    const int64_t CH = 2 * (int64_t)bd;                  // records per chunk: two per thread
+    const int64_t nchunks = (r1 - r0 + CH - 1) / CH;
+    Rec *const rbuf = reinterpret_cast<Rec *>(wb_smem);  // [2][CH]
+    if (threadIdx.x == 0) {
+        mbar_init(&rbar[0], 1);
+        mbar_init(&rbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t q) {                        // thread 0: chunk q into buffer q & 1
+        const int64_t a = r0 + q * CH, b = min(r1, a + CH);
+        Rec *dst = rbuf + (q & 1) * CH;
+        mbar_arrive_expect_tx(&rbar[q & 1], (uint32_t)((b - a) * (int64_t)sizeof(Rec)));
+        int m = find_member_at(p, &Member<T>::r_off, a);
+        for (int64_t pos = a; pos < b && m < p.nmembers; ++m) {
+            const Member<T> &mm = p.list[m];
+            const int64_t end = min(b, m + 1 < p.nmembers ? p.list[m + 1].r_off : R);
+            if (end > pos)
+                bulk_g2s(dst + (pos - a), reinterpret_cast<const Rec *>(mm.rec) + (pos - mm.r_off),
+                         (uint32_t)((end - pos) * (int64_t)sizeof(Rec)), &rbar[q & 1]);
+            pos = end;
+        }
+    };
+    int64_t issued = 0, consumed = 0;                    // thread 0's bookkeeping
+    if (threadIdx.x == 0 && nchunks > 0) {
+        issue(0);
+        issued = 1;
+    }
     int cm = m0;
     WallRegs<T> M;
     load_wall(p.list[cm], M);
     int64_t r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
-    for (int64_t g = r0 + threadIdx.x; g < r1;) {
-        if (g >= r_end) {
-            if (want_stats && nacc) flush(cm);
-            do {
-                ++cm;
-                r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
-            } while (g >= r_end);
-            load_wall(p.list[cm], M);
+    for (int64_t q = 0; q < nchunks; ++q) {
+        if (threadIdx.x == 0 && q + 1 < nchunks) {       // its buffer was released by the sync below
+            issue(q + 1);
+            issued = q + 2;
         }
-        const int64_t g1 = g + bd;
-        const bool two = g1 < r1 && g1 < r_end;
-        const int64_t ta = g - M.r_off, tb = g1 - M.r_off;
-        const VEL *const vu = reinterpret_cast<const VEL *>(M.u);
-        const VEL *const vv = reinterpret_cast<const VEL *>(M.v);
-        const VEL *const vw = reinterpret_cast<const VEL *>(M.w);
-        const BandOut<T> a =
-            band_model<T, VEL>(M.rec, ta, ta < M.nb_w, vu, vv, vw, M.nx, M.ny, M.plane, M.logz0, M.log_phi_c, M.kappa2);
-        BandOut<T> b;
-        if (two)
-            b = band_model<T, VEL>(M.rec, tb, tb < M.nb_w, vu, vv, vw, M.nx, M.ny, M.plane, M.logz0, M.log_phi_c,
-                                   M.kappa2);
-        store_regs(M, a, ta < M.nb_w);
-        stats_add(acc, ta < M.nb_w ? 0 : 1, a.tw, a.ur);
-        if (two) {
-            store_regs(M, b, tb < M.nb_w);
-            stats_add(acc, tb < M.nb_w ? 0 : 1, b.tw, b.ur);
+        const bool ok = mbar_wait(&rbar[q & 1], (uint32_t)((q >> 1) & 1), p.status, kDevStatusFullTimeout);
+        if (ok && threadIdx.x == 0) consumed = q + 1;
+        const int64_t c0 = r0 + q * CH, c1 = min(r1, c0 + CH);
+        const Rec *const chunk = rbuf + (q & 1) * CH;
+        for (int64_t g = c0 + threadIdx.x; ok && g < c1;) {
+            if (g >= r_end) {
+                if (want_stats && nacc) flush(cm);
+                do {
+                    ++cm;
+                    r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
+                } while (g >= r_end);
+                load_wall(p.list[cm], M);
+            }
+            const int64_t g1 = g + bd;
+            const bool two = g1 < c1 && g1 < r_end;
+            const int64_t ta = g - M.r_off, tb = g1 - M.r_off;
+            const VEL *const vu = reinterpret_cast<const VEL *>(M.u);
+            const VEL *const vv = reinterpret_cast<const VEL *>(M.v);
+            const VEL *const vw = reinterpret_cast<const VEL *>(M.w);
+            // FP32: both nodes' gathers in flight before any arithmetic; FP64 (twice
+            // the registers per value): one node after the other
+            constexpr bool kPair = sizeof(T) == 4;
+            BandIn<T> ia, ib;
+            band_fetch_shared<T, VEL>(chunk + (g - c0), vu, vv, vw, M.nx, M.ny, M.plane, ia);
+            if (kPair && two) band_fetch_shared<T, VEL>(chunk + (g1 - c0), vu, vv, vw, M.nx, M.ny, M.plane, ib);
+            const BandOut<T> a = band_finish<T>(ia, ta < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+            store_regs(M, a, ta < M.nb_w);
+            stats_add(acc, ta < M.nb_w ? 0 : 1, a.tw, a.ur);
+            if (two) {
+                if (!kPair) band_fetch_shared<T, VEL>(chunk + (g1 - c0), vu, vv, vw, M.nx, M.ny, M.plane, ib);
+                const BandOut<T> b = band_finish<T>(ib, tb < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+                store_regs(M, b, tb < M.nb_w);
+                stats_add(acc, tb < M.nb_w ? 0 : 1, b.tw, b.ur);
+            }
+            nacc = 1;
+            g += two ? 2 * bd : bd;
         }
-        nacc = 1;
-        g += two ? 2 * bd : bd;
+        __syncthreads();                                  // buffer q & 1 is free again
     }
+    if (threadIdx.x == 0)                                 // after a time-out: let issued copies land
+        for (int64_t q = consumed; q < issued; ++q) mbar_drain(&rbar[q & 1], (uint32_t)((q >> 1) & 1));
     if (want_stats) {
         __syncwarp();
         const int key = nacc ? cm : -1;
@@ -1477,17 +1526,19 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
     p.nmembers = nmembers;
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
-    if (wall_blocks <= 0) {
-        // one wave of resident blocks (occupancy of this instantiation, once per process)
-        static int per_sm = 0;
-        if (per_sm == 0) {
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wall_batch<T, VEL>, 256, 0);
-            if (e != cudaSuccess) return cuda_status(h0, e, "batch wall occupancy");
-            if (per_sm < 1) per_sm = 1;
-        }
-        wall_blocks = per_sm * h0->sm_count;
+    // two chunks of 2 x 256 records in shared memory
+    const size_t wsmem = 2 * 2 * 256 * sizeof(typename RecOf<T>::type);
+    static int per_sm = 0;                 // once per instantiation and process
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_wall_batch<T, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)wsmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wall_batch<T, VEL>, 256, wsmem);
+        if (e != cudaSuccess) return cuda_status(h0, e, "batch wall occupancy");
+        if (per_sm < 1) per_sm = 1;
     }
-    k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, 0, stream>>>(p);
+    if (wall_blocks <= 0) wall_blocks = per_sm * h0->sm_count;   // one wave of resident blocks
+    k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, wsmem, stream>>>(p);
     int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
     if (st) return st;
     return launch_stencil_ty<T, VEL, 0, kAfterWall>(h0, p, c, stream, true, max_nx);

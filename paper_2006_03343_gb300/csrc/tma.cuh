@@ -85,6 +85,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
     }
 }
 
+// Waits (bounded by kWaitLimitNs, whatever the status word says) for the phase
+// of `bar` with the given parity: used before a block that gave up exits, so
+// that no bulk copy it issued still lands in its shared memory afterwards.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity)
+{
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_timer_ns() - t0 > kWaitLimitNs) return;
+}
+
 // 1D bulk copy global -> shared, completing `bytes` transaction bytes on `bar`.
 // dst and src must be 16-byte aligned and bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
