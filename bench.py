@@ -62,7 +62,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cubes", choices=["cubes", "hill", "ridge", "ensemble"])
+    ap.add_argument("--workload", default="cubes", choices=["cubes", "hill", "ridge", "ensemble", "adjoint"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--vel-dtype", default=None, choices=[None, "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -633,12 +633,82 @@ def run_ensemble(args):
     return 0
 
 
+def run_adjoint(args):
+    """The adjoint workload (random multi-hill terrain 256x128x128, per-cell ln z0,
+    seeded weights g): wmibm_backward (dL/du, dL/dv, dL/dw, dL/d ln z0 of
+    L = sum g . f) and, for comparison, the forward wall stress + force with the
+    same ln z0 field, each replayed from its own CUDA graph; gradients checked
+    against the FP64 oracle adjoint."""
+    import torch
+    from paper_2006_03343_gb300 import build, inputs, wmibm
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    case, g = inputs.adjoint_case(dtype=args.dtype)
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=tdt)
+    h = wmibm.Handle.from_case(case, dtype=args.dtype)
+    u, v, w = d(case.u), d(case.v), d(case.w)
+    tau = [d(case.tau[k]) for k in inputs.TAU_NAMES]
+    f = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(3)]
+    s_log = np.log(case.z0)
+    logz0 = d(s_log)
+    gd = [d(x) for x in g]
+    grads = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(4)]
+    h.set_log_z0(logz0)                     # builds the transpose map (once, before capture)
+    fwd = lambda: h.wall_stress_force(u, v, w, tau, f)
+    bwd = lambda: h.backward(gd, (u, v, w), *grads)
+    graphs = []
+    for fn in (fwd, bwd):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            fn()
+        graphs.append(gr)
+    flush = L2Flush(dev)
+    fwd_ms = timed_run(graphs[0].replay, stream, flush, args.steps)
+    bwd_ms = timed_run(graphs[1].replay, stream, flush, args.steps)
+    status = h.device_status()
+    accuracy = None
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        ref = oracle.adjoint(case.grid, case.phi_uv, case.phi_w, rd(s_log), case.phi_c, case.phi_b,
+                             rd(case.u), rd(case.v), rd(case.w), [rd(x) for x in g])
+        accuracy = {}
+        for name, got, r in zip(("du", "dv", "dw", "dlogz0"), grads, ref):
+            gg = got.double().cpu().numpy()
+            accuracy[name] = float(np.max(np.abs(gg - r)) / max(np.max(np.abs(r)), 1e-300))
+    npts = case.npoints
+    line = {"metric": "IBM stage adjoint throughput (Gpts/s)", "unit": "Gpts/s",
+            "value": npts / (float(np.mean(bwd_ms)) * 1e-3) / 1e9, "ms_per_step": float(np.mean(bwd_ms)),
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "adjoint: random multi-hill 256x128x128, per-cell ln z0, seeded g",
+                       "band_nodes": int(h.list_size(wmibm.LIST_BAND_W) + h.list_size(wmibm.LIST_BAND_UV)),
+                       "l2": L2_NOTE},
+            "forward_same_log_z0": {"ms_per_step": float(np.mean(fwd_ms)),
+                                    "value": npts / (float(np.mean(fwd_ms)) * 1e-3) / 1e9, "unit": "Gpts/s"},
+            "normwise_error_vs_oracle_adjoint": accuracy,
+            "gpu_launches": 2 * args.steps,       # k_adjoint_records + k_adjoint_gather per timed backward
+            "device_status": status}
+    print(json.dumps(line))
+    h.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 
