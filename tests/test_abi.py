@@ -99,3 +99,31 @@ def test_calls_reject_null_handle(lib):
     assert lib.wmibm_list_size(None, 0) == -1
     assert lib.wmibm_traffic_bytes(None, 0) == -1
     lib.wmibm_destroy(None)
+
+
+def test_later_entry_points_reject_null_arguments(lib):
+    """The step, adjoint, tuning and batch entry points refuse NULL handles and
+    tables on the host, before anything reaches a GPU."""
+    from paper_2006_03343_gb300 import wmibm
+    tau = (ctypes.c_void_p * 6)()
+    three = (ctypes.c_void_p * 3)()
+    assert lib.wmibm_step(None, None, None, None, tau, None, None, None, None, 0.0, None, None) == wmibm.EINVAL
+    assert lib.wmibm_wall_stress_force(None, None, None, None, tau, None, None, None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_force_mask(None, tau, None, None, None, None, None, None, None, 0.0, None) == wmibm.EINVAL
+    assert lib.wmibm_wall_stress_noalloc(None, None, None, None, tau, None, None) == wmibm.EINVAL
+    assert lib.wmibm_set_log_z0(None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_backward(None, three, three, None, None, None, None, None) == wmibm.EINVAL
+    t = wmibm.Tuning()
+    assert lib.wmibm_set_tuning(None, ctypes.byref(t)) == wmibm.EINVAL
+    assert lib.wmibm_get_tuning(None, ctypes.byref(t)) == wmibm.EINVAL
+    out = ctypes.c_void_p()
+    assert lib.wmibm_batch_create(ctypes.byref(out), None, 1, None) == wmibm.EINVAL and not out.value
+    handles = (ctypes.c_void_p * 1)()
+    assert lib.wmibm_batch_create(ctypes.byref(out), handles, 1, None) == wmibm.EINVAL      # NULL member
+    assert lib.wmibm_batch_create(ctypes.byref(out), handles, 0, None) == wmibm.EINVAL      # no members
+    assert lib.wmibm_batch_step(None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_batch_wall_stress_force(None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_batch_set_fields(None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_batch_traffic_bytes(None, 0) == -1
+    assert lib.wmibm_batch_points(None) == -1
+    lib.wmibm_batch_destroy(None)
