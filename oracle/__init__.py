@@ -5,6 +5,9 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``; never by the product package.
 The arithmetic lives in ``wmibm_oracle.c`` (plain C, double precision, loops in
 the paper's order); this module compiles it with gcc and marshals numpy arrays.
+The pseudo-spectral derivatives of Eqs. 13-14 are written here with numpy's FP64
+FFT as the library step: a 2-D transform of each z-plane, exactly as the sum over
+(k_x, k_y) is stated.
 
 Functions and the passages they follow:
   classify      Sec. 3.3, node classes on the w-grid and the uv-grid
@@ -13,11 +16,15 @@ Functions and the passages they follow:
   wall_stress   Sec. 3.3, Eq. 28 and the tensor rotation tau_ij = a_im a_jn tau'_mn
   wall_model_node  the same wall model evaluated at a single node
   force         Eq. 2 / Eq. 18: f = -div(tau) on the staggered grid (Eqs. 15-16)
+  horizontal_derivatives  Eqs. 13-14, pseudo-spectral d/dx and d/dy of one field
+  force_spectral  f = -div(tau) with the horizontal derivatives of Eqs. 13-14
   mask          Sec. 3.2, Eq. 27: the body velocity condition
   adjoint       chain rule of wall_stress + force for L = <g, f>
 
-Every function here is pinned by ``tests/test_oracle_pins.py`` against closed
-forms, invariants and brute force (see the docstrings there).
+Every function here is pinned against closed forms, invariants and brute force
+(see the docstrings there): ``tests/test_oracle_pins.py`` (wall stress, central-
+difference divergence, mask), ``tests/test_oracle_adjoint.py`` (adjoint) and
+``tests/test_oracle_spectral.py`` (pseudo-spectral divergence).
 """
 from __future__ import annotations
 
@@ -174,6 +181,55 @@ def force(grid, tau):
     fx, fy, fz = (np.empty(shp, np.float64) for _ in range(3))
     _load().orc_force(nx, ny, nz, lx, ly, lz, _p(tau["txx"]), _p(tau["txy"]), _p(tau["tyy"]),
                       _p(tau["tzz"]), _p(tau["txz"]), _p(tau["tyz"]), _p(fx), _p(fy), _p(fz))
+    return fx, fy, fz
+
+
+def wavenumbers(n, length):
+    """Wavenumbers of an n-point periodic direction of length L (Eqs. 13-14):
+    k_m = 2 pi m / L with m = 0, 1, ..., then negative m from the top of the range.
+    For even n the Nyquist mode m = n/2 is given k = 0: i k A for it would not be
+    the transform of a real field, so it carries no first derivative."""
+    m = np.arange(n)
+    m = np.where(m < (n + 1) // 2, m, m - n).astype(np.float64)
+    if n % 2 == 0:
+        m[n // 2] = 0.0
+    return 2.0 * np.pi * m / float(length)
+
+
+def horizontal_derivatives(grid, a):
+    """Eqs. 13-14 for one field a[k][j][i]: per z-plane the Fourier amplitudes
+    A(k_x, k_y) (2-D FFT divided by nx ny), then the sums over (k_x, k_y) of
+    i k_x A e^{i(k_x x + k_y y)} and i k_y A e^{i(k_x x + k_y y)} -> (da/dx, da/dy)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    amp = np.fft.fft2(np.asarray(a, np.float64), axes=(1, 2)) / (nx * ny)
+    kx = wavenumbers(nx, lx)[None, None, :]
+    ky = wavenumbers(ny, ly)[None, :, None]
+    # ifft2 divides by nx ny; the synthesis sum does not
+    ddx = np.fft.ifft2(1j * kx * amp, axes=(1, 2)) * (nx * ny)
+    ddy = np.fft.ifft2(1j * ky * amp, axes=(1, 2)) * (nx * ny)
+    return np.ascontiguousarray(ddx.real), np.ascontiguousarray(ddy.real)
+
+
+def force_spectral(grid, tau):
+    """f = -div(tau) (Eq. 2 / Eq. 18) with the paper's own horizontal scheme: x and y
+    derivatives pseudo-spectral (Eqs. 13-14), vertical ones the staggered differences
+    of Eqs. 15-16.  f_x, f_y sit on uv-levels and take (t_.z[k+1] - t_.z[k]) / dz of the
+    w-level stresses; f_z sits on w-levels and takes (tzz[k] - tzz[k-1]) / dz.
+    f_x = f_y = 0 on the ghost uv-level nz-1; f_z = 0 on the floor and the lid.
+    -> (fx, fy, fz)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    dz = lz / (nz - 1)
+    t = {k: np.asarray(v, np.float64) for k, v in tau.items()}
+    dxx_dx, _ = horizontal_derivatives(grid, t["txx"])
+    dxy_dx, dxy_dy = horizontal_derivatives(grid, t["txy"])
+    _, dyy_dy = horizontal_derivatives(grid, t["tyy"])
+    dxz_dx, _ = horizontal_derivatives(grid, t["txz"])
+    _, dyz_dy = horizontal_derivatives(grid, t["tyz"])
+    shp = t["txx"].shape
+    fx, fy, fz = (np.zeros(shp, np.float64) for _ in range(3))
+    fx[:-1] = -(dxx_dx[:-1] + dxy_dy[:-1] + (t["txz"][1:] - t["txz"][:-1]) / dz)
+    fy[:-1] = -(dxy_dx[:-1] + dyy_dy[:-1] + (t["tyz"][1:] - t["tyz"][:-1]) / dz)
+    fz[1:-1] = -(dxz_dx[1:-1] + dyz_dy[1:-1] + (t["tzz"][1:-1] - t["tzz"][:-2]) / dz)
     return fx, fy, fz
 
 
