@@ -62,7 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cubes", choices=["cubes", "hill", "ridge", "ensemble", "adjoint"])
+    ap.add_argument("--workload", default="cubes",
+                    choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--vel-dtype", default=None, choices=[None, "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -161,6 +162,8 @@ class ClockSampler:
 
 def make_case(args):
     from paper_2006_03343_gb300 import inputs
+    if args.workload == "spectral":           # the paper's horizontal scheme on the 3-D hill grid
+        return inputs.hill(dtype=args.dtype)
     return inputs.make(args.workload, dtype=args.dtype)
 
 
@@ -224,7 +227,10 @@ def run_reference(args):
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, u, v, w, tau)
-        oracle.force(case.grid, tau)
+        if args.workload == "spectral":
+            oracle.force_spectral(case.grid, tau)
+        else:
+            oracle.force(case.grid, tau)
         if s >= args.warmup:
             per_step.append(time.perf_counter() - t0)
     total = sum(per_step)
@@ -235,7 +241,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args, case),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} full passes of wall stress + force over the workload (FP64 CPU oracle)"},
+                             "sample": f"{args.steps} full passes of wall stress + "
+                                       f"{'spectral ' if args.workload == 'spectral' else ''}force over the "
+                                       f"workload (FP64 CPU oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -701,6 +709,202 @@ def run_adjoint(args):
     return 0
 
 
+SPECTRAL_SOURCES = ("spectral.cu", "tma.cuh", "internal.cuh")      # the spectral kernel's sources
+
+
+def spectral_digest():
+    h = hashlib.sha256()
+    for name in SPECTRAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_03343_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def spectral_traffic(dtype):
+    """DRAM bytes per launch of k_spectral from the committed ncu summary, if it was
+    taken on the current spectral sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"spectral_hill_{dtype}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != spectral_digest():
+        return None
+    return float(m_bytes.group(1))
+
+
+def run_spectral(args):
+    """The stage with the paper's own horizontal scheme on the 3-D hill grid
+    (512 x 256 x 256): wall stress (a1) then the pseudo-spectral forcing of
+    Eqs. 13-14 (a2), one CUDA graph per step.  Roofline of k_spectral against the
+    measured copy peak with its algorithmic 9 arrays per point; accuracy on sampled
+    levels against the FP64 oracle; the central-difference forcing timed beside it."""
+    import torch
+    from paper_2006_03343_gb300 import build, inputs, wmibm
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    case = make_case(args)
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=tdt)
+    h = wmibm.Handle.from_case(case, dtype=args.dtype)
+    u, v, w = d(case.u), d(case.v), d(case.w)
+    tau = [d(case.tau[k]) for k in inputs.TAU_NAMES]
+    f = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(3)]
+    stats = h.new_stats()
+    step_fn = lambda: (h.wall_stress(u, v, w, tau, stats), h.force_spectral(tau, f))
+    fns = {"step": step_fn, "wall": lambda: h.wall_stress(u, v, w, tau, stats),
+           "spectral": lambda: h.force_spectral(tau, f), "central": lambda: h.force(tau, f)}
+    # first pass on the pristine inputs, kept for the accuracy report
+    step_fn()
+    torch.cuda.synchronize()
+    first_f = [x.double().cpu().numpy() for x in f]
+    graphs = {}
+    for name, fn in fns.items():
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        graphs[name] = g
+    flush = L2Flush(dev)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
+    if sampler:
+        sampler.start()
+    t_soak = time.perf_counter()
+    while not args.profile and time.perf_counter() - t_soak < 1.0:
+        for _ in range(10):
+            flush.zero_()
+            graphs["step"].replay()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = timed_run(graphs["step"].replay, stream, flush, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    parts = {name: timed_run(graphs[name].replay, stream, flush, args.steps) for name in ("wall", "spectral", "central")}
+    warm_ms = timed_run(graphs["step"].replay, stream, NoFlush(), args.steps)
+    status = h.device_status()
+    value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
+
+    peak, peak_kind = measured_peak()
+    kbytes = h.traffic_bytes(1)              # 6 stress reads + 3 force writes per point
+    kms = float(np.mean(parts["spectral"]))
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    step_bytes = h.traffic_bytes(0) + kbytes
+
+    e2e = None
+    if not args.no_e2e and not args.profile:
+        host_in = [torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (case.u, case.v, case.w)]
+        host_tau = [torch.from_numpy(case.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
+        host_f = [torch.empty(case.shape, dtype=tdt).pin_memory() for _ in range(3)]
+        host_stats = torch.empty(10, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
+        d2h = sum(t.numel() * t.element_size() for t in host_f) + host_stats.numel() * 8
+
+        def e2e_step():
+            for dst, src in zip((u, v, w), host_in):
+                dst.copy_(src, non_blocking=True)
+            for dst, src in zip(tau, host_tau):
+                dst.copy_(src, non_blocking=True)
+            h.wall_stress(u, v, w, tau, stats)
+            h.force_spectral(tau, f)
+            for dst, src in zip(host_f, f):
+                dst.copy_(src, non_blocking=True)
+            host_stats.copy_(stats, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps * case.npoints / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        import oracle
+        oracle.build()
+        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        tau_o = {k: rd(case.tau[k]) for k in inputs.TAU_NAMES}
+        t0 = time.perf_counter()
+        oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b,
+                           rd(case.u), rd(case.v), rd(case.w), tau_o)
+        t_wall = time.perf_counter() - t0
+        # the spectral divergence on a slab of levels (the oracle's FFTs are per plane)
+        nx, ny, nz, lx, ly, lz = case.grid
+        dz = lz / (nz - 1)
+        k0, nk = 100, 34
+        slab = {k: np.ascontiguousarray(t[k0 - 1:k0 - 1 + nk]) for k, t in tau_o.items()}
+        t0 = time.perf_counter()
+        ref = oracle.force_spectral((nx, ny, nk, lx, ly, (nk - 1) * dz), slab)
+        t_slab = time.perf_counter() - t0
+        per_pass = t_wall + t_slab * nz / nk
+        cpu = {"value": case.npoints / per_pass / 1e9, "unit": UNIT, "cores": oracle.openmp_threads(),
+               "kind": "oracle",
+               "sample": f"one full pass of the oracle's wall stress ({t_wall:.1f} s) plus its spectral divergence "
+                         f"on {nk} of {nz} levels ({t_slab:.1f} s, numpy FFT, scaled to all levels)"}
+        accuracy = {}
+        for c, name in enumerate(("fx", "fy", "fz")):
+            got = first_f[c][k0:k0 + nk - 2]
+            r = ref[c][1:nk - 1]
+            accuracy[name] = float(np.max(np.abs(got - r)) / max(np.max(np.abs(r)), 1e-300))
+        accuracy["levels"] = f"{k0}..{k0 + nk - 3} of the first GPU pass against the oracle (its own wall stress)"
+
+    if rank == 0:
+        shape = h.spectral_shape()
+        line = {"metric": "IBM wall-stress+spectral-forcing throughput (Gpts/s)", "value": value, "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+                "data": "synthetic",
+                "config": dict(workload_config(args, case),
+                               workload=f"spectral: 3-D hill {case.grid[0]}x{case.grid[1]}x{case.grid[2]}, "
+                                        "x/y derivatives of Eqs. 13-14"),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": spectral_traffic(args.dtype),
+                             "kernel": "k_spectral (row and column FFT units, one persistent launch)",
+                             "kernel_ms": kms, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                             "algorithmic_bytes_per_launch": kbytes},
+                "step_bytes": step_bytes,
+                "step_gbs": step_bytes / (float(np.mean(step_ms)) * 1e-3) / 1e9,
+                "warm_l2": {"ms_per_step": float(np.mean(warm_ms)),
+                            "value": args.steps * case.npoints / (sum(warm_ms) * 1e-3) / 1e9, "unit": UNIT},
+                "parts_ms": {"a1_wall_alone": float(np.mean(parts["wall"])),
+                             "a2_spectral_alone": float(np.mean(parts["spectral"])),
+                             "a2_central_difference_alone": float(np.mean(parts["central"]))},
+                "spectral_shape": {"rows_per_row_unit": shape[0], "columns_per_column_unit": shape[1],
+                                   "levels_per_chunk": shape[2], "smem_bytes": shape[3]},
+                "timing": "per step: CUDA events around one graph replay of wall stress then the spectral forcing",
+                "gpu_launches": 3 * args.steps,      # k_wall, k_stats_emit, k_spectral
+                "device_status": status, "accuracy": accuracy,
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -709,6 +913,8 @@ def main(argv=None):
         return run_ensemble(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "spectral":
+        return run_spectral(args)
     return run_ours(args)
 
 

@@ -130,6 +130,28 @@ int wmibm_wall_stress(wmibm_handle *h, const void *u, const void *v, const void 
 int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream);
 
 /*
+ * wmibm_force_spectral - the forcing f = -div(tau) with the paper's own
+ * horizontal scheme: x and y derivatives pseudo-spectral (Sec. 2.4, Eqs. 13-14:
+ * the derivative of each periodic plane is the sum over (k_x, k_y) of i k A-hat
+ * e^{i(k_x x + k_y y)}), vertical differences as in wmibm_force (Eqs. 15-16).
+ * The Nyquist wavenumber of each direction carries no first derivative.
+ * Arguments, layout and boundary rows as in wmibm_force.  One persistent launch
+ * (FFT lines in shared memory, FP32 or FP64 as the handle's dtype); tau and
+ * f must not overlap.
+ * Requires nx and ny powers of two in [2, 2048]: otherwise EINVAL, before any
+ * GPU work.  Errors: EINVAL, ESTATE, ECUDA.
+ */
+int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream);
+
+/*
+ * wmibm_spectral_shape - the tile of wmibm_force_spectral's launch (host query):
+ * out[0] rows per row unit, out[1] columns per column unit, out[2] z-levels per
+ * chunk of the dispense order, out[3] shared-memory bytes per block.
+ * Returns EINVAL for a NULL argument or a grid without spectral support.
+ */
+int wmibm_spectral_shape(const wmibm_handle *h, int64_t out[4]);
+
+/*
  * wmibm_mask - the immersed-boundary velocity condition (Sec. 3.2, Eq. 27):
  * where phi <= 0 (each component on its own grid) the velocity becomes
  * 3 dt/2 * grad p, or 0 when gradp is NULL; elsewhere it is untouched.

@@ -305,6 +305,7 @@ void free_handle(wmibm_handle *h)
     if (h->adj_offs) cudaFree(h->adj_offs);
     if (h->adj_ent) cudaFree(h->adj_ent);
     if (h->adj_grad) cudaFree(h->adj_grad);
+    spectral_free(h);
     free(h);
 }
 
@@ -543,6 +544,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         TRY(cudaMalloc(&h->dev_status, sizeof(int)), "cudaMalloc status");
         TRY(cudaMemsetAsync(h->dev_status, 0, sizeof(int), stream), "memset status");
         TRY(cudaStreamSynchronize(stream), "init state");
+        status = spectral_setup(h, stream);
+        if (status != WMIBM_OK) goto fail;
 
         const int64_t es = (int64_t)elem_size(o.dtype), vs = (int64_t)elem_size(o.vel_dtype);
         const int64_t *L = h->lists.n;

@@ -46,6 +46,8 @@ struct StencilConfig {
     int rows, stages, consumer_warps, wall_warps, blocks_per_sm;
 };
 
+struct SpecState;              // tables, counters and tile shapes of the spectral forcing (spectral.cu)
+
 }  // namespace wmibm
 
 struct wmibm_handle {
@@ -77,6 +79,7 @@ struct wmibm_handle {
     int32_t *adj_ent;           // record * 8 + corner (bit 0: +x, bit 1: +y, bit 2: +z)
     int64_t adj_m[2];
     void *adj_grad;             // per record: dL/du_hat (3) and dL/d(ln z0) (1), dtype
+    wmibm::SpecState *spec;     // spectral forcing state, or NULL when nx or ny is not a power of two
     char err[512];
 };
 
@@ -88,6 +91,8 @@ namespace wmibm {
 int set_error(wmibm_handle *h, int status, const char *fmt, ...);
 int check_device(wmibm_handle *h);
 int cuda_status(wmibm_handle *h, cudaError_t e, const char *what);
+int spectral_setup(wmibm_handle *h, cudaStream_t stream);     // spectral.cu, once per handle
+void spectral_free(wmibm_handle *h);
 
 inline size_t elem_size(int32_t t) { return t == WMIBM_F64 ? 8 : (t == WMIBM_BF16 ? 2 : 4); }
 

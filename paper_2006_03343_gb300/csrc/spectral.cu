@@ -1,0 +1,594 @@
+// The forcing f = -div(tau) with the paper's own horizontal scheme (Eq. 2 /
+// Eq. 18 of Liu & Stevens, arXiv:2006.03343): x and y derivatives
+// pseudo-spectral (Eqs. 13-14), vertical ones the staggered differences of
+// Eqs. 15-16,
+//   f_x(uv k) = -[d_x txx + d_y txy + (txz[k+1] - txz[k])/dz]
+//   f_y(uv k) = -[d_x txy + d_y tyy + (tyz[k+1] - tyz[k])/dz]
+//   f_z(w k)  = -[d_x txz + d_y tyz + (tzz[k] - tzz[k-1])/dz]
+// with f_x = f_y = 0 on the ghost uv level and f_z = 0 on the floor and lid.
+//
+// The 2-D transform of Eqs. 13-14 factors by direction: multiplying the plane's
+// amplitudes by i k_x touches the x index only, so d_x is the 1-D spectral
+// derivative of every x-row and d_y that of every y-column.  The Nyquist bin of
+// each direction carries no first derivative.  One persistent launch works
+// through two kinds of unit:
+//   row unit    (level k, rx rows): d_x of txx, txy, txz plus the vertical
+//               terms -> writes the partial forcing into f
+//   column unit (level k, wy columns): d_y of txy, tyy, tyz, subtracted from f
+// Each unit stages its lines in shared memory, two real lines per complex
+// sequence (z = a + i b; the derivative operator is real, so D z = D a + i D b),
+// runs a radix-8/4/2 Stockham FFT, multiplies by i k / N while loading the first
+// pass of a second forward FFT of the conjugate (IFFT(y) = conj(FFT(conj y))/N),
+// and writes.  Units are dispensed by an atomic ticket in chunks of kc levels:
+// the row units of chunk c, then the column units of chunk c-1.  A column unit
+// on level k waits (bounded) until all row units of level k have finished, so
+// the partial forcing and the stresses the two unit kinds share are re-read
+// from L2 while DRAM streams each array once.  Row units never wait, and every
+// row unit a column unit depends on was dispensed earlier to a running block,
+// so the waits end whatever the grid size.
+#include <math.h>
+#include <stdlib.h>
+
+#include "internal.cuh"
+#include "tma.cuh"
+
+namespace wmibm {
+
+constexpr int kSpecMaxLog = 11;         // lines of up to 2048 points
+constexpr int kSpecThreads = 256;
+constexpr int kSpecBudget = 3200;       // complex elements per shared buffer aimed at (FP32; half for FP64)
+constexpr double kSpecChunkBytes = 24.0 * 1024 * 1024;   // L2 footprint of one chunk of levels
+
+struct SpecState {
+    int lognx, logny;
+    int rx, wy;                 // rows per row unit, columns per column unit
+    int ldx, ldy;               // shared-memory stride of a sequence (complex elements, padded by one)
+    int kc, nchunks;
+    int xpl, ypl;               // units per level
+    int64_t total;
+    size_t smem;
+    void *twx, *twy;            // omega_N^m = exp(-2 pi i m / N), m < N (dtype complex)
+    void *knx, *kny;            // k_m / N per bin, Nyquist bin 0 (dtype)
+    unsigned int *ctr;          // [0] ticket, [1] exit ticket, [2 + k] row units finished on level k
+};
+
+}  // namespace wmibm
+
+using namespace wmibm;
+
+namespace {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<float> {
+    using type = float2;
+};
+template <>
+struct Cx<double> {
+    using type = double2;
+};
+
+template <typename T>
+struct SpecParams {
+    const T *txx, *txy, *tyy, *tzz, *txz, *tyz;
+    T *fx, *fy, *fz;
+    const typename Cx<T>::type *twx, *twy;
+    const T *knx, *kny;
+    unsigned int *ctr;
+    int *status;
+    int32_t nx, ny, nz;
+    int32_t lognx, logny, logrx, logwy;
+    int32_t ldx, ldy;
+    int32_t kc, nchunks, xpl, ypl;
+    int64_t total;
+    int32_t buf;              // complex elements per shared buffer
+    T rdz;
+};
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C>
+__device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }       // -i a
+
+// R-point forward DFT in registers, natural order in and out:
+// V[q] = sum_r v[r] exp(-2 pi i r q / R).
+template <typename T, int R>
+struct Dft;
+
+template <typename T>
+struct Dft<T, 2> {
+    template <typename C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        const C a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    }
+};
+
+template <typename T>
+struct Dft<T, 4> {
+    template <typename C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        const C s0 = cadd(v[0], v[2]), d0 = csub(v[0], v[2]);
+        const C s1 = cadd(v[1], v[3]), d1 = cmi(csub(v[1], v[3]));
+        v[0] = cadd(s0, s1);
+        v[2] = csub(s0, s1);
+        v[1] = cadd(d0, d1);
+        v[3] = csub(d0, d1);
+    }
+};
+
+template <typename T>
+struct Dft<T, 8> {
+    // even / odd halves by two 4-point DFTs, joined with exp(-2 pi i q / 8)
+    template <typename C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<T, 4>::run(e);
+        Dft<T, 4>::run(o);
+        const T h = T(0.70710678118654752440);
+        o[1] = C{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};      // (1 - i)/sqrt 2
+        o[2] = cmi(o[2]);                                             // -i
+        o[3] = C{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};     // (-1 - i)/sqrt 2
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = cadd(e[q], o[q]);
+            v[q + 4] = csub(e[q], o[q]);
+        }
+    }
+};
+
+// One Stockham pass of radix R over S sequences of length N = 2^logN, from a to
+// b, after logNs earlier passes.  Butterfly j of a sequence reads elements
+// j + r N/R, twiddles them by omega_N^(r jm N/(Ns R)) with jm = j mod Ns, and
+// writes element (j - jm) R + jm + r Ns.  PRE: multiply each input (bin m) by
+// i k_m / N and conjugate it first, i.e. v -> (-kn_m v.y, -kn_m v.x).
+template <typename T, int R, bool PRE>
+__device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict__ a,
+                                         typename Cx<T>::type *__restrict__ b, int S, int logN, int logNs, int ld,
+                                         const typename Cx<T>::type *__restrict__ tw, const T *__restrict__ kn)
+{
+    using C = typename Cx<T>::type;
+    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int lognb = logN - logR;
+    const int nb = 1 << lognb;
+    const int total = S << lognb;
+    const int tshift = logN - logNs - logR;
+    const int msk = (1 << logNs) - 1;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int s = t >> lognb, j = t & (nb - 1);
+        const C *in = a + s * ld;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+        if (PRE) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T k = __ldg(kn + j + r * nb);
+                v[r] = C{-k * v[r].y, -k * v[r].x};
+            }
+        }
+        const int jm = j & msk;
+        if (jm) {
+            const int step = jm << tshift;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + r * step));
+        }
+        Dft<T, R>::run(v);
+        C *out = b + s * ld + ((j - jm) << logR) + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[r << logNs] = v[r];
+    }
+}
+
+// Forward FFT of S sequences (stride ld) held in a, b as scratch; returns the
+// buffer that holds the result.  Ends with a block barrier.
+template <typename T, bool PRE>
+__device__ typename Cx<T>::type *fft_block(typename Cx<T>::type *a, typename Cx<T>::type *b, int S, int logN,
+                                           int ld, const typename Cx<T>::type *tw, const T *kn)
+{
+    int logNs = 0;
+    bool first = true;
+    while (logNs < logN) {
+        const int left = logN - logNs;
+        int logR;
+        if (left >= 3) {
+            if (PRE && first) fft_pass<T, 8, true>(a, b, S, logN, logNs, ld, tw, kn);
+            else fft_pass<T, 8, false>(a, b, S, logN, logNs, ld, tw, kn);
+            logR = 3;
+        } else if (left == 2) {
+            if (PRE && first) fft_pass<T, 4, true>(a, b, S, logN, logNs, ld, tw, kn);
+            else fft_pass<T, 4, false>(a, b, S, logN, logNs, ld, tw, kn);
+            logR = 2;
+        } else {
+            if (PRE && first) fft_pass<T, 2, true>(a, b, S, logN, logNs, ld, tw, kn);
+            else fft_pass<T, 2, false>(a, b, S, logN, logNs, ld, tw, kn);
+            logR = 1;
+        }
+        __syncthreads();
+        typename Cx<T>::type *t = a;
+        a = b;
+        b = t;
+        logNs += logR;
+        first = false;
+    }
+    return a;
+}
+
+// Spectral derivative of the S staged sequences: conj(FFT(conj(i k/N * FFT(z)))).
+// The returned buffer holds (D a, -D b) for each z = a + i b.
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::type *derive(typename Cx<T>::type *a, typename Cx<T>::type *b, int S,
+                                                        int logN, int ld, const typename Cx<T>::type *tw,
+                                                        const T *kn)
+{
+    typename Cx<T>::type *r1 = fft_block<T, false>(a, b, S, logN, ld, tw, kn);
+    return fft_block<T, true>(r1, r1 == a ? b : a, S, logN, ld, tw, kn);
+}
+
+// Row unit: level k, rows j0 .. j0 + rx - 1.  Sequences: s < rx is row j0 + s
+// as txx + i txy; rx + q holds rows j0 + 2q and j0 + 2q + 1 of txz.
+template <typename T>
+__device__ void row_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typename Cx<T>::type *B, int k, int j0)
+{
+    using C = typename Cx<T>::type;
+    const int rx = 1 << p.logrx;
+    const int n = rx << p.lognx;
+    const int64_t plane = (int64_t)p.nx * p.ny;
+    const int64_t base = (int64_t)k * plane + (int64_t)j0 * p.nx;
+    if (k == p.nz - 1) {                    // ghost uv level / lid: f = 0
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            p.fx[base + e] = T(0);
+            p.fy[base + e] = T(0);
+            p.fz[base + e] = T(0);
+        }
+        return;
+    }
+    const int ld = p.ldx;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int r = e >> p.lognx, i = e & (p.nx - 1);
+        const int64_t o = base + e;
+        A[r * ld + i] = C{__ldg(p.txx + o), __ldg(p.txy + o)};
+        reinterpret_cast<T *>(A + (rx + (r >> 1)) * ld + i)[r & 1] = __ldg(p.txz + o);
+    }
+    __syncthreads();
+    const C *R = derive<T>(A, B, rx + rx / 2, p.lognx, ld, p.twx, p.knx);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int r = e >> p.lognx, i = e & (p.nx - 1);
+        const int64_t o = base + e;
+        const C d = R[r * ld + i];                          // (d_x txx, -d_x txy)
+        const C dd = R[(rx + (r >> 1)) * ld + i];
+        const T dxz = (r & 1) ? -dd.y : dd.x;               // d_x txz
+        const T xz0 = __ldg(p.txz + o), xz1 = __ldg(p.txz + o + plane);
+        const T yz0 = __ldg(p.tyz + o), yz1 = __ldg(p.tyz + o + plane);
+        p.fx[o] = -(d.x + (xz1 - xz0) * p.rdz);
+        p.fy[o] = -(-d.y + (yz1 - yz0) * p.rdz);
+        p.fz[o] = (k == 0) ? T(0) : -(dxz + (__ldg(p.tzz + o) - __ldg(p.tzz + o - plane)) * p.rdz);
+    }
+}
+
+// Column unit: level k, columns i0 .. i0 + wy - 1.  Sequences: c < wy is column
+// i0 + c as txy + i tyy; wy + q holds columns i0 + 2q and i0 + 2q + 1 of tyz.
+template <typename T>
+__device__ void column_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typename Cx<T>::type *B, int k, int i0)
+{
+    using C = typename Cx<T>::type;
+    if (k == p.nz - 1) return;              // f stays 0 there (written by the row units)
+    const int wy = 1 << p.logwy;
+    const int n = wy << p.logny;
+    const int64_t base = (int64_t)k * p.nx * p.ny + i0;
+    const int ld = p.ldy;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int j = e >> p.logwy, c = e & (wy - 1);
+        const int64_t o = base + (int64_t)j * p.nx + c;
+        A[c * ld + j] = C{__ldg(p.txy + o), __ldg(p.tyy + o)};
+        reinterpret_cast<T *>(A + (wy + (c >> 1)) * ld + j)[c & 1] = __ldg(p.tyz + o);
+    }
+    __syncthreads();
+    const C *R = derive<T>(A, B, wy + wy / 2, p.logny, ld, p.twy, p.kny);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int j = e >> p.logwy, c = e & (wy - 1);
+        const int64_t o = base + (int64_t)j * p.nx + c;
+        const C d = R[c * ld + j];                          // (d_y txy, -d_y tyy)
+        const C dd = R[(wy + (c >> 1)) * ld + j];
+        const T dyz = (c & 1) ? -dd.y : dd.x;               // d_y tyz
+        p.fx[o] = __ldcg(p.fx + o) - d.x;
+        p.fy[o] = __ldcg(p.fy + o) + d.y;
+        if (k > 0) p.fz[o] = __ldcg(p.fz + o) - dyz;
+    }
+}
+
+// Waits until *ctr >= target (acquire, GPU scope); bounded by kWaitLimitNs.
+__device__ bool wait_level(const unsigned int *ctr, unsigned int target, int *status)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(128);
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if ((it & 7u) == 0) {
+            if (*(volatile int *)status != 0) return false;
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
+                atomicExch(status, kDevStatusBarrierTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+// Unit u of the dispense order -> kind (0 row, 1 column), level, index within the level.
+// Phase ph (0 .. nchunks): row units of chunk ph, then column units of chunk ph - 1.
+template <typename T>
+__device__ void decode_unit(const SpecParams<T> &p, int64_t u, int *kind, int *level, int *idx)
+{
+    auto start = [&](int ph) -> int64_t {
+        const int64_t a = min((int64_t)ph * p.kc, (int64_t)p.nz);
+        const int64_t b = min((int64_t)max(ph - 1, 0) * p.kc, (int64_t)p.nz);
+        return a * p.xpl + b * p.ypl;
+    };
+    int lo = 0, hi = p.nchunks;             // largest ph with start(ph) <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start(mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    int64_t o = u - start(lo);
+    const int64_t nrow = lo < p.nchunks ? (min((int64_t)(lo + 1) * p.kc, (int64_t)p.nz) - (int64_t)lo * p.kc) * p.xpl
+                                        : 0;
+    if (o < nrow) {
+        *kind = 0;
+        *level = lo * p.kc + (int)(o / p.xpl);
+        *idx = (int)(o % p.xpl);
+    } else {
+        o -= nrow;
+        *kind = 1;
+        *level = (lo - 1) * p.kc + (int)(o / p.ypl);
+        *idx = (int)(o % p.ypl);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSpecThreads, 2) k_spectral(SpecParams<T> p)
+{
+    using C = typename Cx<T>::type;
+    extern __shared__ __align__(16) unsigned char spec_smem[];
+    C *A = reinterpret_cast<C *>(spec_smem);
+    C *B = A + p.buf;
+    __shared__ int s_kind, s_level, s_idx, s_last;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t u = (int64_t)atomicAdd(p.ctr, 1u);
+            int kind = -1, level = 0, idx = 0;
+            if (u < p.total) {
+                decode_unit(p, u, &kind, &level, &idx);
+                // a column unit needs every row unit of its level finished
+                if (kind == 1 && !wait_level(p.ctr + 2 + level, (unsigned)p.xpl, p.status)) kind = 2;
+            }
+            s_kind = kind;
+            s_level = level;
+            s_idx = idx;
+        }
+        __syncthreads();
+        const int kind = s_kind, level = s_level, idx = s_idx;
+        if (kind < 0) break;
+        if (kind == 0) {
+            row_unit<T>(p, A, B, level, idx << p.logrx);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(p.ctr + 2 + level, 1u);
+            }
+        } else if (kind == 1) {
+            column_unit<T>(p, A, B, level, idx << p.logwy);
+            __syncthreads();
+        } else {
+            __syncthreads();                // gave up waiting: the unit is skipped, the status says so
+        }
+    }
+    // the last block out re-arms the counters for the next launch: every block
+    // has taken its final ticket and passed its waits by then
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(p.ctr + 1, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int k = threadIdx.x; k < p.nz; k += blockDim.x) p.ctr[2 + k] = 0u;
+        if (threadIdx.x == 0) p.ctr[0] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            p.ctr[1] = 0u;
+        }
+    }
+}
+
+int ilog2_exact(int n)
+{
+    if (n < 1 || (n & (n - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+template <typename T>
+int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
+{
+    using C = typename Cx<T>::type;
+    const int n[2] = {h->nx, h->ny};
+    const double len[2] = {h->lx, h->ly};
+    void **tw[2] = {&s->twx, &s->twy};
+    void **kn[2] = {&s->knx, &s->kny};
+    for (int d = 0; d < 2; ++d) {
+        const int N = n[d];
+        C *ht = (C *)malloc(sizeof(C) * N);
+        T *hk = (T *)malloc(sizeof(T) * N);
+        if (!ht || !hk) {
+            free(ht);
+            free(hk);
+            return set_error(nullptr, WMIBM_ENOMEM, "host memory for the spectral tables");
+        }
+        for (int m = 0; m < N; ++m) {
+            const double a = 2.0 * M_PI * (double)m / (double)N;
+            ht[m].x = (T)cos(a);
+            ht[m].y = (T)(-sin(a));
+            // wavenumber of bin m: m below N/2, m - N above, 0 for the Nyquist bin
+            const int mm = (2 * m < N) ? m : (2 * m == N ? 0 : m - N);
+            hk[m] = (T)(2.0 * M_PI * (double)mm / len[d] / (double)N);
+        }
+        cudaError_t e = cudaMalloc(tw[d], sizeof(C) * N);
+        if (e == cudaSuccess) e = cudaMalloc(kn[d], sizeof(T) * N);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(*tw[d], ht, sizeof(C) * N, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(*kn[d], hk, sizeof(T) * N, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        free(ht);
+        free(hk);
+        if (e != cudaSuccess) return cuda_status(nullptr, e, "spectral tables");
+    }
+    return WMIBM_OK;
+}
+
+template <typename T>
+int launch_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, cudaStream_t stream)
+{
+    const SpecState *s = h->spec;
+    SpecParams<T> p;
+    p.txx = (const T *)tau[0]; p.txy = (const T *)tau[1]; p.tyy = (const T *)tau[2];
+    p.tzz = (const T *)tau[3]; p.txz = (const T *)tau[4]; p.tyz = (const T *)tau[5];
+    p.fx = (T *)fx; p.fy = (T *)fy; p.fz = (T *)fz;
+    p.twx = (const typename Cx<T>::type *)s->twx;
+    p.twy = (const typename Cx<T>::type *)s->twy;
+    p.knx = (const T *)s->knx;
+    p.kny = (const T *)s->kny;
+    p.ctr = s->ctr;
+    p.status = h->dev_status;
+    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
+    p.lognx = s->lognx; p.logny = s->logny;
+    p.logrx = ilog2_exact(s->rx); p.logwy = ilog2_exact(s->wy);
+    p.ldx = s->ldx; p.ldy = s->ldy;
+    p.kc = s->kc; p.nchunks = s->nchunks; p.xpl = s->xpl; p.ypl = s->ypl;
+    p.total = s->total;
+    p.buf = (int)(s->smem / (2 * sizeof(typename Cx<T>::type)));
+    p.rdz = (T)(1.0 / h->dz);
+    cudaError_t e = cudaFuncSetAttribute(k_spectral<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral shared memory");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral<T>, kSpecThreads, s->smem);
+    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral occupancy");
+    if (per_sm < 1) return set_error(h, WMIBM_EINVAL, "spectral units do not fit on an SM");
+    int64_t grid = (int64_t)per_sm * h->sm_count;
+    if (grid > s->total) grid = s->total;
+    k_spectral<T><<<(unsigned)grid, kSpecThreads, s->smem, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_spectral launch");
+}
+
+}  // namespace
+
+namespace wmibm {
+
+// Called once by wmibm_init: tables, counters and tile shapes of the spectral
+// forcing when nx and ny are powers of two in [2, 2^kSpecMaxLog]; otherwise the
+// handle has no spectral state and wmibm_force_spectral returns WMIBM_EINVAL.
+// Errors go to the thread's last error (the handle is not returned on failure).
+int spectral_setup(wmibm_handle *h, cudaStream_t stream)
+{
+    h->spec = nullptr;
+    const int lx = ilog2_exact(h->nx), ly = ilog2_exact(h->ny);
+    if (lx < 1 || ly < 1 || lx > kSpecMaxLog || ly > kSpecMaxLog) return WMIBM_OK;
+    SpecState *s = (SpecState *)calloc(1, sizeof(SpecState));
+    if (!s) return set_error(nullptr, WMIBM_ENOMEM, "host memory for the spectral state");
+    h->spec = s;
+    s->lognx = lx;
+    s->logny = ly;
+    const bool f64 = h->dtype == WMIBM_F64;
+    const size_t cs = f64 ? 16 : 8;
+    const int budget = f64 ? kSpecBudget / 2 : kSpecBudget;
+    // rows per row unit: even power of two dividing ny, 1.5 rx (nx + 1) within the budget
+    s->ldx = h->nx + 1;
+    s->rx = 2;
+    while (s->rx * 2 <= h->ny && 3 * (s->rx * 2) / 2 * s->ldx <= budget) s->rx *= 2;
+    s->ldy = h->ny + 1;
+    s->wy = 2;
+    while (s->wy * 2 <= h->nx && 3 * (s->wy * 2) / 2 * s->ldy <= budget) s->wy *= 2;
+    const int64_t ex = (int64_t)3 * s->rx / 2 * s->ldx, ey = (int64_t)3 * s->wy / 2 * s->ldy;
+    s->smem = 2 * cs * (size_t)(ex > ey ? ex : ey);
+    s->xpl = h->ny / s->rx;
+    s->ypl = h->nx / s->wy;
+    const double level_bytes = 9.0 * (double)h->nx * (double)h->ny * (double)elem_size(h->dtype);
+    s->kc = (int)(kSpecChunkBytes / level_bytes);
+    if (s->kc < 1) s->kc = 1;
+    if (s->kc > h->nz) s->kc = h->nz;
+    s->nchunks = (h->nz + s->kc - 1) / s->kc;
+    s->total = (int64_t)h->nz * (s->xpl + s->ypl);
+    int st = f64 ? upload_tables<double>(h, s, stream) : upload_tables<float>(h, s, stream);
+    if (st) return st;
+    cudaError_t e = cudaMalloc(&s->ctr, sizeof(unsigned int) * (size_t)(h->nz + 2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ctr, 0, sizeof(unsigned int) * (size_t)(h->nz + 2), stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(nullptr, e, "spectral counters");
+    return WMIBM_OK;
+}
+
+void spectral_free(wmibm_handle *h)
+{
+    SpecState *s = h ? h->spec : nullptr;
+    if (!s) return;
+    if (s->twx) cudaFree(s->twx);
+    if (s->twy) cudaFree(s->twy);
+    if (s->knx) cudaFree(s->knx);
+    if (s->kny) cudaFree(s->kny);
+    if (s->ctr) cudaFree(s->ctr);
+    free(s);
+    h->spec = nullptr;
+}
+
+// Shape of the spectral launch, for the bench and the tests: [rows per row unit,
+// columns per column unit, levels per chunk, shared bytes per block].
+int spectral_shape(const wmibm_handle *h, int64_t out[4])
+{
+    const SpecState *s = h->spec;
+    if (!s) return WMIBM_EINVAL;
+    out[0] = s->rx;
+    out[1] = s->wy;
+    out[2] = s->kc;
+    out[3] = (int64_t)s->smem;
+    return WMIBM_OK;
+}
+
+}  // namespace wmibm
+
+extern "C" int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz,
+                                    void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!tau || !fx || !fy || !fz) return set_error(h, WMIBM_EINVAL, "NULL stress or force pointer");
+    for (int c = 0; c < 6; ++c)
+        if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
+    if (!h->spec)
+        return set_error(h, WMIBM_EINVAL, "spectral derivatives need nx and ny powers of two in [2, %d] (got %d x %d)",
+                         1 << kSpecMaxLog, h->nx, h->ny);
+    int st = check_device(h);
+    if (st) return st;
+    if (h->dtype == WMIBM_F64) return launch_spectral<double>(h, tau, fx, fy, fz, (cudaStream_t)stream);
+    return launch_spectral<float>(h, tau, fx, fy, fz, (cudaStream_t)stream);
+}
+
+extern "C" int wmibm_spectral_shape(const wmibm_handle *h, int64_t out[4])
+{
+    if (!h || !out) return WMIBM_EINVAL;
+    return wmibm::spectral_shape(h, out);
+}

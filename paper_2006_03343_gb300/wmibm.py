@@ -29,7 +29,7 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
-            "wmibm_backward", "wmibm_batch_wall_stress_force")
+            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape")
 
 
 class WmibmError(RuntimeError):
@@ -92,6 +92,10 @@ def load(path: Optional[str] = None):
     L.wmibm_wall_stress.restype = ctypes.c_int
     L.wmibm_force.argtypes = [_VP, _PVP, _VP, _VP, _VP, _VP]
     L.wmibm_force.restype = ctypes.c_int
+    L.wmibm_force_spectral.argtypes = [_VP, _PVP, _VP, _VP, _VP, _VP]
+    L.wmibm_force_spectral.restype = ctypes.c_int
+    L.wmibm_spectral_shape.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
+    L.wmibm_spectral_shape.restype = ctypes.c_int
     L.wmibm_mask.argtypes = [_VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_mask.restype = ctypes.c_int
     L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
@@ -271,6 +275,21 @@ class Handle:
         self._check(self._L.wmibm_force(self._h, _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
                                         _stream_ptr(stream)))
 
+    def force_spectral(self, tau: Sequence, f: Sequence, stream=None):
+        """f = -div(tau) with pseudo-spectral x and y derivatives (Eqs. 13-14)."""
+        for t in list(tau) + list(f):
+            self._field(t)
+        self._check(self._L.wmibm_force_spectral(self._h, _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
+                                                 _stream_ptr(stream)))
+
+    def spectral_shape(self):
+        """(rows per row unit, columns per column unit, levels per chunk, shared bytes
+        per block) of the spectral launch, or None without spectral support."""
+        out = (ctypes.c_int64 * 4)()
+        if self._L.wmibm_spectral_shape(self._h, out) != OK:
+            return None
+        return tuple(int(x) for x in out)
+
     def mask(self, u, v, w, gradp=None, dt=0.0, stream=None):
         for t in (u, v, w):
             self._field(t, vel=True)
@@ -392,6 +411,9 @@ class PreparedStep:
 
     def force(self, stream=None):
         self.h._check(self._L.wmibm_force(self.h._h, self._tau, *self._f, _stream_ptr(stream)))
+
+    def force_spectral(self, stream=None):
+        self.h._check(self._L.wmibm_force_spectral(self.h._h, self._tau, *self._f, _stream_ptr(stream)))
 
     def wall_stress_force(self, stream=None):
         self.h._check(self._L.wmibm_wall_stress_force(self.h._h, self._u, self._v, self._w, self._tau, *self._f,

@@ -102,8 +102,8 @@ def test_calls_reject_null_handle(lib):
 
 
 def test_later_entry_points_reject_null_arguments(lib):
-    """The step, adjoint, tuning and batch entry points refuse NULL handles and
-    tables on the host, before anything reaches a GPU."""
+    """The step, spectral, adjoint, tuning and batch entry points refuse NULL
+    handles and tables on the host, before anything reaches a GPU."""
     from paper_2006_03343_gb300 import wmibm
     tau = (ctypes.c_void_p * 6)()
     three = (ctypes.c_void_p * 3)()
@@ -111,6 +111,8 @@ def test_later_entry_points_reject_null_arguments(lib):
     assert lib.wmibm_wall_stress_force(None, None, None, None, tau, None, None, None, None, None) == wmibm.EINVAL
     assert lib.wmibm_force_mask(None, tau, None, None, None, None, None, None, None, 0.0, None) == wmibm.EINVAL
     assert lib.wmibm_wall_stress_noalloc(None, None, None, None, tau, None, None) == wmibm.EINVAL
+    assert lib.wmibm_force_spectral(None, tau, None, None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_spectral_shape(None, (ctypes.c_int64 * 4)()) == wmibm.EINVAL
     assert lib.wmibm_set_log_z0(None, None, None) == wmibm.EINVAL
     assert lib.wmibm_backward(None, three, three, None, None, None, None, None) == wmibm.EINVAL
     t = wmibm.Tuning()
