@@ -138,8 +138,8 @@ int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, v
  * Arguments, layout and boundary rows as in wmibm_force.  One persistent launch
  * (FFT lines in shared memory, FP32 or FP64 as the handle's dtype); tau and
  * f must not overlap.
- * Requires nx and ny powers of two in [2, 2048]: otherwise EINVAL, before any
- * GPU work.  Errors: EINVAL, ESTATE, ECUDA.
+ * Requires nx and ny powers of two in [2, 2048] for FP32, [2, 1024] for FP64:
+ * otherwise EINVAL, before any GPU work.  Errors: EINVAL, ESTATE, ECUDA.
  */
 int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream);
 

@@ -34,7 +34,7 @@
 
 namespace wmibm {
 
-constexpr int kSpecMaxLog = 11;         // lines of up to 2048 points
+constexpr int kSpecMaxLog = 11;         // lines of up to 2048 points (FP32; 1024 for FP64)
 constexpr int kSpecThreads = 256;
 constexpr int kSpecBudget = 3200;       // complex elements per shared buffer aimed at (FP32; half for FP64)
 constexpr double kSpecChunkBytes = 24.0 * 1024 * 1024;   // L2 footprint of one chunk of levels
@@ -42,7 +42,7 @@ constexpr double kSpecChunkBytes = 24.0 * 1024 * 1024;   // L2 footprint of one 
 struct SpecState {
     int lognx, logny;
     int rx, wy;                 // rows per row unit, columns per column unit
-    int ldx, ldy;               // shared-memory stride of a sequence (complex elements, padded by one)
+    int ldx, ldy;               // shared-memory stride of a sequence (complex elements, skewed and padded)
     int kc, nchunks;
     int xpl, ypl;               // units per level
     int64_t total;
@@ -94,6 +94,10 @@ template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 template <typename C>
 __device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }       // -i a
+
+// Element e of a sequence sits at e + e/32 in shared memory: the padding spreads
+// the stride-R writes of the first Stockham pass over the banks.
+__device__ __forceinline__ int sk(int e) { return e + (e >> 5); }
 
 // R-point forward DFT in registers, natural order in and out:
 // V[q] = sum_r v[r] exp(-2 pi i r q / R).
@@ -150,8 +154,10 @@ struct Dft<T, 8> {
 // One Stockham pass of radix R over S sequences of length N = 2^logN, from a to
 // b, after logNs earlier passes.  Butterfly j of a sequence reads elements
 // j + r N/R, twiddles them by omega_N^(r jm N/(Ns R)) with jm = j mod Ns, and
-// writes element (j - jm) R + jm + r Ns.  PRE: multiply each input (bin m) by
-// i k_m / N and conjugate it first, i.e. v -> (-kn_m v.y, -kn_m v.x).
+// writes element (j - jm) R + jm + r Ns.  The pass's twiddles are a table of
+// its own, tw[(r - 1) Ns + jm], so that a warp's loads of one r are contiguous.
+// PRE: multiply each input (bin m) by i k_m / N and conjugate it first, i.e.
+// v -> (-kn_m v.y, -kn_m v.x).
 template <typename T, int R, bool PRE>
 __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict__ a,
                                          typename Cx<T>::type *__restrict__ b, int S, int logN, int logNs, int ld,
@@ -162,14 +168,13 @@ __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict_
     const int lognb = logN - logR;
     const int nb = 1 << lognb;
     const int total = S << lognb;
-    const int tshift = logN - logNs - logR;
     const int msk = (1 << logNs) - 1;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    for (int t = threadIdx.x; t < total; t += kSpecThreads) {
         const int s = t >> lognb, j = t & (nb - 1);
         const C *in = a + s * ld;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+        for (int r = 0; r < R; ++r) v[r] = in[sk(j + r * nb)];
         if (PRE) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -178,26 +183,82 @@ __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict_
             }
         }
         const int jm = j & msk;
-        if (jm) {
-            const int step = jm << tshift;
+        if (logNs > 0) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + r * step));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + ((r - 1) << logNs) + jm));
         }
         Dft<T, R>::run(v);
-        C *out = b + s * ld + ((j - jm) << logR) + jm;
+        C *out = b + s * ld;
+        const int o0 = ((j - jm) << logR) + jm;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[r << logNs] = v[r];
+        for (int r = 0; r < R; ++r) out[sk(o0 + (r << logNs))] = v[r];
+    }
+}
+
+// The first Stockham pass (Ns = 1, no twiddles) of the first transform, read
+// straight from the planar staging P (planes of n = L x N values): sequence s < L
+// is plane0 + i plane1 of line s, sequence L + q is plane 2 of lines 2q and 2q + 1.
+// ROWS: the staging is [line][pos] and consecutive threads take consecutive
+// butterflies of one sequence; otherwise it is [pos][line] and consecutive
+// threads take consecutive sequences of one butterfly, so that both the staging
+// reads and the skewed sequence writes stay spread over the banks.
+template <typename T, int R, bool ROWS>
+__device__ __forceinline__ void fft_first_pass(const T *__restrict__ P, typename Cx<T>::type *__restrict__ b,
+                                               int logL, int logN, int ld)
+{
+    using C = typename Cx<T>::type;
+    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int L = 1 << logL;
+    const int S = L + L / 2;
+    const int lognb = logN - logR;
+    const int nb = 1 << lognb;
+    const int n = L << logN;
+    const int total = S << lognb;
+    for (int t = threadIdx.x; t < total; t += kSpecThreads) {
+        int s, j;
+        if (ROWS) {
+            s = t >> lognb;
+            j = t & (nb - 1);
+        } else {
+            j = t / S;
+            s = t - j * S;
+        }
+        C v[R];
+        if (s < L) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int pos = j + r * nb;
+                const int e = ROWS ? (s << logN) + pos : (pos << logL) + s;
+                v[r] = C{P[e], P[n + e]};
+            }
+        } else {
+            const int l0 = 2 * (s - L);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int pos = j + r * nb;
+                if (ROWS) {
+                    v[r] = C{P[2 * n + (l0 << logN) + pos], P[2 * n + ((l0 + 1) << logN) + pos]};
+                } else {
+                    const C q = *reinterpret_cast<const C *>(P + 2 * n + (pos << logL) + l0);
+                    v[r] = q;
+                }
+            }
+        }
+        Dft<T, R>::run(v);
+        C *out = b + s * ld;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[sk(j * R + r)] = v[r];
     }
 }
 
 // Forward FFT of S sequences (stride ld) held in a, b as scratch; returns the
-// buffer that holds the result.  Ends with a block barrier.
+// buffer that holds the result.  tw: the per-pass twiddle tables, one after the
+// other (N - 1 entries in all).  Ends with a block barrier.
 template <typename T, bool PRE>
 __device__ typename Cx<T>::type *fft_block(typename Cx<T>::type *a, typename Cx<T>::type *b, int S, int logN,
-                                           int ld, const typename Cx<T>::type *tw, const T *kn)
+                                           int ld, const typename Cx<T>::type *tw, const T *kn, int logNs = 0)
 {
-    int logNs = 0;
-    bool first = true;
+    bool first = logNs == 0;
     while (logNs < logN) {
         const int left = logN - logNs;
         int logR;
@@ -215,6 +276,7 @@ __device__ typename Cx<T>::type *fft_block(typename Cx<T>::type *a, typename Cx<
             logR = 1;
         }
         __syncthreads();
+        tw += ((1 << logR) - 1) << logNs;      // this pass's table: Ns (R - 1) entries
         typename Cx<T>::type *t = a;
         a = b;
         b = t;
@@ -224,21 +286,78 @@ __device__ typename Cx<T>::type *fft_block(typename Cx<T>::type *a, typename Cx<
     return a;
 }
 
-// Spectral derivative of the S staged sequences: conj(FFT(conj(i k/N * FFT(z)))).
-// The returned buffer holds (D a, -D b) for each z = a + i b.
-template <typename T>
-__device__ __forceinline__ typename Cx<T>::type *derive(typename Cx<T>::type *a, typename Cx<T>::type *b, int S,
-                                                        int logN, int ld, const typename Cx<T>::type *tw,
-                                                        const T *kn)
+// Spectral derivative of the staged lines: z = plane0 + i plane1 (and the plane-2
+// pairs), conj(FFT(conj(i k/N * FFT(z)))).  The first pass reads the planar
+// staging P and writes A; P is scratch afterwards.  The returned buffer holds
+// (D a, -D b) for each z = a + i b.
+template <typename T, bool ROWS>
+__device__ __forceinline__ typename Cx<T>::type *derive(T *P, typename Cx<T>::type *A, int logL, int logN, int ld,
+                                                        const typename Cx<T>::type *tw, const T *kn)
 {
-    typename Cx<T>::type *r1 = fft_block<T, false>(a, b, S, logN, ld, tw, kn);
-    return fft_block<T, true>(r1, r1 == a ? b : a, S, logN, ld, tw, kn);
+    using C = typename Cx<T>::type;
+    C *B = reinterpret_cast<C *>(P);
+    const int S = (1 << logL) + (1 << logL) / 2;
+    const int logR = logN >= 3 ? 3 : logN;
+    if (logR == 3) fft_first_pass<T, 8, ROWS>(P, A, logL, logN, ld);
+    else if (logR == 2) fft_first_pass<T, 4, ROWS>(P, A, logL, logN, ld);
+    else fft_first_pass<T, 2, ROWS>(P, A, logL, logN, ld);
+    __syncthreads();
+    C *r1 = A;
+    if (logR < logN) r1 = fft_block<T, false>(A, B, S, logN, ld, tw + ((1 << logR) - 1), kn, logR);
+    return fft_block<T, true>(r1, r1 == A ? B : A, S, logN, ld, tw, kn);
 }
 
-// Row unit: level k, rows j0 .. j0 + rx - 1.  Sequences: s < rx is row j0 + s
-// as txx + i txy; rx + q holds rows j0 + 2q and j0 + 2q + 1 of txz.
+// Asynchronous global -> shared copies (cp.async; completion by commit groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issues the copies of a unit's input lines into the planar staging buffer P:
+// three planes of n = lines x line-length values (row unit: txx, txy, txz rows
+// j0 .. j0 + rx - 1; column unit: txy, tyy, tyz as [ny][wy] strips), then
+// commits the group (an empty group when the unit needs no input).
+template <typename T, int VB>
+__device__ void stage_unit(const SpecParams<T> &p, T *P, int kind, int level, int idx)
+{
+    constexpr int V = VB / (int)sizeof(T);            // values per copy
+    if (kind == 0 && level < p.nz - 1) {
+        const int logn = p.logrx + p.lognx;
+        const int64_t base = (int64_t)level * p.nx * p.ny + ((int64_t)idx << logn);
+        const int per = (1 << logn) / V;
+        for (int c = threadIdx.x; c < 3 * per; c += kSpecThreads) {
+            const int f = c / per, q = c - f * per;
+            const T *src = f == 0 ? p.txx : (f == 1 ? p.txy : p.txz);
+            cp_async<VB>(P + ((int64_t)f << logn) + q * V, src + base + q * V);
+        }
+    } else if (kind == 1 && level < p.nz - 1) {
+        const int logn = p.logny + p.logwy;
+        const int64_t base = (int64_t)level * p.nx * p.ny + ((int64_t)idx << p.logwy);
+        const int per_row = (1 << p.logwy) / V;
+        const int per = per_row << p.logny;
+        for (int c = threadIdx.x; c < 3 * per; c += kSpecThreads) {
+            const int f = c / per, q = c - f * per;
+            const int j = q / per_row, cc = q - j * per_row;
+            const T *src = f == 0 ? p.txy : (f == 1 ? p.tyy : p.tyz);
+            cp_async<VB>(P + ((int64_t)f << logn) + (j << p.logwy) + cc * V, src + base + (int64_t)j * p.nx + cc * V);
+        }
+    }
+    cp_async_commit();
+}
+
+// Row unit on level k, rows j0 .. j0 + rx - 1, whose input lines are staged in
+// P: d_x of txx, txy (sequences s < rx) and txz (rows 2q, 2q + 1 in rx + q),
+// plus the vertical terms -> the partial forcing in f.  P is scratch afterwards.
 template <typename T>
-__device__ void row_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typename Cx<T>::type *B, int k, int j0)
+__device__ void row_unit(const SpecParams<T> &p, T *P, typename Cx<T>::type *A, int k, int j0)
 {
     using C = typename Cx<T>::type;
     const int rx = 1 << p.logrx;
@@ -246,7 +365,7 @@ __device__ void row_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typena
     const int64_t plane = (int64_t)p.nx * p.ny;
     const int64_t base = (int64_t)k * plane + (int64_t)j0 * p.nx;
     if (k == p.nz - 1) {                    // ghost uv level / lid: f = 0
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        for (int e = threadIdx.x; e < n; e += kSpecThreads) {
             p.fx[base + e] = T(0);
             p.fy[base + e] = T(0);
             p.fz[base + e] = T(0);
@@ -254,58 +373,20 @@ __device__ void row_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typena
         return;
     }
     const int ld = p.ldx;
+    const C *R = derive<T, true>(P, A, p.logrx, p.lognx, ld, p.twx, p.knx);
 #pragma unroll 4
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < n; e += kSpecThreads) {
         const int r = e >> p.lognx, i = e & (p.nx - 1);
         const int64_t o = base + e;
-        A[r * ld + i] = C{__ldg(p.txx + o), __ldg(p.txy + o)};
-        reinterpret_cast<T *>(A + (rx + (r >> 1)) * ld + i)[r & 1] = __ldg(p.txz + o);
-    }
-    __syncthreads();
-    const C *R = derive<T>(A, B, rx + rx / 2, p.lognx, ld, p.twx, p.knx);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int r = e >> p.lognx, i = e & (p.nx - 1);
-        const int64_t o = base + e;
-        const C d = R[r * ld + i];                          // (d_x txx, -d_x txy)
-        const C dd = R[(rx + (r >> 1)) * ld + i];
-        const T dxz = (r & 1) ? -dd.y : dd.x;               // d_x txz
         const T xz0 = __ldg(p.txz + o), xz1 = __ldg(p.txz + o + plane);
         const T yz0 = __ldg(p.tyz + o), yz1 = __ldg(p.tyz + o + plane);
+        const T zz0 = __ldg(p.tzz + o), zzm = k > 0 ? __ldg(p.tzz + o - plane) : T(0);
+        const C d = R[r * ld + sk(i)];                      // (d_x txx, -d_x txy)
+        const C dd = R[(rx + (r >> 1)) * ld + sk(i)];
+        const T dxz = (r & 1) ? -dd.y : dd.x;               // d_x txz
         p.fx[o] = -(d.x + (xz1 - xz0) * p.rdz);
         p.fy[o] = -(-d.y + (yz1 - yz0) * p.rdz);
-        p.fz[o] = (k == 0) ? T(0) : -(dxz + (__ldg(p.tzz + o) - __ldg(p.tzz + o - plane)) * p.rdz);
-    }
-}
-
-// Column unit: level k, columns i0 .. i0 + wy - 1.  Sequences: c < wy is column
-// i0 + c as txy + i tyy; wy + q holds columns i0 + 2q and i0 + 2q + 1 of tyz.
-template <typename T>
-__device__ void column_unit(const SpecParams<T> &p, typename Cx<T>::type *A, typename Cx<T>::type *B, int k, int i0)
-{
-    using C = typename Cx<T>::type;
-    if (k == p.nz - 1) return;              // f stays 0 there (written by the row units)
-    const int wy = 1 << p.logwy;
-    const int n = wy << p.logny;
-    const int64_t base = (int64_t)k * p.nx * p.ny + i0;
-    const int ld = p.ldy;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int j = e >> p.logwy, c = e & (wy - 1);
-        const int64_t o = base + (int64_t)j * p.nx + c;
-        A[c * ld + j] = C{__ldg(p.txy + o), __ldg(p.tyy + o)};
-        reinterpret_cast<T *>(A + (wy + (c >> 1)) * ld + j)[c & 1] = __ldg(p.tyz + o);
-    }
-    __syncthreads();
-    const C *R = derive<T>(A, B, wy + wy / 2, p.logny, ld, p.twy, p.kny);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int j = e >> p.logwy, c = e & (wy - 1);
-        const int64_t o = base + (int64_t)j * p.nx + c;
-        const C d = R[c * ld + j];                          // (d_y txy, -d_y tyy)
-        const C dd = R[(wy + (c >> 1)) * ld + j];
-        const T dyz = (c & 1) ? -dd.y : dd.x;               // d_y tyz
-        p.fx[o] = __ldcg(p.fx + o) - d.x;
-        p.fy[o] = __ldcg(p.fy + o) + d.y;
-        if (k > 0) p.fz[o] = __ldcg(p.fz + o) - dyz;
+        p.fz[o] = (k == 0) ? T(0) : -(dxz + (zz0 - zzm) * p.rdz);
     }
 }
 
@@ -327,6 +408,36 @@ __device__ bool wait_level(const unsigned int *ctr, unsigned int target, int *st
                 return false;
             }
         }
+    }
+}
+
+// Column unit on level k, columns i0 .. i0 + wy - 1, staged in P: d_y of txy, tyy
+// (sequences c < wy) and tyz (columns 2q, 2q + 1 in wy + q), subtracted from f
+// once every row unit of level k has written its partial forcing.
+template <typename T>
+__device__ void column_unit(const SpecParams<T> &p, T *P, typename Cx<T>::type *A, int k, int i0, int *s_go)
+{
+    using C = typename Cx<T>::type;
+    if (k == p.nz - 1) return;              // f stays 0 there (written by the row units)
+    const int wy = 1 << p.logwy;
+    const int n = wy << p.logny;
+    const int64_t base = (int64_t)k * p.nx * p.ny + i0;
+    const int ld = p.ldy;
+    const C *R = derive<T, false>(P, A, p.logwy, p.logny, ld, p.twy, p.kny);
+    if (threadIdx.x == 0) *s_go = wait_level(p.ctr + 2 + k, (unsigned)p.xpl, p.status) ? 1 : 0;
+    __syncthreads();
+    if (!*s_go) return;                     // gave up waiting: skipped, the status says so
+#pragma unroll 4
+    for (int e = threadIdx.x; e < n; e += kSpecThreads) {
+        const int j = e >> p.logwy, c = e & (wy - 1);
+        const int64_t o = base + (int64_t)j * p.nx + c;
+        const T fx0 = __ldcg(p.fx + o), fy0 = __ldcg(p.fy + o), fz0 = __ldcg(p.fz + o);
+        const C d = R[c * ld + sk(j)];                      // (d_y txy, -d_y tyy)
+        const C dd = R[(wy + (c >> 1)) * ld + sk(j)];
+        const T dyz = (c & 1) ? -dd.y : dd.x;               // d_y tyz
+        p.fx[o] = fx0 - d.x;
+        p.fy[o] = fy0 + d.y;
+        if (k > 0) p.fz[o] = fz0 - dyz;
     }
 }
 
@@ -362,43 +473,58 @@ __device__ void decode_unit(const SpecParams<T> &p, int64_t u, int *kind, int *l
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSpecThreads, 2) k_spectral(SpecParams<T> p)
+__device__ __forceinline__ void claim(const SpecParams<T> &p, int *slot)
+{
+    const int64_t u = (int64_t)atomicAdd(p.ctr, 1u);
+    int kind = -1, level = 0, idx = 0;
+    if (u < p.total) decode_unit(p, u, &kind, &level, &idx);
+    slot[0] = kind;
+    slot[1] = level;
+    slot[2] = idx;
+}
+
+// Persistent loop: each block holds the unit it works on and the next one, whose
+// input lines stream into the other staging buffer meanwhile.  A column unit
+// waits only for the row units of its level, which hold smaller tickets; the
+// unfinished unit with the smallest ticket can always proceed, so the loop
+// ends.  Shared memory: staging buffers P0, P1 and the FFT buffer A, each buf
+// complex elements.
+template <typename T, int VB>
+__global__ void __launch_bounds__(kSpecThreads, sizeof(T) == 4 ? 3 : 2) k_spectral(SpecParams<T> p)
 {
     using C = typename Cx<T>::type;
     extern __shared__ __align__(16) unsigned char spec_smem[];
     C *A = reinterpret_cast<C *>(spec_smem);
-    C *B = A + p.buf;
-    __shared__ int s_kind, s_level, s_idx, s_last;
+    T *const P0 = reinterpret_cast<T *>(A + p.buf);
+    T *const P1 = reinterpret_cast<T *>(A + 2 * p.buf);
+    __shared__ int s_u[2][3];
+    __shared__ int s_go, s_last;
+    int cur = 0;
+    if (threadIdx.x == 0) claim(p, s_u[0]);
+    __syncthreads();
+    stage_unit<T, VB>(p, P0, s_u[0][0], s_u[0][1], s_u[0][2]);
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int64_t u = (int64_t)atomicAdd(p.ctr, 1u);
-            int kind = -1, level = 0, idx = 0;
-            if (u < p.total) {
-                decode_unit(p, u, &kind, &level, &idx);
-                // a column unit needs every row unit of its level finished
-                if (kind == 1 && !wait_level(p.ctr + 2 + level, (unsigned)p.xpl, p.status)) kind = 2;
-            }
-            s_kind = kind;
-            s_level = level;
-            s_idx = idx;
-        }
-        __syncthreads();
-        const int kind = s_kind, level = s_level, idx = s_idx;
+        const int kind = s_u[cur][0], level = s_u[cur][1], idx = s_u[cur][2];
         if (kind < 0) break;
+        if (threadIdx.x == 0) claim(p, s_u[cur ^ 1]);
+        __syncthreads();
+        stage_unit<T, VB>(p, cur ? P0 : P1, s_u[cur ^ 1][0], s_u[cur ^ 1][1], s_u[cur ^ 1][2]);
+        cp_async_wait<1>();                 // this unit's lines have landed (the next unit's may not)
+        __syncthreads();
         if (kind == 0) {
-            row_unit<T>(p, A, B, level, idx << p.logrx);
+            row_unit<T>(p, cur ? P1 : P0, A, level, idx << p.logrx);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
                 atomicAdd(p.ctr + 2 + level, 1u);
             }
-        } else if (kind == 1) {
-            column_unit<T>(p, A, B, level, idx << p.logwy);
-            __syncthreads();
         } else {
-            __syncthreads();                // gave up waiting: the unit is skipped, the status says so
+            column_unit<T>(p, cur ? P1 : P0, A, level, idx << p.logwy, &s_go);
+            __syncthreads();
         }
+        cur ^= 1;
     }
+    cp_async_wait<0>();
     // the last block out re-arms the counters for the next launch: every block
     // has taken its final ticket and passed its waits by then
     if (threadIdx.x == 0) {
@@ -407,7 +533,7 @@ __global__ void __launch_bounds__(kSpecThreads, 2) k_spectral(SpecParams<T> p)
     }
     __syncthreads();
     if (s_last) {
-        for (int k = threadIdx.x; k < p.nz; k += blockDim.x) p.ctr[2 + k] = 0u;
+        for (int k = threadIdx.x; k < p.nz; k += kSpecThreads) p.ctr[2 + k] = 0u;
         if (threadIdx.x == 0) p.ctr[0] = 0u;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -442,10 +568,21 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
             free(hk);
             return set_error(nullptr, WMIBM_ENOMEM, "host memory for the spectral tables");
         }
+        // per-pass twiddles: pass (Ns, R) holds omega_N^(r jm N/(Ns R)) at (r - 1) Ns + jm
+        int at = 0;
+        for (int logNs = 0, logN = ilog2_exact(N); logNs < logN;) {
+            const int logR = logN - logNs >= 3 ? 3 : logN - logNs;
+            const int Ns = 1 << logNs, R = 1 << logR;
+            for (int r = 1; r < R; ++r)
+                for (int jm = 0; jm < Ns; ++jm) {
+                    const double a = 2.0 * M_PI * (double)r * (double)jm / (double)(Ns * R);
+                    ht[at].x = (T)cos(a);
+                    ht[at].y = (T)(-sin(a));
+                    ++at;
+                }
+            logNs += logR;
+        }
         for (int m = 0; m < N; ++m) {
-            const double a = 2.0 * M_PI * (double)m / (double)N;
-            ht[m].x = (T)cos(a);
-            ht[m].y = (T)(-sin(a));
             // wavenumber of bin m: m below N/2, m - N above, 0 for the Nyquist bin
             const int mm = (2 * m < N) ? m : (2 * m == N ? 0 : m - N);
             hk[m] = (T)(2.0 * M_PI * (double)mm / len[d] / (double)N);
@@ -460,6 +597,22 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
         if (e != cudaSuccess) return cuda_status(nullptr, e, "spectral tables");
     }
     return WMIBM_OK;
+}
+
+template <typename T, int VB>
+int run_spectral(wmibm_handle *h, const SpecParams<T> &p, const SpecState *s, cudaStream_t stream)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_spectral<T, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)s->smem);
+    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral shared memory");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral<T, VB>, kSpecThreads, s->smem);
+    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral occupancy");
+    if (per_sm < 1) return set_error(h, WMIBM_EINVAL, "spectral units do not fit on an SM");
+    int64_t grid = (int64_t)per_sm * h->sm_count;
+    if (grid > s->total) grid = s->total;
+    k_spectral<T, VB><<<(unsigned)grid, kSpecThreads, s->smem, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_spectral launch");
 }
 
 template <typename T>
@@ -482,18 +635,13 @@ int launch_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *f
     p.ldx = s->ldx; p.ldy = s->ldy;
     p.kc = s->kc; p.nchunks = s->nchunks; p.xpl = s->xpl; p.ypl = s->ypl;
     p.total = s->total;
-    p.buf = (int)(s->smem / (2 * sizeof(typename Cx<T>::type)));
+    p.buf = (int)(s->smem / (3 * sizeof(typename Cx<T>::type)));
     p.rdz = (T)(1.0 / h->dz);
-    cudaError_t e = cudaFuncSetAttribute(k_spectral<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
-    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral shared memory");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral<T>, kSpecThreads, s->smem);
-    if (e != cudaSuccess) return cuda_status(h, e, "k_spectral occupancy");
-    if (per_sm < 1) return set_error(h, WMIBM_EINVAL, "spectral units do not fit on an SM");
-    int64_t grid = (int64_t)per_sm * h->sm_count;
-    if (grid > s->total) grid = s->total;
-    k_spectral<T><<<(unsigned)grid, kSpecThreads, s->smem, stream>>>(p);
-    return cuda_status(h, cudaGetLastError(), "k_spectral launch");
+    // 16-byte copies when every staged line segment starts on a 16-byte boundary
+    bool v16 = (h->nx * sizeof(T)) % 16 == 0 && (s->wy * sizeof(T)) % 16 == 0;
+    for (int c = 0; c < 6; ++c) v16 = v16 && ((uintptr_t)tau[c] & 15u) == 0;
+    if (v16) return run_spectral<T, 16>(h, p, s, stream);
+    return run_spectral<T, (int)sizeof(T)>(h, p, s, stream);
 }
 
 }  // namespace
@@ -501,14 +649,16 @@ int launch_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *f
 namespace wmibm {
 
 // Called once by wmibm_init: tables, counters and tile shapes of the spectral
-// forcing when nx and ny are powers of two in [2, 2^kSpecMaxLog]; otherwise the
+// forcing when nx and ny are powers of two in [2, 2048] (FP32) or [2, 1024]
+// (FP64, whose three shared buffers would not fit otherwise); otherwise the
 // handle has no spectral state and wmibm_force_spectral returns WMIBM_EINVAL.
 // Errors go to the thread's last error (the handle is not returned on failure).
 int spectral_setup(wmibm_handle *h, cudaStream_t stream)
 {
     h->spec = nullptr;
     const int lx = ilog2_exact(h->nx), ly = ilog2_exact(h->ny);
-    if (lx < 1 || ly < 1 || lx > kSpecMaxLog || ly > kSpecMaxLog) return WMIBM_OK;
+    const int maxlog = h->dtype == WMIBM_F64 ? kSpecMaxLog - 1 : kSpecMaxLog;
+    if (lx < 1 || ly < 1 || lx > maxlog || ly > maxlog) return WMIBM_OK;
     SpecState *s = (SpecState *)calloc(1, sizeof(SpecState));
     if (!s) return set_error(nullptr, WMIBM_ENOMEM, "host memory for the spectral state");
     h->spec = s;
@@ -518,14 +668,15 @@ int spectral_setup(wmibm_handle *h, cudaStream_t stream)
     const size_t cs = f64 ? 16 : 8;
     const int budget = f64 ? kSpecBudget / 2 : kSpecBudget;
     // rows per row unit: even power of two dividing ny, 1.5 rx (nx + 1) within the budget
-    s->ldx = h->nx + 1;
+    s->ldx = h->nx + (h->nx >> 5) + 1;       // skewed sequence (e + e/32) plus one: odd-ish bank offset
     s->rx = 2;
     while (s->rx * 2 <= h->ny && 3 * (s->rx * 2) / 2 * s->ldx <= budget) s->rx *= 2;
-    s->ldy = h->ny + 1;
+    s->ldy = h->ny + (h->ny >> 5) + 1;
     s->wy = 2;
     while (s->wy * 2 <= h->nx && 3 * (s->wy * 2) / 2 * s->ldy <= budget) s->wy *= 2;
     const int64_t ex = (int64_t)3 * s->rx / 2 * s->ldx, ey = (int64_t)3 * s->wy / 2 * s->ldy;
-    s->smem = 2 * cs * (size_t)(ex > ey ? ex : ey);
+    const int64_t buf = ((ex > ey ? ex : ey) + 1) & ~(int64_t)1;    // even: 16-byte aligned buffers
+    s->smem = 3 * cs * (size_t)buf;
     s->xpl = h->ny / s->rx;
     s->ypl = h->nx / s->wy;
     const double level_bytes = 9.0 * (double)h->nx * (double)h->ny * (double)elem_size(h->dtype);
@@ -580,7 +731,7 @@ extern "C" int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], v
         if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
     if (!h->spec)
         return set_error(h, WMIBM_EINVAL, "spectral derivatives need nx and ny powers of two in [2, %d] (got %d x %d)",
-                         1 << kSpecMaxLog, h->nx, h->ny);
+                         h->dtype == WMIBM_F64 ? 1 << (kSpecMaxLog - 1) : 1 << kSpecMaxLog, h->nx, h->ny);
     int st = check_device(h);
     if (st) return st;
     if (h->dtype == WMIBM_F64) return launch_spectral<double>(h, tau, fx, fy, fz, (cudaStream_t)stream);

@@ -2,7 +2,7 @@
 Eqs. 13-14, vertical differences by Eqs. 15-16) against the FP64 oracle's
 force_spectral on the same seeded stresses: small grids that span several row
 and column units, several level chunks and the edge sizes (2-point lines, the
-2048-point maximum, nx < ny and nx > ny); the full 512 x 256 x 256 hill grid on
+longest lines (2048 points FP32, 1024 FP64), nx < ny and nx > ny); the full 512 x 256 x 256 hill grid on
 sampled levels; graph replay; determinism; and the stage a1 + spectral a2
 against the oracle's wall stress followed by its spectral divergence."""
 import numpy as np
@@ -72,10 +72,11 @@ def test_spectral_force_matches_oracle(wm, oracle_mod, shape, dtype):
 
 
 @pytest.mark.parametrize("shape,dtype", [((512, 256, 12), "f32"), ((512, 256, 8), "f64"), ((2048, 4, 3), "f32"),
-                                         ((8, 2048, 3), "f64")])
+                                         ((8, 2048, 3), "f32"), ((1024, 8, 3), "f64"), ((4, 1024, 3), "f64")])
 def test_spectral_force_several_chunks_and_longest_lines(wm, oracle_mod, shape, dtype):
     """Grids whose level chunks are fewer than the levels (the column units wait on
-    row units of earlier chunks) and 2048-point lines in either direction."""
+    row units of earlier chunks) and the longest lines in either direction (2048
+    points in FP32, 1024 in FP64)."""
     h, grid = _handle(wm, shape, dtype)
     rx, wy, kc, smem = h.spectral_shape()
     nx, ny, nz = shape
@@ -165,13 +166,20 @@ def test_spectral_graph_replay_and_determinism(wm):
 
 
 def test_unsupported_grid_is_rejected(wm):
-    """nx or ny not a power of two: EINVAL with a message, nothing launched."""
+    """nx or ny not a power of two, or FP64 lines longer than 1024 points: EINVAL
+    with a message, nothing launched."""
     h, grid = _handle(wm, (48, 32, 5), "f32")
     assert h.spectral_shape() is None
     tau = [torch.zeros(h.shape, dtype=torch.float32, device="cuda") for _ in range(6)]
     f = [torch.zeros(h.shape, dtype=torch.float32, device="cuda") for _ in range(3)]
     with pytest.raises(wm.WmibmError, match="power"):
         h.force_spectral(tau, f)
+    h64, _ = _handle(wm, (2048, 4, 3), "f64")              # FP64 lines stop at 1024 points
+    assert h64.spectral_shape() is None
+    tau = [torch.zeros(h64.shape, dtype=torch.float64, device="cuda") for _ in range(6)]
+    f = [torch.zeros(h64.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    with pytest.raises(wm.WmibmError, match="power"):
+        h64.force_spectral(tau, f)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
