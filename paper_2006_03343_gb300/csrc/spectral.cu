@@ -83,6 +83,7 @@ struct SpecParams {
     int32_t kc, nchunks, xpl, ypl;
     int64_t total;
     int32_t buf;              // complex elements per shared buffer
+    int32_t v16;              // stage with 16-byte copies (every staged segment 16-byte aligned)
     T rdz;
 };
 
@@ -151,49 +152,75 @@ struct Dft<T, 8> {
     }
 };
 
-// One Stockham pass of radix R over S sequences of length N = 2^logN, from a to
-// b, after logNs earlier passes.  Butterfly j of a sequence reads elements
-// j + r N/R, twiddles them by omega_N^(r jm N/(Ns R)) with jm = j mod Ns, and
-// writes element (j - jm) R + jm + r Ns.  The pass's twiddles are a table of
-// its own, tw[(r - 1) Ns + jm], so that a warp's loads of one r are contiguous.
+// One Stockham pass of radix R = min(8, N/Ns) over S sequences of length
+// N = 2^LOGN, from a to b, after passes that reached Ns = 2^LOGNS.  Butterfly j
+// of a sequence reads elements j + r N/R, twiddles them by
+// omega_N^(r jm N/(Ns R)) with jm = j mod Ns, and writes element
+// (j - jm) R + jm + r Ns.  The pass's twiddles are a table of its own,
+// tw[(r - 1) Ns + jm], so that a warp's loads of one r are contiguous.  With N
+// and Ns known at compile time every shared address is a base plus an
+// immediate: since N/R and Ns divide 32 or are multiples of it,
+// sk(j + r N/R) = sk(j) + r N/R + (r N/R)/32 and sk(o0 + r Ns) = sk(o0) + r Ns + (r Ns)/32.
 // PRE: multiply each input (bin m) by i k_m / N and conjugate it first, i.e.
 // v -> (-kn_m v.y, -kn_m v.x).
-template <typename T, int R, bool PRE>
+template <typename T, int LOGN, int LOGNS, bool PRE>
 __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict__ a,
-                                         typename Cx<T>::type *__restrict__ b, int S, int logN, int logNs, int ld,
+                                         typename Cx<T>::type *__restrict__ b, int S, int ld,
                                          const typename Cx<T>::type *__restrict__ tw, const T *__restrict__ kn)
 {
     using C = typename Cx<T>::type;
-    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
-    const int lognb = logN - logR;
-    const int nb = 1 << lognb;
-    const int total = S << lognb;
-    const int msk = (1 << logNs) - 1;
+    constexpr int LOGR = LOGN - LOGNS >= 3 ? 3 : LOGN - LOGNS;
+    constexpr int R = 1 << LOGR;
+    constexpr int LOGNB = LOGN - LOGR;
+    constexpr int NB = 1 << LOGNB;
+    constexpr int NS = 1 << LOGNS;
+    const int total = S << LOGNB;
     for (int t = threadIdx.x; t < total; t += kSpecThreads) {
-        const int s = t >> lognb, j = t & (nb - 1);
-        const C *in = a + s * ld;
+        const int s = t >> LOGNB, j = t & (NB - 1);
+        const C *in = a + s * ld + sk(j);
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[sk(j + r * nb)];
+        for (int r = 0; r < R; ++r) v[r] = in[r * NB + ((r * NB) >> 5)];
         if (PRE) {
+            const T *k0 = kn + j;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const T k = __ldg(kn + j + r * nb);
+                const T k = __ldg(k0 + r * NB);
                 v[r] = C{-k * v[r].y, -k * v[r].x};
             }
         }
-        const int jm = j & msk;
-        if (logNs > 0) {
+        const int jm = j & (NS - 1);
+        if (LOGNS > 0) {
+            const typename Cx<T>::type *w0 = tw + jm;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + ((r - 1) << logNs) + jm));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(w0 + (r - 1) * NS));
         }
         Dft<T, R>::run(v);
-        C *out = b + s * ld;
-        const int o0 = ((j - jm) << logR) + jm;
+        C *out = b + s * ld + sk(((j - jm) << LOGR) + jm);
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[sk(o0 + (r << logNs))] = v[r];
+        for (int r = 0; r < R; ++r) out[r * NS + ((r * NS) >> 5)] = v[r];
     }
 }
+
+// The remaining passes of a transform, from Ns = 2^LOGNS on, ping-ponging
+// between a and b with a block barrier after each; returns the buffer that holds
+// the result.  tw points at the table of the pass that starts at LOGNS.
+template <typename T, int LOGN, int LOGNS, bool PRE>
+struct Passes {
+    using C = typename Cx<T>::type;
+    __device__ __forceinline__ static C *run(C *a, C *b, int S, int ld, const C *tw, const T *kn)
+    {
+        constexpr int LOGR = LOGN - LOGNS >= 3 ? 3 : LOGN - LOGNS;
+        fft_pass<T, LOGN, LOGNS, PRE>(a, b, S, ld, tw, kn);
+        __syncthreads();
+        return Passes<T, LOGN, LOGNS + LOGR, false>::run(b, a, S, ld, tw + (((1 << LOGR) - 1) << LOGNS), kn);
+    }
+};
+template <typename T, int LOGN, bool PRE>
+struct Passes<T, LOGN, LOGN, PRE> {
+    using C = typename Cx<T>::type;
+    __device__ __forceinline__ static C *run(C *a, C *, int, int, const C *, const T *) { return a; }
+};
 
 // The first Stockham pass (Ns = 1, no twiddles) of the first transform, read
 // straight from the planar staging P (planes of n = L x N values): sequence s < L
@@ -202,109 +229,89 @@ __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict_
 // butterflies of one sequence; otherwise it is [pos][line] and consecutive
 // threads take consecutive sequences of one butterfly, so that both the staging
 // reads and the skewed sequence writes stay spread over the banks.
-template <typename T, int R, bool ROWS>
+template <typename T, int LOGN, bool ROWS>
 __device__ __forceinline__ void fft_first_pass(const T *__restrict__ P, typename Cx<T>::type *__restrict__ b,
-                                               int logL, int logN, int ld)
+                                               int logL, int ld)
 {
     using C = typename Cx<T>::type;
-    constexpr int logR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    constexpr int LOGR = LOGN >= 3 ? 3 : LOGN;
+    constexpr int R = 1 << LOGR;
+    constexpr int LOGNB = LOGN - LOGR;
+    constexpr int NB = 1 << LOGNB;
     const int L = 1 << logL;
     const int S = L + L / 2;
-    const int lognb = logN - logR;
-    const int nb = 1 << lognb;
-    const int n = L << logN;
-    const int total = S << lognb;
+    const int n = L << LOGN;
+    const int total = S << LOGNB;
     for (int t = threadIdx.x; t < total; t += kSpecThreads) {
         int s, j;
         if (ROWS) {
-            s = t >> lognb;
-            j = t & (nb - 1);
+            s = t >> LOGNB;
+            j = t & (NB - 1);
         } else {
             j = t / S;
             s = t - j * S;
         }
         C v[R];
         if (s < L) {
+            const T *p0 = ROWS ? P + (s << LOGN) + j : P + (j << logL) + s;
+            const int step = ROWS ? NB : NB << logL;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int pos = j + r * nb;
-                const int e = ROWS ? (s << logN) + pos : (pos << logL) + s;
-                v[r] = C{P[e], P[n + e]};
-            }
+            for (int r = 0; r < R; ++r) v[r] = C{p0[r * step], p0[n + r * step]};
         } else {
             const int l0 = 2 * (s - L);
+            if (ROWS) {
+                const T *p0 = P + 2 * n + (l0 << LOGN) + j;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int pos = j + r * nb;
-                if (ROWS) {
-                    v[r] = C{P[2 * n + (l0 << logN) + pos], P[2 * n + ((l0 + 1) << logN) + pos]};
-                } else {
-                    const C q = *reinterpret_cast<const C *>(P + 2 * n + (pos << logL) + l0);
-                    v[r] = q;
-                }
+                for (int r = 0; r < R; ++r) v[r] = C{p0[r * NB], p0[(1 << LOGN) + r * NB]};
+            } else {
+                const C *p0 = reinterpret_cast<const C *>(P + 2 * n + (j << logL) + l0);
+                const int step = (NB << logL) / 2;      // complex elements between r and r + 1
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = p0[r * step];
             }
         }
         Dft<T, R>::run(v);
-        C *out = b + s * ld;
+        C *out = b + s * ld + sk(j * R);
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[sk(j * R + r)] = v[r];
+        for (int r = 0; r < R; ++r) out[r] = v[r];
     }
 }
 
-// Forward FFT of S sequences (stride ld) held in a, b as scratch; returns the
-// buffer that holds the result.  tw: the per-pass twiddle tables, one after the
-// other (N - 1 entries in all).  Ends with a block barrier.
-template <typename T, bool PRE>
-__device__ typename Cx<T>::type *fft_block(typename Cx<T>::type *a, typename Cx<T>::type *b, int S, int logN,
-                                           int ld, const typename Cx<T>::type *tw, const T *kn, int logNs = 0)
+template <typename T, bool ROWS, int LOGN>
+__device__ __forceinline__ typename Cx<T>::type *derive_n(T *P, typename Cx<T>::type *A, int logL, int ld,
+                                                          const typename Cx<T>::type *tw, const T *kn)
 {
-    bool first = logNs == 0;
-    while (logNs < logN) {
-        const int left = logN - logNs;
-        int logR;
-        if (left >= 3) {
-            if (PRE && first) fft_pass<T, 8, true>(a, b, S, logN, logNs, ld, tw, kn);
-            else fft_pass<T, 8, false>(a, b, S, logN, logNs, ld, tw, kn);
-            logR = 3;
-        } else if (left == 2) {
-            if (PRE && first) fft_pass<T, 4, true>(a, b, S, logN, logNs, ld, tw, kn);
-            else fft_pass<T, 4, false>(a, b, S, logN, logNs, ld, tw, kn);
-            logR = 2;
-        } else {
-            if (PRE && first) fft_pass<T, 2, true>(a, b, S, logN, logNs, ld, tw, kn);
-            else fft_pass<T, 2, false>(a, b, S, logN, logNs, ld, tw, kn);
-            logR = 1;
-        }
-        __syncthreads();
-        tw += ((1 << logR) - 1) << logNs;      // this pass's table: Ns (R - 1) entries
-        typename Cx<T>::type *t = a;
-        a = b;
-        b = t;
-        logNs += logR;
-        first = false;
-    }
-    return a;
+    using C = typename Cx<T>::type;
+    constexpr int LOGR = LOGN >= 3 ? 3 : LOGN;
+    C *B = reinterpret_cast<C *>(P);
+    const int S = (1 << logL) + (1 << logL) / 2;
+    fft_first_pass<T, LOGN, ROWS>(P, A, logL, ld);
+    __syncthreads();
+    C *r1 = Passes<T, LOGN, LOGR, false>::run(A, B, S, ld, tw + ((1 << LOGR) - 1), kn);
+    return Passes<T, LOGN, 0, true>::run(r1, r1 == A ? B : A, S, ld, tw, kn);
 }
 
 // Spectral derivative of the staged lines: z = plane0 + i plane1 (and the plane-2
-// pairs), conj(FFT(conj(i k/N * FFT(z)))).  The first pass reads the planar
-// staging P and writes A; P is scratch afterwards.  The returned buffer holds
-// (D a, -D b) for each z = a + i b.
+// pairs), conj(FFT(conj(i k/N * FFT(z)))), for N = 2^logN, 2 <= N <= 2048.  The
+// first pass reads the planar staging P and writes A; P is scratch afterwards.
+// The returned buffer holds (D a, -D b) for each z = a + i b.
 template <typename T, bool ROWS>
 __device__ __forceinline__ typename Cx<T>::type *derive(T *P, typename Cx<T>::type *A, int logL, int logN, int ld,
                                                         const typename Cx<T>::type *tw, const T *kn)
 {
-    using C = typename Cx<T>::type;
-    C *B = reinterpret_cast<C *>(P);
-    const int S = (1 << logL) + (1 << logL) / 2;
-    const int logR = logN >= 3 ? 3 : logN;
-    if (logR == 3) fft_first_pass<T, 8, ROWS>(P, A, logL, logN, ld);
-    else if (logR == 2) fft_first_pass<T, 4, ROWS>(P, A, logL, logN, ld);
-    else fft_first_pass<T, 2, ROWS>(P, A, logL, logN, ld);
-    __syncthreads();
-    C *r1 = A;
-    if (logR < logN) r1 = fft_block<T, false>(A, B, S, logN, ld, tw + ((1 << logR) - 1), kn, logR);
-    return fft_block<T, true>(r1, r1 == A ? B : A, S, logN, ld, tw, kn);
+    switch (logN) {
+    case 1: return derive_n<T, ROWS, 1>(P, A, logL, ld, tw, kn);
+    case 2: return derive_n<T, ROWS, 2>(P, A, logL, ld, tw, kn);
+    case 3: return derive_n<T, ROWS, 3>(P, A, logL, ld, tw, kn);
+    case 4: return derive_n<T, ROWS, 4>(P, A, logL, ld, tw, kn);
+    case 5: return derive_n<T, ROWS, 5>(P, A, logL, ld, tw, kn);
+    case 6: return derive_n<T, ROWS, 6>(P, A, logL, ld, tw, kn);
+    case 7: return derive_n<T, ROWS, 7>(P, A, logL, ld, tw, kn);
+    case 8: return derive_n<T, ROWS, 8>(P, A, logL, ld, tw, kn);
+    case 9: return derive_n<T, ROWS, 9>(P, A, logL, ld, tw, kn);
+    case 10: return derive_n<T, ROWS, 10>(P, A, logL, ld, tw, kn);
+    default: return derive_n<T, ROWS, 11>(P, A, logL, ld, tw, kn);
+    }
 }
 
 // Asynchronous global -> shared copies (cp.async; completion by commit groups).
@@ -326,7 +333,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // j0 .. j0 + rx - 1; column unit: txy, tyy, tyz as [ny][wy] strips), then
 // commits the group (an empty group when the unit needs no input).
 template <typename T, int VB>
-__device__ void stage_unit(const SpecParams<T> &p, T *P, int kind, int level, int idx)
+__device__ __forceinline__ void stage_copies(const SpecParams<T> &p, T *P, int kind, int level, int idx)
 {
     constexpr int V = VB / (int)sizeof(T);            // values per copy
     if (kind == 0 && level < p.nz - 1) {
@@ -350,6 +357,13 @@ __device__ void stage_unit(const SpecParams<T> &p, T *P, int kind, int level, in
             cp_async<VB>(P + ((int64_t)f << logn) + (j << p.logwy) + cc * V, src + base + (int64_t)j * p.nx + cc * V);
         }
     }
+}
+
+template <typename T>
+__device__ void stage_unit(const SpecParams<T> &p, T *P, int kind, int level, int idx)
+{
+    if (p.v16) stage_copies<T, 16>(p, P, kind, level, idx);
+    else stage_copies<T, (int)sizeof(T)>(p, P, kind, level, idx);
     cp_async_commit();
 }
 
@@ -489,7 +503,7 @@ __device__ __forceinline__ void claim(const SpecParams<T> &p, int *slot)
 // unfinished unit with the smallest ticket can always proceed, so the loop
 // ends.  Shared memory: staging buffers P0, P1 and the FFT buffer A, each buf
 // complex elements.
-template <typename T, int VB>
+template <typename T>
 __global__ void __launch_bounds__(kSpecThreads, sizeof(T) == 4 ? 3 : 2) k_spectral(SpecParams<T> p)
 {
     using C = typename Cx<T>::type;
@@ -502,13 +516,13 @@ __global__ void __launch_bounds__(kSpecThreads, sizeof(T) == 4 ? 3 : 2) k_spectr
     int cur = 0;
     if (threadIdx.x == 0) claim(p, s_u[0]);
     __syncthreads();
-    stage_unit<T, VB>(p, P0, s_u[0][0], s_u[0][1], s_u[0][2]);
+    stage_unit<T>(p, P0, s_u[0][0], s_u[0][1], s_u[0][2]);
     for (;;) {
         const int kind = s_u[cur][0], level = s_u[cur][1], idx = s_u[cur][2];
         if (kind < 0) break;
         if (threadIdx.x == 0) claim(p, s_u[cur ^ 1]);
         __syncthreads();
-        stage_unit<T, VB>(p, cur ? P0 : P1, s_u[cur ^ 1][0], s_u[cur ^ 1][1], s_u[cur ^ 1][2]);
+        stage_unit<T>(p, cur ? P0 : P1, s_u[cur ^ 1][0], s_u[cur ^ 1][1], s_u[cur ^ 1][2]);
         cp_async_wait<1>();                 // this unit's lines have landed (the next unit's may not)
         __syncthreads();
         if (kind == 0) {
@@ -599,19 +613,19 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
     return WMIBM_OK;
 }
 
-template <typename T, int VB>
+template <typename T>
 int run_spectral(wmibm_handle *h, const SpecParams<T> &p, const SpecState *s, cudaStream_t stream)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_spectral<T, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_spectral<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)s->smem);
     if (e != cudaSuccess) return cuda_status(h, e, "k_spectral shared memory");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral<T, VB>, kSpecThreads, s->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral<T>, kSpecThreads, s->smem);
     if (e != cudaSuccess) return cuda_status(h, e, "k_spectral occupancy");
     if (per_sm < 1) return set_error(h, WMIBM_EINVAL, "spectral units do not fit on an SM");
     int64_t grid = (int64_t)per_sm * h->sm_count;
     if (grid > s->total) grid = s->total;
-    k_spectral<T, VB><<<(unsigned)grid, kSpecThreads, s->smem, stream>>>(p);
+    k_spectral<T><<<(unsigned)grid, kSpecThreads, s->smem, stream>>>(p);
     return cuda_status(h, cudaGetLastError(), "k_spectral launch");
 }
 
@@ -640,8 +654,8 @@ int launch_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *f
     // 16-byte copies when every staged line segment starts on a 16-byte boundary
     bool v16 = (h->nx * sizeof(T)) % 16 == 0 && (s->wy * sizeof(T)) % 16 == 0;
     for (int c = 0; c < 6; ++c) v16 = v16 && ((uintptr_t)tau[c] & 15u) == 0;
-    if (v16) return run_spectral<T, 16>(h, p, s, stream);
-    return run_spectral<T, (int)sizeof(T)>(h, p, s, stream);
+    p.v16 = v16 ? 1 : 0;
+    return run_spectral<T>(h, p, s, stream);
 }
 
 }  // namespace
