@@ -6,7 +6,9 @@ stencil, or the wall kernel followed by the stencil -- and a grid of tile
 shapes (rows per strip, shared-memory stages, consumer warps, warps of the
 wall kernel) with CUDA events on the launching stream (L2 flushed before every
 timed call), keeps the fastest, applies it to the handle and caches it in a
-JSON file keyed by GPU, precision and grid size.
+JSON file keyed by GPU, precision and grid size.  A single-launch form is taken
+only when it beats the best two-launch form by more than 2 %; closer than that
+the two are a tie and the two-launch form is kept.
 
 The timed calls go through the C ABI like any other call; nothing here
 computes anything of the method.
@@ -27,6 +29,7 @@ CONSUMERS = (2, 3, 4, 6, 8)
 WALL_WARPS = (4, 8)
 
 SMEM_LIMIT = 200 * 1024
+SINGLE_MARGIN = 0.02       # relative margin by which the single-launch form must win
 
 
 def cache_path() -> str:
@@ -129,6 +132,7 @@ def tune(handle, fields, reps: int = 9, use_cache: bool = True, budget_s: float 
         return dict(cache[key], cached=True)
     flush = _Flush(handle.device)
     best = None
+    best_form = {}                          # fastest (ms, tuning) per form: "two_launch" or "single_launch"
     tried = 0
     t_start = time.perf_counter()
     for cand in candidates(handle):
@@ -143,11 +147,20 @@ def tune(handle, fields, reps: int = 9, use_cache: bool = True, budget_s: float 
             print(f"  {ms * 1e3:8.1f} us  {cand}")
         if best is None or ms < best[0]:
             best = (ms, cand)
+        form = "two_launch" if cand.get("force_path") == 3 else "single_launch"
+        if form not in best_form or ms < best_form[form][0]:
+            best_form[form] = (ms, cand)
     if best is None:
         handle.set_tuning()
         return {"tuning": {}, "ms": None, "tried": tried}
+    # a single launch must beat the two-launch form by more than SINGLE_MARGIN to be chosen: within that the two
+    # forms are a tie, and the two-launch form keeps each kernel measurable against its own roofline
+    if "two_launch" in best_form and best[1].get("force_path") != 3 and \
+            best[0] > (1.0 - SINGLE_MARGIN) * best_form["two_launch"][0]:
+        best = best_form["two_launch"]
     handle.set_tuning(**best[1])
-    result = {"tuning": best[1], "ms": best[0], "tried": tried}
+    result = {"tuning": best[1], "ms": best[0], "tried": tried,
+              "forms_ms": {k: v[0] for k, v in best_form.items()}}
     if use_cache:
         cache = _load_cache(path)
         cache[key] = result
