@@ -7,7 +7,7 @@ The arithmetic lives in ``wmibm_oracle.c`` (plain C, double precision, loops in
 the paper's order); this module compiles it with gcc and marshals numpy arrays.
 The pseudo-spectral derivatives of Eqs. 13-14 are written here with numpy's FP64
 FFT as the library step: a 2-D transform of each z-plane, exactly as the sum over
-(k_x, k_y) is stated.
+(k_x, k_y) is stated.  The Smagorinsky stress (Eqs. 4-7) is plain numpy as well.
 
 Functions and the passages they follow:
   classify      Sec. 3.3, node classes on the w-grid and the uv-grid
@@ -18,13 +18,15 @@ Functions and the passages they follow:
   force         Eq. 2 / Eq. 18: f = -div(tau) on the staggered grid (Eqs. 15-16)
   horizontal_derivatives  Eqs. 13-14, pseudo-spectral d/dx and d/dy of one field
   force_spectral  f = -div(tau) with the horizontal derivatives of Eqs. 13-14
+  sgs_stress    Eqs. 4-7, the Smagorinsky stress with Mason's wall damping at fluid nodes
   mask          Sec. 3.2, Eq. 27: the body velocity condition
   adjoint       chain rule of wall_stress + force for L = <g, f>
 
 Every function here is pinned against closed forms, invariants and brute force
 (see the docstrings there): ``tests/test_oracle_pins.py`` (wall stress, central-
 difference divergence, mask), ``tests/test_oracle_adjoint.py`` (adjoint) and
-``tests/test_oracle_spectral.py`` (pseudo-spectral divergence).
+``tests/test_oracle_spectral.py`` (pseudo-spectral divergence) and
+``tests/test_oracle_sgs.py`` (Smagorinsky stress).
 """
 from __future__ import annotations
 
@@ -231,6 +233,81 @@ def force_spectral(grid, tau):
     fy[:-1] = -(dxy_dx[:-1] + dyy_dy[:-1] + (t["tyz"][1:] - t["tyz"][:-1]) / dz)
     fz[1:-1] = -(dxz_dx[1:-1] + dyz_dy[1:-1] + (t["tzz"][1:-1] - t["tzz"][:-2]) / dz)
     return fx, fy, fz
+
+
+def _ddx(q, h):
+    """Periodic central difference along x (the last axis)."""
+    return (np.roll(q, -1, axis=2) - np.roll(q, 1, axis=2)) / (2.0 * h)
+
+
+def _ddy(q, h):
+    """Periodic central difference along y (the middle axis)."""
+    return (np.roll(q, -1, axis=1) - np.roll(q, 1, axis=1)) / (2.0 * h)
+
+
+def mixing_length_sq(phi, z0, cs, kappa, grid):
+    """Eq. 7 with n = 2: 1/lambda^2 = 1/lambda_0^2 + 1/[kappa (z + z0)]^2 with
+    lambda_0 = C_s l, l = (dx dy dz)^(1/3) (Eq. 6), and z the node's distance phi
+    above the surface -> lambda^2."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    ell = (lx / nx * ly / ny * lz / (nz - 1)) ** (1.0 / 3.0)
+    lam0 = cs * ell
+    return 1.0 / (1.0 / lam0 ** 2 + 1.0 / (kappa * (phi + z0)) ** 2)
+
+
+def sgs_stress(grid, phi_uv, phi_w, z0, phi_b, u, v, w, tau, cs=0.16, kappa=0.4):
+    """Smagorinsky stress (Eqs. 4-7) written into tau (dict of 6 arrays) at fluid nodes.
+
+    tau_ij = -2 nu_t S_ij, S = (grad u + grad u^T)/2, nu_t = lambda^2 |S|,
+    |S| = sqrt(2 S:S), lambda from mixing_length_sq (Mason's damping, z -> phi).
+    Each component sits on its own node: S11, S22, S12, S33 on uv-nodes (S33 from
+    the w-levels above and below, Eq. 16), S13, S23 on w-nodes (the z-derivative of
+    u, v from the uv-levels below and above, Eq. 15); x, y derivatives are periodic
+    central differences.  |S| on a uv-node averages S13, S23 of the w-levels below
+    and above it; on a w-node it averages S11, S22, S33, S12 of the uv-levels below
+    and above it.  At the floor w-level S13, S23 repeat those of the level above;
+    at the lid they are 0 (no stress there, Eq. 10); both enter only that average.  Fluid nodes are those of neither the band nor
+    the solid class (Sec. 3.3); band and solid entries, the ghost uv-level and the
+    floor w-level keep their values; at the lid w-level tau_xz = tau_yz = 0
+    (Eq. 10).  z0: scalar or per-cell array."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    dx, dy, dz = lx / nx, ly / ny, lz / (nz - 1)
+    u, v, w = (np.asarray(a, np.float64) for a in (u, v, w))
+    S11 = _ddx(u, dx)
+    S22 = _ddy(v, dy)
+    S12 = 0.5 * (_ddy(u, dy) + _ddx(v, dx))
+    S33 = np.zeros_like(u)
+    S33[:-1] = (w[1:] - w[:-1]) / dz
+    S13 = np.zeros_like(u)
+    S23 = np.zeros_like(u)
+    S13[1:-1] = 0.5 * ((u[1:-1] - u[:-2]) / dz + _ddx(w, dx)[1:-1])
+    S23[1:-1] = 0.5 * ((v[1:-1] - v[:-2]) / dz + _ddy(w, dy)[1:-1])
+    S13[0], S23[0] = S13[1], S23[1]
+    # |S| on uv-levels 0 .. nz-2 and on w-levels 1 .. nz-2
+    s13u = 0.5 * (S13[:-1] + S13[1:])
+    s23u = 0.5 * (S23[:-1] + S23[1:])
+    mag_uv = np.sqrt(2.0 * (S11[:-1] ** 2 + S22[:-1] ** 2 + S33[:-1] ** 2)
+                     + 4.0 * (S12[:-1] ** 2 + s13u ** 2 + s23u ** 2))
+    avg = lambda q: 0.5 * (q[:-2] + q[1:-1])          # uv-levels k-1 and k for w-levels k = 1 .. nz-2
+    mag_w = np.sqrt(2.0 * (avg(S11) ** 2 + avg(S22) ** 2 + avg(S33) ** 2)
+                    + 4.0 * (avg(S12) ** 2 + S13[1:-1] ** 2 + S23[1:-1] ** 2))
+    z0a = z0 if np.isscalar(z0) else np.asarray(z0, np.float64)
+    lam_uv = mixing_length_sq(np.asarray(phi_uv, np.float64), z0a, cs, kappa, grid)
+    lam_w = mixing_length_sq(np.asarray(phi_w, np.float64), z0a, cs, kappa, grid)
+    cls_uv, cls_w = classify(grid, phi_uv, phi_w, phi_b)
+    fl_uv = cls_uv[:-1] == 0
+    nu_uv = lam_uv[:-1] * mag_uv
+    for name, S in (("txx", S11), ("tyy", S22), ("tzz", S33), ("txy", S12)):
+        t = tau[name][:-1]
+        t[fl_uv] = (-2.0 * nu_uv * S[:-1])[fl_uv]
+    fl_w = cls_w[1:-1] == 0
+    nu_w = lam_w[1:-1] * mag_w
+    for name, S in (("txz", S13), ("tyz", S23)):
+        t = tau[name][1:-1]
+        t[fl_w] = (-2.0 * nu_w * S[1:-1])[fl_w]
+        lid = tau[name][-1]
+        lid[cls_w[-1] == 0] = 0.0
+    return tau
 
 
 def mask(grid, phi_uv, phi_w, u, v, w, gradp=None, dt=0.0):
