@@ -144,6 +144,40 @@ int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, v
 int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream);
 
 /*
+ * wmibm_sgs_wall_terms - the per-node wall term of Mason's damping (Sec. 2.2,
+ * Eq. 7 with n = 2) for wmibm_sgs_stress: 1/[kappa (phi + z0)]^2 at fluid nodes
+ * (uv-grid phi > 2 phi_b, w-grid phi > phi_b: neither band nor solid, Sec. 3.3),
+ * -1 elsewhere.  Computed on the host in FP64, stored in the handle's dtype.
+ *   phi_uv, phi_w : HOST, N each, FP64, the same fields as given to wmibm_init
+ *   z0            : HOST, scalar (z0_is_field = 0) or per-cell [k][j][i] (1)
+ *   wt_uv, wt_w   : DEVICE, N each (dtype), caller-owned, written
+ * Synchronizes the stream; call it once per geometry, before any stream capture.
+ * Errors: EINVAL, ENOMEM, ESTATE, ECUDA.
+ */
+int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const double *phi_w, const double *z0,
+                         int32_t z0_is_field, void *wt_uv, void *wt_w, void *stream);
+
+/*
+ * wmibm_sgs_stress - the Smagorinsky sub-grid stress with Mason's wall damping
+ * (Sec. 2.2, Eqs. 4-7) written into tau at fluid nodes: tau_ij = -2 nu_t S_ij,
+ * nu_t = lambda^2 |S|, |S| = sqrt(2 S:S), 1/lambda^2 = 1/(C_s l)^2 + wall term,
+ * l = (dx dy dz)^(1/3), z of Eq. 7 = the node's phi.  S11, S22, S12 (periodic
+ * central differences) and S33 (Eq. 16) on uv-nodes, S13, S23 on w-nodes (Eq. 15);
+ * |S| on a uv-node averages S13, S23 of the w-levels around it (the floor repeats
+ * the level above, the lid counts 0), on a w-node S11, S22, S33, S12 of the
+ * uv-levels around it.  Band and solid entries, the ghost uv-level and the floor
+ * w-level are left as they are (run wmibm_wall_stress afterwards for the band);
+ * the lid's fluid tau_xz, tau_yz become 0 (Eq. 10).
+ *   u, v, w       : DEVICE velocity (vel_dtype), read only
+ *   wt_uv, wt_w   : DEVICE wall terms from wmibm_sgs_wall_terms
+ *   tau           : 6 DEVICE stress fields (dtype), written at fluid nodes
+ *   cs            : the Smagorinsky coefficient C_s (the paper uses 0.16), > 0
+ * Errors: EINVAL, ESTATE, ECUDA.
+ */
+int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
+                     const void *wt_w, void *const tau[6], double cs, void *stream);
+
+/*
  * wmibm_spectral_shape - the tile of wmibm_force_spectral's launch (host query):
  * out[0] rows per row unit, out[1] columns per column unit, out[2] z-levels per
  * chunk of the dispense order, out[3] shared-memory bytes per block.

@@ -1,0 +1,198 @@
+// The Smagorinsky sub-grid stress with Mason's wall damping (Eqs. 4-7 of Liu &
+// Stevens, arXiv:2006.03343) at the fluid nodes:
+//   tau_ij = -2 nu_t S_ij,  S = (grad u + grad u^T)/2,  nu_t = lambda^2 |S|,
+//   |S| = sqrt(2 S:S),  1/lambda^2 = 1/lambda_0^2 + 1/[kappa (z + z0)]^2,
+//   lambda_0 = C_s (dx dy dz)^(1/3),
+// with z the node's distance phi above the immersed surface.  Each component
+// sits on its own node: S11, S22, S12 (periodic central differences) and S33
+// (the w-levels above and below, Eq. 16) on uv-nodes; S13, S23 on w-nodes (the
+// uv-levels below and above, Eq. 15).  |S| on a uv-node averages S13, S23 of
+// the w-levels below and above it (the floor repeats the level above it, the
+// stress-free lid contributes 0); on a w-node it averages S11, S22, S33, S12 of
+// the uv-levels below and above it.  Band and solid entries (the wall model's),
+// the ghost uv-level and the floor w-level are left as they are; the lid's
+// fluid tau_xz, tau_yz become 0 (Eq. 10).
+//
+// One thread per node (i, j, k) forms the uv-node components and the w-node
+// components of that index; neighbours come through L1/L2, so DRAM sees each
+// velocity array and wall-term array once and the stress arrays once.
+#include <math.h>
+#include <stdlib.h>
+
+#include "internal.cuh"
+
+using namespace wmibm;
+
+namespace {
+
+template <typename T, typename V>
+struct SgsParams {
+    const V *u, *v, *w;
+    const T *wt_uv, *wt_w;      // 1/[kappa (phi + z0)]^2 at fluid nodes, -1 elsewhere
+    T *txx, *txy, *tyy, *tzz, *txz, *tyz;
+    int32_t nx, ny, nz;
+    T cx, cy, rdz;              // 1/(2 dx), 1/(2 dy), 1/dz
+    T inv_lam0_sq;              // 1/lambda_0^2
+};
+
+template <typename T, typename V>
+struct Field {
+    const V *p;
+    int32_t nx, ny;
+    int64_t plane;
+    __device__ __forceinline__ T at(int i, int j, int k) const
+    {
+        return load_vel<V, T>(p, (int64_t)k * plane + (int64_t)j * nx + i);
+    }
+};
+
+// S13 (or S23 with (v, y)) on w-level k at column (i, j): 1/2 [(q[k] - q[k-1])/dz + d_x w]
+// for 1 <= k <= nz-2; the floor repeats level 1; the lid is 0.
+template <typename T, typename V>
+__device__ __forceinline__ T shear_w(const Field<T, V> &q, const Field<T, V> &w, int i, int j, int k, int ia, int ib,
+                                     int ja, int jb, T ch, T rdz, int nz)
+{
+    if (k == nz - 1) return T(0);
+    if (k == 0) k = 1;
+    return T(0.5) * ((q.at(i, j, k) - q.at(i, j, k - 1)) * rdz + (w.at(ib, jb, k) - w.at(ia, ja, k)) * ch);
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const int64_t plane = (int64_t)p.nx * p.ny;
+    const int64_t o = (int64_t)k * plane + (int64_t)j * p.nx + i;
+    const int im = i == 0 ? p.nx - 1 : i - 1, ip = i + 1 == p.nx ? 0 : i + 1;
+    const int jm = j == 0 ? p.ny - 1 : j - 1, jp = j + 1 == p.ny ? 0 : j + 1;
+    const Field<T, V> U{p.u, p.nx, p.ny, plane}, Vf{p.v, p.nx, p.ny, plane}, W{p.w, p.nx, p.ny, plane};
+
+    // uv-node (i, j, k), physical levels 0 .. nz-2
+    if (k <= p.nz - 2) {
+        const T wt = p.wt_uv[o];
+        if (wt >= T(0)) {
+            const T s11 = (U.at(ip, j, k) - U.at(im, j, k)) * p.cx;
+            const T s22 = (Vf.at(i, jp, k) - Vf.at(i, jm, k)) * p.cy;
+            const T s12 = T(0.5) * ((U.at(i, jp, k) - U.at(i, jm, k)) * p.cy + (Vf.at(ip, j, k) - Vf.at(im, j, k)) * p.cx);
+            const T s33 = (W.at(i, j, k + 1) - W.at(i, j, k)) * p.rdz;
+            const T s13 = T(0.5) * (shear_w(U, W, i, j, k, im, ip, j, j, p.cx, p.rdz, p.nz) +
+                                    shear_w(U, W, i, j, k + 1, im, ip, j, j, p.cx, p.rdz, p.nz));
+            const T s23 = T(0.5) * (shear_w(Vf, W, i, j, k, i, i, jm, jp, p.cy, p.rdz, p.nz) +
+                                    shear_w(Vf, W, i, j, k + 1, i, i, jm, jp, p.cy, p.rdz, p.nz));
+            const T mag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
+            const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);       // -2 lambda^2 |S|
+            p.txx[o] = nu2 * s11;
+            p.tyy[o] = nu2 * s22;
+            p.tzz[o] = nu2 * s33;
+            p.txy[o] = nu2 * s12;
+        }
+    }
+    // w-node (i, j, k): interior levels; the lid's fluid entries are 0; the floor is left
+    if (k >= 1) {
+        const T wt = p.wt_w[o];
+        if (wt >= T(0)) {
+            if (k == p.nz - 1) {
+                p.txz[o] = T(0);
+                p.tyz[o] = T(0);
+            } else {
+                const T s13 = shear_w(U, W, i, j, k, im, ip, j, j, p.cx, p.rdz, p.nz);
+                const T s23 = shear_w(Vf, W, i, j, k, i, i, jm, jp, p.cy, p.rdz, p.nz);
+                // S11, S22, S12, S33 averaged over uv-levels k-1 and k
+                T a11 = 0, a22 = 0, a12 = 0, a33 = 0;
+#pragma unroll
+                for (int kk = k - 1; kk <= k; ++kk) {
+                    a11 += (U.at(ip, j, kk) - U.at(im, j, kk)) * p.cx;
+                    a22 += (Vf.at(i, jp, kk) - Vf.at(i, jm, kk)) * p.cy;
+                    a12 += T(0.5) * ((U.at(i, jp, kk) - U.at(i, jm, kk)) * p.cy + (Vf.at(ip, j, kk) - Vf.at(im, j, kk)) * p.cx);
+                    a33 += (W.at(i, j, kk + 1) - W.at(i, j, kk)) * p.rdz;
+                }
+                a11 *= T(0.5);
+                a22 *= T(0.5);
+                a12 *= T(0.5);
+                a33 *= T(0.5);
+                const T mag = sqrt(T(2) * (a11 * a11 + a22 * a22 + a33 * a33) + T(4) * (a12 * a12 + s13 * s13 + s23 * s23));
+                const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);
+                p.txz[o] = nu2 * s13;
+                p.tyz[o] = nu2 * s23;
+            }
+        }
+    }
+}
+
+template <typename T, typename V>
+int launch_sgs(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv, const void *wt_w,
+               void *const tau[6], double cs, cudaStream_t stream)
+{
+    SgsParams<T, V> p;
+    p.u = (const V *)u; p.v = (const V *)v; p.w = (const V *)w;
+    p.wt_uv = (const T *)wt_uv; p.wt_w = (const T *)wt_w;
+    p.txx = (T *)tau[0]; p.txy = (T *)tau[1]; p.tyy = (T *)tau[2];
+    p.tzz = (T *)tau[3]; p.txz = (T *)tau[4]; p.tyz = (T *)tau[5];
+    p.nx = h->nx; p.ny = h->ny; p.nz = h->nz;
+    p.cx = (T)(1.0 / (2.0 * h->dx));
+    p.cy = (T)(1.0 / (2.0 * h->dy));
+    p.rdz = (T)(1.0 / h->dz);
+    const double lam0 = cs * cbrt(h->dx * h->dy * h->dz);
+    p.inv_lam0_sq = (T)(1.0 / (lam0 * lam0));
+    const int bx = h->nx >= 64 ? 64 : 32;
+    const int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((h->nx + bx - 1) / bx, (h->ny + by - 1) / by, h->nz);
+    if (grid.y > 65535 || grid.z > 65535) return set_error(h, WMIBM_EINVAL, "grid too large for the SGS launch");
+    k_sgs<T, V><<<grid, block, 0, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_sgs launch");
+}
+
+}  // namespace
+
+extern "C" int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const double *phi_w, const double *z0,
+                                    int32_t z0_is_field, void *wt_uv, void *wt_w, void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!phi_uv || !phi_w || !z0 || !wt_uv || !wt_w) return set_error(h, WMIBM_EINVAL, "NULL argument");
+    int st = check_device(h);
+    if (st) return st;
+    const int64_t n = h->n;
+    const size_t es = elem_size(h->dtype);
+    void *host = malloc(2 * n * es);
+    if (!host) return set_error(h, WMIBM_ENOMEM, "host memory for the wall terms");
+    const double pb = h->phi_b, kap = h->kappa;
+    for (int g = 0; g < 2; ++g) {
+        const double *phi = g == 0 ? phi_uv : phi_w;
+        for (int64_t q = 0; q < n; ++q) {
+            const double f = phi[q];
+            const double zz = z0_is_field ? z0[q] : z0[0];
+            // fluid: neither band nor solid (uv-grid: phi > 2 phi_b; w-grid: phi > phi_b), the
+            // inclusive comparisons of the node classes at init
+            const bool fluid = g == 0 ? f > 2.0 * pb : f > pb;
+            const double val = fluid ? 1.0 / ((kap * (f + zz)) * (kap * (f + zz))) : -1.0;
+            if (h->dtype == WMIBM_F64) ((double *)host)[g * n + q] = val;
+            else ((float *)host)[g * n + q] = (float)val;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(wt_uv, host, n * es, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wt_w, (char *)host + n * es, n * es, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(host);
+    return cuda_status(h, e, "wall terms upload");
+}
+
+extern "C" int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
+                                const void *wt_w, void *const tau[6], double cs, void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!u || !v || !w || !wt_uv || !wt_w || !tau) return set_error(h, WMIBM_EINVAL, "NULL argument");
+    for (int c = 0; c < 6; ++c)
+        if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
+    if (!(cs > 0.0)) return set_error(h, WMIBM_EINVAL, "the Smagorinsky coefficient must be positive");
+    int st = check_device(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->dtype == WMIBM_F64) return launch_sgs<double, double>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
+    if (h->vel_dtype == WMIBM_BF16) return launch_sgs<float, __nv_bfloat16>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
+    return launch_sgs<float, float>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
+}

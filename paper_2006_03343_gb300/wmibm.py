@@ -29,7 +29,7 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
-            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape")
+            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress")
 
 
 class WmibmError(RuntimeError):
@@ -96,6 +96,10 @@ def load(path: Optional[str] = None):
     L.wmibm_force_spectral.restype = ctypes.c_int
     L.wmibm_spectral_shape.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
     L.wmibm_spectral_shape.restype = ctypes.c_int
+    L.wmibm_sgs_wall_terms.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP]
+    L.wmibm_sgs_wall_terms.restype = ctypes.c_int
+    L.wmibm_sgs_stress.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
+    L.wmibm_sgs_stress.restype = ctypes.c_int
     L.wmibm_mask.argtypes = [_VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_mask.restype = ctypes.c_int
     L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
@@ -281,6 +285,30 @@ class Handle:
             self._field(t)
         self._check(self._L.wmibm_force_spectral(self._h, _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
                                                  _stream_ptr(stream)))
+
+    def sgs_wall_terms(self, phi_uv, phi_w, z0, stream=None):
+        """The per-node wall terms of Mason's damping for sgs_stress -> (wt_uv, wt_w) device tensors
+        (phi_uv, phi_w: the host FP64 fields given at init; z0 scalar or per-cell)."""
+        import torch
+        phi_uv = np.ascontiguousarray(phi_uv, np.float64)
+        phi_w = np.ascontiguousarray(phi_w, np.float64)
+        if np.isscalar(z0):
+            z0a, is_field = np.array([float(z0)], np.float64), 0
+        else:
+            z0a, is_field = np.ascontiguousarray(z0, np.float64), 1
+        wt = [torch.empty(self.shape, dtype=self.torch_dtype, device=self.device) for _ in range(2)]
+        self._check(self._L.wmibm_sgs_wall_terms(self._h, phi_uv.ctypes.data, phi_w.ctypes.data, z0a.ctypes.data,
+                                                 is_field, _dptr(wt[0]), _dptr(wt[1]), _stream_ptr(stream)))
+        return wt[0], wt[1]
+
+    def sgs_stress(self, u, v, w, wall_terms, tau: Sequence, cs=0.16, stream=None):
+        """Smagorinsky stress with Mason's damping (Eqs. 4-7) into tau at fluid nodes."""
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in list(wall_terms) + list(tau):
+            self._field(t)
+        self._check(self._L.wmibm_sgs_stress(self._h, _dptr(u), _dptr(v), _dptr(w), _dptr(wall_terms[0]),
+                                             _dptr(wall_terms[1]), _ptrs(tau), float(cs), _stream_ptr(stream)))
 
     def spectral_shape(self):
         """(rows per row unit, columns per column unit, levels per chunk, shared bytes

@@ -102,7 +102,7 @@ def test_calls_reject_null_handle(lib):
 
 
 def test_later_entry_points_reject_null_arguments(lib):
-    """The step, spectral, adjoint, tuning and batch entry points refuse NULL
+    """The step, spectral, SGS, adjoint, tuning and batch entry points refuse NULL
     handles and tables on the host, before anything reaches a GPU."""
     from paper_2006_03343_gb300 import wmibm
     tau = (ctypes.c_void_p * 6)()
@@ -113,6 +113,8 @@ def test_later_entry_points_reject_null_arguments(lib):
     assert lib.wmibm_wall_stress_noalloc(None, None, None, None, tau, None, None) == wmibm.EINVAL
     assert lib.wmibm_force_spectral(None, tau, None, None, None, None) == wmibm.EINVAL
     assert lib.wmibm_spectral_shape(None, (ctypes.c_int64 * 4)()) == wmibm.EINVAL
+    assert lib.wmibm_sgs_wall_terms(None, None, None, None, 0, None, None, None) == wmibm.EINVAL
+    assert lib.wmibm_sgs_stress(None, None, None, None, None, None, tau, 0.16, None) == wmibm.EINVAL
     assert lib.wmibm_set_log_z0(None, None, None) == wmibm.EINVAL
     assert lib.wmibm_backward(None, three, three, None, None, None, None, None) == wmibm.EINVAL
     t = wmibm.Tuning()
