@@ -13,9 +13,10 @@
 // the ghost uv-level and the floor w-level are left as they are; the lid's
 // fluid tau_xz, tau_yz become 0 (Eq. 10).
 //
-// One thread per node (i, j, k) forms the uv-node components and the w-node
-// components of that index; neighbours come through L1/L2, so DRAM sees each
-// velocity array and wall-term array once and the stress arrays once.
+// One thread per column (i, j) marches up a chunk of levels, forming each
+// level's uv strain and w shear once; x and y neighbours come through L1, so
+// DRAM sees each velocity array and wall-term array once and the stress arrays
+// once.
 #include <math.h>
 #include <stdlib.h>
 
@@ -46,79 +47,104 @@ struct Field {
     }
 };
 
-// S13 (or S23 with (v, y)) on w-level k at column (i, j): 1/2 [(q[k] - q[k-1])/dz + d_x w]
-// for 1 <= k <= nz-2; the floor repeats level 1; the lid is 0.
-template <typename T, typename V>
-__device__ __forceinline__ T shear_w(const Field<T, V> &q, const Field<T, V> &w, int i, int j, int k, int ia, int ib,
-                                     int ja, int jb, T ch, T rdz, int nz)
-{
-    if (k == nz - 1) return T(0);
-    if (k == 0) k = 1;
-    return T(0.5) * ((q.at(i, j, k) - q.at(i, j, k - 1)) * rdz + (w.at(ib, jb, k) - w.at(ia, ja, k)) * ch);
-}
+// The strain of uv-level k at column (i, j): S11, S22, S12 (periodic central
+// differences) and S33 (Eq. 16), for 0 <= k <= nz-2.
+template <typename T>
+struct Uv {
+    T s11, s22, s12, s33;
+};
+// The shear of w-level k at column (i, j): S13, S23 (Eq. 15) for 1 <= k <= nz-2;
+// the floor repeats level 1, the lid is 0.
+template <typename T>
+struct Ws {
+    T s13, s23;
+};
 
 template <typename T, typename V>
-__global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p)
+struct Column {
+    Field<T, V> U, Vf, W;
+    int i, j, im, ip, jm, jp, nz;
+    T cx, cy, rdz;
+
+    __device__ __forceinline__ Uv<T> uv(int k) const
+    {
+        Uv<T> a;
+        a.s11 = (U.at(ip, j, k) - U.at(im, j, k)) * cx;
+        a.s22 = (Vf.at(i, jp, k) - Vf.at(i, jm, k)) * cy;
+        a.s12 = T(0.5) * ((U.at(i, jp, k) - U.at(i, jm, k)) * cy + (Vf.at(ip, j, k) - Vf.at(im, j, k)) * cx);
+        a.s33 = (W.at(i, j, k + 1) - W.at(i, j, k)) * rdz;
+        return a;
+    }
+    __device__ __forceinline__ Ws<T> ws(int k) const
+    {
+        if (k >= nz - 1) return Ws<T>{T(0), T(0)};
+        if (k == 0) k = 1;
+        Ws<T> b;
+        b.s13 = T(0.5) * ((U.at(i, j, k) - U.at(i, j, k - 1)) * rdz + (W.at(ip, j, k) - W.at(im, j, k)) * cx);
+        b.s23 = T(0.5) * ((Vf.at(i, j, k) - Vf.at(i, j, k - 1)) * rdz + (W.at(i, jp, k) - W.at(i, jm, k)) * cy);
+        return b;
+    }
+};
+
+// One thread per column (i, j) marching up a chunk of kc levels: each level's uv
+// strain and w shear are formed once and reused by the uv-node above/below and
+// the w-node between them.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p, int kc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
     if (i >= p.nx || j >= p.ny) return;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(k0 + kc, p.nz);
     const int64_t plane = (int64_t)p.nx * p.ny;
-    const int64_t o = (int64_t)k * plane + (int64_t)j * p.nx + i;
-    const int im = i == 0 ? p.nx - 1 : i - 1, ip = i + 1 == p.nx ? 0 : i + 1;
-    const int jm = j == 0 ? p.ny - 1 : j - 1, jp = j + 1 == p.ny ? 0 : j + 1;
-    const Field<T, V> U{p.u, p.nx, p.ny, plane}, Vf{p.v, p.nx, p.ny, plane}, W{p.w, p.nx, p.ny, plane};
+    Column<T, V> c;
+    c.U = Field<T, V>{p.u, p.nx, p.ny, plane};
+    c.Vf = Field<T, V>{p.v, p.nx, p.ny, plane};
+    c.W = Field<T, V>{p.w, p.nx, p.ny, plane};
+    c.i = i; c.j = j;
+    c.im = i == 0 ? p.nx - 1 : i - 1; c.ip = i + 1 == p.nx ? 0 : i + 1;
+    c.jm = j == 0 ? p.ny - 1 : j - 1; c.jp = j + 1 == p.ny ? 0 : j + 1;
+    c.nz = p.nz; c.cx = p.cx; c.cy = p.cy; c.rdz = p.rdz;
 
-    // uv-node (i, j, k), physical levels 0 .. nz-2
-    if (k <= p.nz - 2) {
-        const T wt = p.wt_uv[o];
-        if (wt >= T(0)) {
-            const T s11 = (U.at(ip, j, k) - U.at(im, j, k)) * p.cx;
-            const T s22 = (Vf.at(i, jp, k) - Vf.at(i, jm, k)) * p.cy;
-            const T s12 = T(0.5) * ((U.at(i, jp, k) - U.at(i, jm, k)) * p.cy + (Vf.at(ip, j, k) - Vf.at(im, j, k)) * p.cx);
-            const T s33 = (W.at(i, j, k + 1) - W.at(i, j, k)) * p.rdz;
-            const T s13 = T(0.5) * (shear_w(U, W, i, j, k, im, ip, j, j, p.cx, p.rdz, p.nz) +
-                                    shear_w(U, W, i, j, k + 1, im, ip, j, j, p.cx, p.rdz, p.nz));
-            const T s23 = T(0.5) * (shear_w(Vf, W, i, j, k, i, i, jm, jp, p.cy, p.rdz, p.nz) +
-                                    shear_w(Vf, W, i, j, k + 1, i, i, jm, jp, p.cy, p.rdz, p.nz));
-            const T mag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
-            const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);       // -2 lambda^2 |S|
-            p.txx[o] = nu2 * s11;
-            p.tyy[o] = nu2 * s22;
-            p.tzz[o] = nu2 * s33;
-            p.txy[o] = nu2 * s12;
-        }
-    }
-    // w-node (i, j, k): interior levels; the lid's fluid entries are 0; the floor is left
-    if (k >= 1) {
-        const T wt = p.wt_w[o];
-        if (wt >= T(0)) {
-            if (k == p.nz - 1) {
-                p.txz[o] = T(0);
-                p.tyz[o] = T(0);
-            } else {
-                const T s13 = shear_w(U, W, i, j, k, im, ip, j, j, p.cx, p.rdz, p.nz);
-                const T s23 = shear_w(Vf, W, i, j, k, i, i, jm, jp, p.cy, p.rdz, p.nz);
-                // S11, S22, S12, S33 averaged over uv-levels k-1 and k
-                T a11 = 0, a22 = 0, a12 = 0, a33 = 0;
-#pragma unroll
-                for (int kk = k - 1; kk <= k; ++kk) {
-                    a11 += (U.at(ip, j, kk) - U.at(im, j, kk)) * p.cx;
-                    a22 += (Vf.at(i, jp, kk) - Vf.at(i, jm, kk)) * p.cy;
-                    a12 += T(0.5) * ((U.at(i, jp, kk) - U.at(i, jm, kk)) * p.cy + (Vf.at(ip, j, kk) - Vf.at(im, j, kk)) * p.cx);
-                    a33 += (W.at(i, j, kk + 1) - W.at(i, j, kk)) * p.rdz;
-                }
-                a11 *= T(0.5);
-                a22 *= T(0.5);
-                a12 *= T(0.5);
-                a33 *= T(0.5);
-                const T mag = sqrt(T(2) * (a11 * a11 + a22 * a22 + a33 * a33) + T(4) * (a12 * a12 + s13 * s13 + s23 * s23));
-                const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);
-                p.txz[o] = nu2 * s13;
-                p.tyz[o] = nu2 * s23;
+    Uv<T> a_prev = k0 >= 1 ? c.uv(k0 - 1) : Uv<T>{0, 0, 0, 0};
+    Ws<T> b_cur = c.ws(k0);
+    int64_t o = (int64_t)k0 * plane + (int64_t)j * p.nx + i;
+    for (int k = k0; k < k1; ++k, o += plane) {
+        const Uv<T> a_cur = k <= p.nz - 2 ? c.uv(k) : Uv<T>{0, 0, 0, 0};
+        const Ws<T> b_next = c.ws(k + 1);
+        if (k <= p.nz - 2) {                                // uv-node (i, j, k)
+            const T wt = p.wt_uv[o];
+            if (wt >= T(0)) {
+                const T s13 = T(0.5) * (b_cur.s13 + b_next.s13), s23 = T(0.5) * (b_cur.s23 + b_next.s23);
+                const T mag = sqrt(T(2) * (a_cur.s11 * a_cur.s11 + a_cur.s22 * a_cur.s22 + a_cur.s33 * a_cur.s33) +
+                                   T(4) * (a_cur.s12 * a_cur.s12 + s13 * s13 + s23 * s23));
+                const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);       // -2 lambda^2 |S|
+                p.txx[o] = nu2 * a_cur.s11;
+                p.tyy[o] = nu2 * a_cur.s22;
+                p.tzz[o] = nu2 * a_cur.s33;
+                p.txy[o] = nu2 * a_cur.s12;
             }
         }
+        if (k >= 1) {                                       // w-node (i, j, k); the floor is left
+            const T wt = p.wt_w[o];
+            if (wt >= T(0)) {
+                if (k == p.nz - 1) {
+                    p.txz[o] = T(0);
+                    p.tyz[o] = T(0);
+                } else {
+                    const T a11 = T(0.5) * (a_prev.s11 + a_cur.s11), a22 = T(0.5) * (a_prev.s22 + a_cur.s22);
+                    const T a12 = T(0.5) * (a_prev.s12 + a_cur.s12), a33 = T(0.5) * (a_prev.s33 + a_cur.s33);
+                    const T mag = sqrt(T(2) * (a11 * a11 + a22 * a22 + a33 * a33) +
+                                       T(4) * (a12 * a12 + b_cur.s13 * b_cur.s13 + b_cur.s23 * b_cur.s23));
+                    const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);
+                    p.txz[o] = nu2 * b_cur.s13;
+                    p.tyz[o] = nu2 * b_cur.s23;
+                }
+            }
+        }
+        a_prev = a_cur;
+        b_cur = b_next;
     }
 }
 
@@ -139,10 +165,11 @@ int launch_sgs(wmibm_handle *h, const void *u, const void *v, const void *w, con
     p.inv_lam0_sq = (T)(1.0 / (lam0 * lam0));
     const int bx = h->nx >= 64 ? 64 : 32;
     const int by = 256 / bx;
+    const int kc = 8;                       // levels per thread
     dim3 block(bx, by, 1);
-    dim3 grid((h->nx + bx - 1) / bx, (h->ny + by - 1) / by, h->nz);
+    dim3 grid((h->nx + bx - 1) / bx, (h->ny + by - 1) / by, (h->nz + kc - 1) / kc);
     if (grid.y > 65535 || grid.z > 65535) return set_error(h, WMIBM_EINVAL, "grid too large for the SGS launch");
-    k_sgs<T, V><<<grid, block, 0, stream>>>(p);
+    k_sgs<T, V><<<grid, block, 0, stream>>>(p, kc);
     return cuda_status(h, cudaGetLastError(), "k_sgs launch");
 }
 
