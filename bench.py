@@ -31,6 +31,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "IBM wall-stress+forcing throughput (Gpts/s)"
+METRIC_SPECTRAL = "IBM wall-stress+spectral-forcing throughput (Gpts/s)"
+METRIC_SGS = "IBM stress stage from the velocity (SGS + wall stress + forcing) throughput (Gpts/s)"
 UNIT = "Gpts/s"
 L2_FLUSH_BYTES = 256 << 20
 L2_NOTE = ("flushed between steps outside the timed events: a 256 MiB write, then a 256 MiB read of another "
@@ -63,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cubes",
-                    choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral"])
+                    choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral", "sgs"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--spectral-levels", type=int, default=None,
                     help="spectral workload: levels of the hill grid (default 256; smaller for profiler captures)")
@@ -164,6 +166,8 @@ class ClockSampler:
 
 def make_case(args):
     from paper_2006_03343_gb300 import inputs
+    if args.workload == "sgs":                # the stage from the velocity on the cube array
+        return inputs.cubes(dtype=args.dtype)
     if args.workload == "spectral":           # the paper's horizontal scheme on the 3-D hill grid
         if args.spectral_levels:                # the same planes, fewer levels (profiler captures)
             return inputs.hill(shape=inputs.HILL_SHAPE[:2] + (args.spectral_levels,), dtype=args.dtype)
@@ -228,8 +232,13 @@ def run_reference(args):
     oracle.build()
     tau = {k: v.copy() for k, v in case.tau.items()}
     u, v, w = case.u.copy(), case.v.copy(), case.w.copy()
+    if args.workload in ("spectral", "sgs"):
+        # their numpy parts (the FFTs, the SGS stress) are single-threaded: run the C parts on one core too
+        oracle.set_threads(1)
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
+        if args.workload == "sgs":
+            oracle.sgs_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_b, u, v, w, tau)
         oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, u, v, w, tau)
         if args.workload == "spectral":
             oracle.force_spectral(case.grid, tau)
@@ -239,14 +248,15 @@ def run_reference(args):
             per_step.append(time.perf_counter() - t0)
     total = sum(per_step)
     value = args.steps * case.npoints / total / 1e9
-    # the spectral divergence is numpy's single-threaded FFT and the wall-stress loop is sequential
-    threads = 1 if args.workload == "spectral" else oracle.openmp_threads()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+    threads = oracle.openmp_threads()
+    metric = {"spectral": METRIC_SPECTRAL, "sgs": METRIC_SGS}.get(args.workload, METRIC)
+    line = {"metric": metric, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args, case),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} full passes of wall stress + "
+                             "sample": f"{args.steps} full passes of "
+                                       f"{'SGS stress + ' if args.workload == 'sgs' else ''}wall stress + "
                                        f"{'spectral ' if args.workload == 'spectral' else ''}force over the "
                                        f"workload (FP64 CPU oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -878,7 +888,7 @@ def run_spectral(args):
 
     if rank == 0:
         shape = h.spectral_shape()
-        line = {"metric": "IBM wall-stress+spectral-forcing throughput (Gpts/s)", "value": value, "unit": UNIT,
+        line = {"metric": METRIC_SPECTRAL, "value": value, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
                 "data": "synthetic",
@@ -910,6 +920,172 @@ def run_spectral(args):
     return 0
 
 
+def sgs_bytes(case, es, vs):
+    """Algorithmic bytes of one wmibm_sgs_stress launch: the three velocity arrays and the two
+    wall-term arrays read once, the stress components written at the nodes they are computed on
+    (4 per fluid uv-node below the ghost level, 2 per fluid w-node above the floor)."""
+    n = case.npoints
+    fluid_uv = int(np.count_nonzero(case.phi_uv[:-1] > 2 * case.phi_b))
+    fluid_w = int(np.count_nonzero(case.phi_w[1:] > case.phi_b))
+    return n * (3 * vs + 2 * es) + (4 * fluid_uv + 2 * fluid_w) * es
+
+
+def run_sgs(args):
+    """The stress stage from the velocity on the cube array (256 x 128 x 128): the
+    Smagorinsky stress with Mason's damping at fluid nodes (Eqs. 4-7), then wall
+    stress + forcing (a1 + a2, the autotuned form), one CUDA graph per step.
+    Roofline of k_sgs; accuracy against the oracle's same chain."""
+    import torch
+    from paper_2006_03343_gb300 import build, inputs, wmibm
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    case = inputs.cubes(dtype=args.dtype)
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=tdt)
+    h = wmibm.Handle.from_case(case, dtype=args.dtype)
+    u, v, w = d(case.u), d(case.v), d(case.w)
+    tau = [d(case.tau[k]) for k in inputs.TAU_NAMES]
+    f = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(3)]
+    stats = h.new_stats()
+    wt = h.sgs_wall_terms(case.phi_uv, case.phi_w, case.z0)
+    tuned = None
+    if not args.no_tune:
+        from paper_2006_03343_gb300 import autotune
+        tuned = autotune.tune(h, (u, v, w, tau, f, stats))
+    step_fn = lambda: (h.sgs_stress(u, v, w, wt, tau), h.wall_stress_force(u, v, w, tau, f, stats))
+    step_fn()
+    torch.cuda.synchronize()
+    first = ([t.double().cpu().numpy() for t in tau], [x.double().cpu().numpy() for x in f])
+    fns = {"step": step_fn, "sgs": lambda: h.sgs_stress(u, v, w, wt, tau),
+           "a12": lambda: h.wall_stress_force(u, v, w, tau, f, stats)}
+    graphs = {}
+    for name, fn in fns.items():
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        graphs[name] = g
+    flush = L2Flush(dev)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
+    if sampler:
+        sampler.start()
+    t_soak = time.perf_counter()
+    while not args.profile and time.perf_counter() - t_soak < 1.0:
+        for _ in range(20):
+            flush.zero_()
+            graphs["step"].replay()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = timed_run(graphs["step"].replay, stream, flush, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    parts = {name: timed_run(graphs[name].replay, stream, flush, args.steps) for name in ("sgs", "a12")}
+    status = h.device_status()
+    value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
+    es = 8 if args.dtype == "f64" else 4
+    kbytes = sgs_bytes(case, es, es)
+    kms = float(np.mean(parts["sgs"]))
+    peak, peak_kind = measured_peak()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    one_launch = h.get_tuning().force_path != 3
+    launches = 1 + (1 if one_launch else 2)
+
+    e2e = None
+    if not args.no_e2e and not args.profile:
+        host_in = [torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (case.u, case.v, case.w)]
+        host_tau = [torch.from_numpy(case.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
+        host_f = [torch.empty(case.shape, dtype=tdt).pin_memory() for _ in range(3)]
+        h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
+        d2h = sum(t.numel() * t.element_size() for t in host_f)
+
+        def e2e_step():
+            for dst, src in zip((u, v, w), host_in):
+                dst.copy_(src, non_blocking=True)
+            for dst, src in zip(tau, host_tau):
+                dst.copy_(src, non_blocking=True)
+            h.sgs_stress(u, v, w, wt, tau)
+            h.wall_stress_force(u, v, w, tau, f, stats)
+            for dst, src in zip(host_f, f):
+                dst.copy_(src, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps * case.npoints / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        import oracle
+        oracle.build()
+        threads = oracle.openmp_threads()
+        oracle.set_threads(1)
+        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        tau_o = {k: rd(case.tau[k]) for k in inputs.TAU_NAMES}
+        ou, ov, ow = rd(case.u), rd(case.v), rd(case.w)
+        t0 = time.perf_counter()
+        oracle.sgs_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_b, ou, ov, ow, tau_o)
+        oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, ou, ov, ow, tau_o)
+        f_o = oracle.force(case.grid, tau_o)
+        el = time.perf_counter() - t0
+        oracle.set_threads(threads)
+        cpu = {"value": case.npoints / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full pass of the oracle's SGS stress (numpy), wall stress and force on one core "
+                         f"({el:.1f} s)"}
+        accuracy = {}
+        for k, g in zip(inputs.TAU_NAMES, first[0]):
+            r = tau_o[k]
+            accuracy[f"tau_{k}"] = float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300))
+        for c, g in enumerate(first[1]):
+            r = f_o[c]
+            accuracy[f"f{'xyz'[c]}"] = float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300))
+
+    if rank == 0:
+        line = {"metric": METRIC_SGS, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": dict(workload_config(args, case),
+                               workload=f"sgs: cube array {case.grid[0]}x{case.grid[1]}x{case.grid[2]}, "
+                                        "Smagorinsky C_s = 0.16 with Mason's damping, then a1 + a2"),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "k_sgs (column march, one thread per (i, j))", "kernel_ms": kms,
+                             "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                             "algorithmic_bytes_per_launch": kbytes},
+                "parts_ms": {"sgs_alone": kms, "a1_a2_alone": float(np.mean(parts["a12"]))},
+                "tuning": tuned,
+                "timing": "per step: CUDA events around one graph replay of the SGS stress then wall stress + force",
+                "gpu_launches": launches * args.steps,
+                "device_status": status, "accuracy": accuracy,
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -920,6 +1096,8 @@ def main(argv=None):
         return run_adjoint(args)
     if args.workload == "spectral":
         return run_spectral(args)
+    if args.workload == "sgs":
+        return run_sgs(args)
     return run_ours(args)
 
 
