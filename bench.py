@@ -934,7 +934,8 @@ def run_sgs(args):
     """The stress stage from the velocity on the cube array (256 x 128 x 128): the
     Smagorinsky stress with Mason's damping at fluid nodes (Eqs. 4-7), then wall
     stress + forcing (a1 + a2, the autotuned form), one CUDA graph per step.
-    Roofline of k_sgs; accuracy against the oracle's same chain."""
+    Roofline of k_sgs; accuracy against the oracle's same chain.  The fused form
+    (a1, then wmibm_sgs_force) is timed beside it in parts_ms."""
     import torch
     from paper_2006_03343_gb300 import build, inputs, wmibm
     rank, world, local = dist_env()
@@ -964,8 +965,11 @@ def run_sgs(args):
     step_fn()
     torch.cuda.synchronize()
     first = ([t.double().cpu().numpy() for t in tau], [x.double().cpu().numpy() for x in f])
+    f2 = [torch.empty(case.shape, dtype=tdt, device=dev) for _ in range(3)]
     fns = {"step": step_fn, "sgs": lambda: h.sgs_stress(u, v, w, wt, tau),
-           "a12": lambda: h.wall_stress_force(u, v, w, tau, f, stats)}
+           "a12": lambda: h.wall_stress_force(u, v, w, tau, f, stats),
+           # the fused form: a1, then the stress formed on the fly inside the divergence (never written)
+           "fused": lambda: (h.wall_stress(u, v, w, tau, stats), h.sgs_force(u, v, w, wt, tau, f2))}
     graphs = {}
     for name, fn in fns.items():
         for _ in range(max(args.warmup, 3)):
@@ -991,7 +995,7 @@ def run_sgs(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    parts = {name: timed_run(graphs[name].replay, stream, flush, args.steps) for name in ("sgs", "a12")}
+    parts = {name: timed_run(graphs[name].replay, stream, flush, args.steps) for name in ("sgs", "a12", "fused")}
     status = h.device_status()
     value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
     es = 8 if args.dtype == "f64" else 4
@@ -1073,7 +1077,8 @@ def run_sgs(args):
                              "kernel": "k_sgs (column march, one thread per (i, j))", "kernel_ms": kms,
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                              "algorithmic_bytes_per_launch": kbytes},
-                "parts_ms": {"sgs_alone": kms, "a1_a2_alone": float(np.mean(parts["a12"]))},
+                "parts_ms": {"sgs_alone": kms, "a1_a2_alone": float(np.mean(parts["a12"])),
+                             "fused_a1_then_sgs_force": float(np.mean(parts["fused"]))},
                 "tuning": tuned,
                 "timing": "per step: CUDA events around one graph replay of the SGS stress then wall stress + force",
                 "gpu_launches": launches * args.steps,

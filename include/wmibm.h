@@ -145,9 +145,10 @@ int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, vo
 
 /*
  * wmibm_sgs_wall_terms - the per-node wall term of Mason's damping (Sec. 2.2,
- * Eq. 7 with n = 2) for wmibm_sgs_stress: 1/[kappa (phi + z0)]^2 at fluid nodes
- * (uv-grid phi > 2 phi_b, w-grid phi > phi_b: neither band nor solid, Sec. 3.3),
- * -1 elsewhere.  Computed on the host in FP64, stored in the handle's dtype.
+ * Eq. 7 with n = 2) for wmibm_sgs_stress and wmibm_sgs_force: 1/[kappa (phi + z0)]^2
+ * at fluid nodes (uv-grid phi > 2 phi_b, w-grid phi > phi_b: neither band nor
+ * solid, Sec. 3.3), -1 at band nodes, -2 at solid nodes.  Computed on the host
+ * in FP64, stored in the handle's dtype.
  *   phi_uv, phi_w : HOST, N each, FP64, the same fields as given to wmibm_init
  *   z0            : HOST, scalar (z0_is_field = 0) or per-cell [k][j][i] (1)
  *   wt_uv, wt_w   : DEVICE, N each (dtype), caller-owned, written
@@ -176,6 +177,22 @@ int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const double *ph
  */
 int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
                      const void *wt_w, void *const tau[6], double cs, void *stream);
+
+/*
+ * wmibm_sgs_force - the forcing f = -div(tau) of wmibm_force with the fluid stress
+ * formed on the fly from the velocity, as wmibm_sgs_stress would write it, in one
+ * pass that never writes tau: at each node tau is the Smagorinsky stress (fluid),
+ * the value in tau (band: call wmibm_wall_stress first; and the floor w-level),
+ * or 0 (solid; the lid's fluid tau_xz, tau_yz).  Equal to wmibm_sgs_stress, then
+ * wmibm_wall_stress, then wmibm_force, up to rounding, with about 32 instead of
+ * about 80 bytes per node moved.
+ *   u, v, w, wt_uv, wt_w, cs : as in wmibm_sgs_stress
+ *   tau           : 6 DEVICE stress fields (dtype), read at band nodes and on the floor only
+ *   fx, fy, fz    : DEVICE forcing (dtype), written everywhere (0 on the ghost level, floor and lid as in wmibm_force)
+ * Errors: EINVAL, ESTATE, ECUDA.
+ */
+int wmibm_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
+                    const void *wt_w, const void *const tau[6], void *fx, void *fy, void *fz, double cs, void *stream);
 
 /*
  * wmibm_spectral_shape - the tile of wmibm_force_spectral's launch (host query):

@@ -29,7 +29,7 @@ namespace {
 template <typename T, typename V>
 struct SgsParams {
     const V *u, *v, *w;
-    const T *wt_uv, *wt_w;      // 1/[kappa (phi + z0)]^2 at fluid nodes, -1 elsewhere
+    const T *wt_uv, *wt_w;      // 1/[kappa (phi + z0)]^2 at fluid nodes, -1 at band, -2 at solid nodes
     T *txx, *txy, *tyy, *tzz, *txz, *tyz;
     int32_t nx, ny, nz;
     T cx, cy, rdz;              // 1/(2 dx), 1/(2 dy), 1/dz
@@ -86,6 +86,36 @@ struct Column {
     }
 };
 
+// Stress of a fluid uv-node from its level's strain and the shear of the w-levels below
+// and above it: (txx, tyy, tzz, txy) = -2 lambda^2 |S| (S11, S22, S33, S12).
+template <typename T>
+__device__ __forceinline__ void uv_stress(const Uv<T> &a, const Ws<T> &lo, const Ws<T> &hi, T wt, T inv_lam0_sq,
+                                          T out[4])
+{
+    const T s13 = T(0.5) * (lo.s13 + hi.s13), s23 = T(0.5) * (lo.s23 + hi.s23);
+    const T mag = sqrt(T(2) * (a.s11 * a.s11 + a.s22 * a.s22 + a.s33 * a.s33) +
+                       T(4) * (a.s12 * a.s12 + s13 * s13 + s23 * s23));
+    const T nu2 = T(-2) * mag / (inv_lam0_sq + wt);          // -2 lambda^2 |S|
+    out[0] = nu2 * a.s11;
+    out[1] = nu2 * a.s22;
+    out[2] = nu2 * a.s33;
+    out[3] = nu2 * a.s12;
+}
+
+// Stress of a fluid interior w-node from its shear and the strain of the uv-levels
+// below and above it: (txz, tyz) = -2 lambda^2 |S| (S13, S23).
+template <typename T>
+__device__ __forceinline__ void w_stress(const Uv<T> &lo, const Uv<T> &hi, const Ws<T> &b, T wt, T inv_lam0_sq,
+                                         T out[2])
+{
+    const T a11 = T(0.5) * (lo.s11 + hi.s11), a22 = T(0.5) * (lo.s22 + hi.s22);
+    const T a12 = T(0.5) * (lo.s12 + hi.s12), a33 = T(0.5) * (lo.s33 + hi.s33);
+    const T mag = sqrt(T(2) * (a11 * a11 + a22 * a22 + a33 * a33) + T(4) * (a12 * a12 + b.s13 * b.s13 + b.s23 * b.s23));
+    const T nu2 = T(-2) * mag / (inv_lam0_sq + wt);
+    out[0] = nu2 * b.s13;
+    out[1] = nu2 * b.s23;
+}
+
 // One thread per column (i, j) marching up a chunk of kc levels: each level's uv
 // strain and w shear are formed once and reused by the uv-node above/below and
 // the w-node between them.
@@ -116,36 +146,182 @@ __global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p, int kc)
         if (k <= p.nz - 2) {                                // uv-node (i, j, k)
             const T wt = p.wt_uv[o];
             if (wt >= T(0)) {
-                const T s13 = T(0.5) * (b_cur.s13 + b_next.s13), s23 = T(0.5) * (b_cur.s23 + b_next.s23);
-                const T mag = sqrt(T(2) * (a_cur.s11 * a_cur.s11 + a_cur.s22 * a_cur.s22 + a_cur.s33 * a_cur.s33) +
-                                   T(4) * (a_cur.s12 * a_cur.s12 + s13 * s13 + s23 * s23));
-                const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);       // -2 lambda^2 |S|
-                p.txx[o] = nu2 * a_cur.s11;
-                p.tyy[o] = nu2 * a_cur.s22;
-                p.tzz[o] = nu2 * a_cur.s33;
-                p.txy[o] = nu2 * a_cur.s12;
+                T t[4];
+                uv_stress(a_cur, b_cur, b_next, wt, p.inv_lam0_sq, t);
+                p.txx[o] = t[0];
+                p.tyy[o] = t[1];
+                p.tzz[o] = t[2];
+                p.txy[o] = t[3];
             }
         }
         if (k >= 1) {                                       // w-node (i, j, k); the floor is left
             const T wt = p.wt_w[o];
             if (wt >= T(0)) {
-                if (k == p.nz - 1) {
-                    p.txz[o] = T(0);
-                    p.tyz[o] = T(0);
-                } else {
-                    const T a11 = T(0.5) * (a_prev.s11 + a_cur.s11), a22 = T(0.5) * (a_prev.s22 + a_cur.s22);
-                    const T a12 = T(0.5) * (a_prev.s12 + a_cur.s12), a33 = T(0.5) * (a_prev.s33 + a_cur.s33);
-                    const T mag = sqrt(T(2) * (a11 * a11 + a22 * a22 + a33 * a33) +
-                                       T(4) * (a12 * a12 + b_cur.s13 * b_cur.s13 + b_cur.s23 * b_cur.s23));
-                    const T nu2 = T(-2) * mag / (p.inv_lam0_sq + wt);
-                    p.txz[o] = nu2 * b_cur.s13;
-                    p.tyz[o] = nu2 * b_cur.s23;
-                }
+                T t[2] = {T(0), T(0)};                      // the lid: no stress (Eq. 10)
+                if (k < p.nz - 1) w_stress(a_prev, a_cur, b_cur, wt, p.inv_lam0_sq, t);
+                p.txz[o] = t[0];
+                p.tyz[o] = t[1];
             }
         }
         a_prev = a_cur;
         b_cur = b_next;
     }
+}
+
+// ---------------------------------------------------------------------------
+// The stress and the forcing in one pass.  A block owns a tile of TX x TY output
+// columns and one column of halo around it: each of its (TX+2) x (TY+2) threads
+// marches one column up a chunk of levels, forms the stress of its uv-node and
+// w-node on every level -- the Smagorinsky stress at fluid nodes, the wall
+// model's value (read from tau) at band nodes, 0 at solid nodes, the caller's
+// value on the floor w-level -- and leaves the level in shared memory; the
+// interior threads then form f = -div tau (Eq. 2 / Eq. 18, Eqs. 15-16) with the
+// operations of the central-difference force kernel.  The stress arrays are only
+// read (band nodes and the floor), never written.
+constexpr int kFuseX = 32, kFuseY = 8;          // threads per block: tile plus halo
+constexpr int kFuseLevels = 16;                 // levels per block
+
+template <typename T, typename V>
+struct FuseParams {
+    SgsParams<T, V> s;
+    T *fx, *fy, *fz;
+    T cz;                                       // 1/dz of the divergence
+};
+
+template <typename T, typename V>
+__device__ __forceinline__ void node_uv(const FuseParams<T, V> &p, const Column<T, V> &c, int k, int64_t o,
+                                        const Uv<T> &a, const Ws<T> &lo, const Ws<T> &hi, T out[4])
+{
+    const T wt = p.s.wt_uv[o];
+    if (wt >= T(0)) {
+        uv_stress(a, lo, hi, wt, p.s.inv_lam0_sq, out);
+    } else if (wt > T(-1.5)) {                  // band: the wall model's stress
+        out[0] = p.s.txx[o];
+        out[1] = p.s.tyy[o];
+        out[2] = p.s.tzz[o];
+        out[3] = p.s.txy[o];
+    } else {
+        out[0] = out[1] = out[2] = out[3] = T(0);
+    }
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void node_w(const FuseParams<T, V> &p, int k, int64_t o, const Uv<T> &lo, const Uv<T> &hi,
+                                       const Ws<T> &b, T out[2])
+{
+    const T wt = p.s.wt_w[o];
+    if (wt < T(-1.5)) {                         // solid
+        out[0] = out[1] = T(0);
+    } else if (wt < T(0) || k == 0) {           // band, or the floor level: the values given
+        out[0] = p.s.txz[o];
+        out[1] = p.s.tyz[o];
+    } else if (k == p.s.nz - 1) {               // fluid lid: no stress
+        out[0] = out[1] = T(0);
+    } else {
+        w_stress(lo, hi, b, wt, p.s.inv_lam0_sq, out);
+    }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kFuseX * kFuseY) k_sgs_force(FuseParams<T, V> p)
+{
+    __shared__ T sxx[kFuseY][kFuseX], sxy[kFuseY][kFuseX], syy[kFuseY][kFuseX];
+    __shared__ T sxz[kFuseY][kFuseX], syz[kFuseY][kFuseX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = p.s.nx, ny = p.s.ny, nz = p.s.nz;
+    const int ci = blockIdx.x * (kFuseX - 2) - 1 + tx;          // this thread's column, before wrapping
+    const int cj = blockIdx.y * (kFuseY - 2) - 1 + ty;
+    const int i = ((ci % nx) + nx) % nx, j = ((cj % ny) + ny) % ny;
+    const bool out_col = tx >= 1 && tx <= kFuseX - 2 && ty >= 1 && ty <= kFuseY - 2 && ci < nx && cj < ny;
+    const int64_t plane = (int64_t)nx * ny;
+    Column<T, V> c;
+    c.U = Field<T, V>{p.s.u, nx, ny, plane};
+    c.Vf = Field<T, V>{p.s.v, nx, ny, plane};
+    c.W = Field<T, V>{p.s.w, nx, ny, plane};
+    c.i = i; c.j = j;
+    c.im = i == 0 ? nx - 1 : i - 1; c.ip = i + 1 == nx ? 0 : i + 1;
+    c.jm = j == 0 ? ny - 1 : j - 1; c.jp = j + 1 == ny ? 0 : j + 1;
+    c.nz = nz; c.cx = p.s.cx; c.cy = p.s.cy; c.rdz = p.s.rdz;
+    const Uv<T> zero_uv{0, 0, 0, 0};
+
+    const int k0 = blockIdx.z * kFuseLevels;
+    const int k1 = min(k0 + kFuseLevels, nz);
+    const int64_t col = (int64_t)j * nx + i;
+    // state entering level k: the strain of uv-level k and the shear of w-level k,
+    // the stress of w-node k and the tzz of uv-node k-1
+    Uv<T> a_k = k0 <= nz - 2 ? c.uv(k0) : zero_uv;
+    Ws<T> b_k = c.ws(k0);
+    T wk[2];
+    {
+        const Uv<T> a_m = k0 >= 1 ? c.uv(k0 - 1) : zero_uv;
+        node_w(p, k0, (int64_t)k0 * plane + col, a_m, a_k, b_k, wk);
+    }
+    T zz_m = T(0);
+    if (k0 >= 1) {
+        const Uv<T> a_m = c.uv(k0 - 1);
+        T t[4];
+        node_uv(p, c, k0 - 1, (int64_t)(k0 - 1) * plane + col, a_m, c.ws(k0 - 1), b_k, t);
+        zz_m = t[2];
+    }
+    for (int k = k0; k < k1; ++k) {
+        const int64_t o = (int64_t)k * plane + col;
+        const Uv<T> a_n = k + 1 <= nz - 2 ? c.uv(k + 1) : zero_uv;
+        const Ws<T> b_n = c.ws(k + 1);
+        T uvk[4] = {T(0), T(0), T(0), T(0)};
+        if (k <= nz - 2) node_uv(p, c, k, o, a_k, b_k, b_n, uvk);
+        T wn[2] = {T(0), T(0)};
+        if (k + 1 <= nz - 1) node_w(p, k + 1, o + plane, a_k, a_n, b_n, wn);
+        sxx[ty][tx] = uvk[0];
+        syy[ty][tx] = uvk[1];
+        sxy[ty][tx] = uvk[3];
+        sxz[ty][tx] = wk[0];
+        syz[ty][tx] = wk[1];
+        __syncthreads();
+        if (out_col) {
+            const bool top = k == nz - 1;
+            const T fxv = -((sxx[ty][tx + 1] - sxx[ty][tx - 1]) * p.s.cx + (sxy[ty + 1][tx] - sxy[ty - 1][tx]) * p.s.cy +
+                            (wn[0] - wk[0]) * p.cz);
+            const T fyv = -((sxy[ty][tx + 1] - sxy[ty][tx - 1]) * p.s.cx + (syy[ty + 1][tx] - syy[ty - 1][tx]) * p.s.cy +
+                            (wn[1] - wk[1]) * p.cz);
+            const T fzv = -((sxz[ty][tx + 1] - sxz[ty][tx - 1]) * p.s.cx + (syz[ty + 1][tx] - syz[ty - 1][tx]) * p.s.cy +
+                            (uvk[2] - zz_m) * p.cz);
+            p.fx[o] = top ? T(0) : fxv;
+            p.fy[o] = top ? T(0) : fyv;
+            p.fz[o] = (top || k == 0) ? T(0) : fzv;
+        }
+        __syncthreads();
+        a_k = a_n;
+        b_k = b_n;
+        wk[0] = wn[0];
+        wk[1] = wn[1];
+        zz_m = uvk[2];
+    }
+}
+
+template <typename T, typename V>
+int launch_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
+                     const void *wt_w, const void *const tau[6], void *fx, void *fy, void *fz, double cs,
+                     cudaStream_t stream)
+{
+    FuseParams<T, V> p;
+    p.s.u = (const V *)u; p.s.v = (const V *)v; p.s.w = (const V *)w;
+    p.s.wt_uv = (const T *)wt_uv; p.s.wt_w = (const T *)wt_w;
+    p.s.txx = (T *)tau[0]; p.s.txy = (T *)tau[1]; p.s.tyy = (T *)tau[2];
+    p.s.tzz = (T *)tau[3]; p.s.txz = (T *)tau[4]; p.s.tyz = (T *)tau[5];
+    p.s.nx = h->nx; p.s.ny = h->ny; p.s.nz = h->nz;
+    p.s.cx = (T)(1.0 / (2.0 * h->dx));
+    p.s.cy = (T)(1.0 / (2.0 * h->dy));
+    p.s.rdz = (T)(1.0 / h->dz);
+    const double lam0 = cs * cbrt(h->dx * h->dy * h->dz);
+    p.s.inv_lam0_sq = (T)(1.0 / (lam0 * lam0));
+    p.fx = (T *)fx; p.fy = (T *)fy; p.fz = (T *)fz;
+    p.cz = (T)(1.0 / h->dz);
+    dim3 block(kFuseX, kFuseY, 1);
+    dim3 grid((h->nx + kFuseX - 3) / (kFuseX - 2), (h->ny + kFuseY - 3) / (kFuseY - 2),
+              (h->nz + kFuseLevels - 1) / kFuseLevels);
+    if (grid.y > 65535 || grid.z > 65535) return set_error(h, WMIBM_EINVAL, "grid too large for the fused launch");
+    k_sgs_force<T, V><<<grid, block, 0, stream>>>(p);
+    return cuda_status(h, cudaGetLastError(), "k_sgs_force launch");
 }
 
 template <typename T, typename V>
@@ -192,10 +368,11 @@ extern "C" int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const
         for (int64_t q = 0; q < n; ++q) {
             const double f = phi[q];
             const double zz = z0_is_field ? z0[q] : z0[0];
-            // fluid: neither band nor solid (uv-grid: phi > 2 phi_b; w-grid: phi > phi_b), the
-            // inclusive comparisons of the node classes at init
+            // the node classes of init, with the same inclusive comparisons: uv-grid band
+            // 0 <= phi <= 2 phi_b, solid phi < 0; w-grid band |phi| <= phi_b, solid phi < -phi_b
+            const bool solid = g == 0 ? f < 0.0 : f < -pb;
             const bool fluid = g == 0 ? f > 2.0 * pb : f > pb;
-            const double val = fluid ? 1.0 / ((kap * (f + zz)) * (kap * (f + zz))) : -1.0;
+            const double val = fluid ? 1.0 / ((kap * (f + zz)) * (kap * (f + zz))) : (solid ? -2.0 : -1.0);
             if (h->dtype == WMIBM_F64) ((double *)host)[g * n + q] = val;
             else ((float *)host)[g * n + q] = (float)val;
         }
@@ -222,4 +399,24 @@ extern "C" int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, c
     if (h->dtype == WMIBM_F64) return launch_sgs<double, double>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
     if (h->vel_dtype == WMIBM_BF16) return launch_sgs<float, __nv_bfloat16>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
     return launch_sgs<float, float>(h, u, v, w, wt_uv, wt_w, tau, cs, s);
+}
+
+extern "C" int wmibm_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
+                               const void *wt_w, const void *const tau[6], void *fx, void *fy, void *fz, double cs,
+                               void *stream)
+{
+    if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
+    if (!u || !v || !w || !wt_uv || !wt_w || !tau || !fx || !fy || !fz)
+        return set_error(h, WMIBM_EINVAL, "NULL argument");
+    for (int c = 0; c < 6; ++c)
+        if (!tau[c]) return set_error(h, WMIBM_EINVAL, "NULL stress pointer %d", c);
+    if (!(cs > 0.0)) return set_error(h, WMIBM_EINVAL, "the Smagorinsky coefficient must be positive");
+    int st = check_device(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->dtype == WMIBM_F64)
+        return launch_sgs_force<double, double>(h, u, v, w, wt_uv, wt_w, tau, fx, fy, fz, cs, s);
+    if (h->vel_dtype == WMIBM_BF16)
+        return launch_sgs_force<float, __nv_bfloat16>(h, u, v, w, wt_uv, wt_w, tau, fx, fy, fz, cs, s);
+    return launch_sgs_force<float, float>(h, u, v, w, wt_uv, wt_w, tau, fx, fy, fz, cs, s);
 }

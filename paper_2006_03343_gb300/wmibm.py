@@ -29,7 +29,7 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
-            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress")
+            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress", "wmibm_sgs_force")
 
 
 class WmibmError(RuntimeError):
@@ -100,6 +100,8 @@ def load(path: Optional[str] = None):
     L.wmibm_sgs_wall_terms.restype = ctypes.c_int
     L.wmibm_sgs_stress.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_sgs_stress.restype = ctypes.c_int
+    L.wmibm_sgs_force.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, ctypes.c_double, _VP]
+    L.wmibm_sgs_force.restype = ctypes.c_int
     L.wmibm_mask.argtypes = [_VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_mask.restype = ctypes.c_int
     L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
@@ -309,6 +311,17 @@ class Handle:
             self._field(t)
         self._check(self._L.wmibm_sgs_stress(self._h, _dptr(u), _dptr(v), _dptr(w), _dptr(wall_terms[0]),
                                              _dptr(wall_terms[1]), _ptrs(tau), float(cs), _stream_ptr(stream)))
+
+    def sgs_force(self, u, v, w, wall_terms, tau: Sequence, f: Sequence, cs=0.16, stream=None):
+        """f = -div tau with the fluid stress formed from the velocity on the fly (Eqs. 4-7);
+        tau is read at band nodes (run wall_stress first) and on the floor, never written."""
+        for t in (u, v, w):
+            self._field(t, vel=True)
+        for t in list(wall_terms) + list(tau) + list(f):
+            self._field(t)
+        self._check(self._L.wmibm_sgs_force(self._h, _dptr(u), _dptr(v), _dptr(w), _dptr(wall_terms[0]),
+                                            _dptr(wall_terms[1]), _ptrs(tau), _dptr(f[0]), _dptr(f[1]), _dptr(f[2]),
+                                            float(cs), _stream_ptr(stream)))
 
     def spectral_shape(self):
         """(rows per row unit, columns per column unit, levels per chunk, shared bytes

@@ -115,6 +115,7 @@ def test_later_entry_points_reject_null_arguments(lib):
     assert lib.wmibm_spectral_shape(None, (ctypes.c_int64 * 4)()) == wmibm.EINVAL
     assert lib.wmibm_sgs_wall_terms(None, None, None, None, 0, None, None, None) == wmibm.EINVAL
     assert lib.wmibm_sgs_stress(None, None, None, None, None, None, tau, 0.16, None) == wmibm.EINVAL
+    assert lib.wmibm_sgs_force(None, None, None, None, None, None, tau, None, None, None, 0.16, None) == wmibm.EINVAL
     assert lib.wmibm_set_log_z0(None, None, None) == wmibm.EINVAL
     assert lib.wmibm_backward(None, three, three, None, None, None, None, None) == wmibm.EINVAL
     t = wmibm.Tuning()
