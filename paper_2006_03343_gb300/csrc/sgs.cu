@@ -116,9 +116,39 @@ __device__ __forceinline__ void w_stress(const Uv<T> &lo, const Uv<T> &hi, const
     out[1] = nu2 * b.s23;
 }
 
+// The velocity values of level L that, with the centre values of level L-1 and
+// w(L), form the uv strain of level L and the w shear of level L.
+template <typename T>
+struct Raw {
+    T u_ip, u_im, u_jp, u_jm, v_ip, v_im, v_jp, v_jm;  // horizontal neighbours on level L
+    T u_c, v_c;                                         // u, v at (i, j, L)
+    T w_up;                                             // w at (i, j, L+1)
+    T w_ip, w_im, w_jp, w_jm;                           // w neighbours on level L
+};
+
+template <typename T, typename V>
+__device__ __forceinline__ Raw<T> load_raw(const Column<T, V> &c, int L)
+{
+    Raw<T> r;
+    if (L <= c.nz - 2) {
+        r.u_ip = c.U.at(c.ip, c.j, L); r.u_im = c.U.at(c.im, c.j, L);
+        r.u_jp = c.U.at(c.i, c.jp, L); r.u_jm = c.U.at(c.i, c.jm, L);
+        r.v_ip = c.Vf.at(c.ip, c.j, L); r.v_im = c.Vf.at(c.im, c.j, L);
+        r.v_jp = c.Vf.at(c.i, c.jp, L); r.v_jm = c.Vf.at(c.i, c.jm, L);
+        r.u_c = c.U.at(c.i, c.j, L); r.v_c = c.Vf.at(c.i, c.j, L);
+        r.w_up = c.W.at(c.i, c.j, L + 1);
+        r.w_ip = c.W.at(c.ip, c.j, L); r.w_im = c.W.at(c.im, c.j, L);
+        r.w_jp = c.W.at(c.i, c.jp, L); r.w_jm = c.W.at(c.i, c.jm, L);
+    } else {
+        r = Raw<T>{};
+    }
+    return r;
+}
+
 // One thread per column (i, j) marching up a chunk of kc levels: each level's uv
 // strain and w shear are formed once and reused by the uv-node above/below and
-// the w-node between them.
+// the w-node between them.  Software-pipelined: the loads of level k+2 are in
+// flight while level k+1's strain and level k's stresses are formed.
 template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p, int kc)
 {
@@ -138,33 +168,51 @@ __global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p, int kc)
     c.nz = p.nz; c.cx = p.cx; c.cy = p.cy; c.rdz = p.rdz;
 
     Uv<T> a_prev = k0 >= 1 ? c.uv(k0 - 1) : Uv<T>{0, 0, 0, 0};
+    Uv<T> a_cur = k0 <= p.nz - 2 ? c.uv(k0) : Uv<T>{0, 0, 0, 0};
     Ws<T> b_cur = c.ws(k0);
+    // carried centre values of level k0 and w(k0+1), then the raw values of level k0+1
+    T u_c = k0 <= p.nz - 2 ? c.U.at(i, j, k0) : T(0);
+    T v_c = k0 <= p.nz - 2 ? c.Vf.at(i, j, k0) : T(0);
+    T w_c = k0 <= p.nz - 2 ? c.W.at(i, j, k0 + 1) : T(0);
+    Raw<T> raw = load_raw(c, k0 + 1);
     int64_t o = (int64_t)k0 * plane + (int64_t)j * p.nx + i;
     for (int k = k0; k < k1; ++k, o += plane) {
-        const Uv<T> a_cur = k <= p.nz - 2 ? c.uv(k) : Uv<T>{0, 0, 0, 0};
-        const Ws<T> b_next = c.ws(k + 1);
-        if (k <= p.nz - 2) {                                // uv-node (i, j, k)
-            const T wt = p.wt_uv[o];
-            if (wt >= T(0)) {
-                T t[4];
-                uv_stress(a_cur, b_cur, b_next, wt, p.inv_lam0_sq, t);
-                p.txx[o] = t[0];
-                p.tyy[o] = t[1];
-                p.tzz[o] = t[2];
-                p.txy[o] = t[3];
-            }
+        const Raw<T> nxt = load_raw(c, k + 2);                      // in flight during this level
+        const T wt_uv = k <= p.nz - 2 ? p.wt_uv[o] : T(-1);
+        const T wt_w = k >= 1 ? p.wt_w[o] : T(-1);
+        // level k+1 from the raw values: uv strain (valid up to nz-2) and w shear (lid 0)
+        const int L = k + 1;
+        Uv<T> a_next{0, 0, 0, 0};
+        Ws<T> b_next{0, 0};
+        if (L <= p.nz - 2) {
+            a_next.s11 = (raw.u_ip - raw.u_im) * p.cx;
+            a_next.s22 = (raw.v_jp - raw.v_jm) * p.cy;
+            a_next.s12 = T(0.5) * ((raw.u_jp - raw.u_jm) * p.cy + (raw.v_ip - raw.v_im) * p.cx);
+            a_next.s33 = (raw.w_up - w_c) * p.rdz;
+            b_next.s13 = T(0.5) * ((raw.u_c - u_c) * p.rdz + (raw.w_ip - raw.w_im) * p.cx);
+            b_next.s23 = T(0.5) * ((raw.v_c - v_c) * p.rdz + (raw.w_jp - raw.w_jm) * p.cy);
         }
-        if (k >= 1) {                                       // w-node (i, j, k); the floor is left
-            const T wt = p.wt_w[o];
-            if (wt >= T(0)) {
-                T t[2] = {T(0), T(0)};                      // the lid: no stress (Eq. 10)
-                if (k < p.nz - 1) w_stress(a_prev, a_cur, b_cur, wt, p.inv_lam0_sq, t);
-                p.txz[o] = t[0];
-                p.tyz[o] = t[1];
-            }
+        if (wt_uv >= T(0)) {                                        // uv-node (i, j, k)
+            T t[4];
+            uv_stress(a_cur, b_cur, b_next, wt_uv, p.inv_lam0_sq, t);
+            p.txx[o] = t[0];
+            p.tyy[o] = t[1];
+            p.tzz[o] = t[2];
+            p.txy[o] = t[3];
+        }
+        if (wt_w >= T(0)) {                                         // w-node (i, j, k); the floor is left
+            T t[2] = {T(0), T(0)};                                  // the lid: no stress (Eq. 10)
+            if (k < p.nz - 1) w_stress(a_prev, a_cur, b_cur, wt_w, p.inv_lam0_sq, t);
+            p.txz[o] = t[0];
+            p.tyz[o] = t[1];
         }
         a_prev = a_cur;
+        a_cur = a_next;
         b_cur = b_next;
+        u_c = raw.u_c;
+        v_c = raw.v_c;
+        w_c = raw.w_up;
+        raw = nxt;
     }
 }
 
