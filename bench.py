@@ -607,6 +607,20 @@ def run_ensemble(args):
     with torch.cuda.graph(g):
         batch.wall_stress_force(stats)
     torch.cuda.synchronize()
+    # the first replay's results, for the accuracy check against the oracle
+    g.replay()
+    torch.cuda.synchronize()
+    first = {m: ([t.double().cpu().numpy() for t in fields[m][3]], [t.double().cpu().numpy() for t in fields[m][4]])
+             for m in (0, 37)}
+    sampler = ClockSampler(0) if not args.profile else None
+    if sampler:
+        sampler.start()
+    t_soak = time.perf_counter()
+    while not args.profile and time.perf_counter() - t_soak < 1.0:
+        for _ in range(5):
+            flush.zero_()
+            g.replay()
+        torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     for s in range(args.steps):
         flush.zero_()
@@ -614,6 +628,7 @@ def run_ensemble(args):
         g.replay()
         ev[s][1].record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
     ms = [e[0].elapsed_time(e[1]) for e in ev]
     points = batch.points()
     value = points / (float(np.mean(ms)) * 1e-3) / 1e9
@@ -638,6 +653,64 @@ def run_ensemble(args):
     peak, peak_kind = measured_peak()
     achieved = step_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
     shapes = sorted({c.grid[:3] for c in cases})
+
+    # end to end through the public API: every member's velocity and stresses in from pinned host memory,
+    # the batch step, every member's forcing out
+    e2e = None
+    if not args.no_e2e and not args.profile:
+        host = [([torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (c.u, c.v, c.w)] +
+                 [torch.from_numpy(c.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES],
+                 [torch.empty(c.shape, dtype=tdt).pin_memory() for _ in range(3)]) for c in cases]
+        h2d = sum(t.numel() * t.element_size() for ins, _ in host for t in ins)
+        d2h = sum(t.numel() * t.element_size() for _, outs in host for t in outs)
+
+        def e2e_step():
+            for (ins, _), fl in zip(host, fields):
+                for dst, src in zip(list(fl[:3]) + list(fl[3]), ins):
+                    dst.copy_(src, non_blocking=True)
+            batch.wall_stress_force(stats)
+            for (_, outs), fl in zip(host, fields):
+                for dst, src in zip(outs, fl[4]):
+                    dst.copy_(src, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": args.steps * points / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = accuracy = None
+    if not args.no_cpu and not args.profile:
+        import oracle
+        oracle.build()
+        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        accuracy = {}
+        for m, (gtau, gf) in first.items():
+            c = cases[m]
+            tau_o = {k: rd(c.tau[k]) for k in inputs.TAU_NAMES}
+            oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, rd(c.u), rd(c.v), rd(c.w), tau_o)
+            f_o = oracle.force(c.grid, tau_o)
+            err = max(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) for a, b in zip(gf, f_o))
+            accuracy[f"member_{m}_f_normwise_max"] = err
+        # the oracle over the first members, as many as fit about args.cpu_seconds
+        t0 = time.perf_counter()
+        done_pts = 0
+        used = 0
+        for c in cases:
+            tau_o = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
+            oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, tau_o)
+            oracle.force(c.grid, tau_o)
+            done_pts += c.npoints
+            used += 1
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": done_pts / el / 1e9, "unit": UNIT, "cores": oracle.openmp_threads(), "kind": "oracle",
+               "sample": f"wall stress + force of the first {used} of 64 members ({el:.1f} s, FP64 CPU oracle)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
@@ -650,7 +723,8 @@ def run_ensemble(args):
             "one_by_one": {"value": points / (float(np.mean(ms1)) * 1e-3) / 1e9, "unit": UNIT,
                            "ms_per_step": float(np.mean(ms1)),
                            "how": "the 64 members' wall stress + force one after the other, in one CUDA graph"},
-            "gpu_launches": 2 * args.steps, "device_status": handles[0].device_status()}
+            "gpu_launches": 2 * args.steps, "device_status": handles[0].device_status(),
+            "accuracy": accuracy, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line))
     batch.close()
     return 0
@@ -695,18 +769,33 @@ def run_adjoint(args):
     fwd_ms = timed_run(graphs[0].replay, stream, flush, args.steps)
     bwd_ms = timed_run(graphs[1].replay, stream, flush, args.steps)
     status = h.device_status()
-    accuracy = None
+    accuracy = cpu = None
     if not args.no_cpu:
         import oracle
         oracle.build()
         rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        threads = oracle.openmp_threads()
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
         ref = oracle.adjoint(case.grid, case.phi_uv, case.phi_w, rd(s_log), case.phi_c, case.phi_b,
                              rd(case.u), rd(case.v), rd(case.w), [rd(x) for x in g])
+        el = time.perf_counter() - t0
+        oracle.set_threads(threads)
+        cpu = {"value": case.npoints / el / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full pass of the oracle's adjoint on one core ({el:.1f} s)"}
         accuracy = {}
         for name, got, r in zip(("du", "dv", "dw", "dlogz0"), grads, ref):
             gg = got.double().cpu().numpy()
             accuracy[name] = float(np.max(np.abs(gg - r)) / max(np.max(np.abs(r)), 1e-300))
     npts = case.npoints
+    es = 8 if args.dtype == "f64" else 4
+    # algorithmic bytes of one backward: the four gradient fields written once (zeroed, then the touched
+    # nodes), plus the sparse band part, taken as the forward wall model's bytes (the same records, the
+    # transposed stencils of the same velocity nodes)
+    kbytes = 4 * npts * es + h.traffic_bytes(0)
+    kms = float(np.mean(bwd_ms))
+    peak, peak_kind = measured_peak()
+    achieved = kbytes / (kms * 1e-3) / 1e9
     line = {"metric": "IBM stage adjoint throughput (Gpts/s)", "unit": "Gpts/s",
             "value": npts / (float(np.mean(bwd_ms)) * 1e-3) / 1e9, "ms_per_step": float(np.mean(bwd_ms)),
             "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -717,6 +806,11 @@ def run_adjoint(args):
             "forward_same_log_z0": {"ms_per_step": float(np.mean(fwd_ms)),
                                     "value": npts / (float(np.mean(fwd_ms)) * 1e-3) / 1e9, "unit": "Gpts/s"},
             "normwise_error_vs_oracle_adjoint": accuracy,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "wmibm_backward (gradient zeroing, k_adjoint_records, "
+                                                    "k_adjoint_gather)", "kernel_ms": kms,
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": kbytes},
+            "cpu_baseline": cpu,
             "gpu_launches": 2 * args.steps,       # k_adjoint_records + k_adjoint_gather per timed backward
             "device_status": status}
     print(json.dumps(line))
