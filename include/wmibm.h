@@ -188,7 +188,8 @@ int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *
  * about 80 bytes per node moved.
  *   u, v, w, wt_uv, wt_w, cs : as in wmibm_sgs_stress
  *   tau           : 6 DEVICE stress fields (dtype), read at band nodes and on the floor only
- *   fx, fy, fz    : DEVICE forcing (dtype), written everywhere (0 on the ghost level, floor and lid as in wmibm_force)
+ *   fx, fy, fz    : DEVICE forcing (dtype), written everywhere (0 on the ghost level, floor and lid as in
+ *                   wmibm_force); must not overlap tau, the velocity or the wall terms
  * Errors: EINVAL, ESTATE, ECUDA.
  */
 int wmibm_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,

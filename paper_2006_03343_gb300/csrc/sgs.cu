@@ -150,7 +150,7 @@ __device__ __forceinline__ Raw<T> load_raw(const Column<T, V> &c, int L)
 // the w-node between them.  Software-pipelined: the loads of level k+2 are in
 // flight while level k+1's strain and level k's stresses are formed.
 template <typename T, typename V>
-__global__ void __launch_bounds__(256) k_sgs(SgsParams<T, V> p, int kc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_sgs(SgsParams<T, V> p, int kc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
