@@ -20,7 +20,7 @@
  *   k = 0 is the floor and k = nz-1 the lid.  u, v, p and the stresses
  *   txx, txy, tyy, tzz live on uv-nodes; w, txz, tyz live on w-nodes.
  *
- * Readings of the paper where it is silent (each also listed in the design doc):
+ * Readings of the paper where it is silent:
  *   R1  phi_b is a free parameter with 2 phi_b in [dz, 1.5 dz) (Sec. 3.3);
  *       the caller passes it.
  *   R2  the velocity sample point lies at distance phi_c from the SURFACE
