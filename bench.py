@@ -453,6 +453,8 @@ def run_ours(args):
     f64_form = None
     if args.dtype == "f32" and not args.profile:
         g64 = GpuForm(case, "f64", None, dev)
+        g64.step()
+        first64 = g64.host_result()
         if not args.no_tune:
             from paper_2006_03343_gb300 import autotune
             autotune.tune(g64.h, (g64.u, g64.v, g64.w, g64.tau, g64.f, g64.stats))
@@ -465,7 +467,7 @@ def run_ours(args):
         f64_form = {"value": args.steps * case.npoints / (sum(s64) * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": float(np.mean(s64)), "step_gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
                     "bound": "FP64 arithmetic (GB300 FP64 rate), not HBM",
-                    "device_status": g64.h.device_status()}
+                    "device_status": g64.h.device_status(), "first_pass": first64}
         g64.h.close()
         del g64
 
@@ -521,6 +523,10 @@ def run_ours(args):
         cpu["single_thread"] = {"value": g1, "unit": UNIT, "cores": 1,
                                 "sample": f"{p1} full passes ({e1:.1f} s)"}
         accuracy = accuracy_report(first_tau, first_f, ref)
+        if f64_form is not None:
+            f64_form["accuracy"] = accuracy_report(*f64_form.pop("first_pass"), ref)
+    if f64_form is not None:
+        f64_form.pop("first_pass", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -654,6 +660,29 @@ def run_ensemble(args):
     achieved = step_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
     shapes = sorted({c.grid[:3] for c in cases})
 
+    # the plain FP64 batch of the same members, timed the same way, with its error against the oracle
+    f64_form = None
+    if args.dtype == "f32" and not args.profile:
+        d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=torch.float64)
+        h64 = [wmibm.Handle.from_case(c, dtype="f64") for c in cases]
+        fl64 = [(d64(c.u), d64(c.v), d64(c.w), [d64(c.tau[k]) for k in inputs.TAU_NAMES],
+                 [torch.empty(c.shape, dtype=torch.float64, device=dev) for _ in range(3)]) for c in cases]
+        b64 = wmibm.Batch(h64)
+        b64.set_fields(fl64)
+        st64 = b64.new_stats()
+        for _ in range(3):
+            b64.wall_stress_force(st64)
+        torch.cuda.synchronize()
+        first64 = {m: [t.cpu().numpy() for t in fl64[m][4]] for m in (0, 37)}
+        g64 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g64):
+            b64.wall_stress_force(st64)
+        ms64 = timed_run(g64.replay, stream, flush, args.steps)
+        f64_form = {"value": points / (float(np.mean(ms64)) * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": float(np.mean(ms64)), "first": first64}
+        b64.close()
+        del h64, fl64
+
     # end to end through the public API: every member's velocity and stresses in from pinned host memory,
     # the batch step, every member's forcing out
     e2e = None
@@ -696,6 +725,14 @@ def run_ensemble(args):
             f_o = oracle.force(c.grid, tau_o)
             err = max(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) for a, b in zip(gf, f_o))
             accuracy[f"member_{m}_f_normwise_max"] = err
+            if f64_form is not None:
+                # the FP64 batch against the oracle on the unrounded inputs
+                t64 = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
+                oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, t64)
+                f64_o = oracle.force(c.grid, t64)
+                f64_form[f"member_{m}_f_normwise_max"] = max(
+                    float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+                    for a, b in zip(f64_form["first"][m], f64_o))
         # the oracle over the first members, as many as fit about args.cpu_seconds
         t0 = time.perf_counter()
         done_pts = 0
@@ -725,6 +762,9 @@ def run_ensemble(args):
                            "how": "the 64 members' wall stress + force one after the other, in one CUDA graph"},
             "gpu_launches": 2 * args.steps, "device_status": handles[0].device_status(),
             "accuracy": accuracy, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+    if f64_form is not None:
+        f64_form.pop("first", None)
+        line["f64_form"] = f64_form
     print(json.dumps(line))
     batch.close()
     return 0
