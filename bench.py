@@ -232,6 +232,7 @@ def run_reference(args):
     oracle.build()
     tau = {k: v.copy() for k, v in case.tau.items()}
     u, v, w = case.u.copy(), case.v.copy(), case.w.copy()
+    threads_before = oracle.openmp_threads()
     if args.workload in ("spectral", "sgs"):
         # their numpy parts (the FFTs, the SGS stress) are single-threaded: run the C parts on one core too
         oracle.set_threads(1)
@@ -249,6 +250,7 @@ def run_reference(args):
     total = sum(per_step)
     value = args.steps * case.npoints / total / 1e9
     threads = oracle.openmp_threads()
+    oracle.set_threads(threads_before)
     metric = {"spectral": METRIC_SPECTRAL, "sgs": METRIC_SGS}.get(args.workload, METRIC)
     line = {"metric": metric, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,

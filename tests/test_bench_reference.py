@@ -26,3 +26,20 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"]
+
+
+def test_reference_arm_sgs_workload(monkeypatch, capsys):
+    """The reference arm of the SGS workload: the oracle's Smagorinsky stress, wall stress and force
+    on the cube array, reported under the GPU arm's metric, on one core."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main(["--impl", "reference", "--workload", "sgs", "--steps", "1", "--warmup", "0"]) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC_SGS
+    assert d["value"] > 0 and d["cpu_baseline"]["cores"] == 1
+    assert "SGS stress" in d["cpu_baseline"]["sample"]
+    assert d["config"]["nodes"] == 256 * 128 * 128
