@@ -41,12 +41,43 @@ struct AdjParams {
     int64_t m_uv, m_w;
     const int32_t *band_w, *band_uv;   // ascending node lists of the two bands
     T *du, *dv, *dw, *ds;
+    // zeroing of the gradient fields, by the blocks after the records' blocks
+    int64_t n;                    // nodes per field
+    int64_t record_blocks;
+    int32_t vec16;                // the fields are 16-byte aligned and n * sizeof(T) is a multiple of 16
 };
 
+// Clears du, dv, dw (and ds) before the gather writes the touched nodes: zeroing
+// block zb of nzb, grid-stride, 16-byte stores where the fields allow.
+template <typename T>
+__device__ void zero_gradients(const AdjParams<T> &p, int64_t zb, int64_t nzb)
+{
+    T *const outs[4] = {p.du, p.dv, p.dw, p.ds};
+    const int64_t first = zb * kThreads + threadIdx.x, stride = nzb * kThreads;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        T *o = outs[f];
+        if (!o) continue;
+        if (p.vec16) {
+            const int64_t n4 = p.n * (int64_t)sizeof(T) / 16;
+            for (int64_t q = first; q < n4; q += stride) reinterpret_cast<float4 *>(o)[q] = make_float4(0, 0, 0, 0);
+        } else {
+            for (int64_t q = first; q < p.n; q += stride) o[q] = T(0);
+        }
+    }
+}
+
+// Blocks [0, record_blocks): one band record per thread.  The blocks after them
+// clear the gradient fields meanwhile (the gather, next in the stream, writes the
+// touched nodes after both).
 template <typename T, typename VEL>
 __global__ void __launch_bounds__(kThreads) k_adjoint_records(AdjParams<T> p)
 {
     using Rec = typename RecOf<T>::type;
+    if ((int64_t)blockIdx.x >= p.record_blocks) {
+        zero_gradients(p, (int64_t)blockIdx.x - p.record_blocks, (int64_t)gridDim.x - p.record_blocks);
+        return;
+    }
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (t >= p.nrec) return;
     T nxv, nyv, nzv, C, ax, ay, azu, azw;
@@ -286,14 +317,6 @@ template <typename T, typename VEL>
 int backward_impl(wmibm_handle *h, const void *const g[3], const void *const uvw[3], void *du, void *dv, void *dw,
                   void *dlogz0, cudaStream_t stream)
 {
-    const size_t bytes = (size_t)h->n * sizeof(T);
-    cudaError_t e = cudaMemsetAsync(du, 0, bytes, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dv, 0, bytes, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dw, 0, bytes, stream);
-    if (e == cudaSuccess && dlogz0) e = cudaMemsetAsync(dlogz0, 0, bytes, stream);
-    if (e != cudaSuccess) return cuda_status(h, e, "backward: clear outputs");
-    if (h->nrec == 0) return WMIBM_OK;
-
     AdjParams<T> p = {};
     p.rec = h->rec;
     p.nb_w = h->lists.n[WMIBM_LIST_BAND_W];
@@ -326,10 +349,21 @@ int backward_impl(wmibm_handle *h, const void *const g[3], const void *const uvw
     p.dv = (T *)dv;
     p.dw = (T *)dw;
     p.ds = (T *)dlogz0;
-    const unsigned b1 = (unsigned)((h->nrec + kThreads - 1) / kThreads);
-    k_adjoint_records<T, VEL><<<b1, kThreads, 0, stream>>>(p);
+    p.n = h->n;
+    bool al = (h->n * (int64_t)sizeof(T)) % 16 == 0;
+    const void *const outs[4] = {du, dv, dw, dlogz0};
+    for (int f = 0; f < 4; ++f) al = al && ((uintptr_t)outs[f] & 15u) == 0;
+    p.vec16 = al ? 1 : 0;
+    // records' blocks, then zeroing blocks: about two per SM, at most one per 1024 vectors
+    const int64_t b1 = (h->nrec + kThreads - 1) / kThreads;
+    int64_t bz = (h->n * (int64_t)sizeof(T) / 16 + 4 * kThreads - 1) / (4 * kThreads);
+    if (bz > 2 * (int64_t)h->sm_count) bz = 2 * (int64_t)h->sm_count;
+    if (bz < 1) bz = 1;
+    p.record_blocks = b1;
+    k_adjoint_records<T, VEL><<<(unsigned)(b1 + bz), kThreads, 0, stream>>>(p);
     int st = cuda_status(h, cudaGetLastError(), "k_adjoint_records launch");
     if (st) return st;
+    if (h->nrec == 0) return WMIBM_OK;
     const int64_t total = p.m_uv + p.m_w + (dlogz0 ? h->nrec : 0);
     const unsigned b2 = (unsigned)((total + kThreads - 1) / kThreads);
     k_adjoint_gather<T><<<b2, kThreads, 0, stream>>>(p);
