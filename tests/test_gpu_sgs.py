@@ -214,3 +214,50 @@ def test_fused_graph_replay(wm, oracle_mod):
         torch.cuda.synchronize()
         for t, r in zip(f, ref):
             assert np.array_equal(to_host(t), r)
+
+
+def test_sgs_beside_wall_stress_on_two_streams(wm):
+    """The SGS stress writes fluid entries only and the wall model band and solid
+    entries only, so the two may run on two streams at once: the forcing after
+    both (joined by events, also under graph capture) equals the serial chain
+    bit for bit."""
+    case = inputs.cubes(shape=(96, 48, 40), dtype="f32")
+    h, (u, v, w), wt, tau = _gpu_sgs(wm, case, "f32")
+    h.wall_stress(u, v, w, tau)
+    f_ref = [torch.zeros(h.shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+    h.force(tau, f_ref)
+    torch.cuda.synchronize()
+    tau_ref = [t.clone() for t in tau]
+    side = torch.cuda.Stream()
+    f = [torch.zeros(h.shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+
+    def overlapped():
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
+        h.sgs_stress(u, v, w, wt, tau, cs=CS)
+        with torch.cuda.stream(side):
+            h.wall_stress(u, v, w, tau)
+        cur.wait_stream(side)
+        h.force(tau, f)
+
+    def reset():
+        for t, k in zip(tau, inputs.TAU_NAMES):
+            t.copy_(to_dev(case.tau[k], "f32"))
+        for x in f:
+            x.fill_(float("nan"))
+
+    reset()
+    overlapped()
+    torch.cuda.synchronize()
+    for a, b in zip(tau + f, tau_ref + f_ref):
+        assert torch.equal(a, b)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        overlapped()
+    for _ in range(3):
+        reset()
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(tau + f, tau_ref + f_ref):
+            assert torch.equal(a, b)
+    assert h.device_status() == wm.OK
