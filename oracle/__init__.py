@@ -21,12 +21,16 @@ Functions and the passages they follow:
   sgs_stress    Eqs. 4-7, the Smagorinsky stress with Mason's wall damping at fluid nodes
   mask          Sec. 3.2, Eq. 27: the body velocity condition
   adjoint       chain rule of wall_stress + force for L = <g, f>
+  heightfield_distance  Sec. 3.1, d = the minimum distance to the immersed boundary, for
+                a height field's piecewise-linear surface (reading R10), by brute force
+  heightfield_sdf  Sec. 3.1, phi = +d in the fluid, -d in the solid, within a reach
 
 Every function here is pinned against closed forms, invariants and brute force
 (see the docstrings there): ``tests/test_oracle_pins.py`` (wall stress, central-
 difference divergence, mask), ``tests/test_oracle_adjoint.py`` (adjoint) and
-``tests/test_oracle_spectral.py`` (pseudo-spectral divergence) and
-``tests/test_oracle_sgs.py`` (Smagorinsky stress).
+``tests/test_oracle_spectral.py`` (pseudo-spectral divergence),
+``tests/test_oracle_sgs.py`` (Smagorinsky stress) and ``tests/test_oracle_sdf.py``
+(height-field distance).
 """
 from __future__ import annotations
 
@@ -90,6 +94,9 @@ def _load():
                                          _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          _D, _D, _D, _D, _D, _D, _D, _D, _D, _D])
             lib.orc_adjoint.restype = ctypes.c_int
+        lib.orc_heightfield_distance.argtypes = [_I64, _I64, _I64, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, _D, _I64, ctypes.c_void_p, ctypes.c_int, _D]
+        lib.orc_heightfield_distance.restype = None
         lib.orc_openmp_threads.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = None
@@ -341,3 +348,49 @@ def adjoint(grid, phi_uv, phi_w, logz0, phi_c, phi_b, u, v, w, g, kappa=0.4):
     if rc != 0:
         raise MemoryError("oracle: no scratch memory for the adjoint")
     return du, dv, dw, ds
+
+
+def heightfield_distance(grid, h2d, is_w, nodes=None):
+    """Sec. 3.1: d = the minimum distance from a node to the immersed boundary, here
+    the piecewise-linear surface through the heights h2d[ny, nx] sampled at the
+    column nodes (reading R10: each cell split along its (i, j)-(i+1, j+1)
+    diagonal), by brute force over every triangle.  Returns d for every node of
+    the uv-grid (is_w False) or the w-grid (is_w True) as [nz, ny, nx], or at the
+    flat indices `nodes`.  Only distances below half the period minus a cell are
+    exact (each triangle is taken at its periodic image nearest the node)."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    hh = np.ascontiguousarray(h2d, dtype=np.float64)
+    assert hh.shape == (ny, nx)
+    if nodes is None:
+        out = np.empty((nz, ny, nx))
+        _load().orc_heightfield_distance(nx, ny, nz, lx, ly, lz, _p(hh), 0, None, int(bool(is_w)), _p(out))
+        return out
+    idx = np.ascontiguousarray(nodes, dtype=np.int64)
+    out = np.empty(idx.shape)
+    _load().orc_heightfield_distance(nx, ny, nz, lx, ly, lz, _p(hh), int(idx.size),
+                                     idx.ctypes.data_as(ctypes.c_void_p), int(bool(is_w)), _p(out))
+    return out
+
+
+def heightfield_sdf(grid, h2d, reach, nodes=None):
+    """Sec. 3.1 with reading R10: phi = +d above the surface and -d below it, the
+    side taken from z - h at the node's own column (a vertex of the surface), for
+    every node within distance `reach` of the surface; beyond it phi = z - h
+    (the same sign, and |z - h| >= d > reach).  Returns (phi_uv, phi_w): [nz, ny,
+    nx] arrays, or the values at the flat indices `nodes` on each grid."""
+    nx, ny, nz, lx, ly, lz = _shape(grid)
+    dx, dy, dz = lx / nx, ly / ny, lz / (nz - 1)
+    assert 0 < reach and reach + dx < 0.5 * lx and reach + dy < 0.5 * ly, "reach too large for the minimum image"
+    hh = np.ascontiguousarray(h2d, dtype=np.float64)
+    out = []
+    for is_w in (False, True):
+        if nodes is None:
+            k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        else:
+            flat = np.asarray(nodes, dtype=np.int64)
+            i, j, k = flat % nx, (flat // nx) % ny, flat // (nx * ny)
+        z = k * dz if is_w else (k + 0.5) * dz
+        vertical = z - hh[j, i]
+        d = heightfield_distance(grid, hh, is_w, nodes)
+        out.append(np.where(d <= reach, np.sign(vertical) * d, vertical))
+    return out[0], out[1]

@@ -41,6 +41,14 @@
  *       Eqs. 8 and 11).
  *   R7  a per-cell roughness z0[k][j][i] serves both the uv-node and the
  *       w-node with the same (i,j,k).
+ *   R10 for terrain given as heights h[j][i] at the column nodes (i dx, j dy),
+ *       the immersed boundary is the piecewise-linear surface through the
+ *       samples: cell [i, i+1] x [j, j+1] is split along the diagonal from
+ *       (i, j) to (i+1, j+1) into two flat triangles, periodic in x and y.
+ *       phi of Sec. 3.1 is the distance d to that surface, signed by
+ *       z - h[j][i] (the node's own column passes through a vertex).  Where d
+ *       exceeds the caller's reach, phi keeps the vertical value z - h[j][i]
+ *       (same sign, magnitude >= d > reach).
  */
 #include <math.h>
 #include <stdint.h>
@@ -673,4 +681,127 @@ int orc_adjoint(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double
             }
     free(gam);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact signed distance to a height field (Sec. 3.1, reading R10).            */
+/* ------------------------------------------------------------------------- */
+
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static void sub3(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[0] - b[0];
+    out[1] = a[1] - b[1];
+    out[2] = a[2] - b[2];
+}
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* distance from p to the segment from a to b: the nearest point is a + t (b - a)
+ * with t the projection parameter clamped to [0, 1] */
+static double segment_distance(const double p[3], const double a[3], const double b[3])
+{
+    double ab[3], ap[3], q[3];
+    sub3(b, a, ab);
+    sub3(p, a, ap);
+    const double l2 = dot3(ab, ab);
+    double t = l2 > 0.0 ? dot3(ap, ab) / l2 : 0.0;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    q[0] = ap[0] - t * ab[0];
+    q[1] = ap[1] - t * ab[1];
+    q[2] = ap[2] - t * ab[2];
+    return sqrt(dot3(q, q));
+}
+
+/* distance from p to the flat triangle (a, b, c): a triangle is convex, so the
+ * nearest point is the orthogonal projection of p onto its plane when that
+ * projection lies inside (then the distance is the distance to the plane), and
+ * otherwise lies on one of the three edges */
+static double triangle_distance(const double p[3], const double a[3], const double b[3], const double c[3])
+{
+    double ab[3], ac[3], n[3], ap[3];
+    sub3(b, a, ab);
+    sub3(c, a, ac);
+    cross3(ab, ac, n);
+    sub3(p, a, ap);
+    const double n2 = dot3(n, n);
+    if (n2 > 0.0) {
+        const double s = dot3(ap, n) / n2;
+        const double q[3] = {p[0] - s * n[0], p[1] - s * n[1], p[2] - s * n[2]};
+        /* q is inside when it lies on the inner side of all three edges */
+        const double *v[3] = {a, b, c};
+        int inside = 1;
+        for (int e = 0; e < 3; ++e) {
+            double edge[3], vq[3], cr[3];
+            sub3(v[(e + 1) % 3], v[e], edge);
+            sub3(q, v[e], vq);
+            cross3(edge, vq, cr);
+            if (dot3(cr, n) < 0.0) inside = 0;
+        }
+        if (inside) return fabs(s) * sqrt(n2);
+    }
+    double d = segment_distance(p, a, b);
+    const double d2 = segment_distance(p, b, c);
+    const double d3 = segment_distance(p, c, a);
+    if (d2 < d) d = d2;
+    if (d3 < d) d = d3;
+    return d;
+}
+
+/* Unsigned distance from each listed node to the piecewise-linear height-field
+ * surface of reading R10, by brute force over every triangle of the surface.
+ * The periodic image of each triangle is the one whose centroid is nearest to
+ * the node (minimum image); that is the nearest image of every point of the
+ * triangle whenever the distance in question is below half the period minus a
+ * cell, which the caller ensures.
+ *   h      : heights [ny][nx]
+ *   nodes  : flat node indices (k*ny + j)*nx + i, or NULL for every node
+ *   is_w   : 1 for w-nodes (z = k dz), 0 for uv-nodes (z = (k + 1/2) dz) */
+void orc_heightfield_distance(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
+                              const double *h, int64_t count, const int64_t *nodes, int is_w, double *dist)
+{
+    const orc_grid G = make_grid(nx, ny, nz, lx, ly, lz);
+    const orc_grid *g = &G;
+    if (!nodes) count = nx * ny * nz;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < count; ++q) {
+        const int64_t idx = nodes ? nodes[q] : q;
+        const int64_t i = idx % nx, j = (idx / nx) % ny, k = idx / (nx * ny);
+        const double p[3] = {i * g->dx, j * g->dy, is_w ? k * g->dz : (k + 0.5) * g->dz};
+        double best = INFINITY;
+        for (int64_t cj = 0; cj < ny; ++cj)
+            for (int64_t ci = 0; ci < nx; ++ci) {
+                /* corners of cell (ci, cj) in unwrapped coordinates */
+                const double x0 = ci * g->dx, x1 = (ci + 1) * g->dx;
+                const double y0 = cj * g->dy, y1 = (cj + 1) * g->dy;
+                const double h00 = h[cj * nx + ci], h10 = h[cj * nx + wrap(ci + 1, nx)];
+                const double h01 = h[wrap(cj + 1, ny) * nx + ci];
+                const double h11 = h[wrap(cj + 1, ny) * nx + wrap(ci + 1, nx)];
+                const double A[3] = {x0, y0, h00}, B[3] = {x1, y0, h10};
+                const double C[3] = {x1, y1, h11}, D[3] = {x0, y1, h01};
+                /* the two triangles on either side of the diagonal A-C */
+                const double *tri[2][3] = {{A, B, C}, {A, C, D}};
+                for (int t = 0; t < 2; ++t) {
+                    const double cx = (tri[t][0][0] + tri[t][1][0] + tri[t][2][0]) / 3.0;
+                    const double cy = (tri[t][0][1] + tri[t][1][1] + tri[t][2][1]) / 3.0;
+                    /* shift the node by whole periods to its image nearest the centroid */
+                    const double sx = lx * round((p[0] - cx) / lx);
+                    const double sy = ly * round((p[1] - cy) / ly);
+                    const double pp[3] = {p[0] - sx, p[1] - sy, p[2]};
+                    const double d = triangle_distance(pp, tri[t][0], tri[t][1], tri[t][2]);
+                    if (d < best) best = d;
+                }
+            }
+        dist[q] = best;
+    }
 }
