@@ -65,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cubes",
-                    choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral", "sgs"])
+                    choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral", "sgs", "sdf"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--spectral-levels", type=int, default=None,
                     help="spectral workload: levels of the hill grid (default 256; smaller for profiler captures)")
@@ -226,6 +226,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "sdf":
+        return run_reference_sdf(args)
     case = make_case(args)
     per_step = []
     import oracle
@@ -261,6 +263,32 @@ def run_reference(args):
                                        f"{'SGS stress + ' if args.workload == 'sgs' else ''}wall stress + "
                                        f"{'spectral ' if args.workload == 'spectral' else ''}force over the "
                                        f"workload (FP64 CPU oracle)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_sdf(args):
+    """The oracle's brute-force height-field distance, as it stands, on one core:
+    each step a bounded sample of near-surface nodes of the same hill."""
+    grid, h, reach = sdf_case()
+    rates, total_nodes, total_el = [], 0, 0.0
+    for s in range(args.warmup + args.steps):
+        rate, done, el = sdf_oracle_sample(grid, h, reach, 1.0)
+        if s >= args.warmup:
+            rates.append(rate)
+            total_nodes += done
+            total_el += el
+    value = total_nodes / total_el / 1e9
+    nx, ny, nz = grid[:3]
+    line = {"metric": METRIC_SDF, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sdf: cosine-squared hill (Eq. 32) height field {nx}x{ny}, {nz} levels, "
+                                   f"both grids, reach {SDF_REACH_CELLS} dz"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{total_nodes} near-surface nodes over {args.steps} steps of about 1 s, "
+                                       f"brute force over all {2 * nx * ny} triangles each (FP64 CPU oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -1243,6 +1271,147 @@ def run_sgs(args):
     return 0
 
 
+METRIC_SDF = "height-field signed distance throughput (Gpts/s)"
+SDF_GRID = (512, 256, 256, 2 * np.pi, np.pi, 1.0)          # the 3-D hill grid (Eq. 32)
+SDF_REACH_CELLS = 4                                         # reach = 4 dz: every class threshold and phi_c lie below
+
+
+def sdf_case():
+    from paper_2006_03343_gb300 import inputs
+    grid = SDF_GRID
+    dz = grid[5] / (grid[2] - 1)
+    return grid, inputs.hill_height(grid), SDF_REACH_CELLS * dz
+
+
+def sdf_oracle_sample(grid, h, reach, seconds):
+    """The oracle's brute-force distance on near-surface nodes of the hill for about
+    `seconds` on one core: (nodes per second, nodes, elapsed)."""
+    import oracle
+    oracle.build()
+    threads = oracle.openmp_threads()
+    oracle.set_threads(1)
+    nx, ny, nz = grid[:3]
+    dz = grid[5] / (nz - 1)
+    k = np.arange(nz)
+    rng = np.random.default_rng(0)
+    done, el, batch = 0, 0.0, 4
+    while el < seconds:
+        cols = rng.integers(0, nx * ny, size=batch)
+        kk = np.clip(np.round(h.reshape(-1)[cols] / dz).astype(np.int64) + rng.integers(-3, 4, size=batch), 0, nz - 1)
+        nodes = kk * nx * ny + cols
+        t0 = time.perf_counter()
+        oracle.heightfield_sdf(grid, h, reach, nodes)
+        el += time.perf_counter() - t0
+        done += batch
+        batch = min(batch * 2, 64)
+    oracle.set_threads(threads)
+    return done / el, done, el
+
+
+def run_sdf(args):
+    """The exact signed distance to the 3-D hill's height field (Sec. 3.1, both
+    grids of 512 x 256 x 256, reach 4 dz): one wmibm_heightfield_sdf per step.
+    Units are grid nodes (each gets its uv- and its w-value)."""
+    import torch
+    from paper_2006_03343_gb300 import build, wmibm
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    grid, h, reach = sdf_case()
+    nx, ny, nz = grid[:3]
+    npts = nx * ny * nz
+    hd = torch.from_numpy(h).to(dev)
+    pu = torch.empty((nz, ny, nx), dtype=torch.float64, device=dev)
+    pw = torch.empty_like(pu)
+    call = lambda: wmibm.heightfield_sdf(grid, hd, reach, pu, pw)
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    flush = L2Flush(dev)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = timed_run(call, stream, flush, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    value, total_ms = aggregate_value(float(sum(ms)), args.steps, npts, world, dev)
+    kms = float(np.mean(ms))
+    kbytes = 2 * npts * 8 + nx * ny * 8              # both distance arrays written once, the heights read once
+    peak, peak_kind = measured_peak()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e and not args.profile:
+        host_h = torch.from_numpy(h.copy()).pin_memory()
+        host_out = [torch.empty((nz, ny, nx), dtype=torch.float64).pin_memory() for _ in range(2)]
+
+        def e2e_step():
+            hd.copy_(host_h, non_blocking=True)
+            call()
+            for dst, src in zip(host_out, (pu, pw)):
+                dst.copy_(src, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        steps = min(args.steps, 10)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * steps * npts / el / 1e9, "unit": UNIT, "steps": steps,
+               "h2d_bytes_per_step": int(h.size * 8), "d2h_bytes_per_step": int(2 * npts * 8)}
+
+    cpu = accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        import oracle
+        rate, done, el = sdf_oracle_sample(grid, h, reach, min(args.cpu_seconds, 12.0))
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} near-surface nodes (both grids) of the same hill, brute force over all "
+                         f"{2 * nx * ny} triangles each, on one core ({el:.1f} s)"}
+        rng = np.random.default_rng(1)
+        cols = rng.integers(0, nx * ny, size=200)
+        dz = grid[5] / (nz - 1)
+        kk = np.clip(np.round(h.reshape(-1)[cols] / dz).astype(np.int64) + rng.integers(-5, 6, size=200), 0, nz - 1)
+        nodes = np.unique(kk * nx * ny + cols)
+        ou, ow = oracle.heightfield_sdf(grid, h, reach, nodes)
+        gu, gw = (t.reshape(-1)[torch.from_numpy(nodes).to(dev)].cpu().numpy() for t in (pu, pw))
+        accuracy = {"max_abs_phi_uv": float(np.max(np.abs(gu - ou))), "max_abs_phi_w": float(np.max(np.abs(gw - ow))),
+                    "nodes": int(nodes.size)}
+
+    if rank == 0:
+        line = {"metric": METRIC_SDF, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"sdf: cosine-squared hill (Eq. 32) height field {nx}x{ny}, "
+                                       f"{nz} levels, both grids, reach {SDF_REACH_CELLS} dz",
+                           "l2": "outputs (537 MB) larger than L2, and L2 flushed between steps outside the events"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "k_heightfield_sdf",
+                             "kernel_ms": kms, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                             "algorithmic_bytes_per_launch": kbytes},
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "max_abs_error_vs_oracle": accuracy,
+                "gpu_launches": args.steps}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -1255,6 +1424,8 @@ def main(argv=None):
         return run_spectral(args)
     if args.workload == "sgs":
         return run_sgs(args)
+    if args.workload == "sdf":
+        return run_sdf(args)
     return run_ours(args)
 
 

@@ -196,6 +196,31 @@ int wmibm_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *w
                     const void *wt_w, const void *const tau[6], void *fx, void *fy, void *fz, double cs, void *stream);
 
 /*
+ * wmibm_heightfield_sdf - the signed distance phi of Sec. 3.1 (+d in the fluid,
+ * -d in the solid, d the minimum distance to the immersed boundary) for terrain
+ * given as heights, on both grids, ready for wmibm_init.  The boundary is the
+ * piecewise-linear surface through the heights: cell [i, i+1] x [j, j+1] is
+ * split along its (i, j)-(i+1, j+1) diagonal into two flat triangles, periodic
+ * in x and y.  The sign is that of z - h[j][i] (the node's column passes
+ * through a vertex).  Nodes within `reach` of the surface get the exact
+ * distance; all others keep z - h[j][i], whose magnitude exceeds the reach, so
+ * class thresholds below the reach (0, phi_b, 2 phi_b, phi_c) see exact values.
+ * No handle: it runs before wmibm_init, which takes phi on the host.
+ *   g              : grid (nx, ny >= 1, nz >= 3, nx*ny*nz < 2^31, lengths > 0)
+ *   height         : DEVICE, ny*nx finite doubles, h[j][i] at (i dx, j dy), read only
+ *   reach          : > 0; the window it spans may hold at most 1024 cells
+ *                    (4 ceil(reach/dx) ceil(reach/dy)) and 128 in each direction
+ *   phi_uv, phi_w  : DEVICE, nx*ny*nz doubles each, [k][j][i], written everywhere;
+ *                    uv-node (i, j, k) at z = (k + 1/2) dz, w-node at z = k dz
+ *   stream         : CUDA stream (NULL = legacy default)
+ * FP64 throughout; the work is queued on the stream (no synchronisation).
+ * Errors (wmibm_last_error(NULL) has the text): EINVAL (NULL pointer, bad grid,
+ * reach not finite or <= 0 or too wide, phi_uv == phi_w), ECUDA.
+ */
+int wmibm_heightfield_sdf(const wmibm_grid *g, const double *height, double reach, double *phi_uv, double *phi_w,
+                          void *stream);
+
+/*
  * wmibm_spectral_shape - the tile of wmibm_force_spectral's launch (host query):
  * out[0] rows per row unit, out[1] columns per column unit, out[2] z-levels per
  * chunk of the dispense order, out[3] shared-memory bytes per block.

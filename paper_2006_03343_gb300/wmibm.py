@@ -29,7 +29,8 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_device_status", "wmibm_force_mask", "wmibm_wall_stress_noalloc", "wmibm_batch_create",
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
-            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress", "wmibm_sgs_force")
+            "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress", "wmibm_sgs_force",
+            "wmibm_heightfield_sdf")
 
 
 class WmibmError(RuntimeError):
@@ -102,6 +103,8 @@ def load(path: Optional[str] = None):
     L.wmibm_sgs_stress.restype = ctypes.c_int
     L.wmibm_sgs_force.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, ctypes.c_double, _VP]
     L.wmibm_sgs_force.restype = ctypes.c_int
+    L.wmibm_heightfield_sdf.argtypes = [ctypes.POINTER(Grid), _VP, ctypes.c_double, _VP, _VP, _VP]
+    L.wmibm_heightfield_sdf.restype = ctypes.c_int
     L.wmibm_mask.argtypes = [_VP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP]
     L.wmibm_mask.restype = ctypes.c_int
     L.wmibm_step.argtypes = [_VP, _VP, _VP, _VP, _PVP, _VP, _VP, _VP, _PVP, ctypes.c_double, _VP, _VP]
@@ -174,6 +177,32 @@ def _stream_ptr(stream) -> Optional[int]:
     if stream is None:
         stream = torch.cuda.current_stream()
     return int(stream.cuda_stream) or None
+
+
+def heightfield_sdf(grid, height, reach, phi_uv=None, phi_w=None, stream=None):
+    """wmibm_heightfield_sdf: the exact signed distance (Sec. 3.1) to the piecewise-
+    linear surface through the heights `height` (a CUDA float64 tensor [ny, nx]),
+    within `reach`; z - h beyond it.  Returns (phi_uv, phi_w), CUDA float64
+    tensors [nz, ny, nx] (allocated unless given)."""
+    import torch
+    L = load()
+    nx, ny, nz, lx, ly, lz = grid
+    if not (isinstance(height, torch.Tensor) and height.is_cuda and height.dtype == torch.float64
+            and height.is_contiguous() and tuple(height.shape) == (ny, nx)):
+        raise ValueError("height must be a contiguous CUDA float64 tensor of shape (ny, nx)")
+    out = []
+    for t in (phi_uv, phi_w):
+        if t is None:
+            t = torch.empty((nz, ny, nx), dtype=torch.float64, device=height.device)
+        elif not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == nx * ny * nz):
+            raise ValueError("phi_uv, phi_w must be contiguous CUDA float64 tensors of nx*ny*nz elements")
+        out.append(t)
+    g = Grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz))
+    st = L.wmibm_heightfield_sdf(ctypes.byref(g), _dptr(height), float(reach), _dptr(out[0]), _dptr(out[1]),
+                                 _stream_ptr(stream))
+    if st != OK:
+        raise WmibmError(st, L.wmibm_last_error(None).decode())
+    return out[0], out[1]
 
 
 class Handle:
