@@ -43,3 +43,19 @@ def test_reference_arm_sgs_workload(monkeypatch, capsys):
     assert d["value"] > 0 and d["cpu_baseline"]["cores"] == 1
     assert "SGS stress" in d["cpu_baseline"]["sample"]
     assert d["config"]["nodes"] == 256 * 128 * 128
+
+
+def test_reference_arm_sdf_workload(monkeypatch, capsys):
+    """The reference arm of the height-field distance: the oracle's brute force on
+    near-surface nodes of the hill, under the GPU arm's metric, on one core."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main(["--impl", "reference", "--workload", "sdf", "--steps", "1", "--warmup", "0"]) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC_SDF
+    assert d["value"] > 0 and d["cpu_baseline"]["cores"] == 1 and d["dtype"] == "f64"
+    assert d["e2e"]["value"] == d["value"]
