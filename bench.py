@@ -1253,7 +1253,7 @@ def run_sgs(args):
                                         "Smagorinsky C_s = 0.16 with Mason's damping beside a1 (two streams), then a2"),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None,
-                             "kernel": "k_sgs (column march, one thread per (i, j))", "kernel_ms": kms,
+                             "kernel": "k_sgs2 (column march, two x-neighbouring columns per thread; k_sgs, one column per thread, for FP64, odd nx or unaligned fields)", "kernel_ms": kms,
                              "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                              "algorithmic_bytes_per_launch": kbytes},
                 "parts_ms": {"sgs_alone": kms, "a1_a2_alone": float(np.mean(parts["a12"])),

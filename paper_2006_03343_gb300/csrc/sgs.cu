@@ -372,6 +372,186 @@ int launch_sgs_force(wmibm_handle *h, const void *u, const void *v, const void *
     return cuda_status(h, cudaGetLastError(), "k_sgs_force launch");
 }
 
+// ---------------------------------------------------------------------------
+// The same march with two x-neighbouring columns per thread (FP32, nx even,
+// every array aligned to two elements): the pair's centre values and its
+// y-neighbours arrive as one two-element load, and the centre of each column is
+// the other's x-neighbour, so a level takes 15 loads for two columns instead of
+// 30, and the wall terms and the stresses move in pairs where both nodes are
+// fluid.  No software pipelining here: the registers it needs would cost the
+// fourth block per SM, which is worth more (measured).
+template <typename T, typename V>
+__device__ __forceinline__ void load2(const V *p, int64_t q, T &a, T &b)
+{
+    if constexpr (sizeof(V) == 8) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p + q));
+        a = (T)t.x;
+        b = (T)t.y;
+    } else if constexpr (sizeof(V) == 4) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p + q));
+        a = (T)t.x;
+        b = (T)t.y;
+    } else {
+        const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + q));
+        a = (T)t.x;
+        b = (T)t.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store2(T *p, int64_t q, T a, T b)
+{
+    if constexpr (sizeof(T) == 8)
+        *reinterpret_cast<double2 *>(p + q) = make_double2(a, b);
+    else
+        *reinterpret_cast<float2 *>(p + q) = make_float2(a, b);
+}
+
+// Raw values of level L for the column pair (i0, i0 + 1): centres, the x-neighbours
+// outside the pair (left of i0, right of i0 + 1), the y-neighbour pairs, and w above.
+template <typename T>
+struct Raw2 {
+    T uc[2], vc[2], wup[2];
+    T u_l, u_r, v_l, v_r, w_l, w_r;
+    T u_jp[2], u_jm[2], v_jp[2], v_jm[2], w_jp[2], w_jm[2];
+};
+
+template <typename T, typename V>
+struct Pair {
+    const V *u, *v, *w;
+    int64_t plane;
+    int32_t nx, nz;
+    int i0, il, ir, j, jm, jp;
+
+    __device__ __forceinline__ Raw2<T> load(int L) const
+    {
+        Raw2<T> r;
+        if (L <= nz - 2) {
+            const int64_t base = (int64_t)L * plane;
+            const int64_t row = base + (int64_t)j * nx, rp = base + (int64_t)jp * nx, rm = base + (int64_t)jm * nx;
+            load2<T, V>(u, row + i0, r.uc[0], r.uc[1]);
+            r.u_l = load_vel<V, T>(u, row + il);
+            r.u_r = load_vel<V, T>(u, row + ir);
+            load2<T, V>(u, rp + i0, r.u_jp[0], r.u_jp[1]);
+            load2<T, V>(u, rm + i0, r.u_jm[0], r.u_jm[1]);
+            load2<T, V>(v, row + i0, r.vc[0], r.vc[1]);
+            r.v_l = load_vel<V, T>(v, row + il);
+            r.v_r = load_vel<V, T>(v, row + ir);
+            load2<T, V>(v, rp + i0, r.v_jp[0], r.v_jp[1]);
+            load2<T, V>(v, rm + i0, r.v_jm[0], r.v_jm[1]);
+            load2<T, V>(w, row + plane + i0, r.wup[0], r.wup[1]);
+            r.w_l = load_vel<V, T>(w, row + il);
+            r.w_r = load_vel<V, T>(w, row + ir);
+            load2<T, V>(w, rp + i0, r.w_jp[0], r.w_jp[1]);
+            load2<T, V>(w, rm + i0, r.w_jm[0], r.w_jm[1]);
+        } else {
+            r = Raw2<T>{};
+        }
+        return r;
+    }
+};
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256, 4) k_sgs2(SgsParams<T, V> p, int kc)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i0 = 2 * t;
+    if (i0 >= p.nx || j >= p.ny) return;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(k0 + kc, p.nz);
+    const int64_t plane = (int64_t)p.nx * p.ny;
+    const int il = i0 == 0 ? p.nx - 1 : i0 - 1, ir = i0 + 2 == p.nx ? 0 : i0 + 2;
+    const int jm = j == 0 ? p.ny - 1 : j - 1, jp = j + 1 == p.ny ? 0 : j + 1;
+    const Pair<T, V> P{p.u, p.v, p.w, plane, p.nx, p.nz, i0, il, ir, j, jm, jp};
+    // the two columns' set-up levels, formed as the one-column march does
+    Column<T, V> c[2];
+    for (int q = 0; q < 2; ++q) {
+        c[q].U = Field<T, V>{p.u, p.nx, p.ny, plane};
+        c[q].Vf = Field<T, V>{p.v, p.nx, p.ny, plane};
+        c[q].W = Field<T, V>{p.w, p.nx, p.ny, plane};
+        c[q].i = i0 + q;
+        c[q].j = j;
+        c[q].im = q == 0 ? il : i0;
+        c[q].ip = q == 0 ? i0 + 1 : ir;
+        c[q].jm = jm;
+        c[q].jp = jp;
+        c[q].nz = p.nz; c[q].cx = p.cx; c[q].cy = p.cy; c[q].rdz = p.rdz;
+    }
+    Uv<T> a_prev[2], a_cur[2];
+    Ws<T> b_cur[2];
+    T u_c[2], v_c[2], w_c[2];
+    for (int q = 0; q < 2; ++q) {
+        a_prev[q] = k0 >= 1 ? c[q].uv(k0 - 1) : Uv<T>{0, 0, 0, 0};
+        a_cur[q] = k0 <= p.nz - 2 ? c[q].uv(k0) : Uv<T>{0, 0, 0, 0};
+        b_cur[q] = c[q].ws(k0);
+        u_c[q] = k0 <= p.nz - 2 ? c[q].U.at(i0 + q, j, k0) : T(0);
+        v_c[q] = k0 <= p.nz - 2 ? c[q].Vf.at(i0 + q, j, k0) : T(0);
+        w_c[q] = k0 <= p.nz - 2 ? c[q].W.at(i0 + q, j, k0 + 1) : T(0);
+    }
+    int64_t o = (int64_t)k0 * plane + (int64_t)j * p.nx + i0;
+    for (int k = k0; k < k1; ++k, o += plane) {
+        const Raw2<T> raw = P.load(k + 1);
+        T wt_uv[2] = {T(-1), T(-1)}, wt_w[2] = {T(-1), T(-1)};
+        if (k <= p.nz - 2) load2<T, T>(p.wt_uv, o, wt_uv[0], wt_uv[1]);
+        if (k >= 1) load2<T, T>(p.wt_w, o, wt_w[0], wt_w[1]);
+        const int L = k + 1;
+        Uv<T> a_next[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        Ws<T> b_next[2] = {{0, 0}, {0, 0}};
+        if (L <= p.nz - 2) {
+            for (int q = 0; q < 2; ++q) {
+                const T u_ip = q == 0 ? raw.uc[1] : raw.u_r, u_im = q == 0 ? raw.u_l : raw.uc[0];
+                const T v_ip = q == 0 ? raw.vc[1] : raw.v_r, v_im = q == 0 ? raw.v_l : raw.vc[0];
+                const T w_ip = q == 0 ? w_c[1] : raw.w_r, w_im = q == 0 ? raw.w_l : w_c[0];
+                a_next[q].s11 = (u_ip - u_im) * p.cx;
+                a_next[q].s22 = (raw.v_jp[q] - raw.v_jm[q]) * p.cy;
+                a_next[q].s12 = T(0.5) * ((raw.u_jp[q] - raw.u_jm[q]) * p.cy + (v_ip - v_im) * p.cx);
+                a_next[q].s33 = (raw.wup[q] - w_c[q]) * p.rdz;
+                b_next[q].s13 = T(0.5) * ((raw.uc[q] - u_c[q]) * p.rdz + (w_ip - w_im) * p.cx);
+                b_next[q].s23 = T(0.5) * ((raw.vc[q] - v_c[q]) * p.rdz + (raw.w_jp[q] - raw.w_jm[q]) * p.cy);
+            }
+        }
+        T tu[2][4], tw[2][2];
+        for (int q = 0; q < 2; ++q) {
+            if (wt_uv[q] >= T(0)) uv_stress(a_cur[q], b_cur[q], b_next[q], wt_uv[q], p.inv_lam0_sq, tu[q]);
+            tw[q][0] = tw[q][1] = T(0);                             // the lid: no stress (Eq. 10)
+            if (wt_w[q] >= T(0) && k < p.nz - 1) w_stress(a_prev[q], a_cur[q], b_cur[q], wt_w[q], p.inv_lam0_sq, tw[q]);
+        }
+        if (wt_uv[0] >= T(0) && wt_uv[1] >= T(0)) {                 // uv-nodes (i0, j, k), (i0 + 1, j, k)
+            store2(p.txx, o, tu[0][0], tu[1][0]);
+            store2(p.tyy, o, tu[0][1], tu[1][1]);
+            store2(p.tzz, o, tu[0][2], tu[1][2]);
+            store2(p.txy, o, tu[0][3], tu[1][3]);
+        } else {
+            for (int q = 0; q < 2; ++q)
+                if (wt_uv[q] >= T(0)) {
+                    p.txx[o + q] = tu[q][0];
+                    p.tyy[o + q] = tu[q][1];
+                    p.tzz[o + q] = tu[q][2];
+                    p.txy[o + q] = tu[q][3];
+                }
+        }
+        if (wt_w[0] >= T(0) && wt_w[1] >= T(0)) {                   // w-nodes; the floor is left
+            store2(p.txz, o, tw[0][0], tw[1][0]);
+            store2(p.tyz, o, tw[0][1], tw[1][1]);
+        } else {
+            for (int q = 0; q < 2; ++q)
+                if (wt_w[q] >= T(0)) {
+                    p.txz[o + q] = tw[q][0];
+                    p.tyz[o + q] = tw[q][1];
+                }
+        }
+        for (int q = 0; q < 2; ++q) {
+            a_prev[q] = a_cur[q];
+            a_cur[q] = a_next[q];
+            b_cur[q] = b_next[q];
+            u_c[q] = raw.uc[q];
+            v_c[q] = raw.vc[q];
+            w_c[q] = raw.wup[q];
+        }
+    }
+}
+
 template <typename T, typename V>
 int launch_sgs(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv, const void *wt_w,
                void *const tau[6], double cs, cudaStream_t stream)
@@ -387,9 +567,28 @@ int launch_sgs(wmibm_handle *h, const void *u, const void *v, const void *w, con
     p.rdz = (T)(1.0 / h->dz);
     const double lam0 = cs * cbrt(h->dx * h->dy * h->dz);
     p.inv_lam0_sq = (T)(1.0 / (lam0 * lam0));
+    const int kc = 8;                       // levels per thread
+    // FP32 only: in FP64 the pair kernel's registers cost more than its loads save (measured)
+    if constexpr (sizeof(T) == 4) {
+        const size_t es = sizeof(T), vs = sizeof(V);
+        bool pairs = h->nx % 2 == 0;
+        for (const void *q : {u, v, w})
+            pairs = pairs && ((uintptr_t)q % (2 * vs)) == 0;
+        for (const void *q : {wt_uv, wt_w, (const void *)tau[0], (const void *)tau[1], (const void *)tau[2],
+                              (const void *)tau[3], (const void *)tau[4], (const void *)tau[5]})
+            pairs = pairs && ((uintptr_t)q % (2 * es)) == 0;
+        if (pairs) {
+            const int half = h->nx / 2;
+            dim3 block(32, 8, 1);
+            dim3 grid((half + 31) / 32, (h->ny + 7) / 8, (h->nz + kc - 1) / kc);
+            if (grid.y > 65535 || grid.z > 65535)
+                return set_error(h, WMIBM_EINVAL, "grid too large for the SGS launch");
+            k_sgs2<T, V><<<grid, block, 0, stream>>>(p, kc);
+            return cuda_status(h, cudaGetLastError(), "k_sgs2 launch");
+        }
+    }
     const int bx = h->nx >= 64 ? 64 : 32;
     const int by = 256 / bx;
-    const int kc = 8;                       // levels per thread
     dim3 block(bx, by, 1);
     dim3 grid((h->nx + bx - 1) / bx, (h->ny + by - 1) / by, (h->nz + kc - 1) / kc);
     if (grid.y > 65535 || grid.z > 65535) return set_error(h, WMIBM_EINVAL, "grid too large for the SGS launch");

@@ -56,8 +56,10 @@ def _check(tau_gpu, tau_ref, dtype):
         assert err <= TOL[dtype], (k, err)
 
 
+# FP32 with even nx runs the two-columns-per-thread kernel, odd nx (and FP64) the one-column march
 CASES = [("ridge", (32, 32, 32), "f64"), ("ridge", (32, 32, 32), "f32"), ("cubes", (96, 48, 40), "f32"),
-         ("cubes", (46, 18, 21), "f64"), ("hill", (64, 32, 24), "f32"), ("hill", (64, 32, 24), "f64")]
+         ("cubes", (46, 18, 21), "f64"), ("hill", (64, 32, 24), "f32"), ("hill", (64, 32, 24), "f64"),
+         ("hill", (63, 20, 17), "f32"), ("ridge", (2, 6, 9), "f32")]
 
 
 @pytest.mark.parametrize("name,shape,dtype", CASES)
@@ -66,6 +68,27 @@ def test_sgs_matches_oracle(wm, oracle_mod, name, shape, dtype):
     h, _, _, tau = _gpu_sgs(wm, case, dtype)
     _check(tau, _oracle_sgs(oracle_mod, case, dtype), dtype)
     assert h.device_status() == wm.OK
+
+
+def test_sgs_unaligned_fields_take_the_one_column_march(wm, oracle_mod):
+    """Fields offset by one element from an aligned allocation (nx even, FP32): the
+    pair loads would be misaligned, so the one-column march runs; same result."""
+    case = inputs.hill(shape=(64, 32, 24), dtype="f32")
+    h = wm.Handle.from_case(case, dtype="f32")
+    wt = h.sgs_wall_terms(case.phi_uv, case.phi_w, case.z0)
+
+    def shifted(a):
+        t = to_dev(a, "f32")
+        buf = torch.empty(t.numel() + 1, dtype=t.dtype, device=t.device)
+        view = buf[1:].view(t.shape)
+        view.copy_(t)
+        return view
+
+    u, v, w = (shifted(x) for x in (case.u, case.v, case.w))
+    tau = [shifted(case.tau[k]) for k in inputs.TAU_NAMES]
+    h.sgs_stress(u, v, w, wt, tau, cs=CS)
+    torch.cuda.synchronize()
+    _check(tau, _oracle_sgs(oracle_mod, case, "f32"), "f32")
 
 
 def test_sgs_bf16_velocity(wm, oracle_mod):
