@@ -379,6 +379,53 @@ class NoFlush:
         pass
 
 
+def pipelined_run(dev, steps, copy_in_parts, compute, copy_out, world=1):
+    """Wall-clock seconds of `steps` end-to-end steps over two buffer sets b = s % 2:
+    each copy_in_parts[q](b) on its own host-to-device stream (several streams keep
+    several copies in flight on the host link), compute(b) on a compute stream,
+    copy_out(b) on a device-to-host stream.  Events order every reuse of a set: its
+    inputs are overwritten only after the step two back computed on them, and its
+    results only after they were copied out.  Every step's copies and call are inside
+    the timed region; all streams are drained before the clock stops."""
+    import torch
+    s_in = [torch.cuda.Stream(device=dev) for _ in copy_in_parts]
+    s_cmp, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_in = [[torch.cuda.Event() for _ in copy_in_parts] for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def one(s):
+        b = s % 2
+        for q, (st, part) in enumerate(zip(s_in, copy_in_parts)):
+            with torch.cuda.stream(st):
+                if s >= 2:
+                    st.wait_event(ev_cmp[b])
+                part(b)
+                ev_in[b][q].record(st)
+        with torch.cuda.stream(s_cmp):
+            for ev in ev_in[b]:
+                s_cmp.wait_event(ev)
+            if s >= 2:
+                s_cmp.wait_event(ev_out[b])
+            compute(b)
+            ev_cmp[b].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_cmp[b])
+            copy_out(b)
+            ev_out[b].record(s_out)
+
+    for s in range(2):
+        one(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        one(s)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
 def timed_run(fn, stream, flush, steps):
     """CUDA-event times (ms) of `steps` calls of fn on `stream`, the L2 flushed
     before each call outside the events."""
@@ -531,13 +578,45 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el_serial = time.perf_counter() - t0
+
+        # the same per-step copies and call, double-buffered over three streams
+        sets = [(form.u, form.v, form.w, form.tau, form.f, form.stats),
+                (torch.empty_like(form.u), torch.empty_like(form.v), torch.empty_like(form.w),
+                 [torch.empty_like(t) for t in form.tau], [torch.empty_like(t) for t in form.f],
+                 torch.zeros_like(form.stats))]
+        host_out = [(host_f, host_stats),
+                    ([torch.empty_like(t).pin_memory() for t in host_f], torch.empty_like(host_stats).pin_memory())]
+
+        def copy_in_part(q, n):
+            # part q of n of the nine input arrays (u, v, w, then the six stresses)
+            def part(b):
+                u_, v_, w_, tau_, _, _ = sets[b]
+                pairs = list(zip((u_, v_, w_), host_in)) + list(zip(tau_, host_tau))
+                for d, s_ in pairs[q::n]:
+                    d.copy_(s_, non_blocking=True)
+            return part
+
+        def compute(b):
+            u_, v_, w_, tau_, f_, st_ = sets[b]
+            h.wall_stress_force(u_, v_, w_, tau_, f_, st_)
+
+        def copy_out(b):
+            for d, s_ in zip(host_out[b][0], sets[b][4]):
+                d.copy_(s_, non_blocking=True)
+            host_out[b][1].copy_(sets[b][5], non_blocking=True)
+
+        # one input stream: the host link is as busy with one as with three (measured: 5.15 and 5.09 Gpts/s)
+        el = pipelined_run(dev, args.steps, [copy_in_part(0, 1)], compute, copy_out, world)
         if world > 1:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            t = torch.tensor([el, el_serial], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+            el, el_serial = (float(x) for x in t.tolist())
         e2e = {"value": world * args.steps * case.npoints / el / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "form": "double-buffered: step s's inputs copied in on one stream while step s-1 computes on a "
+                       "second and step s-2's forcing and stats come back on a third",
+               "serial_value": world * args.steps * case.npoints / el_serial / 1e9}
 
     cpu = None
     accuracy = None
