@@ -173,6 +173,9 @@ int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const double *ph
  *   wt_uv, wt_w   : DEVICE wall terms from wmibm_sgs_wall_terms
  *   tau           : 6 DEVICE stress fields (dtype), written at fluid nodes
  *   cs            : the Smagorinsky coefficient C_s (the paper uses 0.16), > 0
+ * Neither this call nor wmibm_wall_stress reads tau, and the entries they write
+ * are disjoint (fluid here; band and solid there), so the two may run at the
+ * same time on two streams of the handle's device, with wmibm_force after both.
  * Errors: EINVAL, ESTATE, ECUDA.
  */
 int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
