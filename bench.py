@@ -64,8 +64,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cubes",
+    ap.add_argument("--workload", default="ensemble",
                     choices=["cubes", "hill", "ridge", "ensemble", "adjoint", "spectral", "sgs", "sdf"])
+    ap.add_argument("--members", type=int, default=64,
+                    help="ensemble workload: members (default 64; fewer for profiler captures)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--spectral-levels", type=int, default=None,
                     help="spectral workload: levels of the hill grid (default 256; smaller for profiler captures)")
@@ -114,6 +116,24 @@ def profiled_traffic(kernel, workload, dtype, vel_dtype):
     if not m_hash or not m_bytes or m_hash.group(1) != digest:
         return None
     return float(m_bytes.group(1))
+
+
+def profiled_batch_traffic(form, dtype, points):
+    """DRAM bytes of one batch step scaled to `points` nodes from the committed ncu
+    summary of that form (taken on fewer members: the bytes per node carry over,
+    the members being drawn the same way), if it was taken on the current kernel
+    sources (else None)."""
+    name = "batch_interleaved" if form == 5 else "batch_two_launch"
+    path = os.path.join(ROOT, "profiles", f"{name}_ensemble_{dtype}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_node:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_digest():
+        return None
+    return float(m_bytes.group(1)) * points
 
 
 class ClockSampler:
@@ -228,6 +248,8 @@ def run_reference(args):
         return 0
     if args.workload == "sdf":
         return run_reference_sdf(args)
+    if args.workload == "ensemble":
+        return run_reference_ensemble(args)
     case = make_case(args)
     per_step = []
     import oracle
@@ -263,6 +285,43 @@ def run_reference(args):
                                        f"{'SGS stress + ' if args.workload == 'sgs' else ''}wall stress + "
                                        f"{'spectral ' if args.workload == 'spectral' else ''}force over the "
                                        f"workload (FP64 CPU oracle)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_ensemble(args):
+    """The oracle as it stands on the host cores over the batched ensemble: each
+    step is wall stress + force of every member (FP64), the GPU arm's step."""
+    import oracle
+    from paper_2006_03343_gb300 import inputs
+    oracle.build()
+    cases = inputs.ensemble(args.members, dtype=args.dtype)
+    points = sum(c.npoints for c in cases)
+    per_step = []
+    work = [({k: c.tau[k].copy() for k in inputs.TAU_NAMES}, c.u.copy(), c.v.copy(), c.w.copy()) for c in cases]
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for c, (tau, u, v, w) in zip(cases, work):
+            oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, u, v, w, tau)
+            oracle.force(c.grid, tau)
+        if s >= args.warmup:
+            per_step.append(time.perf_counter() - t0)
+    total = sum(per_step)
+    value = args.steps * points / total / 1e9
+    shapes = sorted({c.grid[:3] for c in cases})
+    threads = oracle.openmp_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"ensemble of {len(cases)} random Gaussian-hill terrains, grids {shapes}, "
+                                   f"batched FP32 (one step = wall stress + force of every member)"
+                                   if args.dtype == "f32" else
+                                   f"ensemble of {len(cases)} random Gaussian-hill terrains, grids {shapes}",
+                       "nodes": points, "members": len(cases), "l2": L2_NOTE},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} full passes of wall stress + force over all {len(cases)} "
+                                       f"members (FP64 CPU oracle)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -320,6 +379,27 @@ class GpuForm:
 
         self.call = self.h.prepare_step(self.u, self.v, self.w, self.tau, self.f, self.stats)
         self.graphs = None
+        self.case = case
+
+    def reset_inputs(self):
+        """The velocity and stresses back to the workload's values (the mask and the
+        wall model change them in place)."""
+        import torch
+        from paper_2006_03343_gb300 import inputs
+        for d, a in zip((self.u, self.v, self.w), (self.case.u, self.case.v, self.case.w)):
+            d.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(d.dtype))
+        for d, k in zip(self.tau, inputs.TAU_NAMES):
+            d.copy_(torch.from_numpy(np.ascontiguousarray(self.case.tau[k])).to(d.dtype))
+        for t in self.f:
+            t.fill_(float("nan"))
+        torch.cuda.synchronize()
+
+    def timed_form_result(self):
+        """One pass of exactly what is timed (the captured graph of the tuned shape,
+        or the prepared call) on the workload's inputs, the forcing NaN before it."""
+        self.reset_inputs()
+        self.step()
+        return self.host_result()
 
     def step(self, stream=None, evs=None):
         """One pass of the timed stage, wall stress + force (a1 + a2), through the C
@@ -468,10 +548,6 @@ def run_ours(args):
     h = form.h
     flush = L2Flush(dev)
 
-    # one pass on the pristine inputs, kept for the accuracy report
-    form.step()
-    first_tau, first_f = form.host_result()
-
     tuned = None
     if args.tuning:
         fields = {"force_path": 1}
@@ -509,6 +585,8 @@ def run_ours(args):
     parts = form.parts(stream, flush, args.steps)
     warm_ms = timed_run(form.step, stream, NoFlush(), args.steps)     # L2 not flushed between steps
     status = h.device_status()
+    # the accuracy pass: the timed graph (tuned shape) on the workload's inputs
+    first_tau, first_f = form.timed_form_result()
 
     value, total_ms = aggregate_value(float(sum(step_ms)), args.steps, case.npoints, world, dev)
 
@@ -530,8 +608,6 @@ def run_ours(args):
     f64_form = None
     if args.dtype == "f32" and not args.profile:
         g64 = GpuForm(case, "f64", None, dev)
-        g64.step()
-        first64 = g64.host_result()
         if not args.no_tune:
             from paper_2006_03343_gb300 import autotune
             autotune.tune(g64.h, (g64.u, g64.v, g64.w, g64.tau, g64.f, g64.stats))
@@ -540,6 +616,7 @@ def run_ours(args):
             g64.step()
         g64.capture()
         s64 = g64.timed(stream, flush, args.steps)
+        first64 = g64.timed_form_result()
         b64 = g64.h.traffic_bytes(4)
         f64_form = {"value": args.steps * case.npoints / (sum(s64) * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": float(np.mean(s64)), "step_gbs": b64 / (float(np.mean(s64)) * 1e-3) / 1e9,
@@ -622,6 +699,7 @@ def run_ours(args):
     accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
         gpts, passes, threads, el, ref = oracle_time(case, args.cpu_seconds)
+        ref_rounded = oracle_reference(case, args.dtype, args.vel_dtype) if args.dtype == "f32" else ref
         cpu = {"value": gpts, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{passes} full passes of wall stress + force over the workload ({el:.1f} s, FP64 CPU oracle)"}
         # the same oracle on one core (a shorter sample)
@@ -631,7 +709,12 @@ def run_ours(args):
         oracle.set_threads(threads)
         cpu["single_thread"] = {"value": g1, "unit": UNIT, "cores": 1,
                                 "sample": f"{p1} full passes ({e1:.1f} s)"}
-        accuracy = accuracy_report(first_tau, first_f, ref)
+        accuracy = accuracy_report(first_tau, first_f, ref_rounded)
+        accuracy["reference"] = ("oracle on the same FP32-rounded velocity and stresses" if args.dtype == "f32"
+                                 else "oracle on the same inputs")
+        accuracy["what"] = "the timed form: one replay of the captured graph of the tuned shape"
+        if args.dtype == "f32":
+            accuracy["vs_unrounded_inputs"] = accuracy_report(first_tau, first_f, ref)
         if f64_form is not None:
             f64_form["accuracy"] = accuracy_report(*f64_form.pop("first_pass"), ref)
     if f64_form is not None:
@@ -671,16 +754,33 @@ def run_ours(args):
     return 0
 
 
+def oracle_reference(case, dtype, vel_dtype):
+    """The oracle's wall stress + force on the velocity and stresses rounded to the
+    GPU form's storage types (what the GPU actually reads)."""
+    import torch
+    import oracle
+    from paper_2006_03343_gb300 import inputs
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    vdt = torch.bfloat16 if vel_dtype == "bf16" else tdt
+    rd = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).double().numpy()
+    tau = {k: rd(case.tau[k], tdt) for k in inputs.TAU_NAMES}
+    oracle.wall_stress(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b, rd(case.u, vdt),
+                       rd(case.v, vdt), rd(case.w, vdt), tau)
+    return tau, oracle.force(case.grid, tau)
+
+
 def accuracy_report(gpu_tau, gpu_f, ref):
-    """Normwise max and RMS error of the first GPU pass against the oracle's first pass."""
+    """Normwise max and relative RMS error of a GPU pass against the oracle's pass."""
     from paper_2006_03343_gb300 import inputs
     tau_o, f_o = ref
     out = {}
-    worst_tau = 0.0
+    worst_tau, worst_rms = 0.0, 0.0
     for k, g in zip(inputs.TAU_NAMES, gpu_tau):
         r = tau_o[k]
         worst_tau = max(worst_tau, float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300)))
+        worst_rms = max(worst_rms, float(np.sqrt(np.mean((g - r) ** 2)) / max(np.sqrt(np.mean(r ** 2)), 1e-300)))
     out["tau_normwise_max"] = worst_tau
+    out["tau_relative_rms"] = worst_rms
     errs, rms = [], []
     for g, r in zip(gpu_f, f_o):
         errs.append(float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-300)))
@@ -690,43 +790,85 @@ def accuracy_report(gpu_tau, gpu_f, ref):
     return out
 
 
+ENSEMBLE_FORMS = {3: "two launches: the batch wall kernel, then the batch stencil",
+                  5: "one cooperative launch: the batch stencil with every member's band records as interleaved "
+                     "wall stages"}
+
+
+def parse_tuning(text):
+    """--tuning "rows=2,stages=4,..." -> dict of ints."""
+    return {k: int(v) for k, v in (kv.split("=") for kv in text.split(",") if kv)}
+
+
+def ensemble_errors(gpu_tau, gpu_f, ref_tau, ref_f):
+    """Normwise max and relative RMS errors of one member's six stresses and three
+    forcing components against the oracle's."""
+    from paper_2006_03343_gb300 import inputs
+    out = {"tau_max": 0.0, "tau_rms": 0.0, "f_max": 0.0, "f_rms": 0.0}
+    for k, g in zip(inputs.TAU_NAMES, gpu_tau):
+        r = ref_tau[k]
+        den = max(float(np.max(np.abs(r))), 1e-300)
+        out["tau_max"] = max(out["tau_max"], float(np.max(np.abs(g - r))) / den)
+        out["tau_rms"] = max(out["tau_rms"], float(np.sqrt(np.mean((g - r) ** 2)) /
+                                                   max(float(np.sqrt(np.mean(r ** 2))), 1e-300)))
+    for g, r in zip(gpu_f, ref_f):
+        den = max(float(np.max(np.abs(r))), 1e-300)
+        out["f_max"] = max(out["f_max"], float(np.max(np.abs(g - r))) / den)
+        out["f_rms"] = max(out["f_rms"], float(np.sqrt(np.mean((g - r) ** 2)) /
+                                               max(float(np.sqrt(np.mean(r ** 2))), 1e-300)))
+    return out
+
+
+def worst_errors(per_member):
+    keys = ("tau_max", "tau_rms", "f_max", "f_rms")
+    return {k: max(e[k] for e in per_member) for k in keys}
+
+
 def run_ensemble(args):
-    """The 64-member batched ensemble (grids 64^3 .. 256x128x64): one batch step
-    of wall stress + force (the batch wall kernel, then the batch force kernel),
-    captured once in a CUDA graph and replayed; compared with the members stepped
-    one by one."""
+    """The batched ensemble (default: 64 members of random Gaussian-hill terrain on
+    grids 64^3 .. 256x128x64, 68.7 M nodes): one step is wall stress + force of
+    every member (wmibm_batch_wall_stress_force), in the form and tile shape the
+    autotuner picked, captured once in a CUDA graph and replayed.  Beside it: the
+    plain FP64 batch, the same members one by one, every member's errors against
+    the oracle (tau and f, max and RMS), the end-to-end rate through the batch API
+    with host buffers, and the oracle itself on the host cores."""
     import torch
-    from paper_2006_03343_gb300 import build, inputs, wmibm
+    from paper_2006_03343_gb300 import autotune, build, inputs, wmibm
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    cases = inputs.ensemble(64, dtype=args.dtype)
+    cases = inputs.ensemble(args.members, dtype=args.dtype)
     handles = [wmibm.Handle.from_case(c, dtype=args.dtype) for c in cases]
     tdt = torch.float64 if args.dtype == "f64" else torch.float32
 
-    def fields_of(c):
-        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=tdt)
+    def fields_of(c, dt):
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
         return (d(c.u), d(c.v), d(c.w), [d(c.tau[k]) for k in inputs.TAU_NAMES],
-                [torch.empty(c.shape, dtype=tdt, device=dev) for _ in range(3)])
+                [torch.empty(c.shape, dtype=dt, device=dev) for _ in range(3)])
 
-    fields = [fields_of(c) for c in cases]
+    fields = [fields_of(c, tdt) for c in cases]
     batch = wmibm.Batch(handles)
     batch.set_fields(fields)
     stats = batch.new_stats()
     flush = L2Flush(dev)
+    if args.tuning:
+        batch.set_tuning(**parse_tuning(args.tuning))
+        tuned = {"tuning": batch.get_tuning(), "explicit": True}
+    elif args.no_tune:
+        tuned = {"tuning": {}, "default": True}
+    else:
+        tuned = autotune.tune_batch(batch, stats)
+    form = batch.get_tuning().get("force_path", 0)
+    form = 3 if form == 3 else 5
     for _ in range(max(args.warmup, 3)):
+        flush.zero_()
         batch.wall_stress_force(stats)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         batch.wall_stress_force(stats)
     torch.cuda.synchronize()
-    # the first replay's results, for the accuracy check against the oracle
-    g.replay()
-    torch.cuda.synchronize()
-    first = {m: ([t.double().cpu().numpy() for t in fields[m][3]], [t.double().cpu().numpy() for t in fields[m][4]])
-             for m in (0, 37)}
     sampler = ClockSampler(0) if not args.profile else None
     if sampler:
         sampler.start()
@@ -736,116 +878,153 @@ def run_ensemble(args):
             flush.zero_()
             g.replay()
         torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    for s in range(args.steps):
-        flush.zero_()
-        ev[s][0].record(stream)
-        g.replay()
-        ev[s][1].record(stream)
-    torch.cuda.synchronize()
+    ms = timed_run(g.replay, stream, flush, args.steps)
     clocks = sampler.stop() if sampler else None
-    ms = [e[0].elapsed_time(e[1]) for e in ev]
+    warm_ms = timed_run(g.replay, stream, NoFlush(), args.steps) if not args.profile else None
+    status = handles[0].device_status()
     points = batch.points()
     value = points / (float(np.mean(ms)) * 1e-3) / 1e9
-    # the same members stepped one after the other (prepared calls, one graph)
-    calls = [h.prepare_step(*fl[:3], fl[3], fl[4]) for h, fl in zip(handles, fields)]
-    g1 = torch.cuda.CUDAGraph()
-    for c in calls:
-        c.wall_stress_force()
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g1):
-        for c in calls:
-            c.wall_stress_force()
-    ev1 = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    for s in range(args.steps):
-        flush.zero_()
-        ev1[s][0].record(stream)
-        g1.replay()
-        ev1[s][1].record(stream)
-    torch.cuda.synchronize()
-    ms1 = [e[0].elapsed_time(e[1]) for e in ev1]
     step_bytes = sum(h.traffic_bytes(4) for h in handles)      # wall model + 36 B/pt of every member
     peak, peak_kind = measured_peak()
     achieved = step_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
     shapes = sorted({c.grid[:3] for c in cases})
+    if args.profile:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "profile": True, "tuning": tuned,
+                          "ms_per_step": float(np.mean(ms)), "device_status": status}))
+        return 0
 
-    # the plain FP64 batch of the same members, timed the same way, with its error against the oracle
-    f64_form = None
-    if args.dtype == "f32" and not args.profile:
-        d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=torch.float64)
+    # the same members one after the other (prepared calls, one graph)
+    calls = [h.prepare_step(*fl[:3], fl[3], fl[4]) for h, fl in zip(handles, fields)]
+    for c in calls:
+        c.wall_stress_force()
+    torch.cuda.synchronize()
+    g1 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g1):
+        for c in calls:
+            c.wall_stress_force()
+    ms1 = timed_run(g1.replay, stream, flush, args.steps)
+    del g1, calls
+    # the batch step again, so that every member's fields hold its result
+    g.replay()
+    torch.cuda.synchronize()
+
+    # the plain FP64 batch of the same members, tuned and timed the same way
+    f64_form = b64 = fl64 = None
+    if args.dtype == "f32":
         h64 = [wmibm.Handle.from_case(c, dtype="f64") for c in cases]
-        fl64 = [(d64(c.u), d64(c.v), d64(c.w), [d64(c.tau[k]) for k in inputs.TAU_NAMES],
-                 [torch.empty(c.shape, dtype=torch.float64, device=dev) for _ in range(3)]) for c in cases]
+        fl64 = [fields_of(c, torch.float64) for c in cases]
         b64 = wmibm.Batch(h64)
         b64.set_fields(fl64)
         st64 = b64.new_stats()
+        tuned64 = autotune.tune_batch(b64, st64, budget_s=40.0) if not (args.no_tune or args.tuning) else None
         for _ in range(3):
             b64.wall_stress_force(st64)
         torch.cuda.synchronize()
-        first64 = {m: [t.cpu().numpy() for t in fl64[m][4]] for m in (0, 37)}
         g64 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g64):
             b64.wall_stress_force(st64)
         ms64 = timed_run(g64.replay, stream, flush, args.steps)
+        g64.replay()
+        torch.cuda.synchronize()
         f64_form = {"value": points / (float(np.mean(ms64)) * 1e-3) / 1e9, "unit": UNIT,
-                    "ms_per_step": float(np.mean(ms64)), "first": first64}
-        b64.close()
-        del h64, fl64
+                    "ms_per_step": float(np.mean(ms64)), "tuning": tuned64,
+                    "bound": "FP64 arithmetic (GB300 FP64 rate), not HBM",
+                    "device_status": h64[0].device_status()}
 
-    # end to end through the public API: every member's velocity and stresses in from pinned host memory,
-    # the batch step, every member's forcing out
+    # end to end through the batch API: every member's velocity and stresses in from pinned host memory, the
+    # batch step, every member's forcing and statistics out; double-buffered over two batches of the same
+    # members (step s's inputs go in while step s-1 computes and step s-2's results come back)
     e2e = None
-    if not args.no_e2e and not args.profile:
-        host = [([torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (c.u, c.v, c.w)] +
-                 [torch.from_numpy(c.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES],
-                 [torch.empty(c.shape, dtype=tdt).pin_memory() for _ in range(3)]) for c in cases]
-        h2d = sum(t.numel() * t.element_size() for ins, _ in host for t in ins)
-        d2h = sum(t.numel() * t.element_size() for _, outs in host for t in outs)
+    if not args.no_e2e:
+        host_in = [[torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (c.u, c.v, c.w)] +
+                   [torch.from_numpy(np.ascontiguousarray(c.tau[k])).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
+                   for c in cases]
+        sets = [(batch, fields, stats)]
+        b2_fields = [fields_of(c, tdt) for c in cases]
+        b2 = wmibm.Batch(handles)
+        if batch.get_tuning():
+            b2.set_tuning(**batch.get_tuning())
+        b2.set_fields(b2_fields)
+        sets.append((b2, b2_fields, b2.new_stats()))
+        host_out = [([[torch.empty(c.shape, dtype=tdt).pin_memory() for _ in range(3)] for c in cases],
+                     torch.empty(10 * len(cases), dtype=torch.float64).pin_memory()) for _ in range(2)]
+        h2d = sum(t.numel() * t.element_size() for ins in host_in for t in ins)
+        d2h = sum(t.numel() * t.element_size() for ff in host_out[0][0] for t in ff) + host_out[0][1].numel() * 8
 
-        def e2e_step():
-            for (ins, _), fl in zip(host, fields):
+        def copy_in(b):
+            for ins, fl in zip(host_in, sets[b][1]):
                 for dst, src in zip(list(fl[:3]) + list(fl[3]), ins):
                     dst.copy_(src, non_blocking=True)
-            batch.wall_stress_force(stats)
-            for (_, outs), fl in zip(host, fields):
+
+        def compute(b):
+            sets[b][0].wall_stress_force(sets[b][2])
+
+        def copy_out(b):
+            for outs, fl in zip(host_out[b][0], sets[b][1]):
                 for dst, src in zip(outs, fl[4]):
                     dst.copy_(src, non_blocking=True)
+            host_out[b][1].copy_(sets[b][2], non_blocking=True)
 
-        e2e_step()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = pipelined_run(dev, args.steps, [copy_in], compute, copy_out)
         e2e = {"value": args.steps * points / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h),
+               "form": "double-buffered over two batches of the same members: step s's inputs copied in on one "
+                       "stream while step s-1 computes on a second and step s-2's forcing and stats come back on "
+                       "a third"}
+        b2.close()
+        del b2_fields, host_in, host_out, sets
 
-    cpu = accuracy = None
-    if not args.no_cpu and not args.profile:
-        import oracle
-        oracle.build()
-        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
-        accuracy = {}
-        for m, (gtau, gf) in first.items():
-            c = cases[m]
-            tau_o = {k: rd(c.tau[k]) for k in inputs.TAU_NAMES}
-            oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, rd(c.u), rd(c.v), rd(c.w), tau_o)
-            f_o = oracle.force(c.grid, tau_o)
-            err = max(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) for a, b in zip(gf, f_o))
-            accuracy[f"member_{m}_f_normwise_max"] = err
-            if f64_form is not None:
-                # the FP64 batch against the oracle on the unrounded inputs
-                t64 = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
-                oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, t64)
-                f64_o = oracle.force(c.grid, t64)
-                f64_form[f"member_{m}_f_normwise_max"] = max(
-                    float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
-                    for a, b in zip(f64_form["first"][m], f64_o))
-        # the oracle over the first members, as many as fit about args.cpu_seconds
+    # every member's results against the oracle: the FP32 form against the oracle fed the same FP32-rounded
+    # velocity and stresses (parity) and against the unrounded inputs (storage precision); the FP64 form against
+    # the unrounded inputs
+    import oracle
+    oracle.build()
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wmibm.STATS_DTYPE).reshape(len(cases), 2)
+    rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+    per_parity, per_store, per64 = [], [], []
+    stats_err = 0.0
+    t_acc = time.perf_counter()
+    for m, c in enumerate(cases):
+        gtau = [t.double().cpu().numpy() for t in fields[m][3]]
+        gf = [t.double().cpu().numpy() for t in fields[m][4]]
+        tau_x = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
+        st_x = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, tau_x)
+        f_x = oracle.force(c.grid, tau_x)
+        if args.dtype == "f32":
+            tau_r = {k: rd(c.tau[k]) for k in inputs.TAU_NAMES}
+            st_r = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, rd(c.u), rd(c.v),
+                                      rd(c.w), tau_r)
+            f_r = oracle.force(c.grid, tau_r)
+            per_parity.append(ensemble_errors(gtau, gf, tau_r, f_r))
+            per_store.append(ensemble_errors(gtau, gf, tau_x, f_x))
+            ref_st = st_r
+        else:
+            per_parity.append(ensemble_errors(gtau, gf, tau_x, f_x))
+            ref_st = st_x
+        for bnd in range(2):
+            for col, name in ((1, "sum_tw"), (2, "sum_tw2"), (3, "min_tw"), (4, "max_ur")):
+                r = ref_st[bnd, col]
+                stats_err = max(stats_err, abs(bstats[m][bnd][name] - r) / max(abs(r), 1e-30))
+        if fl64 is not None:
+            per64.append(ensemble_errors([t.cpu().numpy() for t in fl64[m][3]], [t.cpu().numpy() for t in fl64[m][4]],
+                                         tau_x, f_x))
+    accuracy = dict(worst_errors(per_parity), members=len(cases), stats_rel_max=stats_err,
+                    reference="oracle on the same FP32-rounded velocity and stresses" if args.dtype == "f32"
+                    else "oracle on the same inputs",
+                    how=f"every member's 6 stresses and 3 forcing components after the timed graph replays; "
+                        f"worst member ({time.perf_counter() - t_acc:.1f} s)")
+    if args.dtype == "f32":
+        accuracy["vs_unrounded_inputs"] = worst_errors(per_store)
+    if f64_form is not None:
+        f64_form["accuracy"] = dict(worst_errors(per64), members=len(cases), reference="oracle on the same inputs")
+        b64.close()
+        del fl64
+
+    cpu = None
+    if not args.no_cpu:
+        # the oracle over the members in order, as many as fit about args.cpu_seconds
         t0 = time.perf_counter()
-        done_pts = 0
-        used = 0
+        done_pts = used = 0
         for c in cases:
             tau_o = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
             oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, tau_o)
@@ -856,24 +1035,34 @@ def run_ensemble(args):
                 break
         el = time.perf_counter() - t0
         cpu = {"value": done_pts / el / 1e9, "unit": UNIT, "cores": oracle.openmp_threads(), "kind": "oracle",
-               "sample": f"wall stress + force of the first {used} of 64 members ({el:.1f} s, FP64 CPU oracle)"}
+               "sample": f"wall stress + force of the first {used} of {len(cases)} members ({el:.1f} s, FP64 CPU "
+                         f"oracle)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": f"ensemble of 64 random Gaussian-hill terrains, grids {shapes}",
-                       "nodes": points, "l2": L2_NOTE},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "batch step (k_wall_batch + k_stencil)",
+            "config": {"workload": f"ensemble of {len(cases)} random Gaussian-hill terrains, grids {shapes}, "
+                                   f"batched FP32 (one step = wall stress + force of every member)"
+                                   if args.dtype == "f32" else
+                                   f"ensemble of {len(cases)} random Gaussian-hill terrains, grids {shapes}",
+                       "nodes": points, "members": len(cases), "l2": L2_NOTE},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_batch_traffic(form, args.dtype, points),
+                         "kernel": ENSEMBLE_FORMS[form], "kernel_ms": float(np.mean(ms)),
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
-                         "algorithmic_bytes_per_launch": step_bytes},
+                         "algorithmic_bytes_per_launch": step_bytes,
+                         "bytes_how": "every member's wall-model bytes (records, distinct velocity elements, band "
+                                      "and solid stress writes) + 36 B/pt of the stencil (6 stress reads, 3 forcing "
+                                      "writes); the whole batch step"},
+            "tuning": tuned, "form": ENSEMBLE_FORMS[form],
+            "warm_l2": {"ms_per_step": float(np.mean(warm_ms)),
+                        "value": points / (float(np.mean(warm_ms)) * 1e-3) / 1e9, "unit": UNIT,
+                        "how": "the same graph replays with no L2 flush between steps"},
             "one_by_one": {"value": points / (float(np.mean(ms1)) * 1e-3) / 1e9, "unit": UNIT,
                            "ms_per_step": float(np.mean(ms1)),
-                           "how": "the 64 members' wall stress + force one after the other, in one CUDA graph"},
-            "gpu_launches": 2 * args.steps, "device_status": handles[0].device_status(),
-            "accuracy": accuracy, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
-    if f64_form is not None:
-        f64_form.pop("first", None)
-        line["f64_form"] = f64_form
+                           "how": "the members' wall stress + force one after the other, in one CUDA graph"},
+            "timing": "per step: CUDA events around one graph replay of the batch wall stress + force",
+            "gpu_launches": args.steps * (1 if form == 5 else 2), "device_status": status,
+            "accuracy": accuracy, "f64_form": f64_form, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line))
     batch.close()
     return 0

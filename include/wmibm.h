@@ -285,7 +285,9 @@ typedef struct wmibm_tuning {
                                  3 bulk-copy pipeline with the wall model always in a kernel of its
                                  own (no single-launch step), 4 as 1 with the single-launch step's
                                  wall model in dedicated blocks (one per SM) instead of a share of
-                                 every block */
+                                 every block, 5 single launch with the band records cut into "wall
+                                 items" of wall_chunk records, each a stage of the pipeline of the
+                                 block that owns it, spread over the first half of its clean units */
     int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
     int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
     int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */
@@ -294,6 +296,8 @@ typedef struct wmibm_tuning {
     int32_t direct_bx;        /* direct-load kernel: vectors per block row */
     int32_t direct_by;        /* direct-load kernel: rows per block */
     int32_t direct_kc;        /* direct-load kernel: levels per thread */
+    int32_t wall_chunk;       /* interleaved single launch (force_path 5): band records per wall
+                                 stage, capped by a stage buffer (0: two per consumer thread) */
 } wmibm_tuning;
 
 /* Sets / reads the tuning of handle h. EINVAL for out-of-range fields. */

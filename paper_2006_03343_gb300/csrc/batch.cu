@@ -5,6 +5,7 @@
 // memory, so a step is graph-capturable and replays with the same fields.
 #include <stdarg.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <new>
@@ -31,6 +32,8 @@ struct wmibm_batch {
     StencilConfig cfg;
     int64_t clean_total, dirty_total, rec_total, run_total, body_total;
     int64_t traffic[2];
+    std::vector<unsigned char> member0;   // host copy of member 0's descriptor (a batch of one
+                                          // is launched with it as the single-terrain member)
     char err[512];
 };
 
@@ -91,6 +94,9 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
     out->consumer_warps = b->tuning.consumer_warps > 0 ? b->tuning.consumer_warps : 4;
     out->wall_warps = 8;
     out->blocks_per_sm = b->tuning.blocks_per_sm;
+    out->wall_chunk = b->tuning.wall_chunk;
+    // one interleaved launch (force_path 0 or 5) or two launches (3)
+    if (!(b->tuning.force_path == 0 || b->tuning.force_path == 3 || b->tuning.force_path == 5)) return false;
     if (1 + out->consumer_warps > 16) return false;
     *rows_out = rows;
     *stage_elems = (uint32_t)elems;
@@ -124,6 +130,8 @@ int upload_members(wmibm_batch *b, const wmibm_member_fields *fields, cudaStream
     b->rec_total = r_off;
     b->run_total = run_off;
     b->body_total = body_off;
+    b->member0.resize(sizeof(Member<T>));
+    memcpy(b->member0.data(), &host[0], sizeof(Member<T>));
     cudaError_t e = cudaMemcpyAsync(b->dev_members, host.data(), sizeof(Member<T>) * b->count,
                                     cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -146,9 +154,13 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
     p.stats = stats;
     p.bstats = b->bstats;
     p.stage_elems = b->stage_elems;
+    if (b->count == 1) memcpy(&p.one, b->member0.data(), sizeof(Member<T>));   // kernels read p.one then
+    p.wall_done = b->ticket + 1;
+    p.exit_ticket = b->ticket + 2;
     const int wall_blocks = 0;   // one wave of resident blocks
+    const bool interleaved = b->tuning.force_path != 3;
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
-                                  wall_blocks, stream);
+                                  wall_blocks, interleaved, stream);
     if (st) return berr(b, st, "%s", b->members[0]->err);
     return WMIBM_OK;
 }
@@ -182,10 +194,12 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
     const size_t msize = b->dtype == WMIBM_F64 ? sizeof(Member<double>) : sizeof(Member<float>);
     cudaError_t e = cudaMalloc(&b->dev_members, msize * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->bstats, sizeof(double) * 8 * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, sizeof(unsigned));
+    // [0] last-block ticket of the batch wall kernel; [1] wall-done and [2] exit
+    // counters of the interleaved launch (all back at 0 after every launch)
+    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bstats, 0, sizeof(double) * 8 * count, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, sizeof(unsigned), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, 4 * sizeof(unsigned), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess || !batch_config(b, &b->cfg, &b->rows, &b->stage_elems)) {

@@ -44,6 +44,7 @@ struct Lists {
 // Resolved launch shape of the pipelined stencil.
 struct StencilConfig {
     int rows, stages, consumer_warps, wall_warps, blocks_per_sm;
+    int wall_chunk;            // interleaved single launch: band records per wall stage (0: automatic)
 };
 
 struct SpecState;              // tables, counters and tile shapes of the spectral forcing (spectral.cu)

@@ -57,6 +57,12 @@ struct KParams {
     // model first; > 0 = blocks [0, wall_blocks) only evaluate the wall model and
     // the others only stream the stencil; -1 = dedicated, chosen at launch
     int wall_blocks;
+    // interleaved single-launch stage (interleave != 0): the band records, cut
+    // into wall_items slices of wall_chunk records, are stages of the stencil
+    // pipeline of every block (see StageIter)
+    int interleave;
+    int wall_chunk;
+    int64_t wall_items;
 };
 
 template <typename T>
@@ -65,7 +71,7 @@ void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], 
 
 template <typename T, typename VEL>
 int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
-                 const StencilConfig &c, int max_nx, int wall_blocks, cudaStream_t stream);
+                 const StencilConfig &c, int max_nx, int wall_blocks, bool interleaved, cudaStream_t stream);
 
 bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
 

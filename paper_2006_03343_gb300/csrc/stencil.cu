@@ -182,6 +182,16 @@ __device__ int find_member_at(const KParams<T> &p, int64_t Member<T>::*first, in
 // share of the dirty units, cut into segments of consecutive levels of one
 // strip of one member; each segment starts with a prologue stage followed by
 // one main stage per level.
+//
+// Interleaved form (one launch, wall model inside): the block also owns a
+// share of "wall items", slices of wall_chunk consecutive records of the
+// concatenated band-record space.  Each is one stage (the producer stages the
+// records, the consumers evaluate them); they are spread over the first half
+// of the block's clean units, between units, and any left go before the first
+// dirty unit.  After a wall stage the pending unit restarts with a prologue.
+// A block always has at least one wall stage (with no records when the item
+// space is smaller than the grid): its first zeroes the block's share of the
+// solid runs, its last counts the block into wall_done.
 template <typename T>
 struct StageIter {
     const KParams<T> *pp;
@@ -192,6 +202,29 @@ struct StageIter {
     MemberUnits mu;
     int32_t s, k;
     bool prologue, done, dirty, new_member;
+    // interleaved form
+    bool inter, wall, sdone;      // wall: the current stage is a wall stage; sdone: no unit left
+    int64_t wf, wn, wj, wrec;     // first wall item, wall stages, next wall stage, items with records
+    int64_t nclean, cdone;        // the block's clean units, clean main stages emitted
+
+    // a wall stage is due before the pending unit
+    __device__ __forceinline__ bool wall_due() const
+    {
+        if (!inter || wj >= wn) return false;
+        if (sdone || phase != 0) return true;
+        return cdone >= (wj * nclean) / (2 * wn);
+    }
+    // record range [a, e) of the current wall stage (empty for a block without record items)
+    __device__ __forceinline__ void wall_range(int64_t &a, int64_t &e) const
+    {
+        if (wj >= wrec) {
+            a = e = 0;
+            return;
+        }
+        const int64_t q = (int64_t)pp->wall_chunk;
+        a = (wf + wj) * q;
+        e = min(a + q, pp->rec_total);
+    }
 
     __device__ void locate()
     {
@@ -224,12 +257,18 @@ struct StageIter {
             ++phase;
             idx = d0;
         }
-        done = phase >= 2;
-        if (!done) {
+        sdone = phase >= 2;
+        if (!sdone) {
             locate();
             prologue = true;
             dirty = phase == 1;
         }
+    }
+    // after the stage sequence moved on: a wall stage may be due before the pending unit
+    __device__ __forceinline__ void pick()
+    {
+        wall = wall_due();
+        done = sdone && !wall;
     }
     __device__ void init(const KParams<T> &p)
     {
@@ -246,19 +285,46 @@ struct StageIter {
         phase = 0;
         idx = c0;
         new_member = false;
+        inter = p.interleave != 0;
+        nclean = c1 - c0;
+        cdone = 0;
+        wj = 0;
+        if (inter) {
+            const int64_t NW = p.wall_items;
+            wf = NW * sb / nsb;
+            wrec = NW * (sb + 1) / nsb - wf;
+            wn = wrec > 0 ? wrec : 1;
+        } else {
+            wf = wn = wrec = 0;
+        }
         settle();
+        pick();
     }
     // Next stage: the prologue's main stage, or the next unit in the member's
     // order (clean: levels 0 .. da-1 then db .. nz-1 of a strip; dirty: da ..
     // db-1), found without a division; a unit that does not continue the level
-    // sequence of the same strip starts a new segment.
+    // sequence of the same strip starts a new segment.  In the interleaved form
+    // a due wall stage comes first.
     __device__ void next()
     {
         new_member = false;
+        if (wall) {
+            // back to the pending unit, which restarts its segment
+            ++wj;
+            if (!sdone) prologue = true;
+            pick();
+            return;
+        }
         if (prologue) {
             prologue = false;
             return;
         }
+        if (!dirty) ++cdone;
+        advance();
+        pick();
+    }
+    __device__ void advance()
+    {
         ++idx;
         if (idx >= (phase == 0 ? c1 : d1)) {
             settle();
@@ -306,6 +372,7 @@ __device__ __forceinline__ void wait_wall_kernel()
 constexpr int kPlain = 0;       // force only: every unit is clean, no dependency
 constexpr int kAfterWall = 1;   // programmatic dependent of the wall kernel (dirty units, mask wait on it)
 constexpr int kFused = 2;       // the wall phase runs inside the launch (cooperative: all blocks resident)
+constexpr int kInterleaved = 3; // the band records are stages of every block's pipeline (cooperative)
 
 // Waits until *ctr >= target (acquire at GPU scope).  Gives up after
 // kWaitLimitNs, recording kDevStatusBarrierTimeout, or as soon as another wait
@@ -364,6 +431,24 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
         const int b = (int)(g % (uint32_t)p.stages);
         if (g >= (uint32_t)p.stages) {
             if (!mbar_wait(&empty[b], ((g / p.stages) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
+        }
+        if (MODE == kInterleaved && it.wall) {
+            // a wall stage: the item's band records, one bulk copy per member segment
+            using Rec = typename RecOf<T>::type;
+            int64_t a, e;
+            it.wall_range(a, e);
+            mbar_arrive_expect_tx(&full[b], (uint32_t)((e - a) * (int64_t)sizeof(Rec)));
+            Rec *const dst = reinterpret_cast<Rec *>(data + (size_t)b * p.stage_elems);
+            int wm = (p.nmembers == 1 || e <= a) ? 0 : find_member_at(p, &Member<T>::r_off, a);
+            for (int64_t pos = a; pos < e && wm < p.nmembers; ++wm) {
+                const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[wm];
+                const int64_t end = min(e, mm.r_off + mm.nb_w + mm.nb_uv);
+                if (end > pos)
+                    bulk_g2s(dst + (pos - a), reinterpret_cast<const Rec *>(mm.rec) + (pos - mm.r_off),
+                             (uint32_t)((end - pos) * (int64_t)sizeof(Rec)), &full[b]);
+                pos = end;
+            }
+            continue;
         }
         if (it.dirty && !released) {
             // the stresses written by the wall model must be complete and visible
@@ -543,9 +628,13 @@ template <typename T, typename VEL>
 __device__ void wall_phase_fused(const KParams<T> &p, int64_t wb, int64_t nwb, int cw, int nwarps, int lane,
                                  T (*red)[kStatVals]);
 
+template <typename T, typename VEL>
+__device__ void wall_stage(const KParams<T> &p, const typename RecOf<T>::type *recs, int64_t a, int64_t e,
+                           bool first, bool last, int cw, int lane, unsigned *warps_done);
+
 template <typename T, typename VEL, int TY, int MODE>
 __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane,
-                        T (*red)[kStatVals], uint64_t *wallbar)
+                        T (*red)[kStatVals], uint64_t *wallbar, unsigned *warps_done)
 {
     ConsView<T> cv;
     uint32_t g = 0;
@@ -569,10 +658,18 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
             cv.dq = step - cv.dr * cv.nq;
         }
         const int b = (int)(g % (uint32_t)p.stages);
-        if (!mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)) break;
-        if (!it.prologue)
+        // the whole warp gives up together, so that no lane is left behind at a warp-wide operation
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)))
+            break;
+        if (MODE == kInterleaved && it.wall) {
+            int64_t a, e;
+            it.wall_range(a, e);
+            wall_stage<T, VEL>(p, reinterpret_cast<const typename RecOf<T>::type *>(data + (size_t)b * p.stage_elems),
+                               a, e, it.wj == 0, it.wj == it.wn - 1, cw, lane, warps_done);
+        } else if (!it.prologue) {
             consume_level<T, TY>(cv, p.ncons, data + (size_t)b * p.stage_elems, data + (size_t)prevb * p.stage_elems,
                                  it.k, it.s * (TY > 0 ? TY : cv.ty), cw, lane);
+        }
         if (prevb >= 0) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[prevb]);
@@ -1018,6 +1115,147 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
     if (threadIdx.x == 0) *p.ticket = 0u;
 }
 
+// Solid runs [lo, hi) of the launch's concatenated run space (w-runs of a member
+// first), zeroed by warp w of nw: it takes 32 consecutive runs at a time (one
+// descriptor per lane), then zeroes them one after the other with coalesced stores.
+template <typename T>
+__device__ void zero_run_span(const KParams<T> &p, int64_t lo, int64_t hi, int w, int nw, int lane)
+{
+    int cm = -1;
+    T *oxx = nullptr, *oxy = nullptr, *oyy = nullptr, *ozz = nullptr, *oxz = nullptr, *oyz = nullptr;
+    for (int64_t base = lo + (int64_t)w * 32; base < hi; base += (int64_t)nw * 32) {
+        const int64_t t = base + lane;
+        int2 run = make_int2(0, 0);
+        int mrun = 0, wrun = 0;
+        if (t < hi) {
+            mrun = p.nmembers == 1 ? 0 : find_member_at(p, &Member<T>::run_off, t);
+            const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[mrun];
+            const int64_t lt = t - mm.run_off;
+            wrun = lt < mm.nr_w;
+            run = __ldg(wrun ? mm.runs_w + lt : mm.runs_uv + (lt - mm.nr_w));
+        }
+        const int nq = (int)min((int64_t)32, hi - base);
+        for (int q = 0; q < nq; ++q) {
+            const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
+            const int32_t len = __shfl_sync(0xffffffffu, run.y, q);
+            const int m = __shfl_sync(0xffffffffu, mrun, q);
+            const bool is_w = __shfl_sync(0xffffffffu, wrun, q) != 0;
+            if (m != cm) {
+                const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[m];
+                oxx = const_cast<T *>(mm.tau[0]); oxy = const_cast<T *>(mm.tau[1]);
+                oyy = const_cast<T *>(mm.tau[2]); ozz = const_cast<T *>(mm.tau[3]);
+                oxz = const_cast<T *>(mm.tau[4]); oyz = const_cast<T *>(mm.tau[5]);
+                cm = m;
+            }
+            for (int32_t x = lane; x < len; x += 32) {
+                const int64_t idx = (int64_t)start + x;
+                if (is_w) {
+                    oxz[idx] = T(0);
+                    oyz[idx] = T(0);
+                } else {
+                    oxx[idx] = T(0);
+                    oxy[idx] = T(0);
+                    oyy[idx] = T(0);
+                    ozz[idx] = T(0);
+                }
+            }
+        }
+    }
+}
+
+// Wall stage of the interleaved form, run by every consumer warp of the block on
+// the records [a, e) of the launch's concatenated band-record space, staged in
+// shared memory by the producer: the wall model of Sec. 3.3 at each band node,
+// the band statistics of each
+// member into its FP64 accumulator (p.bstats: [member][band][sum tau_w, sum
+// tau_w^2, bits of -min tau_w, bits of max |U_r|]) with one set of reductions
+// per warp and member.  The block's first wall stage also zeroes its share of
+// the solid runs.  After its last, every warp makes its stores visible (also to
+// the bulk copies of other blocks) and counts itself in a shared counter; the
+// warp that completes it counts the block into wall_done.  No block-wide
+// barrier is taken here, so a warp that gave up on a bounded wait cannot hold
+// the others.
+template <typename T, typename VEL>
+__device__ void wall_stage(const KParams<T> &p, const typename RecOf<T>::type *recs, int64_t a, int64_t e,
+                           bool first, bool last, int cw, int lane, unsigned *warps_done)
+{
+    const int nct = p.ncons * 32;
+    const int tid = cw * 32 + lane;
+    const bool want_stats = p.stats != nullptr;
+    T acc[kStatVals];
+    stats_identity(acc);
+    bool nacc = false;
+    int cm = -1;
+    int64_t r_end = 0;
+    WallRegs<T> M;
+    for (int64_t g = a + tid; g < e;) {
+        if (cm < 0 || g >= r_end) {
+            if (want_stats && nacc) {
+                stats_red(acc, p.bstats + (int64_t)cm * 8);
+                stats_identity(acc);
+                nacc = false;
+            }
+            cm = p.nmembers == 1 ? 0 : find_member_at(p, &Member<T>::r_off, g);
+            const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[cm];
+            load_wall(mm, M);
+            r_end = mm.r_off + mm.nb_w + mm.nb_uv;
+        }
+        const int64_t g1 = g + nct;
+        const bool two = g1 < e && g1 < r_end;
+        const int64_t ta = g - M.r_off, tb = g1 - M.r_off;
+        const VEL *const vu = reinterpret_cast<const VEL *>(M.u);
+        const VEL *const vv = reinterpret_cast<const VEL *>(M.v);
+        const VEL *const vw = reinterpret_cast<const VEL *>(M.w);
+        // one node's gathers at a time: inside the stencil kernel a second node's 24
+        // values in flight would spill the consumers' registers
+        constexpr bool kPair = false;
+        BandIn<T> ia, ib;
+        band_fetch_shared<T, VEL>(recs + (g - a), vu, vv, vw, M.nx, M.ny, M.plane, ia);
+        if (kPair && two) band_fetch_shared<T, VEL>(recs + (g1 - a), vu, vv, vw, M.nx, M.ny, M.plane, ib);
+        const BandOut<T> oa = band_finish<T>(ia, ta < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+        store_regs(M, oa, ta < M.nb_w);
+        stats_add(acc, ta < M.nb_w ? 0 : 1, oa.tw, oa.ur);
+        if (two) {
+            if (!kPair) band_fetch_shared<T, VEL>(recs + (g1 - a), vu, vv, vw, M.nx, M.ny, M.plane, ib);
+            const BandOut<T> ob = band_finish<T>(ib, tb < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+            store_regs(M, ob, tb < M.nb_w);
+            stats_add(acc, tb < M.nb_w ? 0 : 1, ob.tw, ob.ur);
+        }
+        nacc = true;
+        g += two ? 2 * nct : nct;
+    }
+    if (want_stats) {
+        const int key = nacc ? cm : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (same == 0xffffffffu) {
+            if (key >= 0) {
+                for (int q = 0; q < 2; ++q) {
+                    acc[4 * q + 0] = warp_sum(acc[4 * q + 0]);
+                    acc[4 * q + 1] = warp_sum(acc[4 * q + 1]);
+                    acc[4 * q + 2] = warp_min(acc[4 * q + 2]);
+                    acc[4 * q + 3] = warp_max(acc[4 * q + 3]);
+                }
+                if (lane == 0) stats_red(acc, p.bstats + (int64_t)key * 8);
+            }
+        } else if (nacc) {
+            stats_red(acc, p.bstats + (int64_t)cm * 8);
+        }
+    }
+    if (first) {
+        const int64_t R = p.run_total, G = gridDim.x;
+        zero_run_span(p, R * blockIdx.x / G, R * (blockIdx.x + 1) / G, cw, p.ncons, lane);
+    }
+    if (last) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();
+        __syncwarp();
+        if (lane == 0 && atomicAdd(warps_done, 1u) == (unsigned)p.ncons - 1) {
+            __threadfence();
+            atomicAdd(p.wall_done, 1u);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------- //
 // stencil kernel
 // ------------------------------------------------------------------------- //
@@ -1083,6 +1321,8 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
     __shared__ T red[16][kStatVals];
     __shared__ uint64_t wallbar; // fused: the block's wall share is done
     __shared__ int s_go;        // consumers: the wall model is complete (mask may run)
+    __shared__ unsigned s_wall_warps;   // interleaved: consumer warps done with the block's wall stages
+    __shared__ int s_last;      // the block is the last one out of a single-launch stage
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + 8;
     T *data = reinterpret_cast<T *>(smem_raw + 256);
@@ -1095,6 +1335,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         }
         mbar_init(&wallbar, 1);
         fence_mbar_init();
+        s_wall_warps = 0;
     }
     __syncthreads();
 
@@ -1115,7 +1356,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         __syncwarp();
     } else {
         const int cw = warp - kFirstConsumer;
-        consume<T, VEL, TY, MODE>(p, data, full, empty, cw, lane, red, &wallbar);
+        consume<T, VEL, TY, MODE>(p, data, full, empty, cw, lane, red, &wallbar, &s_wall_warps);
         if (MODE != kPlain && p.do_mask) {
             // the body mask may change the velocity only after every band stencil read it
             bool go = true;
@@ -1137,15 +1378,41 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
                                    ((int64_t)gridDim.x - wb) * nct);
         }
     }
-    if (MODE == kFused) {
-        // the last block out re-arms both counters for the next launch: every
-        // block has passed its waits on wall_done by then
+    if (MODE == kFused || MODE == kInterleaved) {
+        // the last block out converts the band statistics and re-arms both
+        // counters for the next launch: every block has passed its waits on
+        // wall_done by then
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (atomicAdd(p.exit_ticket, 1u) == gridDim.x - 1) {
-                __threadfence();
-                if (p.stats) stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+            s_last = atomicAdd(p.exit_ticket, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (MODE == kFused) {
+                if (threadIdx.x == 0 && p.stats) stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+            } else if (p.stats) {
+                // every member's accumulator [member][band][4] into its two records, then cleared
+                for (int q = threadIdx.x; q < 2 * p.nmembers; q += blockDim.x) {
+                    const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[q >> 1];
+                    double *src = p.bstats + (int64_t)q * 4;
+                    wmibm_band_stats st;
+                    st.count = (q & 1) ? mm.nb_uv : mm.nb_w;
+                    st.sum_tw = __ldcg(src + 0);
+                    st.sum_tw2 = __ldcg(src + 1);
+                    st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 2)));
+                    st.max_ur = __longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 3)));
+                    if (st.min_tw == 0.0) st.min_tw = 0.0;   // no -0 for an empty band
+                    p.stats[q] = st;
+                    src[0] = 0.0;
+                    src[1] = 0.0;
+                    src[2] = 0.0;
+                    src[3] = 0.0;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
                 atomicExch(p.wall_done, 0u);
                 atomicExch(p.exit_ticket, 0u);
             }
@@ -1190,6 +1457,17 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     int64_t grid = (int64_t)per_sm * h->sm_count;
     if (grid > units) grid = units;
     if (grid < 1) return WMIBM_OK;
+    if (MODE == kInterleaved) {
+        // wall items: slices of wall_chunk band records, each staged in one stage buffer
+        using Rec = typename RecOf<T>::type;
+        const int64_t cap = (int64_t)p.stage_elems * (int64_t)sizeof(T) / (int64_t)sizeof(Rec);
+        int64_t q = c.wall_chunk > 0 ? c.wall_chunk : 2 * 32 * (int64_t)p.ncons;
+        if (q > cap) q = cap;
+        if (q < 1) return set_error(h, WMIBM_EINVAL, "stencil stage holds no band record");
+        p.interleave = 1;
+        p.wall_chunk = (int)q;
+        p.wall_items = (p.rec_total + q - 1) / q;
+    }
     if (MODE == kFused && p.wall_blocks < 0) {
         // dedicated wall blocks: one per SM when the grid has at least two blocks
         // per SM, else a quarter of it; the grid grows by them (up to the resident
@@ -1200,14 +1478,14 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
         if (grid - wbk < 1) wbk = grid - 1;
         p.wall_blocks = wbk > 0 ? (int)wbk : 0;
     }
-    if ((MODE == kAfterWall && pdl) || MODE == kFused) {
+    if ((MODE == kAfterWall && pdl) || MODE == kFused || MODE == kInterleaved) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
-        if (MODE == kFused) {
+        if (MODE == kFused || MODE == kInterleaved) {
             // blocks wait on each other's wall phase: all must be resident
             attr[0].id = cudaLaunchAttributeCooperative;
             attr[0].val.cooperative = 1;
@@ -1268,6 +1546,9 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.sacc = h->sacc;
     p.emit_stats = 0;
     p.wall_blocks = 0;
+    p.interleave = 0;
+    p.wall_chunk = 0;
+    p.wall_items = 0;
 }
 
 template <typename T, typename VEL>
@@ -1393,6 +1674,7 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     c.wall_warps = h->tuning.wall_warps;
     if (1 + c.consumer_warps > 16) return false;
     c.blocks_per_sm = h->tuning.blocks_per_sm;
+    c.wall_chunk = h->tuning.wall_chunk;
     *out = c;
     return true;
 }
@@ -1467,14 +1749,41 @@ int step_fused_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[
     return launch_stencil<T, VEL, kFused>(h, p, c, stream, false, h->nx);
 }
 
+// The whole stage in one cooperative launch with the band records cut into
+// wall items that are stages of every block's pipeline, between its clean units.
+template <typename T, typename VEL>
+int step_interleaved_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
+                          const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
+                          const StencilConfig &c, cudaStream_t stream)
+{
+    KParams<T> p;
+    fill_member<T>(h, p.one, (const void *const *)tau, f, u, v, w, h->logz0, gradp, dt, c.rows);
+    single_params<T>(h, p, true);
+    p.stages = c.stages;
+    p.ncons = c.consumer_warps;
+    p.do_mask = do_mask;
+    p.stats = stats;
+    p.bstats = h->sacc;           // one member: the accumulator has the [band][4] layout
+    return launch_stencil<T, VEL, kInterleaved>(h, p, c, stream, false, h->nx);
+}
+
 // The whole stage in one cooperative launch: the wall model (Sec. 3.3) by the
 // consumer warps of every block while the producers stream the clean stages,
 // the forcing (Eq. 18) once the wall model is complete where a stage needs it,
-// and with do_mask the body mask (Eq. 27).
+// and with do_mask the body mask (Eq. 27).  force_path 5: the wall model as
+// interleaved stages of every block's pipeline instead.
 int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
                        const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
                        const StencilConfig &c, cudaStream_t stream)
 {
+    if (h->tuning.force_path == 5) {
+        if (h->dtype == WMIBM_F64)
+            return step_interleaved_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+        if (h->vel_dtype == WMIBM_BF16)
+            return step_interleaved_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c,
+                                                                stream);
+        return step_interleaved_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+    }
     const bool dedicated = h->tuning.force_path == 4;   // dedicated wall blocks
     if (h->dtype == WMIBM_F64)
         return step_fused_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, dedicated,
@@ -1516,16 +1825,19 @@ int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const
 }
 
 // One batched step: the batch wall kernel, then the batch stencil (force + mask)
-// as its programmatic dependent.  tmpl carries the launch-wide fields.
+// as its programmatic dependent; or (interleaved) one cooperative launch of the
+// batch stencil with every member's band records as wall stages of its blocks.
+// tmpl carries the launch-wide fields.
 template <typename T, typename VEL>
 int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
-                 const StencilConfig &c, int max_nx, int wall_blocks, cudaStream_t stream)
+                 const StencilConfig &c, int max_nx, int wall_blocks, bool interleaved, cudaStream_t stream)
 {
     KParams<T> p = tmpl;
     p.list = dev_members;
     p.nmembers = nmembers;
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
+    if (interleaved) return launch_stencil_ty<T, VEL, 0, kInterleaved>(h0, p, c, stream, false, max_nx);
     // two chunks of 2 x 256 records in shared memory
     const size_t wsmem = 2 * 2 * 256 * sizeof(typename RecOf<T>::type);
     static int per_sm = 0;                 // once per instantiation and process
@@ -1545,10 +1857,10 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
 }
 
 template int batch_launch<float, float>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
-                                        const StencilConfig &, int, int, cudaStream_t);
+                                        const StencilConfig &, int, int, bool, cudaStream_t);
 template int batch_launch<float, __nv_bfloat16>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
-                                                const StencilConfig &, int, int, cudaStream_t);
+                                                const StencilConfig &, int, int, bool, cudaStream_t);
 template int batch_launch<double, double>(wmibm_handle *, const Member<double> *, int, const KParams<double> &,
-                                          const StencilConfig &, int, int, cudaStream_t);
+                                          const StencilConfig &, int, int, bool, cudaStream_t);
 
 }  // namespace wmibm

@@ -53,7 +53,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("force_path", ctypes.c_int32), ("rows", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("consumer_warps", ctypes.c_int32), ("wall_warps", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("direct_bx", ctypes.c_int32), ("direct_by", ctypes.c_int32),
-                ("direct_kc", ctypes.c_int32)]
+                ("direct_kc", ctypes.c_int32), ("wall_chunk", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -531,10 +531,19 @@ class Batch:
         self._check(self._L.wmibm_batch_set_fields(self._b, arr, _stream_ptr(stream)))
 
     def set_tuning(self, **fields):
+        """Replaces the batch's tile shape and form (force_path 3: wall kernel then
+        stencil; 0 or 5: one interleaved launch); the fields given before are set
+        again, since the unit offsets depend on the rows per strip."""
         t = Tuning()
         for k, v in fields.items():
             setattr(t, k, int(v))
         self._check(self._L.wmibm_batch_set_tuning(self._b, ctypes.byref(t)))
+        self._tuning = {k: int(v) for k, v in fields.items()}
+        if self._keep is not None:
+            self.set_fields(self._keep)
+
+    def get_tuning(self) -> dict:
+        return dict(getattr(self, "_tuning", {}))
 
     def new_stats(self):
         import torch

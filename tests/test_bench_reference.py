@@ -59,3 +59,21 @@ def test_reference_arm_sdf_workload(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC_SDF
     assert d["value"] > 0 and d["cpu_baseline"]["cores"] == 1 and d["dtype"] == "f64"
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_ensemble_workload(monkeypatch, capsys):
+    """The reference arm of the default (batched ensemble) workload on a few members:
+    the oracle's wall stress + force over every member, under the GPU arm's metric
+    and workload name."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main(["--impl", "reference", "--members", "3", "--steps", "1", "--warmup", "0"]) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["config"]["members"] == 3 and d["config"]["workload"].startswith("ensemble of 3")
+    assert d["value"] > 0 and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"]

@@ -1,6 +1,8 @@
-"""Batched ensembles: members of uneven grid sizes stepped by the same two
-persistent launches give, member by member, what single-terrain steps give,
-and match the FP64 oracle."""
+"""Batched ensembles: members of uneven grid sizes stepped together give, member
+by member, what single-terrain steps give, and match the FP64 oracle, in both
+batch forms: one cooperative launch with every member's band records as
+interleaved wall stages of the stencil pipeline (force_path 5, the default),
+and the batch wall kernel followed by the batch stencil (force_path 3)."""
 import numpy as np
 import pytest
 
@@ -97,41 +99,105 @@ def test_batch_graph_replay(wm):
     batch.close()
 
 
-def test_batch_tunings(wm, oracle_mod):
+BATCH_TUNINGS = [dict(rows=1, stages=3, consumer_warps=2), dict(rows=2, stages=5, consumer_warps=8),
+                 dict(rows=4, stages=2, consumer_warps=4, blocks_per_sm=1),
+                 dict(rows=2, stages=4, consumer_warps=6, wall_chunk=64),
+                 dict(rows=4, stages=3, consumer_warps=3, wall_chunk=2048),
+                 dict(rows=1, stages=6, consumer_warps=4, wall_chunk=200)]
+
+
+@pytest.mark.parametrize("form", [3, 5])
+@pytest.mark.parametrize("tuning", range(len(BATCH_TUNINGS)))
+def test_batch_tunings(wm, oracle_mod, tuning, form):
+    """Every batch form and a covering set of tile shapes and band-record chunks,
+    against the oracle: stresses, forcing and statistics, with the outputs NaN
+    before the call."""
     cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % 4]) for m in range(5)]
     handles = [wm.Handle.from_case(c) for c in cases]
     batch = wm.Batch(handles)
-    for tun in (dict(rows=1, stages=3, consumer_warps=2), dict(rows=2, stages=5, consumer_warps=8),
-                dict(rows=4, stages=2, consumer_warps=4, blocks_per_sm=1)):
-        batch.set_tuning(**tun)
-        fields = [_fields(c, "f32") for c in cases]
-        batch.set_fields(fields)
-        batch.step()
+    tun = dict(BATCH_TUNINGS[tuning], force_path=form)
+    batch.set_tuning(**tun)
+    fields = [_fields(c, "f32") for c in cases]
+    for fl in fields:
+        for t in fl[4]:
+            t.fill_(float("nan"))
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.wall_stress_force(stats)
+    torch.cuda.synchronize()
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(len(cases), 2)
+    for m, c in enumerate(cases):
+        tau_o, f_o, st_o = oracle_step(oracle_mod, c)
+        for k, t in zip(inputs.TAU_NAMES, fields[m][3]):
+            assert normwise(to_host(t), tau_o[k])[0] <= TOL["f32"], (tun, m, k)
+        for cc in range(3):
+            g = to_host(fields[m][4][cc])
+            assert np.all(np.isfinite(g)), (tun, m, cc)
+            assert normwise(g, f_o[cc])[0] <= TOL["f32"], (tun, m)
+        assert_stats_close(bstats[m], st_o, "f32")
+    assert handles[0].device_status() == wm.OK
+    batch.close()
+
+
+@pytest.mark.parametrize("form", [3, 5])
+def test_batch_forms_bitwise_equal_and_replay(wm, form):
+    """Both batch forms give the same stresses and forcing bit for bit (the same
+    per-node arithmetic), from a CUDA graph replayed twice."""
+    cases = [inputs.ensemble_member(m, shape=SMALL_SHAPES[m % 4]) for m in range(6)]
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    batch.set_tuning(force_path=3)
+    ref = [_fields(c, "f32") for c in cases]
+    batch.set_fields(ref)
+    batch.wall_stress_force()
+    torch.cuda.synchronize()
+    batch.set_tuning(force_path=form)
+    fields = [_fields(c, "f32") for c in cases]
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.wall_stress_force(stats)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.wall_stress_force(stats)
+    for _ in range(2):
+        for fl in fields:
+            for t in fl[4]:
+                t.fill_(float("nan"))
+        g.replay()
         torch.cuda.synchronize()
-        for m, c in enumerate(cases):
-            tau_o, f_o, _ = oracle_step(oracle_mod, c)
-            for cc in range(3):
-                assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], (tun, m)
+        for m in range(len(cases)):
+            for got, r in zip(fields[m][3] + fields[m][4], ref[m][3] + ref[m][4]):
+                assert np.array_equal(to_host(got), to_host(r)), (form, m)
+    assert handles[0].device_status() == wm.OK
     batch.close()
 
 
 def test_full_ensemble_64(wm, oracle_mod):
-    """The 64-member ensemble (grids 64^3 .. 256x128x64), sampled against the oracle."""
+    """The 64-member ensemble (grids 64^3 .. 256x128x64) in both batch forms, every
+    member's stresses, forcing and statistics against the oracle."""
     cases = inputs.ensemble(64)
     handles = [wm.Handle.from_case(c) for c in cases]
     batch = wm.Batch(handles)
-    fields = [_fields(c, "f32") for c in cases]
-    batch.set_fields(fields)
-    stats = batch.new_stats()
-    batch.step(stats)
-    torch.cuda.synchronize()
-    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(64, 2)
-    for m in (0, 17, 42, 63):
-        tau_o, f_o, st_o = oracle_step(oracle_mod, cases[m])
-        for cc in range(3):
-            assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], m
-        assert_stats_close(bstats[m], st_o, "f32")
+    out = {}
+    for form in (5, 3):
+        batch.set_tuning(force_path=form)
+        fields = [_fields(c, "f32") for c in cases]
+        batch.set_fields(fields)
+        stats = batch.new_stats()
+        batch.wall_stress_force(stats)
+        torch.cuda.synchronize()
+        out[form] = (fields, np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(64, 2))
+    for m, c in enumerate(cases):
+        tau_o, f_o, st_o = oracle_step(oracle_mod, c)
+        for form, (fields, bstats) in out.items():
+            for k, t in zip(inputs.TAU_NAMES, fields[m][3]):
+                assert normwise(to_host(t), tau_o[k])[0] <= TOL["f32"], (form, m, k)
+            for cc in range(3):
+                assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], (form, m, cc)
+            assert_stats_close(bstats[m], st_o, "f32")
     assert batch.points() == sum(c.npoints for c in cases)
+    assert handles[0].device_status() == wm.OK
     batch.close()
 
 
@@ -161,4 +227,27 @@ def test_batch_wall_stress_force_equals_single_calls(wm):
         for bnd in range(2):
             assert bstats[m][bnd]["count"] == single[bnd]["count"]
             assert bstats[m][bnd]["sum_tw"] == pytest.approx(single[bnd]["sum_tw"], rel=1e-5)
+    batch.close()
+
+
+@pytest.mark.parametrize("form", [3, 5])
+def test_batch_of_one(wm, oracle_mod, form):
+    """A batch of a single member (its launch reads the member from the kernel
+    parameters, not from the descriptor array) matches the oracle."""
+    case = inputs.ensemble_member(3, shape=(64, 32, 24))
+    h = wm.Handle.from_case(case)
+    batch = wm.Batch([h])
+    batch.set_tuning(force_path=form)
+    fields = [_fields(case, "f32")]
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    batch.wall_stress_force(stats)
+    torch.cuda.synchronize()
+    tau_o, f_o, st_o = oracle_step(oracle_mod, case)
+    for k, t in zip(inputs.TAU_NAMES, fields[0][3]):
+        assert normwise(to_host(t), tau_o[k])[0] <= TOL["f32"], k
+    for cc in range(3):
+        assert normwise(to_host(fields[0][4][cc]), f_o[cc])[0] <= TOL["f32"], cc
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(1, 2)
+    assert_stats_close(bstats[0], st_o, "f32")
     batch.close()
