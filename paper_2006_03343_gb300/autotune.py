@@ -2,9 +2,10 @@
 
 One terrain: times wall stress + force (wmibm_wall_stress_force) of a handle
 over its forms -- one cooperative launch with the wall phase inside the
-pipelined stencil (a share in every block, dedicated wall blocks, or the band
-records as interleaved pipeline stages), or the wall kernel followed by the
-stencil -- and a grid of tile shapes (rows per strip, shared-memory stages,
+pipelined stencil (a share in every block, dedicated wall blocks, the band
+records as interleaved pipeline stages, or wall warps beside the producer and
+consumers of every block), or the wall kernel followed by the stencil -- and a
+grid of tile shapes (rows per strip, shared-memory stages,
 consumer warps, warps of the wall kernel, band records per wall stage) with CUDA
 events on the launching stream (L2 flushed before every timed call), keeps the
 fastest, applies it to the handle and caches it in a JSON file keyed by GPU,
@@ -12,10 +13,11 @@ precision and grid size.  A single-launch form is taken only when it beats the
 best two-launch form by more than 2 %; closer than that the two are a tie and
 the two-launch form is kept.
 
-A batch: the same for wmibm_batch_wall_stress_force over the two batch forms
-(one interleaved cooperative launch, or the batch wall kernel then the batch
-stencil), rows per strip of the widest members, stages, consumer warps and
-band records per wall stage; cached by the members' grid sizes.
+A batch: the same for wmibm_batch_wall_stress_force over the batch forms (one
+cooperative launch with wall warps or with interleaved wall stages, or the
+batch wall kernel then the batch stencil), rows per strip of the widest
+members, stages, consumer warps, wall warps and band records per wall stage;
+cached by the members' grid sizes.
 
 Before a shape is kept, its forcing is compared with the forcing of the
 library's default shape on the same inputs: a shape whose result differs by
@@ -38,6 +40,10 @@ STAGES = (2, 3, 4, 5, 6)
 CONSUMERS = (2, 3, 4, 6, 8)
 WALL_WARPS = (4, 8)
 WALL_CHUNK_PER_THREAD = (0, 4)     # band records per consumer thread and wall stage (0: the library's default)
+WALL_WARPS_IN_BLOCK = (2, 3, 4)     # wall warps beside the producer and consumers (force_path 6)
+
+FORM_NAMES = {1: "single_launch", 2: "direct", 3: "two_launch", 4: "dedicated_wall_blocks", 5: "interleaved",
+              6: "wall_warps"}
 
 SMEM_LIMIT = 200 * 1024
 SINGLE_MARGIN = 0.02       # relative margin by which the single-launch form must win
@@ -86,6 +92,9 @@ def candidates(handle):
             if per:
                 c["wall_chunk"] = per * 32 * cons
             out.append(c)
+        for ww in WALL_WARPS_IN_BLOCK:
+            if 1 + cons + ww <= 16:
+                out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww))
         for wall in WALL_WARPS:
             out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall))
     return out
@@ -102,11 +111,14 @@ def batch_candidates(batch):
         if (6 * rows + 6) * max_nx * es * stages + 256 > SMEM_LIMIT:
             continue
         out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons))
-        for per in (0, 1, 4):
+        for per in (0, 4):
             c = dict(force_path=5, rows=rows, stages=stages, consumer_warps=cons)
             if per:
                 c["wall_chunk"] = per * 32 * cons
             out.append(c)
+        for ww in WALL_WARPS_IN_BLOCK:
+            if 1 + cons + ww <= 16:
+                out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww))
     return out
 
 
@@ -228,8 +240,7 @@ def tune(handle, fields, reps: int = 9, use_cache: bool = True, budget_s: float 
         if verbose:
             print(f"  {ms * 1e3:8.1f} us  {cand}")
         timed.append((ms, cand))
-        form = {1: "single_launch", 4: "dedicated_wall_blocks", 5: "interleaved", 2: "direct",
-                3: "two_launch"}[cand.get("force_path", 1)]
+        form = FORM_NAMES[cand.get("force_path", 1)]
         if form not in best_form or ms < best_form[form][0]:
             best_form[form] = (ms, cand)
     if not timed:
@@ -302,7 +313,7 @@ def tune_batch(batch, stats=None, reps: int = 7, use_cache: bool = True, budget_
         if verbose:
             print(f"  {ms * 1e3:8.1f} us  {cand}")
         timed.append((ms, cand))
-        form = "interleaved" if cand["force_path"] == 5 else "two_launch"
+        form = FORM_NAMES[cand["force_path"]]
         if form not in best_form or ms < best_form[form][0]:
             best_form[form] = (ms, cand)
     if not timed:

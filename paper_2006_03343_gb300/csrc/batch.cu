@@ -92,11 +92,14 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
     out->rows = 0;                 // per member
     out->stages = stages;
     out->consumer_warps = b->tuning.consumer_warps > 0 ? b->tuning.consumer_warps : 4;
-    out->wall_warps = 8;
+    out->wall_warps = b->tuning.wall_warps;
     out->blocks_per_sm = b->tuning.blocks_per_sm;
     out->wall_chunk = b->tuning.wall_chunk;
-    // one interleaved launch (force_path 0 or 5) or two launches (3)
-    if (!(b->tuning.force_path == 0 || b->tuning.force_path == 3 || b->tuning.force_path == 5)) return false;
+    // one launch (force_path 0 or 6: wall warps; 5: interleaved wall stages) or two launches (3)
+    const int fp = b->tuning.force_path;
+    if (!(fp == 0 || fp == 3 || fp == 5 || fp == 6)) return false;
+    if (fp != 3 && fp != 5 && 1 + out->consumer_warps + (out->wall_warps > 0 ? out->wall_warps : 3) > 16)
+        return false;
     if (1 + out->consumer_warps > 16) return false;
     *rows_out = rows;
     *stage_elems = (uint32_t)elems;
@@ -158,9 +161,9 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
     p.wall_done = b->ticket + 1;
     p.exit_ticket = b->ticket + 2;
     const int wall_blocks = 0;   // one wave of resident blocks
-    const bool interleaved = b->tuning.force_path != 3;
+    const int form = b->tuning.force_path == 0 ? 6 : b->tuning.force_path;
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
-                                  wall_blocks, interleaved, stream);
+                                  wall_blocks, form, stream);
     if (st) return berr(b, st, "%s", b->members[0]->err);
     return WMIBM_OK;
 }

@@ -640,7 +640,7 @@ extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
 {
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!t) return set_error(h, WMIBM_EINVAL, "NULL tuning");
-    if (t->force_path < 0 || t->force_path > 5) return set_error(h, WMIBM_EINVAL, "force_path must be 0..5");
+    if (t->force_path < 0 || t->force_path > 6) return set_error(h, WMIBM_EINVAL, "force_path must be 0..6");
     if (t->wall_chunk < 0 || t->wall_chunk > 65536) return set_error(h, WMIBM_EINVAL, "wall_chunk must be 0..65536");
     if (!(t->rows == 0 || t->rows == 1 || t->rows == 2 || t->rows == 4))
         return set_error(h, WMIBM_EINVAL, "rows must be 0, 1, 2 or 4");

@@ -69,7 +69,8 @@ struct wmibm_handle {
     int2 *runs[2];              // solid runs along x (first node, length): w-grid, uv-grid
     int64_t nruns[2];
     int *dev_status;            // set by kernels whose bounded waits gave up
-    int occ_key[8], occ_val[8], occ_next;   // cached occupancy of stencil launch shapes
+    int64_t occ_key[8];         // cached occupancy of stencil launch shapes
+    int occ_val[8], occ_next;
     int32_t dirty_lo, dirty_hi; // stencil levels [lo, hi) whose stages read band or solid entries
     int sm_count;
     wmibm_tuning tuning;

@@ -63,6 +63,9 @@ struct KParams {
     int interleave;
     int wall_chunk;
     int64_t wall_items;
+    // warp-specialized single-launch stage: warps [1 + ncons, 1 + ncons + wall_warps)
+    // of every block evaluate the block's slice of the band records and solid runs
+    int wall_warps;
 };
 
 template <typename T>
@@ -71,7 +74,7 @@ void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], 
 
 template <typename T, typename VEL>
 int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
-                 const StencilConfig &c, int max_nx, int wall_blocks, bool interleaved, cudaStream_t stream);
+                 const StencilConfig &c, int max_nx, int wall_blocks, int form, cudaStream_t stream);
 
 bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const f[3], StencilConfig *out);
 

@@ -373,6 +373,7 @@ constexpr int kPlain = 0;       // force only: every unit is clean, no dependenc
 constexpr int kAfterWall = 1;   // programmatic dependent of the wall kernel (dirty units, mask wait on it)
 constexpr int kFused = 2;       // the wall phase runs inside the launch (cooperative: all blocks resident)
 constexpr int kInterleaved = 3; // the band records are stages of every block's pipeline (cooperative)
+constexpr int kWarpSpec = 4;    // wall warps beside the producer and consumers of every block (cooperative)
 
 // Waits until *ctr >= target (acquire at GPU scope).  Gives up after
 // kWaitLimitNs, recording kDevStatusBarrierTimeout, or as soon as another wait
@@ -1256,6 +1257,91 @@ __device__ void wall_stage(const KParams<T> &p, const typename RecOf<T>::type *r
     }
 }
 
+// Wall warps of the warp-specialized form: warps ww = 0 .. nww-1 of the block's
+// wall group take the block's contiguous slice of the launch's concatenated
+// band records (two records' gathers in flight per thread in FP32), then its
+// share of the solid runs, while the producer and the consumers of the same
+// block stream the clean stencil units.  Band statistics go per member into the
+// FP64 accumulators (p.bstats).  When done, every wall warp makes its stores
+// visible (also to other blocks' bulk copies) and counts itself in a shared
+// counter; the warp that completes it counts the block into wall_done.
+template <typename T, typename VEL>
+__device__ void wall_warps_run(const KParams<T> &p, int ww, int nww, int lane, unsigned *warps_done)
+{
+    const int nt = nww * 32;
+    const int tid = ww * 32 + lane;
+    const int64_t R = p.rec_total, G = gridDim.x, blk = blockIdx.x;
+    const int64_t r0 = R * blk / G, r1 = R * (blk + 1) / G;
+    const bool want_stats = p.stats != nullptr;
+    T acc[kStatVals];
+    stats_identity(acc);
+    bool nacc = false;
+    int cm = -1;
+    int64_t r_end = 0;
+    WallRegs<T> M;
+    for (int64_t g = r0 + tid; g < r1;) {
+        if (cm < 0 || g >= r_end) {
+            if (want_stats && nacc) {
+                stats_red(acc, p.bstats + (int64_t)cm * 8);
+                stats_identity(acc);
+                nacc = false;
+            }
+            cm = p.nmembers == 1 ? 0 : find_member_at(p, &Member<T>::r_off, g);
+            const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[cm];
+            load_wall(mm, M);
+            r_end = mm.r_off + mm.nb_w + mm.nb_uv;
+        }
+        const int64_t g1 = g + nt;
+        const bool two = g1 < r1 && g1 < r_end;
+        const int64_t ta = g - M.r_off, tb = g1 - M.r_off;
+        const VEL *const vu = reinterpret_cast<const VEL *>(M.u);
+        const VEL *const vv = reinterpret_cast<const VEL *>(M.v);
+        const VEL *const vw = reinterpret_cast<const VEL *>(M.w);
+        // FP32: both nodes' gathers in flight before any arithmetic; FP64: one after the other
+        constexpr bool kPair = sizeof(T) == 4;
+        BandIn<T> ia, ib;
+        band_fetch<T, VEL>(M.rec, ta, vu, vv, vw, M.nx, M.ny, M.plane, ia);
+        if (kPair && two) band_fetch<T, VEL>(M.rec, tb, vu, vv, vw, M.nx, M.ny, M.plane, ib);
+        const BandOut<T> oa = band_finish<T>(ia, ta < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+        store_regs(M, oa, ta < M.nb_w);
+        stats_add(acc, ta < M.nb_w ? 0 : 1, oa.tw, oa.ur);
+        if (two) {
+            if (!kPair) band_fetch<T, VEL>(M.rec, tb, vu, vv, vw, M.nx, M.ny, M.plane, ib);
+            const BandOut<T> ob = band_finish<T>(ib, tb < M.nb_w, M.logz0, M.log_phi_c, M.kappa2);
+            store_regs(M, ob, tb < M.nb_w);
+            stats_add(acc, tb < M.nb_w ? 0 : 1, ob.tw, ob.ur);
+        }
+        nacc = true;
+        g += two ? 2 * nt : nt;
+    }
+    if (want_stats) {
+        const int key = nacc ? cm : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (same == 0xffffffffu) {
+            if (key >= 0) {
+                for (int q = 0; q < 2; ++q) {
+                    acc[4 * q + 0] = warp_sum(acc[4 * q + 0]);
+                    acc[4 * q + 1] = warp_sum(acc[4 * q + 1]);
+                    acc[4 * q + 2] = warp_min(acc[4 * q + 2]);
+                    acc[4 * q + 3] = warp_max(acc[4 * q + 3]);
+                }
+                if (lane == 0) stats_red(acc, p.bstats + (int64_t)key * 8);
+            }
+        } else if (nacc) {
+            stats_red(acc, p.bstats + (int64_t)cm * 8);
+        }
+    }
+    const int64_t RU = p.run_total;
+    zero_run_span(p, RU * blk / G, RU * (blk + 1) / G, ww, nww, lane);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && atomicAdd(warps_done, 1u) == (unsigned)nww - 1) {
+        __threadfence();
+        atomicAdd(p.wall_done, 1u);
+    }
+}
+
 // ------------------------------------------------------------------------- //
 // stencil kernel
 // ------------------------------------------------------------------------- //
@@ -1354,6 +1440,9 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         // entry), dirty stages once the wall model is complete
         if (lane == 0) produce<T, TY, MODE>(p, data, full, empty, &wallbar);
         __syncwarp();
+    } else if (MODE == kWarpSpec && warp > p.ncons) {
+        // wall warps: the block's slice of the band records and solid runs
+        wall_warps_run<T, VEL>(p, warp - 1 - p.ncons, p.wall_warps, lane, &s_wall_warps);
     } else {
         const int cw = warp - kFirstConsumer;
         consume<T, VEL, TY, MODE>(p, data, full, empty, cw, lane, red, &wallbar, &s_wall_warps);
@@ -1378,7 +1467,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
                                    ((int64_t)gridDim.x - wb) * nct);
         }
     }
-    if (MODE == kFused || MODE == kInterleaved) {
+    if (MODE == kFused || MODE == kInterleaved || MODE == kWarpSpec) {
         // the last block out converts the band statistics and re-arms both
         // counters for the next launch: every block has passed its waits on
         // wall_done by then
@@ -1437,10 +1526,16 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     if (TY > 0) p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
     const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
     if (smem > (size_t)kMaxDynSmem) return set_error(h, WMIBM_EINVAL, "stencil stages exceed shared memory");
-    const int threads = 32 * (1 + p.ncons);      // producer warp + consumer warps
+    if (MODE == kWarpSpec) {
+        p.wall_warps = c.wall_warps > 0 ? c.wall_warps : 3;
+        if (1 + p.ncons + p.wall_warps > 16) return set_error(h, WMIBM_EINVAL, "more than 16 warps per block");
+    }
+    // producer warp + consumer warps (+ wall warps)
+    const int threads = 32 * (1 + p.ncons + (MODE == kWarpSpec ? p.wall_warps : 0));
     // occupancy of this shape, cached in the handle
-    const int key = MODE | (TY << 2) | (c.stages << 5) | (c.consumer_warps << 9) |
-                    ((TY > 0 ? max_nx : (int)p.stage_elems) << 14);
+    const int64_t key = (int64_t)MODE | ((int64_t)TY << 4) | ((int64_t)c.stages << 8) |
+                        ((int64_t)c.consumer_warps << 12) | ((int64_t)(MODE == kWarpSpec ? p.wall_warps : 0) << 16) |
+                        ((int64_t)(TY > 0 ? max_nx : (int)p.stage_elems) << 20);
     int per_sm = 0;
     for (int q = 0; q < 8; ++q)
         if (h->occ_key[q] == key) per_sm = h->occ_val[q];
@@ -1478,14 +1573,14 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
         if (grid - wbk < 1) wbk = grid - 1;
         p.wall_blocks = wbk > 0 ? (int)wbk : 0;
     }
-    if ((MODE == kAfterWall && pdl) || MODE == kFused || MODE == kInterleaved) {
+    if ((MODE == kAfterWall && pdl) || MODE == kFused || MODE == kInterleaved || MODE == kWarpSpec) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
-        if (MODE == kFused || MODE == kInterleaved) {
+        if (MODE == kFused || MODE == kInterleaved || MODE == kWarpSpec) {
             // blocks wait on each other's wall phase: all must be resident
             attr[0].id = cudaLaunchAttributeCooperative;
             attr[0].val.cooperative = 1;
@@ -1549,6 +1644,7 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.interleave = 0;
     p.wall_chunk = 0;
     p.wall_items = 0;
+    p.wall_warps = 0;
 }
 
 template <typename T, typename VEL>
@@ -1572,7 +1668,7 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
     const int wthreads = blocks ? 256 : 32 * (h->tuning.wall_warps > 0 ? h->tuning.wall_warps : 8);
     if (blocks == 0) {
         int wper = 0;
-        const int wkey = 0x100000 | wthreads | (sizeof(T) == 8 ? 0x200000 : 0);
+        const int64_t wkey = 0x100000 | wthreads | (sizeof(T) == 8 ? 0x200000 : 0);
         for (int q = 0; q < 8; ++q)
             if (h->occ_key[q] == wkey) wper = h->occ_val[q];
         if (wper == 0) {
@@ -1751,10 +1847,11 @@ int step_fused_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[
 
 // The whole stage in one cooperative launch with the band records cut into
 // wall items that are stages of every block's pipeline, between its clean units.
+// warp_spec: the wall model in wall warps beside the producer and consumers instead.
 template <typename T, typename VEL>
 int step_interleaved_impl(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *const f[3],
                           const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
-                          const StencilConfig &c, cudaStream_t stream)
+                          const StencilConfig &c, bool warp_spec, cudaStream_t stream)
 {
     KParams<T> p;
     fill_member<T>(h, p.one, (const void *const *)tau, f, u, v, w, h->logz0, gradp, dt, c.rows);
@@ -1764,6 +1861,7 @@ int step_interleaved_impl(wmibm_handle *h, void *u, void *v, void *w, void *cons
     p.do_mask = do_mask;
     p.stats = stats;
     p.bstats = h->sacc;           // one member: the accumulator has the [band][4] layout
+    if (warp_spec) return launch_stencil<T, VEL, kWarpSpec>(h, p, c, stream, false, h->nx);
     return launch_stencil<T, VEL, kInterleaved>(h, p, c, stream, false, h->nx);
 }
 
@@ -1776,13 +1874,15 @@ int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const t
                        const void *const gradp[3], double dt, int do_mask, wmibm_band_stats *stats,
                        const StencilConfig &c, cudaStream_t stream)
 {
-    if (h->tuning.force_path == 5) {
+    if (h->tuning.force_path == 5 || h->tuning.force_path == 6) {
+        const bool ws = h->tuning.force_path == 6;
         if (h->dtype == WMIBM_F64)
-            return step_interleaved_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+            return step_interleaved_impl<double, double>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, ws,
+                                                         stream);
         if (h->vel_dtype == WMIBM_BF16)
-            return step_interleaved_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c,
+            return step_interleaved_impl<float, __nv_bfloat16>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, ws,
                                                                 stream);
-        return step_interleaved_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, stream);
+        return step_interleaved_impl<float, float>(h, u, v, w, tau, f, gradp, dt, do_mask, stats, c, ws, stream);
     }
     const bool dedicated = h->tuning.force_path == 4;   // dedicated wall blocks
     if (h->dtype == WMIBM_F64)
@@ -1825,19 +1925,21 @@ int wall_model_with_scratch(wmibm_handle *h, const void *u, const void *v, const
 }
 
 // One batched step: the batch wall kernel, then the batch stencil (force + mask)
-// as its programmatic dependent; or (interleaved) one cooperative launch of the
-// batch stencil with every member's band records as wall stages of its blocks.
+// as its programmatic dependent (form 3); or one cooperative launch of the batch
+// stencil with every member's band records as wall stages of its blocks (form 5)
+// or in wall warps beside its producer and consumers (form 6).
 // tmpl carries the launch-wide fields.
 template <typename T, typename VEL>
 int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, const KParams<T> &tmpl,
-                 const StencilConfig &c, int max_nx, int wall_blocks, bool interleaved, cudaStream_t stream)
+                 const StencilConfig &c, int max_nx, int wall_blocks, int form, cudaStream_t stream)
 {
     KParams<T> p = tmpl;
     p.list = dev_members;
     p.nmembers = nmembers;
     p.stages = c.stages;
     p.ncons = c.consumer_warps;
-    if (interleaved) return launch_stencil_ty<T, VEL, 0, kInterleaved>(h0, p, c, stream, false, max_nx);
+    if (form == 5) return launch_stencil_ty<T, VEL, 0, kInterleaved>(h0, p, c, stream, false, max_nx);
+    if (form == 6) return launch_stencil_ty<T, VEL, 0, kWarpSpec>(h0, p, c, stream, false, max_nx);
     // two chunks of 2 x 256 records in shared memory
     const size_t wsmem = 2 * 2 * 256 * sizeof(typename RecOf<T>::type);
     static int per_sm = 0;                 // once per instantiation and process
@@ -1857,10 +1959,10 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
 }
 
 template int batch_launch<float, float>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
-                                        const StencilConfig &, int, int, bool, cudaStream_t);
+                                        const StencilConfig &, int, int, int, cudaStream_t);
 template int batch_launch<float, __nv_bfloat16>(wmibm_handle *, const Member<float> *, int, const KParams<float> &,
-                                                const StencilConfig &, int, int, bool, cudaStream_t);
+                                                const StencilConfig &, int, int, int, cudaStream_t);
 template int batch_launch<double, double>(wmibm_handle *, const Member<double> *, int, const KParams<double> &,
-                                          const StencilConfig &, int, int, bool, cudaStream_t);
+                                          const StencilConfig &, int, int, int, cudaStream_t);
 
 }  // namespace wmibm

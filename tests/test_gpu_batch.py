@@ -1,8 +1,9 @@
 """Batched ensembles: members of uneven grid sizes stepped together give, member
-by member, what single-terrain steps give, and match the FP64 oracle, in both
-batch forms: one cooperative launch with every member's band records as
-interleaved wall stages of the stencil pipeline (force_path 5, the default),
-and the batch wall kernel followed by the batch stencil (force_path 3)."""
+by member, what single-terrain steps give, and match the FP64 oracle, in every
+batch form: one cooperative launch with wall warps beside the stencil warps of
+every block (force_path 6, the default) or with every member's band records as
+interleaved wall stages of the stencil pipeline (force_path 5), and the batch
+wall kernel followed by the batch stencil (force_path 3)."""
 import numpy as np
 import pytest
 
@@ -103,10 +104,12 @@ BATCH_TUNINGS = [dict(rows=1, stages=3, consumer_warps=2), dict(rows=2, stages=5
                  dict(rows=4, stages=2, consumer_warps=4, blocks_per_sm=1),
                  dict(rows=2, stages=4, consumer_warps=6, wall_chunk=64),
                  dict(rows=4, stages=3, consumer_warps=3, wall_chunk=2048),
-                 dict(rows=1, stages=6, consumer_warps=4, wall_chunk=200)]
+                 dict(rows=1, stages=6, consumer_warps=4, wall_chunk=200),
+                 dict(rows=2, stages=3, consumer_warps=3, wall_warps=2),
+                 dict(rows=4, stages=2, consumer_warps=5, wall_warps=6)]
 
 
-@pytest.mark.parametrize("form", [3, 5])
+@pytest.mark.parametrize("form", [3, 5, 6])
 @pytest.mark.parametrize("tuning", range(len(BATCH_TUNINGS)))
 def test_batch_tunings(wm, oracle_mod, tuning, form):
     """Every batch form and a covering set of tile shapes and band-record chunks,
@@ -139,7 +142,7 @@ def test_batch_tunings(wm, oracle_mod, tuning, form):
     batch.close()
 
 
-@pytest.mark.parametrize("form", [3, 5])
+@pytest.mark.parametrize("form", [3, 5, 6])
 def test_batch_forms_bitwise_equal_and_replay(wm, form):
     """Both batch forms give the same stresses and forcing bit for bit (the same
     per-node arithmetic), from a CUDA graph replayed twice."""
@@ -180,7 +183,7 @@ def test_full_ensemble_64(wm, oracle_mod):
     handles = [wm.Handle.from_case(c) for c in cases]
     batch = wm.Batch(handles)
     out = {}
-    for form in (5, 3):
+    for form in (6, 5, 3):
         batch.set_tuning(force_path=form)
         fields = [_fields(c, "f32") for c in cases]
         batch.set_fields(fields)
@@ -230,7 +233,7 @@ def test_batch_wall_stress_force_equals_single_calls(wm):
     batch.close()
 
 
-@pytest.mark.parametrize("form", [3, 5])
+@pytest.mark.parametrize("form", [3, 5, 6])
 def test_batch_of_one(wm, oracle_mod, form):
     """A batch of a single member (its launch reads the member from the kernel
     parameters, not from the descriptor array) matches the oracle."""

@@ -5,7 +5,8 @@ The autotuner times these shapes and keeps the fastest, so the shape behind a
 benchmark number is one of them.  The forms are the single cooperative launch
 with the wall model in every block (force_path 1), the direct-load force
 kernel (2), the wall kernel followed by the pipelined stencil (3), dedicated
-wall blocks (4) and the band records as interleaved pipeline stages (5).  The
+wall blocks (4), the band records as interleaved pipeline stages (5) and wall
+warps beside the producer and consumers of every block (6).  The
 covering set gives each value of every field (rows per strip, stages, consumer
 warps, warps of the wall kernel, records per wall stage) at least once per form.
 The forcing and stress outputs start as NaN where the stage writes them, so a
@@ -33,6 +34,7 @@ SHAPES = {
     4: [(1, 3, 2, 0, 0), (2, 4, 4, 0, 0), (4, 3, 8, 0, 0), (2, 6, 6, 0, 0), (1, 2, 3, 0, 0)],
     5: [(1, 2, 2, 0, 0), (2, 3, 4, 0, 64), (4, 3, 8, 0, 512), (2, 6, 3, 0, 1024), (1, 5, 6, 0, 256),
         (4, 2, 4, 0, 4096)],
+    6: [(1, 2, 2, 1, 0), (2, 3, 4, 3, 0), (4, 3, 8, 4, 0), (2, 6, 3, 2, 0), (1, 5, 6, 8, 0), (4, 2, 4, 6, 0)],
 }
 CASES = [(fp, i) for fp in sorted(SHAPES) for i in range(len(SHAPES[fp]))]
 
@@ -112,7 +114,7 @@ def test_shape_against_oracle(wm, slab_ref, fp, i, dtype):
     h.close()
 
 
-@pytest.mark.parametrize("fp", [1, 3, 4, 5])
+@pytest.mark.parametrize("fp", [1, 3, 4, 5, 6])
 def test_shape_graph_replay_and_step(wm, oracle_mod, fp):
     """One shape per form captured in a CUDA graph and replayed twice (the launch
     re-arms its counters), then the whole step with the body mask (Eq. 27)."""
@@ -181,7 +183,7 @@ def test_batch_autotuner_keeps_a_shape_that_agrees(wm, oracle_mod):
     stats = batch.new_stats()
     res = autotune.tune_batch(batch, stats, reps=3, use_cache=False, budget_s=10.0)
     assert res["tuning"] and res["agreement"] <= autotune.AGREE["f32"]
-    assert set(res["forms_ms"]) <= {"interleaved", "two_launch"}
+    assert set(res["forms_ms"]) <= {"interleaved", "two_launch", "wall_warps"}
     for fl in fields:
         for t in fl[4]:
             t.fill_(float("nan"))
