@@ -298,6 +298,10 @@ typedef struct wmibm_tuning {
     int32_t direct_kc;        /* direct-load kernel: levels per thread */
     int32_t wall_chunk;       /* interleaved single launch (force_path 5): band records per wall
                                  stage, capped by a stage buffer (0: two per consumer thread) */
+    int32_t dyn_chunk;        /* pipelined stencil outside force_path 1, 4, 5: 0 gives every block a
+                                 fixed share of the (strip, level) units; n > 0 lets the blocks take
+                                 runs of units from a counter as they go (clean units, then dirty),
+                                 each run a share of what is left but at least n units */
 } wmibm_tuning;
 
 /* Sets / reads the tuning of handle h. EINVAL for out-of-range fields. */

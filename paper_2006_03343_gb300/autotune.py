@@ -5,8 +5,9 @@ over its forms -- one cooperative launch with the wall phase inside the
 pipelined stencil (a share in every block, dedicated wall blocks, the band
 records as interleaved pipeline stages, or wall warps beside the producer and
 consumers of every block), or the wall kernel followed by the stencil -- and a
-grid of tile shapes (rows per strip, shared-memory stages,
-consumer warps, warps of the wall kernel, band records per wall stage) with CUDA
+grid of tile shapes (rows per strip, shared-memory stages, consumer warps,
+warps of the wall kernel, band records per wall stage, units per take of the
+dynamic dispensing) with CUDA
 events on the launching stream (L2 flushed before every timed call), keeps the
 fastest, applies it to the handle and caches it in a JSON file keyed by GPU,
 precision and grid size.  A single-launch form is taken only when it beats the
@@ -16,8 +17,8 @@ the two-launch form is kept.
 A batch: the same for wmibm_batch_wall_stress_force over the batch forms (one
 cooperative launch with wall warps or with interleaved wall stages, or the
 batch wall kernel then the batch stencil), rows per strip of the widest
-members, stages, consumer warps, wall warps and band records per wall stage;
-cached by the members' grid sizes.
+members, stages, consumer warps, wall warps and the dynamic dispensing; cached
+by the members' grid sizes.
 
 Before a shape is kept, its forcing is compared with the forcing of the
 library's default shape on the same inputs: a shape whose result differs by
@@ -40,7 +41,8 @@ STAGES = (2, 3, 4, 5, 6)
 CONSUMERS = (2, 3, 4, 6, 8)
 WALL_WARPS = (4, 8)
 WALL_CHUNK_PER_THREAD = (0, 4)     # band records per consumer thread and wall stage (0: the library's default)
-WALL_WARPS_IN_BLOCK = (2, 3, 4)     # wall warps beside the producer and consumers (force_path 6)
+WALL_WARPS_IN_BLOCK = (1, 2, 3)     # wall warps beside the producer and consumers (force_path 6)
+DYN_CHUNKS = (0, 16)                # units per take of the dynamic dispensing (0: a fixed share per block)
 
 FORM_NAMES = {1: "single_launch", 2: "direct", 3: "two_launch", 4: "dedicated_wall_blocks", 5: "interleaved",
               6: "wall_warps"}
@@ -71,6 +73,12 @@ def batch_key_of(batch) -> str:
     return f"batch|{name}|{h0.dtype}|{h0.vel_dtype}|{len(batch.handles)}|{digest}"
 
 
+def ring_bytes(rows, stages, nx, es):
+    """Shared memory of the stencil's stage rings: `stages` half-A slots of 3 rows + 4
+    rows of nx elements and stages + 1 half-B slots of 3 rows + 2."""
+    return (stages * (3 * rows + 4) + (stages + 1) * (3 * rows + 2)) * nx * es
+
+
 def candidates(handle):
     nx, ny, nz = (int(x) for x in handle.grid[:3])
     es = 8 if handle.dtype == "f64" else 4
@@ -81,7 +89,7 @@ def candidates(handle):
     for rows, stages, cons in itertools.product(ROWS, STAGES, CONSUMERS):
         if ny % rows or ny < rows + 2:
             continue
-        if (6 * rows + 6) * nx * es * stages + 256 > SMEM_LIMIT:
+        if ring_bytes(rows, stages, nx, es) + 256 > SMEM_LIMIT:
             continue
         # one cooperative launch (wall share in every block, dedicated wall blocks,
         # or interleaved wall stages), or the wall kernel followed by the stencil
@@ -92,11 +100,14 @@ def candidates(handle):
             if per:
                 c["wall_chunk"] = per * 32 * cons
             out.append(c)
-        for ww in WALL_WARPS_IN_BLOCK:
-            if 1 + cons + ww <= 16:
-                out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww))
-        for wall in WALL_WARPS:
-            out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall))
+        for dyn in DYN_CHUNKS:
+            for ww in WALL_WARPS_IN_BLOCK:
+                if 1 + cons + ww <= 16:
+                    out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww,
+                                    dyn_chunk=dyn))
+            for wall in WALL_WARPS:
+                out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall,
+                                dyn_chunk=dyn))
     return out
 
 
@@ -105,20 +116,17 @@ def batch_candidates(batch):
     es = 8 if h0.dtype == "f64" else 4
     max_nx = max(int(h.grid[0]) for h in batch.handles)
     out = []
-    for rows, stages, cons in itertools.product(ROWS, (2, 3, 4, 5), CONSUMERS):
+    for rows, stages, cons in itertools.product((2, 4), (2, 3, 4), (2, 3, 4, 6)):
         # the widest members take `rows` rows per strip; narrower ones more, at about
         # the same stage bytes
-        if (6 * rows + 6) * max_nx * es * stages + 256 > SMEM_LIMIT:
+        if ring_bytes(rows, stages, max_nx, es) + 256 > SMEM_LIMIT:
             continue
-        out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons))
-        for per in (0, 4):
-            c = dict(force_path=5, rows=rows, stages=stages, consumer_warps=cons)
-            if per:
-                c["wall_chunk"] = per * 32 * cons
-            out.append(c)
-        for ww in WALL_WARPS_IN_BLOCK:
-            if 1 + cons + ww <= 16:
-                out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww))
+        out.append(dict(force_path=5, rows=rows, stages=stages, consumer_warps=cons))
+        for dyn in DYN_CHUNKS:
+            out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, dyn_chunk=dyn))
+            for ww in (1, 2, 3):
+                out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww,
+                                dyn_chunk=dyn))
     return out
 
 

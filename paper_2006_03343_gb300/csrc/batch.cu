@@ -26,7 +26,7 @@ struct wmibm_batch {
     int *status;
     int max_nx;
     std::vector<int> rows;      // rows per strip of each member's stencil
-    uint32_t stage_elems;       // elements of the largest member stage
+    uint32_t half_a, half_b;    // elements of the largest member's half-A and half-B stage slots
     int fields_set;
     wmibm_tuning tuning;
     StencilConfig cfg;
@@ -59,16 +59,17 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Tile shape of the batch: the widest members take `rows` x-rows per strip
 // (tuning.rows, default 4); narrower members take proportionally more rows (at
 // most 16, dividing ny) so that every member's stage carries about the same
-// bytes.  The stages hold the largest member stage; as many as fit ~110 KB (2..4)
-// unless the tuning sets them.
-bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out, uint32_t *stage_elems)
+// bytes.  The stage slots hold the largest member's stage halves; as many as fit
+// ~110 KB (2..4) unless the tuning sets them.
+bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out, uint32_t *half_a,
+                  uint32_t *half_b)
 {
     const size_t es = elem_size(b->dtype);
     const int V = 16 / (int)es;
     const int base = b->tuning.rows > 0 ? b->tuning.rows : 4;
     if (!(base == 1 || base == 2 || base == 4)) return false;
     std::vector<int> rows;
-    size_t elems = 0;
+    size_t ha = 0, hb = 0;
     for (auto *h : b->members) {
         if (h->nx % V != 0 || h->nz < 3 || h->ny < 3) return false;
         int target = (int)std::min<int64_t>(16, std::max<int64_t>(1, (int64_t)base * b->max_nx / h->nx));
@@ -80,29 +81,33 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
             }
         if (ty == 0) return false;
         rows.push_back(ty);
-        elems = std::max(elems, (size_t)(6 * ty + 6) * h->nx);
+        ha = std::max(ha, (size_t)(3 * ty + 4) * h->nx);
+        hb = std::max(hb, (size_t)(3 * ty + 2) * h->nx);
     }
-    const size_t stage_bytes = elems * es;
+    auto ring_bytes = [&](int s) { return ((size_t)s * ha + (size_t)(s + 1) * hb) * es; };
     int stages = b->tuning.stages;
     if (stages == 0) {
         stages = 4;
-        while (stages > 2 && (size_t)stages * stage_bytes > 110 * 1024) --stages;
+        while (stages > 2 && ring_bytes(stages) > 110 * 1024) --stages;
     }
-    if (stages < 2 || stages > 8 || (size_t)stages * stage_bytes + 256 > 200 * 1024) return false;
+    if (stages < 2 || stages > 8 || ring_bytes(stages) + 256 > 200 * 1024) return false;
     out->rows = 0;                 // per member
     out->stages = stages;
     out->consumer_warps = b->tuning.consumer_warps > 0 ? b->tuning.consumer_warps : 4;
     out->wall_warps = b->tuning.wall_warps;
     out->blocks_per_sm = b->tuning.blocks_per_sm;
     out->wall_chunk = b->tuning.wall_chunk;
+    out->dyn_chunk = b->tuning.dyn_chunk;
     // one launch (force_path 0 or 6: wall warps; 5: interleaved wall stages) or two launches (3)
+    if (b->tuning.dyn_chunk < 0 || b->tuning.dyn_chunk > 4096) return false;
     const int fp = b->tuning.force_path;
     if (!(fp == 0 || fp == 3 || fp == 5 || fp == 6)) return false;
     if (fp != 3 && fp != 5 && 1 + out->consumer_warps + (out->wall_warps > 0 ? out->wall_warps : 3) > 16)
         return false;
     if (1 + out->consumer_warps > 16) return false;
     *rows_out = rows;
-    *stage_elems = (uint32_t)elems;
+    *half_a = (uint32_t)ha;
+    *half_b = (uint32_t)hb;
     return true;
 }
 
@@ -156,7 +161,8 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
     p.ticket = b->ticket;
     p.stats = stats;
     p.bstats = b->bstats;
-    p.stage_elems = b->stage_elems;
+    p.half_a = b->half_a;
+    p.half_b = b->half_b;
     if (b->count == 1) memcpy(&p.one, b->member0.data(), sizeof(Member<T>));   // kernels read p.one then
     p.wall_done = b->ticket + 1;
     p.exit_ticket = b->ticket + 2;
@@ -198,14 +204,15 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
     cudaError_t e = cudaMalloc(&b->dev_members, msize * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->bstats, sizeof(double) * 8 * count);
     // [0] last-block ticket of the batch wall kernel; [1] wall-done and [2] exit
-    // counters of the interleaved launch (all back at 0 after every launch)
-    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, 4 * sizeof(unsigned));
+    // counters of the single launch; [4..7] the two 64-bit counters of the dynamic
+    // dispensing (all back at 0 after every launch)
+    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, 8 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bstats, 0, sizeof(double) * 8 * count, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, 4 * sizeof(unsigned), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, 8 * sizeof(unsigned), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
-    if (e != cudaSuccess || !batch_config(b, &b->cfg, &b->rows, &b->stage_elems)) {
+    if (e != cudaSuccess || !batch_config(b, &b->cfg, &b->rows, &b->half_a, &b->half_b)) {
         cudaFree(b->dev_members);
         cudaFree(b->bstats);
         cudaFree(b->ticket);
@@ -254,14 +261,15 @@ extern "C" int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t)
     b->tuning = *t;
     StencilConfig c;
     std::vector<int> rows;
-    uint32_t elems = 0;
-    if (!batch_config(b, &c, &rows, &elems)) {
+    uint32_t ha = 0, hb = 0;
+    if (!batch_config(b, &c, &rows, &ha, &hb)) {
         b->tuning = old;
         return berr(b, WMIBM_EINVAL, "tuning does not fit every member");
     }
     b->cfg = c;
     b->rows = rows;
-    b->stage_elems = elems;
+    b->half_a = ha;
+    b->half_b = hb;
     b->fields_set = 0;       // unit offsets depend on the rows per strip: set the fields again
     return WMIBM_OK;
 }

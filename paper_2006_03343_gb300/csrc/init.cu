@@ -459,8 +459,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         TRY(cudaMalloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
         // [0] last-block ticket of the wall kernel, [1] wall-done and [2] exit counters of
         // the fused step launch; all stay 0 between calls
-        TRY(cudaMalloc(&h->ticket, 4 * sizeof(unsigned int)), "cudaMalloc ticket");
-        TRY(cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned int), stream), "memset ticket");
+        TRY(cudaMalloc(&h->ticket, 8 * sizeof(unsigned int)), "cudaMalloc ticket");
+        TRY(cudaMemsetAsync(h->ticket, 0, 8 * sizeof(unsigned int), stream), "memset ticket");
         TRY(cudaMalloc(&h->sacc, 8 * sizeof(double)), "cudaMalloc stats accumulator");
         TRY(cudaMemsetAsync(h->sacc, 0, 8 * sizeof(double), stream), "memset stats accumulator");
 
@@ -642,6 +642,7 @@ extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
     if (!t) return set_error(h, WMIBM_EINVAL, "NULL tuning");
     if (t->force_path < 0 || t->force_path > 6) return set_error(h, WMIBM_EINVAL, "force_path must be 0..6");
     if (t->wall_chunk < 0 || t->wall_chunk > 65536) return set_error(h, WMIBM_EINVAL, "wall_chunk must be 0..65536");
+    if (t->dyn_chunk < 0 || t->dyn_chunk > 4096) return set_error(h, WMIBM_EINVAL, "dyn_chunk must be 0..4096");
     if (!(t->rows == 0 || t->rows == 1 || t->rows == 2 || t->rows == 4))
         return set_error(h, WMIBM_EINVAL, "rows must be 0, 1, 2 or 4");
     if (t->stages != 0 && (t->stages < 2 || t->stages > 8)) return set_error(h, WMIBM_EINVAL, "stages must be 2..8");

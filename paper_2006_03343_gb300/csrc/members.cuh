@@ -34,8 +34,8 @@ struct KParams {
     const Member<T> *list;        // device array of members (nmembers > 1)
     int nmembers;
     int64_t clean_total, dirty_total, rec_total, run_total, body_total;
-    int stages, ncons;
-    uint32_t stage_elems;
+    int stages, ncons;            // stages: depth of the ring of half A (half B has one more slot)
+    uint32_t half_a, half_b;      // elements of a half-A and a half-B slot (the largest member's)
     int *status;
     int do_mask;
     // statistics: single terrain -> per-block partials reduced by the last block;
@@ -66,6 +66,11 @@ struct KParams {
     // warp-specialized single-launch stage: warps [1 + ncons, 1 + ncons + wall_warps)
     // of every block evaluate the block's slice of the band records and solid runs
     int wall_warps;
+    // dynamic dispensing (dyn_chunk > 0): the producers take runs of dyn_chunk units
+    // from the counters dyn_ctr[0] (clean units) and dyn_ctr[1] (dirty units), back
+    // at 0 after every launch, instead of a fixed share per block
+    int dyn_chunk;
+    unsigned long long *dyn_ctr;
 };
 
 template <typename T>

@@ -8,11 +8,13 @@
 // persistent grid.  Per block, lane 0 of warp 0 is the producer: it issues 1D
 // bulk copies of the rows a stage needs into a ring of S shared-memory stages
 // and arms the stage's "full" mbarrier with the byte count.  A stage at level k
-// holds
-//   txx, tzz at k (TY rows), txy, tyy at k (TY + 2 rows: y-halo),
-//   txz at k+1 (TY rows), tyz at k+1 (TY + 2 rows)
-// and the stage before it supplies txz, tyz at k and tzz at k-1, so every
-// stress row is fetched from HBM once per strip.  A segment (consecutive
+// has two halves in two rings of shared-memory slots:
+//   half A: txx at k (TY rows), txy, tyy at k (TY + 2 rows: y-halo)
+//   half B: tzz at k (TY rows), txz at k+1 (TY rows), tyz at k+1 (TY + 2 rows)
+// and the half B of the stage before it supplies txz, tyz at k and tzz at k-1,
+// so every stress row is fetched from HBM once per strip.  Half A is released
+// as soon as its stage is consumed, half B after the next stage: the ring of
+// half B has one slot more, and the producer runs (stages - 1) stages ahead.  A segment (consecutive
 // levels of one strip of one member) starts with a prologue stage that holds
 // only tzz at k-1 and txz, tyz at k.  Consumer warps form f for the TY rows,
 // with x-neighbours from warp shuffles and periodic wrap inside the staged full
@@ -204,6 +206,7 @@ struct StageIter {
     bool prologue, done, dirty, new_member;
     // interleaved form
     bool inter, wall, sdone;      // wall: the current stage is a wall stage; sdone: no unit left
+    bool dyn;                     // units taken in runs from the launch's counters (producer only)
     int64_t wf, wn, wj, wrec;     // first wall item, wall stages, next wall stage, items with records
     int64_t nclean, cdone;        // the block's clean units, clean main stages emitted
 
@@ -253,9 +256,36 @@ struct StageIter {
     }
     __device__ void settle()
     {
-        while (phase < 2 && idx >= (phase == 0 ? c1 : d1)) {
-            ++phase;
-            idx = d0;
+        if (dyn) {
+            // take the next run of units of the current phase (guided: a share of
+            // what is left, at least dyn_chunk units, so that the runs are long while
+            // much is left and short towards the end); when the phase's counter has
+            // passed its total, move on to the dirty units, then stop
+            while (phase < 2 && idx >= (phase == 0 ? c1 : d1)) {
+                const int64_t total = phase == 0 ? pp->clean_total : pp->dirty_total;
+                unsigned long long *ctr = pp->dyn_ctr + phase;
+                const int64_t seen = (int64_t)*(volatile unsigned long long *)ctr;
+                int64_t take = (total - seen) / (2 * (int64_t)gridDim.x);
+                if (take < pp->dyn_chunk) take = pp->dyn_chunk;
+                const int64_t lo = (int64_t)atomicAdd(ctr, (unsigned long long)take);
+                if (lo < total) {
+                    idx = lo;
+                    const int64_t hi = min(total, lo + take);
+                    if (phase == 0)
+                        c1 = hi;
+                    else
+                        d1 = hi;
+                } else {
+                    ++phase;
+                    idx = 0;
+                    d1 = 0;
+                }
+            }
+        } else {
+            while (phase < 2 && idx >= (phase == 0 ? c1 : d1)) {
+                ++phase;
+                idx = d0;
+            }
         }
         sdone = phase >= 2;
         if (!sdone) {
@@ -285,6 +315,10 @@ struct StageIter {
         phase = 0;
         idx = c0;
         new_member = false;
+        dyn = p.dyn_chunk > 0;
+        if (dyn) {
+            idx = c1 = d0 = d1 = 0;
+        }
         inter = p.interleave != 0;
         nclean = c1 - c0;
         cdone = 0;
@@ -352,12 +386,14 @@ struct StageIter {
     }
 };
 
-// First row of each stress slot in a stage of ty-row strips (compile-time
-// constants when the row count is a template argument).
+// First row of each stress slot in the two halves of a stage of ty-row strips
+// (compile-time constants when the row count is a template argument): half A
+// holds 3 ty + 4 rows, half B 3 ty + 2.
 struct Slots {
-    int XX, XY, YY, ZZ, XZ, YZ;
+    int XX, XY, YY;   // half A
+    int ZZ, XZ, YZ;   // half B
     __device__ __forceinline__ explicit Slots(int ty)
-        : XX(0), XY(ty), YY(2 * ty + 2), ZZ(3 * ty + 4), XZ(4 * ty + 4), YZ(5 * ty + 4) {}
+        : XX(0), XY(ty), YY(2 * ty + 2), ZZ(0), XZ(ty), YZ(2 * ty) {}
 };
 
 // Waits until the preceding kernel of the stream (the wall kernel) has
@@ -417,9 +453,15 @@ __device__ __forceinline__ unsigned wall_target(int wall_blocks)
 // done (the rest waits, so that the wall model's gathers meet a quiet memory system).
 constexpr uint32_t kStagesBeforeWall = 1;
 
+// Stage header of the dynamic dispensing (producer -> consumers): member, strip,
+// level and flags.
+constexpr int kHdrPrologue = 1, kHdrNewMember = 2, kHdrDone = 4;
+
 template <typename T, int TY, int MODE>
-__device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *empty, uint64_t *wallbar)
+__device__ void produce(const KParams<T> &p, T *ring_a, T *ring_b, uint64_t *full, uint64_t *empty_a,
+                        uint64_t *empty_b, uint64_t *wallbar, int4 *hdr)
 {
+    const uint32_t SA = (uint32_t)p.stages, SB = SA + 1;
     ProdView<T> v;
     uint32_t g = 0;
     bool released = MODE == kPlain;
@@ -429,17 +471,16 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
         if (MODE == kFused && p.wall_blocks == 0 && g == kStagesBeforeWall) {
             if (!mbar_wait(wallbar, 0u, p.status, kDevStatusBarrierTimeout)) break;
         }
-        const int b = (int)(g % (uint32_t)p.stages);
-        if (g >= (uint32_t)p.stages) {
-            if (!mbar_wait(&empty[b], ((g / p.stages) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
-        }
+        const int b = (int)(g % SA), bb = (int)(g % SB);
+        if (g >= SA && !mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
+        if (g >= SB && !mbar_wait(&empty_b[bb], ((g / SB) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
         if (MODE == kInterleaved && it.wall) {
             // a wall stage: the item's band records, one bulk copy per member segment
             using Rec = typename RecOf<T>::type;
             int64_t a, e;
             it.wall_range(a, e);
             mbar_arrive_expect_tx(&full[b], (uint32_t)((e - a) * (int64_t)sizeof(Rec)));
-            Rec *const dst = reinterpret_cast<Rec *>(data + (size_t)b * p.stage_elems);
+            Rec *const dst = reinterpret_cast<Rec *>(ring_a + (size_t)b * p.half_a);
             int wm = (p.nmembers == 1 || e <= a) ? 0 : find_member_at(p, &Member<T>::r_off, a);
             for (int64_t pos = a; pos < e && wm < p.nmembers; ++wm) {
                 const Member<T> &mm = p.nmembers == 1 ? p.one : p.list[wm];
@@ -462,19 +503,23 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
             asm volatile("fence.proxy.async.global;" ::: "memory");
             released = true;
         }
+        if (it.dyn)   // released to the consumers by the arrive below
+            hdr[b] = make_int4(it.m, it.s, it.k, (it.prologue ? kHdrPrologue : 0) | (it.new_member ? kHdrNewMember : 0));
         const int32_t nx = v.nx, ny = v.ny;
         const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
         const int64_t plane = (int64_t)nx * ny;
-        T *st = data + (size_t)b * p.stage_elems;
+        T *const sta = ring_a + (size_t)b * p.half_a;
+        T *const stb = ring_b + (size_t)bb * p.half_b;
         const int ty = TY > 0 ? TY : v.ty;     // rows per strip (template or per member)
         const Slots S_(ty);
         const int32_t j0 = it.s * ty;
         const int32_t k = it.k;
         // rows [jstart, jstart + cnt) of one level (periodic in j) into consecutive
-        // slot rows: one bulk copy per contiguous piece (two where the interval wraps)
-        auto issue = [&](const T *arr, int32_t lev, int32_t jstart, int32_t cnt, int32_t slot) {
+        // slot rows of a half: one bulk copy per contiguous piece (two where the
+        // interval wraps)
+        auto issue = [&](const T *arr, int32_t lev, int32_t jstart, int32_t cnt, T *half, int32_t slot) {
             const T *base = arr + (int64_t)lev * plane;
-            T *dst = st + (size_t)slot * nx;
+            T *dst = half + (size_t)slot * nx;
             if (jstart < 0) {
                 bulk_g2s(dst, base + (int64_t)(ny - 1) * nx, row_bytes, &full[b]);
                 bulk_g2s(dst + nx, base, (uint32_t)(cnt - 1) * row_bytes, &full[b]);
@@ -491,36 +536,44 @@ __device__ void produce(const KParams<T> &p, T *data, uint64_t *full, uint64_t *
         if (it.prologue) {
             const uint32_t rows = (k > 0 ? ty : 0) + ty + (ty + 2);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
-            if (k > 0) issue(tzz, k - 1, j0, ty, S_.ZZ);
-            issue(txz, k, j0, ty, S_.XZ);
-            issue(tyz, k, j0 - 1, ty + 2, S_.YZ);
+            if (k > 0) issue(tzz, k - 1, j0, ty, stb, S_.ZZ);
+            issue(txz, k, j0, ty, stb, S_.XZ);
+            issue(tyz, k, j0 - 1, ty + 2, stb, S_.YZ);
         } else {
             const bool up = k + 1 < v.nz;
             const uint32_t rows = ty + 2 * (ty + 2) + ty + (up ? ty + (ty + 2) : 0);
             mbar_arrive_expect_tx(&full[b], rows * row_bytes);
-            issue(txx, k, j0, ty, S_.XX);
-            issue(txy, k, j0 - 1, ty + 2, S_.XY);
-            issue(tyy, k, j0 - 1, ty + 2, S_.YY);
-            issue(tzz, k, j0, ty, S_.ZZ);
+            issue(txx, k, j0, ty, sta, S_.XX);
+            issue(txy, k, j0 - 1, ty + 2, sta, S_.XY);
+            issue(tyy, k, j0 - 1, ty + 2, sta, S_.YY);
+            issue(tzz, k, j0, ty, stb, S_.ZZ);
             if (up) {
-                issue(txz, k + 1, j0, ty, S_.XZ);
-                issue(tyz, k + 1, j0 - 1, ty + 2, S_.YZ);
+                issue(txz, k + 1, j0, ty, stb, S_.XZ);
+                issue(tyz, k + 1, j0 - 1, ty + 2, stb, S_.YZ);
             }
         }
     }
     if (!it.done) {
         // gave up: let the copies already issued land before the block exits
-        const uint32_t first = g > (uint32_t)p.stages ? g - p.stages : 0;
-        for (uint32_t q = first; q < g; ++q) mbar_drain(&full[q % p.stages], (q / p.stages) & 1u);
+        const uint32_t first = g > SA ? g - SA : 0;
+        for (uint32_t q = first; q < g; ++q) mbar_drain(&full[q % SA], (q / SA) & 1u);
+    } else if (it.dyn) {
+        // one more stage that only tells the consumers there is nothing left
+        const int b = (int)(g % SA);
+        if (g < SA || mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) {
+            hdr[b] = make_int4(0, 0, 0, kHdrDone);
+            mbar_arrive_expect_tx(&full[b], 0u);
+        }
     }
 }
 
 // ------------------------------------------------------------------------- //
 // consumers: f for the TY rows of a main stage
 // ------------------------------------------------------------------------- //
+// cur: half A of the stage; curb, prvb: half B of the stage and of the one before.
 template <typename T, int TY>
-__device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, const T *prv, int32_t k, int32_t j0,
-                              int cw, int lane)
+__device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, const T *curb, const T *prv,
+                              int32_t k, int32_t j0, int cw, int lane)
 {
     const int ty = TY > 0 ? TY : cv.ty;         // rows per strip (template or per member)
     const Slots S_(ty);
@@ -575,7 +628,7 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
             T xxl, xxr;
             x_neighbours(XXr, xx, xxl, xxr);
             const Pack<T> xym = lds(cur + (S_.XY + r) * nx + i), xyp = lds(cur + (S_.XY + r + 2) * nx + i);
-            const Pack<T> xz1 = lds(cur + (S_.XZ + r) * nx + i);
+            const Pack<T> xz1 = lds(curb + (S_.XZ + r) * nx + i);
             const Pack<T> xz0 = lds(prv + (S_.XZ + r) * nx + i);
             Pack<T> Fx;
 #pragma unroll
@@ -591,7 +644,7 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
             T xyl, xyr;
             x_neighbours(XYc, xy, xyl, xyr);
             const Pack<T> yym = lds(cur + (S_.YY + r) * nx + i), yyp = lds(cur + (S_.YY + r + 2) * nx + i);
-            const Pack<T> yz1 = lds(cur + (S_.YZ + r + 1) * nx + i);
+            const Pack<T> yz1 = lds(curb + (S_.YZ + r + 1) * nx + i);
             const Pack<T> yz0 = lds(prv + (S_.YZ + r + 1) * nx + i);
             Pack<T> Fy;
 #pragma unroll
@@ -607,7 +660,7 @@ __device__ void consume_level(const ConsView<T> &cv, int ncons, const T *cur, co
             T xzl, xzr;
             x_neighbours(XZ0, xz0, xzl, xzr);
             const Pack<T> yz0m = lds(prv + (S_.YZ + r) * nx + i), yz0p = lds(prv + (S_.YZ + r + 2) * nx + i);
-            const Pack<T> zz = lds(cur + (S_.ZZ + r) * nx + i);
+            const Pack<T> zz = lds(curb + (S_.ZZ + r) * nx + i);
             Pack<T> zzm;
             if (!bottom)
                 zzm = lds(prv + (S_.ZZ + r) * nx + i);
@@ -634,12 +687,48 @@ __device__ void wall_stage(const KParams<T> &p, const typename RecOf<T>::type *r
                            bool first, bool last, int cw, int lane, unsigned *warps_done);
 
 template <typename T, typename VEL, int TY, int MODE>
-__device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint64_t *empty, int cw, int lane,
-                        T (*red)[kStatVals], uint64_t *wallbar, unsigned *warps_done)
+__device__ void consume(const KParams<T> &p, const T *ring_a, const T *ring_b, uint64_t *full, uint64_t *empty_a,
+                        uint64_t *empty_b, int cw, int lane, T (*red)[kStatVals], uint64_t *wallbar,
+                        unsigned *warps_done, const int4 *hdr)
 {
     ConsView<T> cv;
     uint32_t g = 0;
-    int prevb = -1;
+    const uint32_t SA = (uint32_t)p.stages, SB = SA + 1;
+    // after stage g: its half A is free, and the half B of the stage before it
+    auto release = [&](uint32_t gg) {
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&empty_a[gg % SA]);
+            if (gg > 0) mbar_arrive(&empty_b[(gg - 1) % SB]);
+        }
+    };
+    if (p.dyn_chunk > 0) {
+        // dynamic dispensing: the unit of each stage comes in its header
+        for (;; ++g) {
+            const int b = (int)(g % SA);
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout)))
+                break;
+            const volatile int *hv = reinterpret_cast<const volatile int *>(&hdr[b]);
+            const int4 hd = make_int4(hv[0], hv[1], hv[2], hv[3]);
+            if (hd.w & kHdrDone) break;
+            if (hd.w & kHdrNewMember) {
+                load_cons(p, hd.x, cv);
+                constexpr int V = VecOf<T>::V;
+                cv.nq = cv.nx / V;
+                const int first = cw * 32 + lane, step = p.ncons * 32;
+                cv.r0 = first / cv.nq;
+                cv.q0 = first - cv.r0 * cv.nq;
+                cv.dr = step / cv.nq;
+                cv.dq = step - cv.dr * cv.nq;
+            }
+            if (!(hd.w & kHdrPrologue))
+                consume_level<T, TY>(cv, p.ncons, ring_a + (size_t)b * p.half_a, ring_b + (size_t)(g % SB) * p.half_b,
+                                     ring_b + (size_t)((g + SB - 1) % SB) * p.half_b, hd.z,
+                                     hd.y * (TY > 0 ? TY : cv.ty), cw, lane);
+            release(g);
+        }
+        return;
+    }
     if (MODE == kFused && p.wall_blocks == 0) {
         // the block's wall share first, while the memory system is quiet; then
         // let the producer stream
@@ -658,24 +747,21 @@ __device__ void consume(const KParams<T> &p, const T *data, uint64_t *full, uint
             cv.dr = step / cv.nq;
             cv.dq = step - cv.dr * cv.nq;
         }
-        const int b = (int)(g % (uint32_t)p.stages);
+        const int b = (int)(g % SA);
         // the whole warp gives up together, so that no lane is left behind at a warp-wide operation
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / p.stages) & 1u, p.status, kDevStatusFullTimeout)))
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout)))
             break;
         if (MODE == kInterleaved && it.wall) {
             int64_t a, e;
             it.wall_range(a, e);
-            wall_stage<T, VEL>(p, reinterpret_cast<const typename RecOf<T>::type *>(data + (size_t)b * p.stage_elems),
+            wall_stage<T, VEL>(p, reinterpret_cast<const typename RecOf<T>::type *>(ring_a + (size_t)b * p.half_a),
                                a, e, it.wj == 0, it.wj == it.wn - 1, cw, lane, warps_done);
         } else if (!it.prologue) {
-            consume_level<T, TY>(cv, p.ncons, data + (size_t)b * p.stage_elems, data + (size_t)prevb * p.stage_elems,
-                                 it.k, it.s * (TY > 0 ? TY : cv.ty), cw, lane);
+            consume_level<T, TY>(cv, p.ncons, ring_a + (size_t)b * p.half_a, ring_b + (size_t)(g % SB) * p.half_b,
+                                 ring_b + (size_t)((g + SB - 1) % SB) * p.half_b, it.k,
+                                 it.s * (TY > 0 ? TY : cv.ty), cw, lane);
         }
-        if (prevb >= 0) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[prevb]);
-        }
-        prevb = b;
+        release(g);
     }
 }
 
@@ -1408,17 +1494,22 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
     __shared__ uint64_t wallbar; // fused: the block's wall share is done
     __shared__ int s_go;        // consumers: the wall model is complete (mask may run)
     __shared__ unsigned s_wall_warps;   // interleaved: consumer warps done with the block's wall stages
+    __shared__ int4 s_hdr[8];           // dynamic dispensing: the unit of each stage
     __shared__ int s_last;      // the block is the last one out of a single-launch stage
+    // barriers: full[8] (per half-A slot), empty_a[8], empty_b[9]; then the two rings
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
-    uint64_t *empty = full + 8;
-    T *data = reinterpret_cast<T *>(smem_raw + 256);
+    uint64_t *empty_a = full + 8;
+    uint64_t *empty_b = full + 16;
+    T *ring_a = reinterpret_cast<T *>(smem_raw + 256);
+    T *ring_b = ring_a + (size_t)p.stages * p.half_a;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int b = 0; b < p.stages; ++b) {
             mbar_init(&full[b], 1);
-            mbar_init(&empty[b], p.ncons);
+            mbar_init(&empty_a[b], p.ncons);
         }
+        for (int b = 0; b <= p.stages; ++b) mbar_init(&empty_b[b], p.ncons);
         mbar_init(&wallbar, 1);
         fence_mbar_init();
         s_wall_warps = 0;
@@ -1438,14 +1529,15 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
     } else if (warp == 0) {
         // producer: clean stages right away (their rows hold no band or solid
         // entry), dirty stages once the wall model is complete
-        if (lane == 0) produce<T, TY, MODE>(p, data, full, empty, &wallbar);
+        if (lane == 0) produce<T, TY, MODE>(p, ring_a, ring_b, full, empty_a, empty_b, &wallbar, s_hdr);
         __syncwarp();
     } else if (MODE == kWarpSpec && warp > p.ncons) {
         // wall warps: the block's slice of the band records and solid runs
         wall_warps_run<T, VEL>(p, warp - 1 - p.ncons, p.wall_warps, lane, &s_wall_warps);
     } else {
         const int cw = warp - kFirstConsumer;
-        consume<T, VEL, TY, MODE>(p, data, full, empty, cw, lane, red, &wallbar, &s_wall_warps);
+        consume<T, VEL, TY, MODE>(p, ring_a, ring_b, full, empty_a, empty_b, cw, lane, red, &wallbar, &s_wall_warps,
+                                  s_hdr);
         if (MODE != kPlain && p.do_mask) {
             // the body mask may change the velocity only after every band stencil read it
             bool go = true;
@@ -1503,6 +1595,22 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
             __syncthreads();
             if (threadIdx.x == 0) {
                 atomicExch(p.wall_done, 0u);
+                if (p.dyn_chunk > 0) {
+                    atomicExch(p.dyn_ctr, 0ull);
+                    atomicExch(p.dyn_ctr + 1, 0ull);
+                }
+                atomicExch(p.exit_ticket, 0u);
+            }
+        }
+    } else if (p.dyn_chunk > 0) {
+        // the last block out re-arms the dispensing counters for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(p.exit_ticket, 1u) == gridDim.x - 1) {
+                __threadfence();
+                atomicExch(p.dyn_ctr, 0ull);
+                atomicExch(p.dyn_ctr + 1, 0ull);
                 atomicExch(p.exit_ticket, 0u);
             }
         }
@@ -1522,10 +1630,16 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
         if (e != cudaSuccess) return cuda_status(h, e, "stencil smem attribute");
         attr_done = true;
     }
-    // TY == 0 (rows per member): the caller sets stage_elems to the largest member stage
-    if (TY > 0) p.stage_elems = (uint32_t)((6 * TY + 6) * max_nx);
-    const size_t smem = 256 + (size_t)c.stages * p.stage_elems * sizeof(T);
+    // TY == 0 (rows per member): the caller sets the halves to the largest member's
+    if (TY > 0) {
+        p.half_a = (uint32_t)((3 * TY + 4) * max_nx);
+        p.half_b = (uint32_t)((3 * TY + 2) * max_nx);
+    }
+    const size_t smem = 256 + ((size_t)c.stages * p.half_a + (size_t)(c.stages + 1) * p.half_b) * sizeof(T);
     if (smem > (size_t)kMaxDynSmem) return set_error(h, WMIBM_EINVAL, "stencil stages exceed shared memory");
+    // dynamic dispensing where the consumers do not walk the stage sequence themselves
+    p.dyn_chunk = (MODE == kFused || MODE == kInterleaved) ? 0 : c.dyn_chunk;
+    p.dyn_ctr = reinterpret_cast<unsigned long long *>(p.ticket + 4);
     if (MODE == kWarpSpec) {
         p.wall_warps = c.wall_warps > 0 ? c.wall_warps : 3;
         if (1 + p.ncons + p.wall_warps > 16) return set_error(h, WMIBM_EINVAL, "more than 16 warps per block");
@@ -1535,7 +1649,7 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     // occupancy of this shape, cached in the handle
     const int64_t key = (int64_t)MODE | ((int64_t)TY << 4) | ((int64_t)c.stages << 8) |
                         ((int64_t)c.consumer_warps << 12) | ((int64_t)(MODE == kWarpSpec ? p.wall_warps : 0) << 16) |
-                        ((int64_t)(TY > 0 ? max_nx : (int)p.stage_elems) << 20);
+                        ((int64_t)(TY > 0 ? max_nx : (int)p.half_a) << 20);
     int per_sm = 0;
     for (int q = 0; q < 8; ++q)
         if (h->occ_key[q] == key) per_sm = h->occ_val[q];
@@ -1555,7 +1669,7 @@ int launch_stencil_ty(wmibm_handle *h, KParams<T> &p, const StencilConfig &c, cu
     if (MODE == kInterleaved) {
         // wall items: slices of wall_chunk band records, each staged in one stage buffer
         using Rec = typename RecOf<T>::type;
-        const int64_t cap = (int64_t)p.stage_elems * (int64_t)sizeof(T) / (int64_t)sizeof(Rec);
+        const int64_t cap = (int64_t)p.half_a * (int64_t)sizeof(T) / (int64_t)sizeof(Rec);
         int64_t q = c.wall_chunk > 0 ? c.wall_chunk : 2 * 32 * (int64_t)p.ncons;
         if (q > cap) q = cap;
         if (q < 1) return set_error(h, WMIBM_EINVAL, "stencil stage holds no band record");
@@ -1629,7 +1743,8 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.body_total = m.nbody_w + m.nbody_uv;
     p.stages = 2;
     p.ncons = 1;
-    p.stage_elems = 0;
+    p.half_a = 0;
+    p.half_b = 0;
     p.status = h->dev_status;
     p.do_mask = 0;
     p.partials = (T *)h->partials;
@@ -1645,6 +1760,8 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.wall_chunk = 0;
     p.wall_items = 0;
     p.wall_warps = 0;
+    p.dyn_chunk = 0;
+    p.dyn_ctr = nullptr;
 }
 
 template <typename T, typename VEL>
@@ -1748,29 +1865,33 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     for (int a = 0; a < 3; ++a)
         if (!aligned16(f[a])) return false;
     StencilConfig c;
-    auto stage_bytes_of = [&](int rows) { return (size_t)(6 * rows + 6) * h->nx * es; };
+    // shared memory of the two rings: `stages` half-A slots of 3 ty + 4 rows of nx
+    // elements and stages + 1 half-B slots of 3 ty + 2 rows
+    auto ring_bytes = [&](int rows, int stages) {
+        return ((size_t)stages * (3 * rows + 4) + (size_t)(stages + 1) * (3 * rows + 2)) * h->nx * es;
+    };
     c.rows = h->tuning.rows;
     c.stages = h->tuning.stages;
     if (c.rows == 0) {
         // default: 2-row strips with at least 3 stages within ~110 KB of shared
         // memory (two or three blocks per SM); 1-row strips when rows are wide
         c.rows = (h->ny % 2 == 0 && h->ny >= 4) ? 2 : 1;
-        if (c.rows == 2 && c.stages == 0 && 3 * stage_bytes_of(2) > 110 * 1024) c.rows = 1;
+        if (c.rows == 2 && c.stages == 0 && ring_bytes(2, 3) > 110 * 1024) c.rows = 1;
     }
     if (!(c.rows == 1 || c.rows == 2 || c.rows == 4)) return false;
     if (h->ny % c.rows != 0 || h->ny < c.rows + 2) return false;
-    const size_t stage_bytes = stage_bytes_of(c.rows);
     if (c.stages == 0) {
         c.stages = 4;
-        while (c.stages > 2 && (size_t)c.stages * stage_bytes > 110 * 1024) --c.stages;
+        while (c.stages > 2 && ring_bytes(c.rows, c.stages) > 110 * 1024) --c.stages;
     }
     if (c.stages < 2 || c.stages > 8) return false;
-    if ((size_t)c.stages * stage_bytes + 256 > (size_t)kMaxDynSmem) return false;
+    if (ring_bytes(c.rows, c.stages) + 256 > (size_t)kMaxDynSmem) return false;
     c.consumer_warps = h->tuning.consumer_warps > 0 ? h->tuning.consumer_warps : 4;
     c.wall_warps = h->tuning.wall_warps;
     if (1 + c.consumer_warps > 16) return false;
     c.blocks_per_sm = h->tuning.blocks_per_sm;
     c.wall_chunk = h->tuning.wall_chunk;
+    c.dyn_chunk = h->tuning.dyn_chunk;
     *out = c;
     return true;
 }

@@ -106,7 +106,9 @@ BATCH_TUNINGS = [dict(rows=1, stages=3, consumer_warps=2), dict(rows=2, stages=5
                  dict(rows=4, stages=3, consumer_warps=3, wall_chunk=2048),
                  dict(rows=1, stages=6, consumer_warps=4, wall_chunk=200),
                  dict(rows=2, stages=3, consumer_warps=3, wall_warps=2),
-                 dict(rows=4, stages=2, consumer_warps=5, wall_warps=6)]
+                 dict(rows=4, stages=2, consumer_warps=5, wall_warps=6),
+                 dict(rows=4, stages=3, consumer_warps=4, wall_warps=3, dyn_chunk=1),
+                 dict(rows=2, stages=3, consumer_warps=3, wall_warps=2, dyn_chunk=13)]
 
 
 @pytest.mark.parametrize("form", [3, 5, 6])

@@ -300,8 +300,8 @@ def test_fused_equals_separate_calls(wm):
 def test_set_tuning_rejects_bad_fields(wm):
     case = inputs.ridge(shape=(16, 8, 8))
     h = wm.Handle.from_case(case, dtype="f32")
-    for bad in (dict(rows=3), dict(stages=9), dict(consumer_warps=13), dict(force_path=6), dict(wall_chunk=-1),
-                dict(wall_chunk=65537)):
+    for bad in (dict(rows=3), dict(stages=9), dict(consumer_warps=13), dict(force_path=7), dict(wall_chunk=-1),
+                dict(wall_chunk=65537), dict(dyn_chunk=-1), dict(dyn_chunk=4097)):
         with pytest.raises(wm.WmibmError):
             h.set_tuning(**bad)
 

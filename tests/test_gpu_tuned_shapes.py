@@ -8,7 +8,8 @@ kernel (2), the wall kernel followed by the pipelined stencil (3), dedicated
 wall blocks (4), the band records as interleaved pipeline stages (5) and wall
 warps beside the producer and consumers of every block (6).  The
 covering set gives each value of every field (rows per strip, stages, consumer
-warps, warps of the wall kernel, records per wall stage) at least once per form.
+warps, warps of the wall kernel, records per wall stage, units per take of the
+dynamic dispensing) at least once per form.
 The forcing and stress outputs start as NaN where the stage writes them, so a
 skipped write shows up; tolerances are those of the parity tests (Sec. 3.3 wall
 model, Eq. 18 forcing).
@@ -26,15 +27,17 @@ torch = pytest.importorskip("torch")
 
 SLAB = (256, 128, 40)
 
-# (force_path, rows, stages, consumer_warps, wall_warps, wall_chunk)
+# (rows, stages, consumer_warps, wall_warps, wall_chunk[, dyn_chunk]) per force_path
 SHAPES = {
     1: [(1, 2, 2, 0, 0), (2, 3, 4, 0, 0), (4, 4, 8, 0, 0), (2, 6, 3, 0, 0), (1, 5, 6, 0, 0), (4, 3, 2, 0, 0)],
-    2: [(0, 0, 0, 0, 0)],
-    3: [(1, 2, 2, 4, 0), (2, 3, 4, 8, 0), (4, 3, 8, 8, 0), (2, 6, 3, 4, 0), (1, 5, 6, 8, 0), (4, 2, 2, 4, 0)],
+    3: [(1, 2, 2, 4, 0), (2, 3, 4, 8, 0), (4, 3, 8, 8, 0), (2, 6, 3, 4, 0), (1, 5, 6, 8, 0), (4, 2, 2, 4, 0),
+        (2, 3, 4, 8, 0, 1), (4, 3, 4, 8, 0, 7), (1, 2, 3, 4, 0, 64)],
     4: [(1, 3, 2, 0, 0), (2, 4, 4, 0, 0), (4, 3, 8, 0, 0), (2, 6, 6, 0, 0), (1, 2, 3, 0, 0)],
     5: [(1, 2, 2, 0, 0), (2, 3, 4, 0, 64), (4, 3, 8, 0, 512), (2, 6, 3, 0, 1024), (1, 5, 6, 0, 256),
         (4, 2, 4, 0, 4096)],
-    6: [(1, 2, 2, 1, 0), (2, 3, 4, 3, 0), (4, 3, 8, 4, 0), (2, 6, 3, 2, 0), (1, 5, 6, 8, 0), (4, 2, 4, 6, 0)],
+    6: [(1, 2, 2, 1, 0), (2, 3, 4, 3, 0), (4, 3, 8, 4, 0), (2, 6, 3, 2, 0), (1, 5, 6, 8, 0), (4, 2, 4, 6, 0),
+        (4, 3, 4, 3, 0, 1), (2, 3, 3, 2, 0, 5), (4, 2, 4, 3, 0, 16), (1, 4, 4, 4, 0, 4096)],
+    2: [(0, 0, 0, 0, 0)],
 }
 CASES = [(fp, i) for fp in sorted(SHAPES) for i in range(len(SHAPES[fp]))]
 
@@ -56,10 +59,11 @@ def slab_ref(oracle_mod):
 
 
 def _tuning(fp, shape):
-    rows, stages, cons, wall, chunk = shape
+    rows, stages, cons, wall, chunk = shape[:5]
+    dyn = shape[5] if len(shape) > 5 else 0
     t = dict(force_path=fp)
     for k, v in (("rows", rows), ("stages", stages), ("consumer_warps", cons), ("wall_warps", wall),
-                 ("wall_chunk", chunk)):
+                 ("wall_chunk", chunk), ("dyn_chunk", dyn)):
         if v:
             t[k] = v
     return t
