@@ -538,7 +538,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    from paper_2006_03343_gb300 import build, inputs
+    from paper_2006_03343_gb300 import build, inputs, wmibm
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
@@ -632,7 +632,7 @@ def run_ours(args):
                    for x in (case.u, case.v, case.w)]
         host_tau = [torch.from_numpy(case.tau[k]).to(form.tdt).pin_memory() for k in inputs.TAU_NAMES]
         host_f = [torch.empty(case.shape, dtype=form.tdt).pin_memory() for _ in range(3)]
-        host_stats = torch.empty(10, dtype=torch.float64).pin_memory()
+        host_stats = torch.empty(2 * wmibm.STATS_WORDS, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
         d2h = sum(t.numel() * t.element_size() for t in host_f) + host_stats.numel() * 8
 
@@ -947,7 +947,8 @@ def run_ensemble(args):
         b2.set_fields(b2_fields)
         sets.append((b2, b2_fields, b2.new_stats()))
         host_out = [([[torch.empty(c.shape, dtype=tdt).pin_memory() for _ in range(3)] for c in cases],
-                     torch.empty(10 * len(cases), dtype=torch.float64).pin_memory()) for _ in range(2)]
+                     torch.empty(2 * wmibm.STATS_WORDS * len(cases), dtype=torch.float64).pin_memory())
+                    for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for ins in host_in for t in ins)
         d2h = sum(t.numel() * t.element_size() for ff in host_out[0][0] for t in ff) + host_out[0][1].numel() * 8
 
@@ -1256,7 +1257,7 @@ def run_spectral(args):
         host_in = [torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (case.u, case.v, case.w)]
         host_tau = [torch.from_numpy(case.tau[k]).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
         host_f = [torch.empty(case.shape, dtype=tdt).pin_memory() for _ in range(3)]
-        host_stats = torch.empty(10, dtype=torch.float64).pin_memory()
+        host_stats = torch.empty(2 * wmibm.STATS_WORDS, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host_in + host_tau)
         d2h = sum(t.numel() * t.element_size() for t in host_f) + host_stats.numel() * 8
 

@@ -65,7 +65,14 @@ typedef struct wmibm_opts {
     double kappa;           /* von Karman constant; <= 0 selects 0.4 (Sec. 2.2) */
     int32_t dtype;          /* WMIBM_F32 or WMIBM_F64: type of tau, f, grad p and of the arithmetic */
     int32_t vel_dtype;      /* storage type of u, v, w: equal to dtype, or WMIBM_BF16 when dtype is F32 */
+    int32_t zclamp;         /* sample points x_c above the top or below the bottom physical level of a
+                               grid (Sec. 3.3 interpolation): WMIBM_ZCLAMP_CLAMP (0) clamps their level
+                               (reading R3) and counts them in wmibm_band_stats.n_zclamped;
+                               WMIBM_ZCLAMP_REJECT (1) makes wmibm_init fail with EINVAL instead */
 } wmibm_opts;
+
+#define WMIBM_ZCLAMP_CLAMP 0
+#define WMIBM_ZCLAMP_REJECT 1
 
 /* Band statistics of one wall-stress pass, one record per band (w, then uv). */
 typedef struct wmibm_band_stats {
@@ -74,6 +81,8 @@ typedef struct wmibm_band_stats {
     double sum_tw2;         /* sum of tau_w^2 */
     double min_tw;          /* most negative tau_w (0 for an empty band) */
     double max_ur;          /* largest tangential speed |U_r| (0 for an empty band) */
+    int64_t n_zclamped;     /* band nodes whose sample point x_c had its level clamped to the physical
+                               levels of the uv-grid or the w-grid (fixed by phi: counted at init) */
 } wmibm_band_stats;
 
 typedef struct wmibm_handle wmibm_handle;
@@ -89,14 +98,14 @@ typedef struct wmibm_handle wmibm_handle;
  *              of cell (i,j,k), shared by uv-node and w-node (i,j,k); 0 < z0 < phi_c
  *   phi_c    : distance above the surface at which the velocity is sampled
  *              (Sec. 3.3, phi_c >= 2 phi_b)
- *   opts     : NULL for defaults (F32, phi_b = dz/2, kappa = 0.4)
+ *   opts     : NULL for defaults (F32, phi_b = dz/2, kappa = 0.4, zclamp = CLAMP)
  * The inputs are copied; the handle keeps no pointer to them.  On the GPU (in
  * FP64) it classifies every node, computes n = grad(phi)/|grad(phi)| by central
  * differences, builds ascending index lists of the band, solid and body nodes
  * and, per band node, the interpolation stencil of x_c = x + (phi_c - phi) n
  * and the factor kappa^2 / ln^2(phi_c/z0).
- * Errors: EINVAL (bad sizes, non-finite phi, z0 out of range, phi_c < 2 phi_b),
- * ENOMEM, ECUDA.  On error *out is NULL.
+ * Errors: EINVAL (bad sizes, non-finite phi, z0 out of range, phi_c < 2 phi_b,
+ * a clamped sample point with zclamp = REJECT), ENOMEM, ECUDA.  On error *out is NULL.
  */
 int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double *phi_uv, const double *phi_w,
                const double *z0, int32_t z0_is_field, double phi_c, const wmibm_opts *opts, void *stream);
@@ -327,13 +336,17 @@ int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream);
  *   Same arguments and results as wmibm_wall_stress (stats up to summation
  *   order).  The kernel's reduction scratch (per-block partial statistics and a
  *   ticket) is a static device array of 131,328 bytes that every GPU loading
- *   the library holds until the process exits; at most 1,048,576 band nodes
- *   (w-band + uv-band) are accepted, larger bands return EINVAL.
+ *   the library holds until the process exits.  The array bounds the kernel's
+ *   blocks (2048); by choice, so that one call is one pass of that grid at two
+ *   records a thread, at most 1,048,576 band nodes (w-band + uv-band) are
+ *   accepted, and larger bands return EINVAL before any GPU work.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current: make that first call
- *   before any stream capture.  All calls share the array and it keeps the last
- *   call's contents (the ticket is cleared on the stream before each launch):
- *   calls that overlap on the GPU, on any handle, race.
+ *   (cudaGetSymbolAddress) with that device current, and so does the first call
+ *   after the device's context was made anew (cudaDeviceReset): make that first
+ *   call before any stream capture.  All calls share the array and it keeps the
+ *   last call's contents (the ticket is cleared on the stream before each
+ *   launch): calls that overlap on the GPU, on any handle, race.  Host threads
+ *   may make calls at the same time (the look-up is locked).
  */
 int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                               wmibm_band_stats *stats, void *stream);
@@ -428,6 +441,13 @@ int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream);
  * step without the body mask); same launches, arguments and results otherwise.
  */
 int wmibm_batch_wall_stress_force(wmibm_batch *b, wmibm_band_stats *stats, void *stream);
+
+/*
+ * wmibm_batch_device_status - reads and clears the batch's device status word,
+ * which its kernels set when one of their bounded waits gave up.  Synchronises
+ * `stream`.  *out receives WMIBM_OK or WMIBM_ETIMEOUT.
+ */
+int wmibm_batch_device_status(wmibm_batch *b, int32_t *out, void *stream);
 
 /* Algorithmic bytes of one batch step: which = 0 wall kernel, 1 force + mask kernel. */
 int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which);

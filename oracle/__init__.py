@@ -151,8 +151,10 @@ def interp(grid, f, is_w, x, y, z):
 def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4, logz0=None):
     """Sec. 3.3 wall stress.  tau: dict of 6 float64 arrays (txx txy tyy tzz txz tyz),
     updated in place.  z0: float or per-cell array; or logz0: per-cell ln z0 (then
-    C = kappa^2 / (ln phi_c - ln z0)^2 and z0 is ignored).  Returns stats [2, 5]:
-    rows (w-band, uv-band), columns (count, sum tau_w, sum tau_w^2, min tau_w, max U_r)."""
+    C = kappa^2 / (ln phi_c - ln z0)^2 and z0 is ignored).  Returns stats [2, 6]:
+    rows (w-band, uv-band), columns (count, sum tau_w, sum tau_w^2, min tau_w, max U_r,
+    nodes whose sample point x_c lies outside the physical levels of the uv-grid or the
+    w-grid, where the interpolation clamps it: reading R3)."""
     nx, ny, nz, lx, ly, lz = _shape(grid)
     if logz0 is not None:
         z0a = np.ascontiguousarray(logz0, np.float64)
@@ -163,14 +165,14 @@ def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4, 
     else:
         z0a = np.ascontiguousarray(z0, np.float64)
         is_field = 1
-    stats = np.zeros(10, np.float64)
+    stats = np.zeros(12, np.float64)
     rc = _load().orc_wall_stress(nx, ny, nz, lx, ly, lz, _p(phi_uv), _p(phi_w), _p(z0a), is_field,
                                  float(phi_c), float(kappa), float(phi_b), _p(u), _p(v), _p(w),
                                  _p(tau["txx"]), _p(tau["txy"]), _p(tau["tyy"]), _p(tau["tzz"]),
                                  _p(tau["txz"]), _p(tau["tyz"]), _p(stats))
     if rc != 0:
         raise ValueError("oracle: z0 must satisfy 0 < z0 < phi_c")
-    return stats.reshape(2, 5)
+    return stats.reshape(2, 6)
 
 
 def wall_model_node(grid, phi, is_w, i, j, k, u, v, w, z0, phi_c, kappa=0.4):

@@ -216,6 +216,7 @@ typedef struct {
     double tau[3][3];
     double tau_w;
     double ur;
+    int zclamped;     /* 1 if x_c lies outside the physical levels of the uv-grid or the w-grid (R3) */
 } orc_node_result;
 
 static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
@@ -231,6 +232,15 @@ static void wall_model_at(const orc_grid *g, const double *phi, int is_w,
     double z = is_w ? (double)k * g->dz : ((double)k + 0.5) * g->dz;
     double d = phi_c - phi[at(g, i, j, k)];
     double xc = x + d * n[0], yc = y + d * n[1], zc = z + d * n[2];
+
+    /* R3: the interpolation clamps the fractional level of z_c to the physical levels
+       of each grid (uv: 0 .. nz-2, w: 0 .. nz-1, the same expressions as in interp);
+       note whether it had to on either grid */
+    {
+        double zeta_uv = zc / g->dz - 0.5, zeta_w = zc / g->dz;
+        out->zclamped = (zeta_uv < 0.0 || zeta_uv > (double)(g->nz - 2) || zeta_w < 0.0 ||
+                         zeta_w > (double)(g->nz - 1)) ? 1 : 0;
+    }
 
     double uc[3];
     uc[0] = interp(g, u, 0, xc, yc, zc);   /* u on the uv-grid */
@@ -284,7 +294,7 @@ static double roughness_log(const double *z0, int z0_mode, int64_t p, double phi
 
 /* Kahan-compensated accumulation of the band statistics. */
 typedef struct {
-    int64_t count;
+    int64_t count, zclamped;
     double sum_tw, c_tw, sum_tw2, c_tw2, min_tw, max_ur;
 } orc_stats_acc;
 
@@ -296,9 +306,10 @@ static void kahan_add(double *sum, double *comp, double x)
     *sum = t;
 }
 
-static void stats_add(orc_stats_acc *s, double tw, double ur)
+static void stats_add(orc_stats_acc *s, double tw, double ur, int zclamped)
 {
     s->count += 1;
+    s->zclamped += zclamped;
     kahan_add(&s->sum_tw, &s->c_tw, tw);
     kahan_add(&s->sum_tw2, &s->c_tw2, tw * tw);
     if (tw < s->min_tw) s->min_tw = tw;
@@ -312,8 +323,9 @@ static void stats_add(orc_stats_acc *s, double tw, double ur)
  * uv-band nodes.
  * z0: scalar (z0_is_field = 0), a per-cell field [k][j][i] (reading R7,
  * z0_is_field = 1) or a per-cell field of ln z0 (z0_is_field = 2).
- * stats (may be NULL): 2 x {count, sum tau_w, sum tau_w^2, min tau_w, max U_r},
- * first for the w-band, then for the uv-band, count stored as a double.
+ * stats (may be NULL): 2 x {count, sum tau_w, sum tau_w^2, min tau_w, max U_r,
+ * nodes whose x_c was clamped in z (R3)}, first for the w-band, then for the
+ * uv-band, counts stored as doubles.
  * Returns 0, or -1 if some z0 does not satisfy 0 < z0 < phi_c.
  */
 int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
@@ -348,7 +360,7 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
                                   kappa, &r);
                     txz[p] = r.tau[0][2];
                     tyz[p] = r.tau[1][2];
-                    stats_add(&acc[0], r.tau_w, r.ur);
+                    stats_add(&acc[0], r.tau_w, r.ur, r.zclamped);
                 }
             }
 
@@ -368,17 +380,18 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
                     txy[p] = r.tau[0][1];
                     tyy[p] = r.tau[1][1];
                     tzz[p] = r.tau[2][2];
-                    stats_add(&acc[1], r.tau_w, r.ur);
+                    stats_add(&acc[1], r.tau_w, r.ur, r.zclamped);
                 }
             }
 
     if (stats) {
         for (int s = 0; s < 2; ++s) {
-            stats[5 * s + 0] = (double)acc[s].count;
-            stats[5 * s + 1] = acc[s].sum_tw;
-            stats[5 * s + 2] = acc[s].sum_tw2;
-            stats[5 * s + 3] = acc[s].min_tw;
-            stats[5 * s + 4] = acc[s].max_ur;
+            stats[6 * s + 0] = (double)acc[s].count;
+            stats[6 * s + 1] = acc[s].sum_tw;
+            stats[6 * s + 2] = acc[s].sum_tw2;
+            stats[6 * s + 3] = acc[s].min_tw;
+            stats[6 * s + 4] = acc[s].max_ur;
+            stats[6 * s + 5] = (double)acc[s].zclamped;
         }
     }
     return 0;

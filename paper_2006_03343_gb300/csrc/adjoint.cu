@@ -288,10 +288,10 @@ int ensure_adjoint_map(wmibm_handle *h, cudaStream_t stream)
     offs.push_back((int32_t)ent.size());
 
     const size_t gbytes = (size_t)h->nrec * 4 * elem_size(h->dtype);
-    e = cudaMalloc(&h->adj_keys, keys.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->adj_offs, offs.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->adj_ent, ent.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->adj_grad, gbytes);
+    e = dev_alloc(&h->adj_keys, keys.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_alloc(&h->adj_offs, offs.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_alloc(&h->adj_ent, ent.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_alloc(&h->adj_grad, gbytes);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->adj_keys, keys.data(), keys.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)

@@ -276,7 +276,8 @@ __device__ void stats_block_reduce(T acc[kStatVals], T (*smem)[kStatVals])
 // (counts from the handle) and re-arms the ticket.  smem must hold 32 rows.
 template <typename T>
 __device__ void stats_finish(T acc[kStatVals], T (*smem)[kStatVals], T *partials, unsigned *ticket,
-                             unsigned nblocks, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv)
+                             unsigned nblocks, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv,
+                             int64_t nzc_w, int64_t nzc_uv)
 {
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -300,6 +301,7 @@ __device__ void stats_finish(T acc[kStatVals], T (*smem)[kStatVals], T *partials
         for (int b = 0; b < 2; ++b) {
             wmibm_band_stats st;
             st.count = b == 0 ? count_w : count_uv;
+            st.n_zclamped = b == 0 ? nzc_w : nzc_uv;
             st.sum_tw = (double)acc[4 * b + 0];
             st.sum_tw2 = (double)acc[4 * b + 1];
             st.min_tw = (double)acc[4 * b + 2];
@@ -332,11 +334,13 @@ __device__ __forceinline__ void stats_red(const T acc[kStatVals], double *sacc)
 
 // Converts the accumulator into wmibm_band_stats[2] and clears it for the next
 // call.  One thread, after every contribution is complete and visible.
-__device__ __forceinline__ void stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv)
+__device__ __forceinline__ void stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv,
+                                           int64_t nzc_w, int64_t nzc_uv)
 {
     for (int b = 0; b < 2; ++b) {
         wmibm_band_stats st;
         st.count = b == 0 ? count_w : count_uv;
+        st.n_zclamped = b == 0 ? nzc_w : nzc_uv;
         st.sum_tw = __ldcg(sacc + 4 * b + 0);
         st.sum_tw2 = __ldcg(sacc + 4 * b + 1);
         st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(sacc + 4 * b + 2)));

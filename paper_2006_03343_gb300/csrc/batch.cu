@@ -32,6 +32,8 @@ struct wmibm_batch {
     StencilConfig cfg;
     int64_t clean_total, dirty_total, rec_total, run_total, body_total;
     int64_t traffic[2];
+    uint64_t wait_ns;
+    int hold_release;
     std::vector<unsigned char> member0;   // host copy of member 0's descriptor (a batch of one
                                           // is launched with it as the single-terrain member)
     char err[512];
@@ -166,6 +168,8 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
     if (b->count == 1) memcpy(&p.one, b->member0.data(), sizeof(Member<T>));   // kernels read p.one then
     p.wall_done = b->ticket + 1;
     p.exit_ticket = b->ticket + 2;
+    p.wait_ns = b->wait_ns;
+    p.hold_release = b->hold_release;
     const int wall_blocks = 0;   // one wave of resident blocks
     const int form = b->tuning.force_path == 0 ? 6 : b->tuning.force_path;
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
@@ -190,10 +194,12 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
             return WMIBM_EINVAL;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != h0->device) return WMIBM_ESTATE;
+    fault_arm();
 
-    wmibm_batch *b = new (std::nothrow) wmibm_batch();
+    wmibm_batch *b = fault_fires() ? nullptr : new (std::nothrow) wmibm_batch();
     if (!b) return WMIBM_ENOMEM;
     b->device = h0->device;
+    fault_wait_settings(&b->wait_ns, &b->hold_release);
     b->count = count;
     b->dtype = h0->dtype;
     b->vel_dtype = h0->vel_dtype;
@@ -201,13 +207,13 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
     b->max_nx = 0;
     for (auto *h : b->members) b->max_nx = std::max(b->max_nx, (int)h->nx);
     const size_t msize = b->dtype == WMIBM_F64 ? sizeof(Member<double>) : sizeof(Member<float>);
-    cudaError_t e = cudaMalloc(&b->dev_members, msize * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->bstats, sizeof(double) * 8 * count);
+    cudaError_t e = dev_alloc(&b->dev_members, msize * count);
+    if (e == cudaSuccess) e = dev_alloc(&b->bstats, sizeof(double) * 8 * count);
     // [0] last-block ticket of the batch wall kernel; [1] wall-done and [2] exit
     // counters of the single launch; [4..7] the two 64-bit counters of the dynamic
     // dispensing (all back at 0 after every launch)
-    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, 8 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(&b->ticket, 8 * sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_alloc(&b->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->bstats, 0, sizeof(double) * 8 * count, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket, 0, 8 * sizeof(unsigned), (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
@@ -218,6 +224,7 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
         cudaFree(b->ticket);
         cudaFree(b->status);
         delete b;
+        if (e == cudaErrorMemoryAllocation) return WMIBM_ENOMEM;
         return e != cudaSuccess ? WMIBM_ECUDA : WMIBM_EINVAL;
     }
     int64_t wall_bytes = 0, force_bytes = 0;
@@ -295,6 +302,22 @@ extern "C" int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *s
 extern "C" int wmibm_batch_wall_stress_force(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
 {
     return batch_run(b, stats, 0, stream);
+}
+
+extern "C" int wmibm_batch_device_status(wmibm_batch *b, int32_t *out, void *stream)
+{
+    if (!b) return WMIBM_EINVAL;
+    if (!out) return berr(b, WMIBM_EINVAL, "NULL output");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return berr(b, WMIBM_ESTATE, "current device is not the batch's device");
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, b->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch device status");
+    *out = v == 0 ? WMIBM_OK : WMIBM_ETIMEOUT;
+    return WMIBM_OK;
 }
 
 extern "C" int64_t wmibm_batch_traffic_bytes(const wmibm_batch *b, int32_t which)

@@ -108,6 +108,7 @@ struct RecParams {
     double dx, dy, dz, phi_c, kappa;
     void *rec;
     int f64;
+    unsigned long long *nclamp;   // [2]: band nodes (w, uv) whose sample point's level is clamped
 };
 
 __device__ __forceinline__ int32_t wrapi(int64_t i, int32_t n)
@@ -162,9 +163,11 @@ __global__ void __launch_bounds__(kThreads) k_records(RecParams p)
 
     double az[2];
     int32_t kb[2];
+    bool clamped = false;
     for (int g = 0; g < 2; ++g) {          // g = 0: uv-grid, g = 1: w-grid
         double zeta = (g == 1) ? zc / p.dz : zc / p.dz - 0.5;
         const int32_t top = (g == 1) ? p.nz - 1 : p.nz - 2;
+        if (zeta < 0.0 || zeta > (double)top) clamped = true;
         zeta = fmin(fmax(zeta, 0.0), (double)top);
         int32_t k0 = (int32_t)floor(zeta);
         if (k0 > top - 1) k0 = top - 1;
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_records(RecParams p)
         az[g] = zeta - (double)k0;
     }
 
+    if (clamped) atomicAdd(p.nclamp + (is_w ? 0 : 1), 1ull);
     const double z0 = p.z0_is_field ? p.z0[idx] : p.z0[0];
     const double lg = log(p.phi_c / z0);
     const double C = (p.kappa * p.kappa) / (lg * lg);
@@ -357,6 +361,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
 {
     cudaStream_t stream = (cudaStream_t)stream_;
     g_init_error[0] = 0;
+    fault_arm();
     if (!out) return set_error(nullptr, WMIBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!g || !phi_uv || !phi_w || !z0) return set_error(nullptr, WMIBM_EINVAL, "NULL grid, phi or z0");
@@ -367,8 +372,10 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     const int64_t n = (int64_t)g->nx * g->ny * g->nz;
     if (n >= ((int64_t)1 << 31) - 16) return set_error(nullptr, WMIBM_EINVAL, "grid has %lld nodes (>= 2^31)", (long long)n);
 
-    wmibm_opts o = {0.0, 0.0, WMIBM_F32, WMIBM_F32};
+    wmibm_opts o = {0.0, 0.0, WMIBM_F32, WMIBM_F32, WMIBM_ZCLAMP_CLAMP};
     if (opts) o = *opts;
+    if (o.zclamp != WMIBM_ZCLAMP_CLAMP && o.zclamp != WMIBM_ZCLAMP_REJECT)
+        return set_error(nullptr, WMIBM_EINVAL, "zclamp must be WMIBM_ZCLAMP_CLAMP or WMIBM_ZCLAMP_REJECT");
     const double dz = g->lz / (double)(g->nz - 1);
     if (!(o.phi_b > 0)) o.phi_b = 0.5 * dz;
     if (!(o.kappa > 0)) o.kappa = 0.4;
@@ -397,9 +404,9 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     const int64_t nblk = (n + kChunk - 1) / kChunk;
     std::vector<int32_t> counts(6 * nblk);
     std::vector<int64_t> offsets(6 * nblk);
-    unsigned long long marks[2] = {0, 0};
+    unsigned long long marks[4] = {0, 0, 0, 0};
 
-    wmibm_handle *h = (wmibm_handle *)calloc(1, sizeof(wmibm_handle));
+    wmibm_handle *h = (wmibm_handle *)host_alloc(sizeof(wmibm_handle));
     if (!h) return set_error(nullptr, WMIBM_ENOMEM, "host allocation failed");
     TRY(cudaGetDevice(&h->device), "cudaGetDevice");
     h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;
@@ -408,14 +415,15 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     h->dy = g->ly / (double)g->ny;
     h->dz = dz;
     h->phi_b = o.phi_b; h->kappa = o.kappa; h->phi_c = phi_c;
+    fault_wait_settings(&h->wait_ns, &h->hold_release);
     h->dtype = o.dtype; h->vel_dtype = o.vel_dtype;
     h->n = n;
 
-    TRY(cudaMalloc(&d_phi_uv, n * sizeof(double)), "cudaMalloc phi_uv");
-    TRY(cudaMalloc(&d_phi_w, n * sizeof(double)), "cudaMalloc phi_w");
-    TRY(cudaMalloc(&d_z0, nz0 * sizeof(double)), "cudaMalloc z0");
-    TRY(cudaMalloc(&d_counts, 6 * nblk * sizeof(int32_t)), "cudaMalloc counts");
-    TRY(cudaMalloc(&d_offsets, 6 * nblk * sizeof(int64_t)), "cudaMalloc offsets");
+    TRY(dev_alloc(&d_phi_uv, n * sizeof(double)), "cudaMalloc phi_uv");
+    TRY(dev_alloc(&d_phi_w, n * sizeof(double)), "cudaMalloc phi_w");
+    TRY(dev_alloc(&d_z0, nz0 * sizeof(double)), "cudaMalloc z0");
+    TRY(dev_alloc(&d_counts, 6 * nblk * sizeof(int32_t)), "cudaMalloc counts");
+    TRY(dev_alloc(&d_offsets, 6 * nblk * sizeof(int64_t)), "cudaMalloc offsets");
     TRY(cudaMemcpyAsync(d_phi_uv, phi_uv, n * sizeof(double), cudaMemcpyHostToDevice, stream), "copy phi_uv");
     TRY(cudaMemcpyAsync(d_phi_w, phi_w, n * sizeof(double), cudaMemcpyHostToDevice, stream), "copy phi_w");
     TRY(cudaMemcpyAsync(d_z0, z0, nz0 * sizeof(double), cudaMemcpyHostToDevice, stream), "copy z0");
@@ -432,7 +440,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             s += counts[l * nblk + b];
         }
         h->lists.n[l] = s;
-        TRY(cudaMalloc(&h->lists.p[l], std::max<int64_t>(s, 1) * sizeof(int32_t)), "cudaMalloc list");
+        TRY(dev_alloc(&h->lists.p[l], std::max<int64_t>(s, 1) * sizeof(int32_t)), "cudaMalloc list");
     }
     TRY(cudaMemcpyAsync(d_offsets, offsets.data(), 6 * nblk * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
         "copy offsets");
@@ -440,9 +448,13 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     TRY(cudaGetLastError(), "k_compact launch");
 
     h->nrec = h->lists.n[0] + h->lists.n[1];
+    // [0, 1]: distinct velocity elements the band stencils read on each grid;
+    // [2, 3]: band nodes (w, uv) whose sample point's level is clamped
+    TRY(dev_alloc(&d_marks, 4 * sizeof(unsigned long long)), "cudaMalloc mark counts");
+    TRY(cudaMemsetAsync(d_marks, 0, 4 * sizeof(unsigned long long), stream), "memset mark counts");
     {
         const size_t rec_size = o.dtype == WMIBM_F64 ? sizeof(RecF64) : sizeof(RecF32);
-        TRY(cudaMalloc(&h->rec, std::max<int64_t>(h->nrec, 1) * rec_size), "cudaMalloc records");
+        TRY(dev_alloc(&h->rec, std::max<int64_t>(h->nrec, 1) * rec_size), "cudaMalloc records");
         if (h->nrec > 0) {
             RecParams rp;
             rp.phi_uv = d_phi_uv; rp.phi_w = d_phi_w; rp.z0 = d_z0; rp.z0_is_field = z0_is_field ? 1 : 0;
@@ -451,24 +463,23 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             rp.nx = h->nx; rp.ny = h->ny; rp.nz = h->nz;
             rp.dx = h->dx; rp.dy = h->dy; rp.dz = h->dz; rp.phi_c = phi_c; rp.kappa = o.kappa;
             rp.rec = h->rec; rp.f64 = o.dtype == WMIBM_F64;
+            rp.nclamp = d_marks + 2;
             k_records<<<(unsigned)((h->nrec + kThreads - 1) / kThreads), kThreads, 0, stream>>>(rp);
             TRY(cudaGetLastError(), "k_records launch");
         }
         TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device), "SM count");
         h->partial_blocks = std::max<int64_t>((h->nrec + kThreads - 1) / kThreads, 16 * (int64_t)h->sm_count);
-        TRY(cudaMalloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
+        TRY(dev_alloc(&h->partials, h->partial_blocks * kStatVals * elem_size(o.dtype)), "cudaMalloc partials");
         // [0] last-block ticket of the wall kernel, [1] wall-done and [2] exit counters of
         // the fused step launch; all stay 0 between calls
-        TRY(cudaMalloc(&h->ticket, 8 * sizeof(unsigned int)), "cudaMalloc ticket");
+        TRY(dev_alloc(&h->ticket, 8 * sizeof(unsigned int)), "cudaMalloc ticket");
         TRY(cudaMemsetAsync(h->ticket, 0, 8 * sizeof(unsigned int), stream), "memset ticket");
-        TRY(cudaMalloc(&h->sacc, 8 * sizeof(double)), "cudaMalloc stats accumulator");
+        TRY(dev_alloc(&h->sacc, 8 * sizeof(double)), "cudaMalloc stats accumulator");
         TRY(cudaMemsetAsync(h->sacc, 0, 8 * sizeof(double), stream), "memset stats accumulator");
 
         // algorithmic bytes: distinct velocity elements read by the band stencils
-        TRY(cudaMalloc(&d_mark, 2 * n), "cudaMalloc marks");
-        TRY(cudaMalloc(&d_marks, 2 * sizeof(unsigned long long)), "cudaMalloc mark counts");
+        TRY(dev_alloc(&d_mark, 2 * n), "cudaMalloc marks");
         TRY(cudaMemsetAsync(d_mark, 0, 2 * n, stream), "memset marks");
-        TRY(cudaMemsetAsync(d_marks, 0, 2 * sizeof(unsigned long long), stream), "memset mark counts");
         if (h->nrec > 0) {
             k_mark<<<(unsigned)((h->nrec + kThreads - 1) / kThreads), kThreads, 0, stream>>>(
                 h->rec, o.dtype == WMIBM_F64, h->nrec, h->nx, h->ny, d_mark, d_mark + n);
@@ -478,6 +489,14 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         TRY(cudaGetLastError(), "k_count_marks launch");
         TRY(cudaMemcpyAsync(marks, d_marks, sizeof(marks), cudaMemcpyDeviceToHost, stream), "copy mark counts");
         TRY(cudaStreamSynchronize(stream), "init kernels");
+        h->nzclamp[0] = (int64_t)marks[2];
+        h->nzclamp[1] = (int64_t)marks[3];
+        if (o.zclamp == WMIBM_ZCLAMP_REJECT && marks[2] + marks[3] > 0) {
+            status = set_error(nullptr, WMIBM_EINVAL,
+                               "%llu w-band and %llu uv-band sample points lie outside the physical levels "
+                               "(zclamp = REJECT)", marks[2], marks[3]);
+            goto fail;
+        }
 
         // levels holding band or solid nodes (first and last entry of each sorted
         // list): stencil stages at levels [lo - 1, hi + 1] read entries the wall
@@ -511,8 +530,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             const int64_t sblk = std::max<int64_t>((nsolid + kChunk - 1) / kChunk, 1);
             std::vector<int32_t> rc(sblk, 0);
             std::vector<int64_t> ro(sblk, 0);
-            TRY(cudaMalloc(&d_counts2, sblk * sizeof(int32_t)), "cudaMalloc run counts");
-            TRY(cudaMalloc(&d_offsets2, sblk * sizeof(int64_t)), "cudaMalloc run offsets");
+            TRY(dev_alloc(&d_counts2, sblk * sizeof(int32_t)), "cudaMalloc run counts");
+            TRY(dev_alloc(&d_offsets2, sblk * sizeof(int64_t)), "cudaMalloc run offsets");
             TRY(cudaMemsetAsync(d_counts2, 0, sblk * sizeof(int32_t), stream), "memset run counts");
             if (nsolid > 0) {
                 k_runs_count<<<(unsigned)sblk, kThreads, 0, stream>>>(solid, nsolid, h->nx, d_counts2);
@@ -527,7 +546,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
                 nr += rc[b];
             }
             h->nruns[gsel] = nr;
-            TRY(cudaMalloc(&h->runs[gsel], std::max<int64_t>(nr, 1) * sizeof(int2)), "cudaMalloc runs");
+            TRY(dev_alloc(&h->runs[gsel], std::max<int64_t>(nr, 1) * sizeof(int2)), "cudaMalloc runs");
             TRY(cudaMemcpyAsync(d_offsets2, ro.data(), sblk * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
                 "copy run offsets");
             if (nsolid > 0) {
@@ -541,7 +560,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             d_counts2 = nullptr;
             d_offsets2 = nullptr;
         }
-        TRY(cudaMalloc(&h->dev_status, sizeof(int)), "cudaMalloc status");
+        TRY(dev_alloc(&h->dev_status, sizeof(int)), "cudaMalloc status");
         TRY(cudaMemsetAsync(h->dev_status, 0, sizeof(int), stream), "memset status");
         TRY(cudaStreamSynchronize(stream), "init state");
         status = spectral_setup(h, stream);

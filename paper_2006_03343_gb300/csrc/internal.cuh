@@ -67,6 +67,9 @@ struct wmibm_handle {
     double *sacc;               // [8] band-statistics accumulator, kept at 0 between calls
     int64_t partial_blocks;
     int64_t traffic[5];
+    int64_t nzclamp[2];         // band nodes (w, uv) whose sample point's level was clamped
+    uint64_t wait_ns;           // limit of the kernels' bounded waits (WMIBM_WAIT_LIMIT_NS at init; 1 s)
+    int hold_release;           // failure-path test: the single launch never releases its dirty stages
     int2 *runs[2];              // solid runs along x (first node, length): w-grid, uv-grid
     int64_t nruns[2];
     int *dev_status;            // set by kernels whose bounded waits gave up
@@ -98,6 +101,19 @@ int spectral_setup(wmibm_handle *h, cudaStream_t stream);     // spectral.cu, on
 void spectral_free(wmibm_handle *h);
 
 inline size_t elem_size(int32_t t) { return t == WMIBM_F64 ? 8 : (t == WMIBM_BF16 ? 2 : 4); }
+
+// Allocations of the library go through these (fault.cu): WMIBM_FAULT=alloc:N,
+// read by fault_arm() at the start of wmibm_init and wmibm_batch_create, makes
+// the N-th one fail (device: cudaErrorMemoryAllocation; host: NULL).
+void fault_arm();
+bool fault_fires();
+// Wait limit and release hold for a new handle or batch: WMIBM_WAIT_LIMIT_NS (ns,
+// default 1e9, kept within [1e5, 1e10]) and WMIBM_FAULT=hold_release.
+void fault_wait_settings(uint64_t *wait_ns, int *hold_release);
+cudaError_t dev_alloc_bytes(void **p, size_t bytes);
+void *host_alloc(size_t bytes);      // zeroed, release with free()
+template <typename P>
+inline cudaError_t dev_alloc(P **p, size_t bytes) { return dev_alloc_bytes(reinterpret_cast<void **>(p), bytes); }
 
 // ------------------------------------------------------------------------- //
 // device helpers

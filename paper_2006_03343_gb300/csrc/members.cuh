@@ -18,6 +18,7 @@ struct Member {
     int64_t c_off, d_off;         // first index in the launch's clean / dirty unit spaces
     const void *rec;              // band records (w-band first)
     int64_t nb_w, nb_uv, r_off;   // band counts; first index in the record space
+    int64_t nzc_w, nzc_uv;        // band nodes whose sample point's level is clamped (reported in the stats)
     const int2 *runs_w, *runs_uv; // solid runs along x
     int64_t nr_w, nr_uv, run_off;
     const int32_t *body_w, *body_uv;
@@ -71,6 +72,11 @@ struct KParams {
     // at 0 after every launch, instead of a fixed share per block
     int dyn_chunk;
     unsigned long long *dyn_ctr;
+    // bounded waits give up after wait_ns; hold_release (a test of the failure path,
+    // read from the environment at init) keeps the single-launch forms from counting
+    // their blocks into wall_done, so that the waits on it run out
+    uint64_t wait_ns;
+    int hold_release;
 };
 
 template <typename T>

@@ -607,7 +607,7 @@ extern "C" int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const
     if (st) return st;
     const int64_t n = h->n;
     const size_t es = elem_size(h->dtype);
-    void *host = malloc(2 * n * es);
+    void *host = host_alloc(2 * n * es);
     if (!host) return set_error(h, WMIBM_ENOMEM, "host memory for the wall terms");
     const double pb = h->phi_b, kap = h->kappa;
     for (int g = 0; g < 2; ++g) {

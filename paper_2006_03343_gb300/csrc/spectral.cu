@@ -575,8 +575,8 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
     void **kn[2] = {&s->knx, &s->kny};
     for (int d = 0; d < 2; ++d) {
         const int N = n[d];
-        C *ht = (C *)malloc(sizeof(C) * N);
-        T *hk = (T *)malloc(sizeof(T) * N);
+        C *ht = (C *)host_alloc(sizeof(C) * N);
+        T *hk = (T *)host_alloc(sizeof(T) * N);
         if (!ht || !hk) {
             free(ht);
             free(hk);
@@ -601,8 +601,8 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
             const int mm = (2 * m < N) ? m : (2 * m == N ? 0 : m - N);
             hk[m] = (T)(2.0 * M_PI * (double)mm / len[d] / (double)N);
         }
-        cudaError_t e = cudaMalloc(tw[d], sizeof(C) * N);
-        if (e == cudaSuccess) e = cudaMalloc(kn[d], sizeof(T) * N);
+        cudaError_t e = dev_alloc(tw[d], sizeof(C) * N);
+        if (e == cudaSuccess) e = dev_alloc(kn[d], sizeof(T) * N);
         if (e == cudaSuccess) e = cudaMemcpyAsync(*tw[d], ht, sizeof(C) * N, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(*kn[d], hk, sizeof(T) * N, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -673,7 +673,7 @@ int spectral_setup(wmibm_handle *h, cudaStream_t stream)
     const int lx = ilog2_exact(h->nx), ly = ilog2_exact(h->ny);
     const int maxlog = h->dtype == WMIBM_F64 ? kSpecMaxLog - 1 : kSpecMaxLog;
     if (lx < 1 || ly < 1 || lx > maxlog || ly > maxlog) return WMIBM_OK;
-    SpecState *s = (SpecState *)calloc(1, sizeof(SpecState));
+    SpecState *s = (SpecState *)host_alloc(sizeof(SpecState));
     if (!s) return set_error(nullptr, WMIBM_ENOMEM, "host memory for the spectral state");
     h->spec = s;
     s->lognx = lx;
@@ -701,7 +701,7 @@ int spectral_setup(wmibm_handle *h, cudaStream_t stream)
     s->total = (int64_t)h->nz * (s->xpl + s->ypl);
     int st = f64 ? upload_tables<double>(h, s, stream) : upload_tables<float>(h, s, stream);
     if (st) return st;
-    cudaError_t e = cudaMalloc(&s->ctr, sizeof(unsigned int) * (size_t)(h->nz + 2));
+    cudaError_t e = dev_alloc(&s->ctr, sizeof(unsigned int) * (size_t)(h->nz + 2));
     if (e == cudaSuccess) e = cudaMemsetAsync(s->ctr, 0, sizeof(unsigned int) * (size_t)(h->nz + 2), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(nullptr, e, "spectral counters");

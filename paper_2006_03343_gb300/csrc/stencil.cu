@@ -411,10 +411,9 @@ constexpr int kFused = 2;       // the wall phase runs inside the launch (cooper
 constexpr int kInterleaved = 3; // the band records are stages of every block's pipeline (cooperative)
 constexpr int kWarpSpec = 4;    // wall warps beside the producer and consumers of every block (cooperative)
 
-// Waits until *ctr >= target (acquire at GPU scope).  Gives up after
-// kWaitLimitNs, recording kDevStatusBarrierTimeout, or as soon as another wait
-// has given up.
-__device__ bool wait_counter(const unsigned *ctr, unsigned target, int *status)
+// Waits until *ctr >= target (acquire at GPU scope).  Gives up after limit_ns,
+// recording kDevStatusBarrierTimeout, or as soon as another wait has given up.
+__device__ bool wait_counter(const unsigned *ctr, unsigned target, int *status, uint64_t limit_ns)
 {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
@@ -426,7 +425,7 @@ __device__ bool wait_counter(const unsigned *ctr, unsigned target, int *status)
         if (v >= target) return true;
         if ((it & 7u) == 0) {
             if (*(volatile int *)status != 0) return false;
-            if (global_timer_ns() - t0 > kWaitLimitNs) {
+            if (global_timer_ns() - t0 > limit_ns) {
                 atomicExch(status, kDevStatusBarrierTimeout);
                 return false;
             }
@@ -469,11 +468,11 @@ __device__ void produce(const KParams<T> &p, T *ring_a, T *ring_b, uint64_t *ful
     for (it.init(p); !it.done; it.next(), ++g) {
         if (it.new_member) load_prod(p, it.m, v);
         if (MODE == kFused && p.wall_blocks == 0 && g == kStagesBeforeWall) {
-            if (!mbar_wait(wallbar, 0u, p.status, kDevStatusBarrierTimeout)) break;
+            if (!mbar_wait(wallbar, 0u, p.status, kDevStatusBarrierTimeout, p.wait_ns)) break;
         }
         const int b = (int)(g % SA), bb = (int)(g % SB);
-        if (g >= SA && !mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
-        if (g >= SB && !mbar_wait(&empty_b[bb], ((g / SB) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) break;
+        if (g >= SA && !mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout, p.wait_ns)) break;
+        if (g >= SB && !mbar_wait(&empty_b[bb], ((g / SB) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout, p.wait_ns)) break;
         if (MODE == kInterleaved && it.wall) {
             // a wall stage: the item's band records, one bulk copy per member segment
             using Rec = typename RecOf<T>::type;
@@ -497,7 +496,7 @@ __device__ void produce(const KParams<T> &p, T *ring_a, T *ring_b, uint64_t *ful
             // to the bulk copies (async proxy) before a dirty stage
             if (MODE == kAfterWall) {
                 wait_wall_kernel();
-            } else if (!wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status)) {
+            } else if (!wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status, p.wait_ns)) {
                 break;
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -560,7 +559,7 @@ __device__ void produce(const KParams<T> &p, T *ring_a, T *ring_b, uint64_t *ful
     } else if (it.dyn) {
         // one more stage that only tells the consumers there is nothing left
         const int b = (int)(g % SA);
-        if (g < SA || mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout)) {
+        if (g < SA || mbar_wait(&empty_a[b], ((g / SA) & 1u) ^ 1u, p.status, kDevStatusEmptyTimeout, p.wait_ns)) {
             hdr[b] = make_int4(0, 0, 0, kHdrDone);
             mbar_arrive_expect_tx(&full[b], 0u);
         }
@@ -706,7 +705,7 @@ __device__ void consume(const KParams<T> &p, const T *ring_a, const T *ring_b, u
         // dynamic dispensing: the unit of each stage comes in its header
         for (;; ++g) {
             const int b = (int)(g % SA);
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout)))
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout, p.wait_ns)))
                 break;
             const volatile int *hv = reinterpret_cast<const volatile int *>(&hdr[b]);
             const int4 hd = make_int4(hv[0], hv[1], hv[2], hv[3]);
@@ -749,7 +748,7 @@ __device__ void consume(const KParams<T> &p, const T *ring_a, const T *ring_b, u
         }
         const int b = (int)(g % SA);
         // the whole warp gives up together, so that no lane is left behind at a warp-wide operation
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout)))
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[b], (g / SA) & 1u, p.status, kDevStatusFullTimeout, p.wait_ns)))
             break;
         if (MODE == kInterleaved && it.wall) {
             int64_t a, e;
@@ -910,14 +909,15 @@ __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
         if (threadIdx.x == 0) stats_red(acc, p.sacc);
     } else if (p.stats) {
         stats_block_reduce(acc, red);
-        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, mm.nb_w, mm.nb_uv);
+        stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, mm.nb_w, mm.nb_uv, mm.nzc_w, mm.nzc_uv);
     }
 }
 
 // Converts the band-statistics accumulator of the preceding wall launch.
-__global__ void k_stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv)
+__global__ void k_stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv,
+                             int64_t nzc_w, int64_t nzc_uv)
 {
-    if (threadIdx.x == 0) stats_emit(sacc, stats, count_w, count_uv);
+    if (threadIdx.x == 0) stats_emit(sacc, stats, count_w, count_uv, nzc_w, nzc_uv);
 }
 
 // One member's wall-model fields, held in registers while a thread walks its
@@ -1097,7 +1097,7 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
             issue(q + 1);
             issued = q + 2;
         }
-        const bool ok = mbar_wait(&rbar[q & 1], (uint32_t)((q >> 1) & 1), p.status, kDevStatusFullTimeout);
+        const bool ok = mbar_wait(&rbar[q & 1], (uint32_t)((q >> 1) & 1), p.status, kDevStatusFullTimeout, p.wait_ns);
         if (ok && threadIdx.x == 0) consumed = q + 1;
         const int64_t c0 = r0 + q * CH, c1 = min(r1, c0 + CH);
         const Rec *const chunk = rbuf + (q & 1) * CH;
@@ -1187,6 +1187,7 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
         double *src = p.bstats + ((int64_t)m * 2 + bnd) * 4;
         wmibm_band_stats st;
         st.count = bnd == 0 ? p.list[m].nb_w : p.list[m].nb_uv;
+        st.n_zclamped = bnd == 0 ? p.list[m].nzc_w : p.list[m].nzc_uv;
         st.sum_tw = __ldcg(src + 0);
         st.sum_tw2 = __ldcg(src + 1);
         st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 2)));
@@ -1338,7 +1339,7 @@ __device__ void wall_stage(const KParams<T> &p, const typename RecOf<T>::type *r
         __syncwarp();
         if (lane == 0 && atomicAdd(warps_done, 1u) == (unsigned)p.ncons - 1) {
             __threadfence();
-            atomicAdd(p.wall_done, 1u);
+            if (!p.hold_release) atomicAdd(p.wall_done, 1u);
         }
     }
 }
@@ -1424,7 +1425,7 @@ __device__ void wall_warps_run(const KParams<T> &p, int ww, int nww, int lane, u
     __syncwarp();
     if (lane == 0 && atomicAdd(warps_done, 1u) == (unsigned)nww - 1) {
         __threadfence();
-        atomicAdd(p.wall_done, 1u);
+        if (!p.hold_release) atomicAdd(p.wall_done, 1u);
     }
 }
 
@@ -1482,7 +1483,7 @@ __device__ void wall_phase_fused(const KParams<T> &p, int64_t wb, int64_t nwb, i
         for (int w = 1; w < nwarps; ++w) stats_combine(acc, red[w]);
         if (p.stats) stats_red(acc, p.sacc);     // converted by the last block out of the launch
         __threadfence();
-        atomicAdd(p.wall_done, 1u);
+        if (!p.hold_release) atomicAdd(p.wall_done, 1u);
     }
 }
 
@@ -1521,7 +1522,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         // statistics of the wall launch before this one (complete: stream order,
         // or the grid dependency of a programmatic launch)
         if (MODE == kAfterWall) wait_wall_kernel();
-        stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+        stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv, p.one.nzc_w, p.one.nzc_uv);
     }
     if (MODE == kFused && p.wall_blocks > 0 && (int)blockIdx.x < p.wall_blocks) {
         // dedicated wall block: every warp evaluates the block's share of the wall model
@@ -1546,7 +1547,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
             } else {
                 consumers_sync(p.ncons);
                 if (cw == 0 && lane == 0)
-                    s_go = wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status) ? 1 : 0;
+                    s_go = wait_counter(p.wall_done, wall_target(p.wall_blocks), p.status, p.wait_ns) ? 1 : 0;
                 consumers_sync(p.ncons);
                 go = s_go != 0;
             }
@@ -1572,7 +1573,8 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
         if (s_last) {
             __threadfence();
             if (MODE == kFused) {
-                if (threadIdx.x == 0 && p.stats) stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv);
+                if (threadIdx.x == 0 && p.stats)
+                    stats_emit(p.sacc, p.stats, p.one.nb_w, p.one.nb_uv, p.one.nzc_w, p.one.nzc_uv);
             } else if (p.stats) {
                 // every member's accumulator [member][band][4] into its two records, then cleared
                 for (int q = threadIdx.x; q < 2 * p.nmembers; q += blockDim.x) {
@@ -1580,6 +1582,7 @@ __global__ void __launch_bounds__(512) k_stencil(KParams<T> p)
                     double *src = p.bstats + (int64_t)q * 4;
                     wmibm_band_stats st;
                     st.count = (q & 1) ? mm.nb_uv : mm.nb_w;
+                    st.n_zclamped = (q & 1) ? mm.nzc_uv : mm.nzc_w;
                     st.sum_tw = __ldcg(src + 0);
                     st.sum_tw2 = __ldcg(src + 1);
                     st.min_tw = -__longlong_as_double((long long)__ldcg(reinterpret_cast<unsigned long long *>(src + 2)));
@@ -1762,6 +1765,8 @@ void single_params(const wmibm_handle *h, KParams<T> &p, bool step)
     p.wall_warps = 0;
     p.dyn_chunk = 0;
     p.dyn_ctr = nullptr;
+    p.wait_ns = h->wait_ns;
+    p.hold_release = h->hold_release;
 }
 
 template <typename T, typename VEL>
@@ -1801,7 +1806,7 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
     k_wall<T, VEL><<<blocks, wthreads, 0, stream>>>(p);
     int st = cuda_status(h, cudaGetLastError(), "k_wall launch");
     if (st || !p.sacc || !emit) return st;
-    k_stats_emit<<<1, 32, 0, stream>>>(p.sacc, stats, p.one.nb_w, p.one.nb_uv);
+    k_stats_emit<<<1, 32, 0, stream>>>(p.sacc, stats, p.one.nb_w, p.one.nb_uv, p.one.nzc_w, p.one.nzc_uv);
     return cuda_status(h, cudaGetLastError(), "k_stats_emit launch");
 }
 
@@ -1829,6 +1834,8 @@ void fill_member(const wmibm_handle *h, Member<T> &m, const void *const tau[6], 
     m.rec = h->rec;
     m.nb_w = h->lists.n[WMIBM_LIST_BAND_W];
     m.nb_uv = h->lists.n[WMIBM_LIST_BAND_UV];
+    m.nzc_w = h->nzclamp[0];
+    m.nzc_uv = h->nzclamp[1];
     m.r_off = 0;
     m.runs_w = h->runs[0]; m.runs_uv = h->runs[1];
     m.nr_w = h->nruns[0]; m.nr_uv = h->nruns[1];

@@ -67,9 +67,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Waits for the phase of `bar` with the given parity to complete.  Gives up
-// (returns false) after kWaitLimitNs, recording `code` in *status, or at once
-// if *status already holds a code.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, int code)
+// (returns false) after limit_ns of %globaltimer, recording `code` in *status,
+// or at once if *status already holds a code.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, int code,
+                                          uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
@@ -77,7 +78,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 7u) == 0) {
             if (*(volatile int *)status != 0) return false;
-            if (global_timer_ns() - t0 > kWaitLimitNs) {
+            if (global_timer_ns() - t0 > limit_ns) {
                 atomicExch(status, code);
                 return false;
             }

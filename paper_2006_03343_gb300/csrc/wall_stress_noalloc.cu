@@ -8,7 +8,11 @@
 // allocates nothing: the per-block partial statistics and the last-block ticket
 // of the wall kernel live in g_wall_scratch below, which every GPU that loads
 // the library holds until the process exits.
+#include <cuda.h>
+
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -25,6 +29,9 @@ namespace {
 constexpr int kThreadsPerBlock = 256;
 constexpr int kRecordsPerThread = 2;
 constexpr unsigned kMaxBlocks = 2048;                                   // blocks of the wall kernel
+// The array bounds only the number of blocks (one partial per block); the kernel
+// walks any number of records with a grid stride.  The record limit is a choice:
+// one call stays within one pass of its grid, two records per thread.
 constexpr int64_t kMaxRecords = (int64_t)kMaxBlocks * kThreadsPerBlock * kRecordsPerThread;   // 1,048,576
 constexpr size_t kTicketBytes = 256;
 constexpr size_t kScratchBytes = kTicketBytes + (size_t)kMaxBlocks * kStatVals * sizeof(double);  // 131,328
@@ -33,7 +40,48 @@ constexpr size_t kScratchBytes = kTicketBytes + (size_t)kMaxBlocks * kStatVals *
 static __device__ __align__(256) unsigned char g_wall_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices];      // device address of g_wall_scratch, per device
+
+// Device address of g_wall_scratch per device, with the id of the context it was
+// looked up in: the module, and with it the array, moves when a device's context
+// is made again (after cudaDeviceReset, for instance), so a new context means a
+// new look-up.  Filled under a lock; several host threads may call at once.
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void *addr;
+};
+ScratchSlot g_scratch[kMaxDevices];
+std::mutex g_scratch_lock;
+
+// Id of the calling thread's current context (driver entry points found once at
+// run time, so that the library needs no link to the driver library); 0 where the
+// driver offers none.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+std::once_flag g_entry_once;
+std::atomic<CtxGetCurrentFn> g_ctx_get_current{nullptr};
+std::atomic<CtxGetIdFn> g_ctx_get_id{nullptr};
+
+unsigned long long current_context_id()
+{
+    std::call_once(g_entry_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current.store(reinterpret_cast<CtxGetCurrentFn>(f));
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id.store(reinterpret_cast<CtxGetIdFn>(f));
+    });
+    CtxGetCurrentFn get_current = g_ctx_get_current.load();
+    CtxGetIdFn get_id = g_ctx_get_id.load();
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 }  // namespace
 
@@ -56,15 +104,22 @@ extern "C" int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const v
         return set_error(h, WMIBM_EINVAL, "device %d beyond the %d devices this entry point serves", h->device,
                          kMaxDevices);
 
-    // set-up, once per device, with that device current: the host-side name of
-    // a __device__ array is not a device address
-    if (g_scratch_addr[h->device] == nullptr) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_wall_scratch);
-        if (e != cudaSuccess) return cuda_status(h, e, "cudaGetSymbolAddress(g_wall_scratch)");
-        g_scratch_addr[h->device] = ptr;
+    // set-up, once per device (and again when its context was made anew), with that
+    // device current: the host-side name of a __device__ array is not a device address
+    unsigned char *base = nullptr;
+    {
+        const unsigned long long ctx = current_context_id();
+        std::lock_guard<std::mutex> lock(g_scratch_lock);
+        ScratchSlot &slot = g_scratch[h->device];
+        if (slot.addr == nullptr || slot.ctx_id != ctx) {
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_wall_scratch);
+            if (e != cudaSuccess) return cuda_status(h, e, "cudaGetSymbolAddress(g_wall_scratch)");
+            slot.addr = ptr;
+            slot.ctx_id = ctx;
+        }
+        base = (unsigned char *)slot.addr;
     }
-    unsigned char *base = (unsigned char *)g_scratch_addr[h->device];
     unsigned *ticket = (unsigned *)base;
     void *partials = base + kTicketBytes;
 

@@ -30,7 +30,7 @@ EXPORTED = ("wmibm_init", "wmibm_wall_stress", "wmibm_force", "wmibm_mask", "wmi
             "wmibm_batch_set_fields", "wmibm_batch_set_tuning", "wmibm_batch_step", "wmibm_batch_traffic_bytes",
             "wmibm_batch_points", "wmibm_batch_last_error", "wmibm_batch_destroy", "wmibm_set_log_z0",
             "wmibm_backward", "wmibm_batch_wall_stress_force", "wmibm_force_spectral", "wmibm_spectral_shape", "wmibm_sgs_wall_terms", "wmibm_sgs_stress", "wmibm_sgs_force",
-            "wmibm_heightfield_sdf")
+            "wmibm_heightfield_sdf", "wmibm_batch_device_status")
 
 
 class WmibmError(RuntimeError):
@@ -46,7 +46,7 @@ class Grid(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("phi_b", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32), ("zclamp", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -65,7 +65,9 @@ class MemberFields(ctypes.Structure):
 
 
 STATS_DTYPE = np.dtype([("count", "<i8"), ("sum_tw", "<f8"), ("sum_tw2", "<f8"), ("min_tw", "<f8"),
-                        ("max_ur", "<f8")])
+                        ("max_ur", "<f8"), ("n_zclamped", "<i8")])
+STATS_WORDS = STATS_DTYPE.itemsize // 8          # 8-byte words of one wmibm_band_stats
+ZCLAMP_CLAMP, ZCLAMP_REJECT = 0, 1
 
 _lib = None
 _VP = ctypes.c_void_p
@@ -131,6 +133,8 @@ def load(path: Optional[str] = None):
     L.wmibm_batch_step.restype = ctypes.c_int
     L.wmibm_batch_wall_stress_force.argtypes = [_VP, _VP, _VP]
     L.wmibm_batch_wall_stress_force.restype = ctypes.c_int
+    L.wmibm_batch_device_status.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32), _VP]
+    L.wmibm_batch_device_status.restype = ctypes.c_int
     L.wmibm_batch_traffic_bytes.argtypes = [_VP, ctypes.c_int32]
     L.wmibm_batch_traffic_bytes.restype = ctypes.c_int64
     L.wmibm_batch_points.argtypes = [_VP]
@@ -209,10 +213,11 @@ class Handle:
     """One terrain on one GPU: wraps wmibm_init / wmibm_destroy and the per-step calls.
 
     dtype: "f32" or "f64" (stress, force and arithmetic); vel_dtype: None (same as
-    dtype) or "bf16" (with f32)."""
+    dtype) or "bf16" (with f32); zclamp: ZCLAMP_CLAMP (clamp the level of sample
+    points outside the grid and count them) or ZCLAMP_REJECT (fail instead)."""
 
     def __init__(self, grid, phi_uv, phi_w, z0, phi_c, phi_b=0.0, dtype="f32", vel_dtype=None, kappa=0.4,
-                 stream=None):
+                 stream=None, zclamp=0):
         import torch
         L = load()
         nx, ny, nz, lx, ly, lz = grid
@@ -232,7 +237,7 @@ class Handle:
             z0a = np.ascontiguousarray(z0, np.float64)
             is_field = 1
         g = Grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz))
-        o = Opts(float(phi_b), float(kappa), DTYPE_CODES[dtype], DTYPE_CODES[self.vel_dtype])
+        o = Opts(float(phi_b), float(kappa), DTYPE_CODES[dtype], DTYPE_CODES[self.vel_dtype], int(zclamp))
         h = ctypes.c_void_p()
         st = L.wmibm_init(ctypes.byref(h), ctypes.byref(g), phi_uv.ctypes.data, phi_w.ctypes.data,
                           z0a.ctypes.data, is_field, float(phi_c), ctypes.byref(o), _stream_ptr(stream))
@@ -242,9 +247,9 @@ class Handle:
         self._L = L
 
     @classmethod
-    def from_case(cls, case, dtype=None, vel_dtype=None, stream=None):
+    def from_case(cls, case, dtype=None, vel_dtype=None, stream=None, zclamp=0):
         return cls(case.grid, case.phi_uv, case.phi_w, case.z0, case.phi_c, case.phi_b,
-                   dtype=dtype or case.dtype, vel_dtype=vel_dtype, stream=stream)
+                   dtype=dtype or case.dtype, vel_dtype=vel_dtype, stream=stream, zclamp=zclamp)
 
     # ------------------------------------------------------------------ #
     def _check(self, st):
@@ -260,7 +265,7 @@ class Handle:
 
     def new_stats(self):
         import torch
-        return torch.zeros(10, dtype=torch.float64, device=self.device)
+        return torch.zeros(2 * STATS_WORDS, dtype=torch.float64, device=self.device)
 
     @staticmethod
     def parse_stats(stats_tensor):
@@ -547,7 +552,7 @@ class Batch:
 
     def new_stats(self):
         import torch
-        return torch.zeros(10 * len(self.handles), dtype=torch.float64, device=self.handles[0].device)
+        return torch.zeros(2 * STATS_WORDS * len(self.handles), dtype=torch.float64, device=self.handles[0].device)
 
     def step(self, stats=None, stream=None):
         self._check(self._L.wmibm_batch_step(self._b, None if stats is None else _dptr(stats), _stream_ptr(stream)))
@@ -559,6 +564,11 @@ class Batch:
 
     def points(self) -> int:
         return int(self._L.wmibm_batch_points(self._b))
+
+    def device_status(self, stream=None) -> int:
+        out = ctypes.c_int32(-1)
+        self._check(self._L.wmibm_batch_device_status(self._b, ctypes.byref(out), _stream_ptr(stream)))
+        return int(out.value)
 
     def traffic_bytes(self, which: int) -> int:
         return int(self._L.wmibm_batch_traffic_bytes(self._b, int(which)))

@@ -11,9 +11,12 @@ STATS_TOL = {"f64": 1e-11, "f32": 1e-5}
 
 
 def normwise(gpu, ref):
-    """max |gpu - ref| / max |ref| (0/0 counts as 0) and the RMS of the error."""
+    """max |gpu - ref| / max |ref| (0/0 counts as 0) and the RMS of the error; a
+    non-finite GPU entry makes the error infinite."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
+    if gpu.size and not np.all(np.isfinite(gpu)):
+        return float("inf"), float("inf")
     den = np.max(np.abs(ref)) if ref.size else 0.0
     err = np.max(np.abs(gpu - ref)) if ref.size else 0.0
     rms = float(np.sqrt(np.mean((gpu - ref) ** 2))) if ref.size else 0.0
@@ -56,9 +59,25 @@ def oracle_step(oracle, case, u=None, v=None, w=None, tau=None):
     return tau, f, stats
 
 
+def poisoned_tau(case):
+    """The case's stresses with NaN at every band and solid node (the entries the
+    wall model writes), so that an entry the GPU leaves unwritten shows up."""
+    out = {}
+    for k in inputs.TAU_NAMES:
+        a = case.tau[k].copy()
+        if inputs.TAU_ON_W[k]:
+            a[case.phi_w <= case.phi_b] = np.nan
+        else:
+            a[case.phi_uv <= 2.0 * case.phi_b] = np.nan
+        out[k] = a
+    return out
+
+
 def gpu_step(handle, case, dtype, vel_dtype=None, offset=0):
     """wall_stress then force through the C ABI; `offset` shifts every device
-    buffer by that many elements (misaligned pointers take the scalar path)."""
+    buffer by that many elements (misaligned pointers take the scalar path).  The
+    forcing starts as NaN everywhere and the stress as NaN where the wall model
+    writes it."""
     import torch
     vel_dtype = vel_dtype or dtype
 
@@ -71,8 +90,9 @@ def gpu_step(handle, case, dtype, vel_dtype=None, offset=0):
         return view
 
     u, v, w = (dev(x, vel_dtype) for x in (case.u, case.v, case.w))
-    tau = [dev(case.tau[k], dtype) for k in inputs.TAU_NAMES]
-    f = [dev(np.zeros(case.shape), dtype) for _ in range(3)]
+    pt = poisoned_tau(case)
+    tau = [dev(pt[k], dtype) for k in inputs.TAU_NAMES]
+    f = [dev(np.full(case.shape, np.nan), dtype) for _ in range(3)]
     stats = handle.new_stats()
     handle.wall_stress(u, v, w, tau, stats)
     handle.force(tau, f)
@@ -93,6 +113,7 @@ def assert_stats_close(gs, os_, dtype):
     tol = STATS_TOL[dtype]
     for b in range(2):
         assert gs[b]["count"] == int(os_[b, 0])
+        assert gs[b]["n_zclamped"] == int(os_[b, 5])
         for col, name in ((1, "sum_tw"), (2, "sum_tw2"), (3, "min_tw"), (4, "max_ur")):
             ref = os_[b, col]
             got = gs[b][name]
@@ -101,12 +122,14 @@ def assert_stats_close(gs, os_, dtype):
 
 
 def gpu_fused(handle, case, dtype, vel_dtype=None, with_stats=True):
-    """The fused wall stress + force pass through the C ABI."""
+    """The fused wall stress + force pass through the C ABI (outputs poisoned with
+    NaN as in gpu_step)."""
     import torch
     vel_dtype = vel_dtype or dtype
     u, v, w = (to_dev(x, vel_dtype) for x in (case.u, case.v, case.w))
-    tau = [to_dev(case.tau[k], dtype) for k in inputs.TAU_NAMES]
-    f = [to_dev(np.zeros(case.shape), dtype) for _ in range(3)]
+    pt = poisoned_tau(case)
+    tau = [to_dev(pt[k], dtype) for k in inputs.TAU_NAMES]
+    f = [to_dev(np.full(case.shape, np.nan), dtype) for _ in range(3)]
     stats = handle.new_stats() if with_stats else None
     handle.wall_stress_force(u, v, w, tau, f, stats)
     torch.cuda.synchronize()

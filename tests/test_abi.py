@@ -132,3 +132,28 @@ def test_later_entry_points_reject_null_arguments(lib):
     assert lib.wmibm_batch_traffic_bytes(None, 0) == -1
     assert lib.wmibm_batch_points(None) == -1
     lib.wmibm_batch_destroy(None)
+
+
+def test_init_rejects_unknown_zclamp_mode(lib):
+    from paper_2006_03343_gb300 import wmibm
+    phi = np.ones((5, 4, 4))
+    o = wmibm.Opts(0.0, 0.0, wmibm.F32, wmibm.F32, 7)
+    st, h, msg = _init(lib, (4, 4, 5, 1.0, 1.0, 1.0), phi, phi, np.array([1e-4]), 1.5 / 4, o)
+    assert st == wmibm.EINVAL and "zclamp" in msg and not h.value
+
+
+def test_injected_allocation_failure_before_any_gpu_work(lib, monkeypatch):
+    """WMIBM_FAULT=alloc:1 fails the first allocation of wmibm_init (the handle's
+    host memory, made before any CUDA call): ENOMEM, no handle, a message; unset,
+    the same call gets past it (to the device query, which has no GPU here)."""
+    from paper_2006_03343_gb300 import wmibm
+    phi = np.ones((5, 4, 4))
+    args = ((4, 4, 5, 1.0, 1.0, 1.0), phi, phi, np.array([1e-4]), 1.5 / 4)
+    monkeypatch.setenv("WMIBM_FAULT", "alloc:1")
+    st, h, msg = _init(lib, *args)
+    assert st == wmibm.ENOMEM and not h.value and "allocation" in msg
+    monkeypatch.delenv("WMIBM_FAULT")
+    st, h, _ = _init(lib, *args)
+    assert st != wmibm.ENOMEM
+    if st == wmibm.OK:
+        lib.wmibm_destroy(h)

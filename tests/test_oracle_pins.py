@@ -60,6 +60,39 @@ def test_flat_wall_log_law(oracle_mod, theta, field_z0):
     np.testing.assert_allclose(stats[0, 2], nx * ny * ustar ** 4, rtol=1e-13)
     np.testing.assert_allclose(stats[0, 3], -ustar ** 2, rtol=1e-13)
     np.testing.assert_allclose(stats[0, 4], (ustar / KAPPA) * math.log(1.5 * dz / z0), rtol=1e-13)
+    assert stats[0, 5] == 0 and stats[1, 5] == 0          # x_c = 1.5 dz lies inside both grids
+
+
+# --------------------------------------------------------------------------- #
+# reading R3: sample points beyond the physical levels are clamped, and counted
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("above", [False, True])
+def test_zclamp_count_flat_wall_near_lid(oracle_mod, above):
+    """A flat wall at height h (phi = z - h, n = (0,0,1) exactly): every band node
+    samples at z_c = h + phi_c (Sec. 3.3, reading R2).  The top physical uv-level is
+    (nz - 1.5) dz (the level nz - 1 lies above the lid) and the top w-level (nz - 1) dz,
+    so the interpolation clamps every band node's sample point exactly when
+    h + phi_c > (nz - 1.5) dz, and none otherwise.  The clamped sample takes the top
+    uv-level's velocity; w is 0 there in this field."""
+    nx, ny, nz = 8, 6, 17
+    dz = 1.0 / (nz - 1)
+    phi_c = 1.5 * dz
+    top_uv = (nz - 1.5) * dz
+    h = top_uv - phi_c + (0.2 if above else -0.2) * dz
+    grid = (nx, ny, nz, 1.0, 1.0, 1.0)
+    z_uv = (np.arange(nz) + 0.5) * dz
+    z_w = np.arange(nz) * dz
+    phi_uv = np.ascontiguousarray(np.broadcast_to((z_uv - h)[:, None, None], (nz, ny, nx)))
+    phi_w = np.ascontiguousarray(np.broadcast_to((z_w - h)[:, None, None], (nz, ny, nx)))
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((nz, ny, nx))
+    v = rng.standard_normal((nz, ny, nx))
+    w = rng.standard_normal((nz, ny, nx))
+    tau = _fresh_tau((nz, ny, nx), 0.0)
+    stats = oracle_mod.wall_stress(grid, phi_uv, phi_w, 1e-4, phi_c, 0.5 * dz, u, v, w, tau)
+    assert stats[0, 0] > 0 and stats[1, 0] > 0
+    for b in range(2):
+        assert stats[b, 5] == (stats[b, 0] if above else 0)
 
 
 # --------------------------------------------------------------------------- #
