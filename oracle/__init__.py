@@ -170,6 +170,8 @@ def wall_stress(grid, phi_uv, phi_w, z0, phi_c, phi_b, u, v, w, tau, kappa=0.4, 
                                  float(phi_c), float(kappa), float(phi_b), _p(u), _p(v), _p(w),
                                  _p(tau["txx"]), _p(tau["txy"]), _p(tau["tyy"]), _p(tau["tzz"]),
                                  _p(tau["txz"]), _p(tau["tyz"]), _p(stats))
+    if rc == -2:
+        raise MemoryError("oracle: out of memory in the wall-stress pass")
     if rc != 0:
         raise ValueError("oracle: z0 must satisfy 0 < z0 < phi_c")
     return stats.reshape(2, 6)

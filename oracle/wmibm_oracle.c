@@ -317,6 +317,77 @@ static void stats_add(orc_stats_acc *s, double tw, double ur, int zclamped)
 }
 
 /*
+ * The wall model on one grid (is_w: the w-grid, writing txz, tyz; else the
+ * uv-grid, writing txx, txy, tyy, tzz), the levels shared among threads: a
+ * level's band nodes are evaluated in its own loop, their (tau_w, |U_r|, clamp)
+ * kept at the node's place in the grid's band order (counted per level first),
+ * and the statistics added afterwards on one thread in that order, so that they
+ * come out exactly as from a single loop over the nodes.  Returns 0, or -2 when
+ * memory runs out.
+ */
+static int wall_stress_grid(const orc_grid *g, const double *phi, int is_w, double phi_b,
+                            const double *z0, int z0_is_field, double phi_c, double kappa,
+                            const double *u, const double *v, const double *w, double *t[4],
+                            orc_stats_acc *acc)
+{
+    const int64_t nx = g->nx, ny = g->ny, nz = g->nz;
+    int64_t *first = (int64_t *)calloc((size_t)nz + 1, sizeof(int64_t));
+    if (!first) return -2;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i)
+                if (classify_node(phi[at(g, i, j, k)], phi_b, is_w) == ORC_BAND) ++c;
+        first[k + 1] = c;
+    }
+    for (int64_t k = 0; k < nz; ++k) first[k + 1] += first[k];
+    const int64_t nband = first[nz];
+    double *res = (double *)malloc(sizeof(double) * 3 * (size_t)(nband > 0 ? nband : 1));
+    if (!res) {
+        free(first);
+        return -2;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nz; ++k) {
+        int64_t q = first[k];
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = at(g, i, j, k);
+                int c = classify_node(phi[p], phi_b, is_w);
+                if (c == ORC_SOLID) {
+                    if (is_w) {
+                        t[0][p] = 0.0; t[1][p] = 0.0;
+                    } else {
+                        t[0][p] = 0.0; t[1][p] = 0.0; t[2][p] = 0.0; t[3][p] = 0.0;
+                    }
+                } else if (c == ORC_BAND) {
+                    orc_node_result r;
+                    wall_model_at(g, phi, is_w, i, j, k, u, v, w, roughness_log(z0, z0_is_field, p, phi_c), phi_c,
+                                  kappa, &r);
+                    if (is_w) {
+                        t[0][p] = r.tau[0][2];   /* txz */
+                        t[1][p] = r.tau[1][2];   /* tyz */
+                    } else {
+                        t[0][p] = r.tau[0][0];   /* txx */
+                        t[1][p] = r.tau[0][1];   /* txy */
+                        t[2][p] = r.tau[1][1];   /* tyy */
+                        t[3][p] = r.tau[2][2];   /* tzz */
+                    }
+                    res[3 * q + 0] = r.tau_w;
+                    res[3 * q + 1] = r.ur;
+                    res[3 * q + 2] = (double)r.zclamped;
+                    ++q;
+                }
+            }
+    }
+    for (int64_t q = 0; q < nband; ++q) stats_add(acc, res[3 * q + 0], res[3 * q + 1], (int)res[3 * q + 2]);
+    free(res);
+    free(first);
+    return 0;
+}
+
+/*
  * One wall-stress pass (Sec. 3.3).  tau arrays are in/out: fluid values pass
  * through, band values are replaced by the wall model, solid values are set
  * to zero.  txz, tyz are modeled at w-band nodes; txx, txy, tyy, tzz at
@@ -326,7 +397,7 @@ static void stats_add(orc_stats_acc *s, double tw, double ur, int zclamped)
  * stats (may be NULL): 2 x {count, sum tau_w, sum tau_w^2, min tau_w, max U_r,
  * nodes whose x_c was clamped in z (R3)}, first for the w-band, then for the
  * uv-band, counts stored as doubles.
- * Returns 0, or -1 if some z0 does not satisfy 0 < z0 < phi_c.
+ * Returns 0, -1 if some z0 does not satisfy 0 < z0 < phi_c, -2 if memory runs out.
  */
 int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, double lz,
                     const double *phi_uv, const double *phi_w,
@@ -345,44 +416,10 @@ int orc_wall_stress(int64_t nx, int64_t ny, int64_t nz, double lx, double ly, do
     orc_stats_acc acc[2];
     memset(acc, 0, sizeof(acc));
 
-    /* w-grid: txz, tyz */
-    for (int64_t k = 0; k < nz; ++k)
-        for (int64_t j = 0; j < ny; ++j)
-            for (int64_t i = 0; i < nx; ++i) {
-                int64_t p = at(&g, i, j, k);
-                int c = classify_node(phi_w[p], phi_b, 1);
-                if (c == ORC_SOLID) {
-                    txz[p] = 0.0;
-                    tyz[p] = 0.0;
-                } else if (c == ORC_BAND) {
-                    orc_node_result r;
-                    wall_model_at(&g, phi_w, 1, i, j, k, u, v, w, roughness_log(z0, z0_is_field, p, phi_c), phi_c,
-                                  kappa, &r);
-                    txz[p] = r.tau[0][2];
-                    tyz[p] = r.tau[1][2];
-                    stats_add(&acc[0], r.tau_w, r.ur, r.zclamped);
-                }
-            }
-
-    /* uv-grid: txx, txy, tyy, tzz */
-    for (int64_t k = 0; k < nz; ++k)
-        for (int64_t j = 0; j < ny; ++j)
-            for (int64_t i = 0; i < nx; ++i) {
-                int64_t p = at(&g, i, j, k);
-                int c = classify_node(phi_uv[p], phi_b, 0);
-                if (c == ORC_SOLID) {
-                    txx[p] = 0.0; txy[p] = 0.0; tyy[p] = 0.0; tzz[p] = 0.0;
-                } else if (c == ORC_BAND) {
-                    orc_node_result r;
-                    wall_model_at(&g, phi_uv, 0, i, j, k, u, v, w, roughness_log(z0, z0_is_field, p, phi_c), phi_c,
-                                  kappa, &r);
-                    txx[p] = r.tau[0][0];
-                    txy[p] = r.tau[0][1];
-                    tyy[p] = r.tau[1][1];
-                    tzz[p] = r.tau[2][2];
-                    stats_add(&acc[1], r.tau_w, r.ur, r.zclamped);
-                }
-            }
+    double *tw_[4] = { txz, tyz, NULL, NULL };              /* w-grid: txz, tyz */
+    double *tuv[4] = { txx, txy, tyy, tzz };                /* uv-grid: txx, txy, tyy, tzz */
+    if (wall_stress_grid(&g, phi_w, 1, phi_b, z0, z0_is_field, phi_c, kappa, u, v, w, tw_, &acc[0])) return -2;
+    if (wall_stress_grid(&g, phi_uv, 0, phi_b, z0, z0_is_field, phi_c, kappa, u, v, w, tuv, &acc[1])) return -2;
 
     if (stats) {
         for (int s = 0; s < 2; ++s) {
