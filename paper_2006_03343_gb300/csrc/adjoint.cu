@@ -374,6 +374,7 @@ int backward_impl(wmibm_handle *h, const void *const g[3], const void *const uvw
 
 extern "C" int wmibm_set_log_z0(wmibm_handle *h, const void *logz0, void *stream)
 {
+    ApiRange nvtx_range("wmibm_set_log_z0");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_device(h);
     if (st) return st;
@@ -388,6 +389,7 @@ extern "C" int wmibm_set_log_z0(wmibm_handle *h, const void *logz0, void *stream
 extern "C" int wmibm_backward(wmibm_handle *h, const void *const g[3], const void *const uvw[3], void *du,
                               void *dv, void *dw, void *dlogz0, void *stream)
 {
+    ApiRange nvtx_range("wmibm_backward");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!g || !g[0] || !g[1] || !g[2]) return set_error(h, WMIBM_EINVAL, "NULL forcing weight g");
     if (!uvw || !uvw[0] || !uvw[1] || !uvw[2]) return set_error(h, WMIBM_EINVAL, "NULL velocity pointer");

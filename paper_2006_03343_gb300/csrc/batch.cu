@@ -182,6 +182,7 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
 
 extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *members, int32_t count, void *stream)
 {
+    ApiRange nvtx_range("wmibm_batch_create");
     if (!out) return WMIBM_EINVAL;
     *out = nullptr;
     if (!members || count < 1 || count > kMaxBatchMembers) return WMIBM_EINVAL;
@@ -240,6 +241,7 @@ extern "C" int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *member
 
 extern "C" int wmibm_batch_set_fields(wmibm_batch *b, const wmibm_member_fields *fields, void *stream)
 {
+    ApiRange nvtx_range("wmibm_batch_set_fields");
     if (!b) return WMIBM_EINVAL;
     if (!fields) return berr(b, WMIBM_EINVAL, "NULL fields");
     int dev = -1;
@@ -263,6 +265,7 @@ extern "C" int wmibm_batch_set_fields(wmibm_batch *b, const wmibm_member_fields 
 
 extern "C" int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t)
 {
+    ApiRange nvtx_range("wmibm_batch_set_tuning");
     if (!b || !t) return WMIBM_EINVAL;
     wmibm_tuning old = b->tuning;
     b->tuning = *t;
@@ -296,16 +299,19 @@ static int batch_run(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, void 
 
 extern "C" int wmibm_batch_step(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
 {
+    ApiRange nvtx_range("wmibm_batch_step");
     return batch_run(b, stats, 1, stream);
 }
 
 extern "C" int wmibm_batch_wall_stress_force(wmibm_batch *b, wmibm_band_stats *stats, void *stream)
 {
+    ApiRange nvtx_range("wmibm_batch_wall_stress_force");
     return batch_run(b, stats, 0, stream);
 }
 
 extern "C" int wmibm_batch_device_status(wmibm_batch *b, int32_t *out, void *stream)
 {
+    ApiRange nvtx_range("wmibm_batch_device_status");
     if (!b) return WMIBM_EINVAL;
     if (!out) return berr(b, WMIBM_EINVAL, "NULL output");
     int dev = -1;
@@ -338,6 +344,7 @@ extern "C" const char *wmibm_batch_last_error(const wmibm_batch *b) { return b ?
 
 extern "C" void wmibm_batch_destroy(wmibm_batch *b)
 {
+    ApiRange nvtx_range("wmibm_batch_destroy");
     if (!b) return;
     cudaDeviceSynchronize();
     cudaFree(b->dev_members);

@@ -211,6 +211,7 @@ int force_any(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, voi
 
 extern "C" int wmibm_force(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *stream)
 {
+    ApiRange nvtx_range("wmibm_force");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!tau || !fx || !fy || !fz) return set_error(h, WMIBM_EINVAL, "NULL stress or force pointer");
     for (int c = 0; c < 6; ++c)

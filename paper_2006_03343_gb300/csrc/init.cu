@@ -359,6 +359,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
                           const double *z0, int32_t z0_is_field, double phi_c, const wmibm_opts *opts,
                           void *stream_)
 {
+    ApiRange nvtx_range("wmibm_init");
     cudaStream_t stream = (cudaStream_t)stream_;
     g_init_error[0] = 0;
     fault_arm();
@@ -610,6 +611,7 @@ extern "C" int64_t wmibm_list_size(const wmibm_handle *h, int32_t which)
 
 extern "C" int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap, void *stream)
 {
+    ApiRange nvtx_range("wmibm_export_list");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (which < 0 || which > 5) return set_error(h, WMIBM_EINVAL, "list %d does not exist", which);
     if (!dst || cap < h->lists.n[which])
@@ -632,6 +634,7 @@ extern "C" int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which)
 
 extern "C" void wmibm_destroy(wmibm_handle *h)
 {
+    ApiRange nvtx_range("wmibm_destroy");
     if (!h) return;
     cudaDeviceSynchronize();
     free_handle(h);
@@ -657,6 +660,7 @@ extern "C" const char *wmibm_last_error(const wmibm_handle *h)
 
 extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
 {
+    ApiRange nvtx_range("wmibm_set_tuning");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!t) return set_error(h, WMIBM_EINVAL, "NULL tuning");
     if (t->force_path < 0 || t->force_path > 6) return set_error(h, WMIBM_EINVAL, "force_path must be 0..6");
@@ -685,6 +689,7 @@ extern "C" int wmibm_get_tuning(const wmibm_handle *h, wmibm_tuning *t)
 
 extern "C" int wmibm_device_status(wmibm_handle *h, int32_t *out, void *stream)
 {
+    ApiRange nvtx_range("wmibm_device_status");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!out) return set_error(h, WMIBM_EINVAL, "NULL output");
     int st = check_device(h);

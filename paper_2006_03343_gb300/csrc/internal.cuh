@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdarg.h>
@@ -101,6 +102,16 @@ int spectral_setup(wmibm_handle *h, cudaStream_t stream);     // spectral.cu, on
 void spectral_free(wmibm_handle *h);
 
 inline size_t elem_size(int32_t t) { return t == WMIBM_F64 ? 8 : (t == WMIBM_BF16 ? 2 : 4); }
+
+// An NVTX range around one entry point of the C ABI (host side: the argument
+// checks and the enqueueing of its launches), named after it, so that profiler
+// timelines show each call; without a profiler attached it costs a branch.
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
 
 // Allocations of the library go through these (fault.cu): WMIBM_FAULT=alloc:N,
 // read by fault_arm() at the start of wmibm_init and wmibm_batch_create, makes

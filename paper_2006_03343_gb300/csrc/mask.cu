@@ -144,6 +144,7 @@ int mask_impl(wmibm_handle *h, void *u, void *v, void *w, const void *const grad
 extern "C" int wmibm_mask(wmibm_handle *h, void *u, void *v, void *w, const void *const gradp[3], double dt,
                           void *stream)
 {
+    ApiRange nvtx_range("wmibm_mask");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!u || !v || !w) return set_error(h, WMIBM_EINVAL, "NULL velocity pointer");
     if (gradp && (!gradp[0] || !gradp[1] || !gradp[2]))
@@ -168,6 +169,7 @@ extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const voi
                                        void *const tau[6], void *fx, void *fy, void *fz, wmibm_band_stats *stats,
                                        void *stream)
 {
+    ApiRange nvtx_range("wmibm_wall_stress_force");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;
@@ -181,6 +183,7 @@ extern "C" int wmibm_wall_stress_force(wmibm_handle *h, const void *u, const voi
 extern "C" int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz, void *u,
                                 void *v, void *w, const void *const gradp[3], double dt, void *stream)
 {
+    ApiRange nvtx_range("wmibm_force_mask");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, const_cast<void *const *>(tau), fx, fy, fz);
     if (st) return st;
@@ -194,6 +197,7 @@ extern "C" int wmibm_force_mask(wmibm_handle *h, const void *const tau[6], void 
 extern "C" int wmibm_step(wmibm_handle *h, void *u, void *v, void *w, void *const tau[6], void *fx, void *fy,
                           void *fz, const void *const gradp[3], double dt, wmibm_band_stats *stats, void *stream)
 {
+    ApiRange nvtx_range("wmibm_step");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     int st = check_fields(h, u, v, w, tau, fx, fy, fz);
     if (st) return st;

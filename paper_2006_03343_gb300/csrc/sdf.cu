@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(kSdfCols * kSdfLanes) k_heightfield_sdf(const 
 extern "C" int wmibm_heightfield_sdf(const wmibm_grid *g, const double *height, double reach, double *phi_uv,
                                      double *phi_w, void *stream)
 {
+    ApiRange nvtx_range("wmibm_heightfield_sdf");
     if (!g || !height || !phi_uv || !phi_w) return set_error(nullptr, WMIBM_EINVAL, "NULL grid or field pointer");
     if (g->nx < 1 || g->ny < 1 || g->nz < 3) return set_error(nullptr, WMIBM_EINVAL, "bad grid sizes");
     const int64_t n = (int64_t)g->nx * g->ny * g->nz;

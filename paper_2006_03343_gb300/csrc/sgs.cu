@@ -601,6 +601,7 @@ int launch_sgs(wmibm_handle *h, const void *u, const void *v, const void *w, con
 extern "C" int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const double *phi_w, const double *z0,
                                     int32_t z0_is_field, void *wt_uv, void *wt_w, void *stream)
 {
+    ApiRange nvtx_range("wmibm_sgs_wall_terms");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!phi_uv || !phi_w || !z0 || !wt_uv || !wt_w) return set_error(h, WMIBM_EINVAL, "NULL argument");
     int st = check_device(h);
@@ -635,6 +636,7 @@ extern "C" int wmibm_sgs_wall_terms(wmibm_handle *h, const double *phi_uv, const
 extern "C" int wmibm_sgs_stress(wmibm_handle *h, const void *u, const void *v, const void *w, const void *wt_uv,
                                 const void *wt_w, void *const tau[6], double cs, void *stream)
 {
+    ApiRange nvtx_range("wmibm_sgs_stress");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!u || !v || !w || !wt_uv || !wt_w || !tau) return set_error(h, WMIBM_EINVAL, "NULL argument");
     for (int c = 0; c < 6; ++c)
@@ -652,6 +654,7 @@ extern "C" int wmibm_sgs_force(wmibm_handle *h, const void *u, const void *v, co
                                const void *wt_w, const void *const tau[6], void *fx, void *fy, void *fz, double cs,
                                void *stream)
 {
+    ApiRange nvtx_range("wmibm_sgs_force");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!u || !v || !w || !wt_uv || !wt_w || !tau || !fx || !fy || !fz)
         return set_error(h, WMIBM_EINVAL, "NULL argument");

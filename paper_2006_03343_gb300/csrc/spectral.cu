@@ -739,6 +739,7 @@ int spectral_shape(const wmibm_handle *h, int64_t out[4])
 extern "C" int wmibm_force_spectral(wmibm_handle *h, const void *const tau[6], void *fx, void *fy, void *fz,
                                     void *stream)
 {
+    ApiRange nvtx_range("wmibm_force_spectral");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!tau || !fx || !fy || !fz) return set_error(h, WMIBM_EINVAL, "NULL stress or force pointer");
     for (int c = 0; c < 6; ++c)

@@ -23,6 +23,7 @@ int wall_stress_impl(wmibm_handle *h, const void *u, const void *v, const void *
 extern "C" int wmibm_wall_stress(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                                  wmibm_band_stats *stats, void *stream)
 {
+    ApiRange nvtx_range("wmibm_wall_stress");
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!u || !v || !w || !tau) return set_error(h, WMIBM_EINVAL, "NULL velocity or stress pointer");
     for (int c = 0; c < 6; ++c)

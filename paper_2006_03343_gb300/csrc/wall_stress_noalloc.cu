@@ -88,6 +88,7 @@ unsigned long long current_context_id()
 extern "C" int wmibm_wall_stress_noalloc(wmibm_handle *h, const void *u, const void *v, const void *w,
                                          void *const tau[6], wmibm_band_stats *stats, void *stream_)
 {
+    ApiRange nvtx_range("wmibm_wall_stress_noalloc");
     cudaStream_t stream = (cudaStream_t)stream_;
     if (!h) return set_error(nullptr, WMIBM_EINVAL, "NULL handle");
     if (!u || !v || !w || !tau) return set_error(h, WMIBM_EINVAL, "NULL velocity or stress pointer");
