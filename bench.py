@@ -123,7 +123,7 @@ def profiled_batch_traffic(form, dtype, points):
     summary of that form (taken on fewer members: the bytes per node carry over,
     the members being drawn the same way), if it was taken on the current kernel
     sources (else None)."""
-    name = "batch_interleaved" if form == 5 else "batch_two_launch"
+    name = {3: "batch_two_launch", 5: "batch_interleaved", 6: "batch_wall_warps"}[form]
     path = os.path.join(ROOT, "profiles", f"{name}_ensemble_{dtype}.md")
     try:
         text = open(path).read()
@@ -790,9 +790,11 @@ def accuracy_report(gpu_tau, gpu_f, ref):
     return out
 
 
-ENSEMBLE_FORMS = {3: "two launches: the batch wall kernel, then the batch stencil",
+ENSEMBLE_FORMS = {3: "two launches: the batch wall kernel, then the batch stencil as its programmatic dependent",
                   5: "one cooperative launch: the batch stencil with every member's band records as interleaved "
-                     "wall stages"}
+                     "wall stages",
+                  6: "one cooperative launch: the batch stencil with wall warps beside its producer and consumer "
+                     "warps"}
 
 
 def parse_tuning(text):
@@ -860,7 +862,7 @@ def run_ensemble(args):
     else:
         tuned = autotune.tune_batch(batch, stats)
     form = batch.get_tuning().get("force_path", 0)
-    form = 3 if form == 3 else 5
+    form = 6 if form == 0 else form
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         batch.wall_stress_force(stats)
@@ -1062,7 +1064,7 @@ def run_ensemble(args):
                            "ms_per_step": float(np.mean(ms1)),
                            "how": "the members' wall stress + force one after the other, in one CUDA graph"},
             "timing": "per step: CUDA events around one graph replay of the batch wall stress + force",
-            "gpu_launches": args.steps * (1 if form == 5 else 2), "device_status": status,
+            "gpu_launches": args.steps * (2 if form == 3 else 1), "device_status": status,
             "accuracy": accuracy, "f64_form": f64_form, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line))
     batch.close()
