@@ -311,6 +311,10 @@ typedef struct wmibm_tuning {
                                  fixed share of the (strip, level) units; n > 0 lets the blocks take
                                  runs of units from a counter as they go (clean units, then dirty),
                                  each run a share of what is left but at least n units */
+    int32_t wall_grid;        /* wall kernel of the two-launch forms (force_path 3, batch included):
+                                 blocks per SM of its grid (0: as many as fit); fewer leave room on
+                                 every SM for the stencil launch that follows as its programmatic
+                                 dependent, whose clean units then stream meanwhile */
 } wmibm_tuning;
 
 /* Sets / reads the tuning of handle h. EINVAL for out-of-range fields. */

@@ -6,8 +6,8 @@ pipelined stencil (a share in every block, dedicated wall blocks, the band
 records as interleaved pipeline stages, or wall warps beside the producer and
 consumers of every block), or the wall kernel followed by the stencil -- and a
 grid of tile shapes (rows per strip, shared-memory stages, consumer warps,
-warps of the wall kernel, band records per wall stage, units per take of the
-dynamic dispensing) with CUDA
+warps and blocks per SM of the wall kernel, band records per wall stage, units
+per take of the dynamic dispensing) with CUDA
 events on the launching stream (L2 flushed before every timed call), keeps the
 fastest, applies it to the handle and caches it in a JSON file keyed by GPU,
 precision and grid size.  A single-launch form is taken only when it beats the
@@ -43,6 +43,7 @@ WALL_WARPS = (4, 8)
 WALL_CHUNK_PER_THREAD = (0, 4)     # band records per consumer thread and wall stage (0: the library's default)
 WALL_WARPS_IN_BLOCK = (1, 2, 3)     # wall warps beside the producer and consumers (force_path 6)
 DYN_CHUNKS = (0, 16)                # units per take of the dynamic dispensing (0: a fixed share per block)
+WALL_GRIDS = (0, 2)                 # blocks per SM of the separate wall kernel (0: as many as fit)
 
 FORM_NAMES = {1: "single_launch", 2: "direct", 3: "two_launch", 4: "dedicated_wall_blocks", 5: "interleaved",
               6: "wall_warps"}
@@ -106,8 +107,12 @@ def candidates(handle):
                     out.append(dict(force_path=6, rows=rows, stages=stages, consumer_warps=cons, wall_warps=ww,
                                     dyn_chunk=dyn))
             for wall in WALL_WARPS:
-                out.append(dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall,
-                                dyn_chunk=dyn))
+                for wg in WALL_GRIDS:
+                    c = dict(force_path=3, rows=rows, stages=stages, consumer_warps=cons, wall_warps=wall,
+                             dyn_chunk=dyn)
+                    if wg:
+                        c["wall_grid"] = wg
+                    out.append(c)
     return out
 
 

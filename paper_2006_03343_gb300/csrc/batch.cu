@@ -100,6 +100,8 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
     out->blocks_per_sm = b->tuning.blocks_per_sm;
     out->wall_chunk = b->tuning.wall_chunk;
     out->dyn_chunk = b->tuning.dyn_chunk;
+    out->wall_grid = b->tuning.wall_grid;
+    if (b->tuning.wall_grid < 0 || b->tuning.wall_grid > 32) return false;
     // one launch (force_path 0 or 6: wall warps; 5: interleaved wall stages) or two launches (3)
     if (b->tuning.dyn_chunk < 0 || b->tuning.dyn_chunk > 4096) return false;
     const int fp = b->tuning.force_path;

@@ -666,6 +666,7 @@ extern "C" int wmibm_set_tuning(wmibm_handle *h, const wmibm_tuning *t)
     if (t->force_path < 0 || t->force_path > 6) return set_error(h, WMIBM_EINVAL, "force_path must be 0..6");
     if (t->wall_chunk < 0 || t->wall_chunk > 65536) return set_error(h, WMIBM_EINVAL, "wall_chunk must be 0..65536");
     if (t->dyn_chunk < 0 || t->dyn_chunk > 4096) return set_error(h, WMIBM_EINVAL, "dyn_chunk must be 0..4096");
+    if (t->wall_grid < 0 || t->wall_grid > 32) return set_error(h, WMIBM_EINVAL, "wall_grid must be 0..32");
     if (!(t->rows == 0 || t->rows == 1 || t->rows == 2 || t->rows == 4))
         return set_error(h, WMIBM_EINVAL, "rows must be 0, 1, 2 or 4");
     if (t->stages != 0 && (t->stages < 2 || t->stages > 8)) return set_error(h, WMIBM_EINVAL, "stages must be 2..8");

@@ -47,6 +47,7 @@ struct StencilConfig {
     int rows, stages, consumer_warps, wall_warps, blocks_per_sm;
     int wall_chunk;            // interleaved single launch: band records per wall stage (0: automatic)
     int dyn_chunk;             // units per take of the dynamic dispensing (0: a fixed share per block)
+    int wall_grid;             // blocks per SM of the separate wall kernel (0: as many as fit)
 };
 
 struct SpecState;              // tables, counters and tile shapes of the spectral forcing (spectral.cu)

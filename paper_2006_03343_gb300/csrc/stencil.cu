@@ -1801,6 +1801,7 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
             h->occ_key[slot] = wkey;
             h->occ_val[slot] = wper;
         }
+        if (h->tuning.wall_grid > 0 && h->tuning.wall_grid < wper) wper = h->tuning.wall_grid;
         blocks = (unsigned)std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
     }
     k_wall<T, VEL><<<blocks, wthreads, 0, stream>>>(p);
@@ -1899,6 +1900,7 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     c.blocks_per_sm = h->tuning.blocks_per_sm;
     c.wall_chunk = h->tuning.wall_chunk;
     c.dyn_chunk = h->tuning.dyn_chunk;
+    c.wall_grid = h->tuning.wall_grid;
     *out = c;
     return true;
 }
@@ -2079,7 +2081,11 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
         if (e != cudaSuccess) return cuda_status(h0, e, "batch wall occupancy");
         if (per_sm < 1) per_sm = 1;
     }
-    if (wall_blocks <= 0) wall_blocks = per_sm * h0->sm_count;   // one wave of resident blocks
+    if (wall_blocks <= 0) {
+        // one wave of resident blocks, or the tuning's blocks per SM
+        const int bps = (c.wall_grid > 0 && c.wall_grid < per_sm) ? c.wall_grid : per_sm;
+        wall_blocks = bps * h0->sm_count;
+    }
     k_wall_batch<T, VEL><<<(unsigned)wall_blocks, 256, wsmem, stream>>>(p);
     int st = cuda_status(h0, cudaGetLastError(), "k_wall_batch launch");
     if (st) return st;

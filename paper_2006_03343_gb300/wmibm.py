@@ -53,7 +53,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("force_path", ctypes.c_int32), ("rows", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("consumer_warps", ctypes.c_int32), ("wall_warps", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("direct_bx", ctypes.c_int32), ("direct_by", ctypes.c_int32),
-                ("direct_kc", ctypes.c_int32), ("wall_chunk", ctypes.c_int32), ("dyn_chunk", ctypes.c_int32)]
+                ("direct_kc", ctypes.c_int32), ("wall_chunk", ctypes.c_int32), ("dyn_chunk", ctypes.c_int32),
+                ("wall_grid", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
