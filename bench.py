@@ -836,9 +836,15 @@ def run_ensemble(args):
     with host buffers, and the oracle itself on the host cores."""
     import torch
     from paper_2006_03343_gb300 import autotune, build, inputs, wmibm
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
     build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     cases = inputs.ensemble(args.members, dtype=args.dtype)
     handles = [wmibm.Handle.from_case(c, dtype=args.dtype) for c in cases]
@@ -871,7 +877,7 @@ def run_ensemble(args):
     with torch.cuda.graph(g):
         batch.wall_stress_force(stats)
     torch.cuda.synchronize()
-    sampler = ClockSampler(0) if not args.profile else None
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.profile else None
     if sampler:
         sampler.start()
     t_soak = time.perf_counter()
@@ -880,39 +886,50 @@ def run_ensemble(args):
             flush.zero_()
             g.replay()
         torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     ms = timed_run(g.replay, stream, flush, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     warm_ms = timed_run(g.replay, stream, NoFlush(), args.steps) if not args.profile else None
     status = handles[0].device_status()
     points = batch.points()
-    value = points / (float(np.mean(ms)) * 1e-3) / 1e9
+    # every rank steps its own copy of the ensemble (weak scaling): all ranks' nodes over the slowest rank's time
+    value, total_ms = aggregate_value(float(sum(ms)), args.steps, points, world, dev)
     step_bytes = sum(h.traffic_bytes(4) for h in handles)      # wall model + 36 B/pt of every member
     peak, peak_kind = measured_peak()
     achieved = step_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
     shapes = sorted({c.grid[:3] for c in cases})
     if args.profile:
-        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "profile": True, "tuning": tuned,
-                          "ms_per_step": float(np.mean(ms)), "device_status": status}))
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "profile": True, "tuning": tuned,
+                              "ms_per_step": float(np.mean(ms)), "device_status": status}))
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return 0
+    extras = world == 1      # the comparisons, the FP64 form and the oracle: at N = 1 only
 
     # the same members one after the other (prepared calls, one graph)
-    calls = [h.prepare_step(*fl[:3], fl[3], fl[4]) for h, fl in zip(handles, fields)]
-    for c in calls:
-        c.wall_stress_force()
-    torch.cuda.synchronize()
-    g1 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g1):
+    ms1 = [float("nan")]
+    if extras:
+        calls = [h.prepare_step(*fl[:3], fl[3], fl[4]) for h, fl in zip(handles, fields)]
         for c in calls:
             c.wall_stress_force()
-    ms1 = timed_run(g1.replay, stream, flush, args.steps)
-    del g1, calls
+        torch.cuda.synchronize()
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1):
+            for c in calls:
+                c.wall_stress_force()
+        ms1 = timed_run(g1.replay, stream, flush, args.steps)
+        del g1, calls
     # the batch step again, so that every member's fields hold its result
     g.replay()
     torch.cuda.synchronize()
 
     # the plain FP64 batch of the same members, tuned and timed the same way
     f64_form = b64 = fl64 = None
-    if args.dtype == "f32":
+    if args.dtype == "f32" and extras:
         h64 = [wmibm.Handle.from_case(c, dtype="f64") for c in cases]
         fl64 = [fields_of(c, torch.float64) for c in cases]
         b64 = wmibm.Batch(h64)
@@ -968,8 +985,12 @@ def run_ensemble(args):
                     dst.copy_(src, non_blocking=True)
             host_out[b][1].copy_(sets[b][2], non_blocking=True)
 
-        el = pipelined_run(dev, args.steps, [copy_in], compute, copy_out)
-        e2e = {"value": args.steps * points / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        el = pipelined_run(dev, args.steps, [copy_in], compute, copy_out, world)
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps * points / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
                "form": "double-buffered over two batches of the same members: step s's inputs copied in on one "
                        "stream while step s-1 computes on a second and step s-2's forcing and stats come back on "
@@ -977,54 +998,56 @@ def run_ensemble(args):
         b2.close()
         del b2_fields, host_in, host_out, sets
 
-    # every member's results against the oracle: the FP32 form against the oracle fed the same FP32-rounded
-    # velocity and stresses (parity) and against the unrounded inputs (storage precision); the FP64 form against
-    # the unrounded inputs
-    import oracle
-    oracle.build()
-    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wmibm.STATS_DTYPE).reshape(len(cases), 2)
-    rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
-    per_parity, per_store, per64 = [], [], []
-    stats_err = 0.0
-    t_acc = time.perf_counter()
-    for m, c in enumerate(cases):
-        gtau = [t.double().cpu().numpy() for t in fields[m][3]]
-        gf = [t.double().cpu().numpy() for t in fields[m][4]]
-        tau_x = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
-        st_x = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, tau_x)
-        f_x = oracle.force(c.grid, tau_x)
+    accuracy = None
+    if extras:
+        # every member's results against the oracle: the FP32 form against the oracle fed the same FP32-rounded
+        # velocity and stresses (parity) and against the unrounded inputs (storage precision); the FP64 form against
+        # the unrounded inputs
+        import oracle
+        oracle.build()
+        bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wmibm.STATS_DTYPE).reshape(len(cases), 2)
+        rd = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tdt).double().numpy()
+        per_parity, per_store, per64 = [], [], []
+        stats_err = 0.0
+        t_acc = time.perf_counter()
+        for m, c in enumerate(cases):
+            gtau = [t.double().cpu().numpy() for t in fields[m][3]]
+            gf = [t.double().cpu().numpy() for t in fields[m][4]]
+            tau_x = {k: c.tau[k].copy() for k in inputs.TAU_NAMES}
+            st_x = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, c.u, c.v, c.w, tau_x)
+            f_x = oracle.force(c.grid, tau_x)
+            if args.dtype == "f32":
+                tau_r = {k: rd(c.tau[k]) for k in inputs.TAU_NAMES}
+                st_r = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, rd(c.u), rd(c.v),
+                                          rd(c.w), tau_r)
+                f_r = oracle.force(c.grid, tau_r)
+                per_parity.append(ensemble_errors(gtau, gf, tau_r, f_r))
+                per_store.append(ensemble_errors(gtau, gf, tau_x, f_x))
+                ref_st = st_r
+            else:
+                per_parity.append(ensemble_errors(gtau, gf, tau_x, f_x))
+                ref_st = st_x
+            for bnd in range(2):
+                for col, name in ((1, "sum_tw"), (2, "sum_tw2"), (3, "min_tw"), (4, "max_ur")):
+                    r = ref_st[bnd, col]
+                    stats_err = max(stats_err, abs(bstats[m][bnd][name] - r) / max(abs(r), 1e-30))
+            if fl64 is not None:
+                per64.append(ensemble_errors([t.cpu().numpy() for t in fl64[m][3]], [t.cpu().numpy() for t in fl64[m][4]],
+                                             tau_x, f_x))
+        accuracy = dict(worst_errors(per_parity), members=len(cases), stats_rel_max=stats_err,
+                        reference="oracle on the same FP32-rounded velocity and stresses" if args.dtype == "f32"
+                        else "oracle on the same inputs",
+                        how=f"every member's 6 stresses and 3 forcing components after the timed graph replays; "
+                            f"worst member ({time.perf_counter() - t_acc:.1f} s)")
         if args.dtype == "f32":
-            tau_r = {k: rd(c.tau[k]) for k in inputs.TAU_NAMES}
-            st_r = oracle.wall_stress(c.grid, c.phi_uv, c.phi_w, c.z0, c.phi_c, c.phi_b, rd(c.u), rd(c.v),
-                                      rd(c.w), tau_r)
-            f_r = oracle.force(c.grid, tau_r)
-            per_parity.append(ensemble_errors(gtau, gf, tau_r, f_r))
-            per_store.append(ensemble_errors(gtau, gf, tau_x, f_x))
-            ref_st = st_r
-        else:
-            per_parity.append(ensemble_errors(gtau, gf, tau_x, f_x))
-            ref_st = st_x
-        for bnd in range(2):
-            for col, name in ((1, "sum_tw"), (2, "sum_tw2"), (3, "min_tw"), (4, "max_ur")):
-                r = ref_st[bnd, col]
-                stats_err = max(stats_err, abs(bstats[m][bnd][name] - r) / max(abs(r), 1e-30))
-        if fl64 is not None:
-            per64.append(ensemble_errors([t.cpu().numpy() for t in fl64[m][3]], [t.cpu().numpy() for t in fl64[m][4]],
-                                         tau_x, f_x))
-    accuracy = dict(worst_errors(per_parity), members=len(cases), stats_rel_max=stats_err,
-                    reference="oracle on the same FP32-rounded velocity and stresses" if args.dtype == "f32"
-                    else "oracle on the same inputs",
-                    how=f"every member's 6 stresses and 3 forcing components after the timed graph replays; "
-                        f"worst member ({time.perf_counter() - t_acc:.1f} s)")
-    if args.dtype == "f32":
-        accuracy["vs_unrounded_inputs"] = worst_errors(per_store)
-    if f64_form is not None:
-        f64_form["accuracy"] = dict(worst_errors(per64), members=len(cases), reference="oracle on the same inputs")
-        b64.close()
-        del fl64
+            accuracy["vs_unrounded_inputs"] = worst_errors(per_store)
+        if f64_form is not None:
+            f64_form["accuracy"] = dict(worst_errors(per64), members=len(cases), reference="oracle on the same inputs")
+            b64.close()
+            del fl64
 
     cpu = None
-    if not args.no_cpu:
+    if extras and not args.no_cpu:
         # the oracle over the members in order, as many as fit about args.cpu_seconds
         t0 = time.perf_counter()
         done_pts = used = 0
@@ -1040,8 +1063,9 @@ def run_ensemble(args):
         cpu = {"value": done_pts / el / 1e9, "unit": UNIT, "cores": oracle.openmp_threads(), "kind": "oracle",
                "sample": f"wall stress + force of the first {used} of {len(cases)} members ({el:.1f} s, FP64 CPU "
                          f"oracle)"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": f"ensemble of {len(cases)} random Gaussian-hill terrains, grids {shapes}, "
                                    f"batched FP32 (one step = wall stress + force of every member)"
@@ -1062,12 +1086,18 @@ def run_ensemble(args):
                         "how": "the same graph replays with no L2 flush between steps"},
             "one_by_one": {"value": points / (float(np.mean(ms1)) * 1e-3) / 1e9, "unit": UNIT,
                            "ms_per_step": float(np.mean(ms1)),
-                           "how": "the members' wall stress + force one after the other, in one CUDA graph"},
+                           "how": "the members' wall stress + force one after the other, in one CUDA graph"}
+            if extras else None,
             "timing": "per step: CUDA events around one graph replay of the batch wall stress + force",
             "gpu_launches": args.steps * (2 if form == 3 else 1), "device_status": status,
             "accuracy": accuracy, "f64_form": f64_form, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
-    print(json.dumps(line))
+    if world > 1:
+        line["config"]["parallelism"] = f"{world} ranks, one GPU each, every rank its own copy of the ensemble"
+    if rank == 0:
+        print(json.dumps(line))
     batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

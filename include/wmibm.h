@@ -69,6 +69,11 @@ typedef struct wmibm_opts {
                                grid (Sec. 3.3 interpolation): WMIBM_ZCLAMP_CLAMP (0) clamps their level
                                (reading R3) and counts them in wmibm_band_stats.n_zclamped;
                                WMIBM_ZCLAMP_REJECT (1) makes wmibm_init fail with EINVAL instead */
+    int32_t own_x0, own_x1; /* 0, 0: the handle owns every node.  Otherwise 0 <= own_x0 < own_x1 <= nx:
+                               it owns the nodes with own_x0 <= i < own_x1, and the others are halo
+                               planes of a slab of a larger domain cut along x: they serve the normals
+                               and stencils of owned nodes but are never band, solid or body nodes, so
+                               every per-node output there is left to the slab that owns them */
 } wmibm_opts;
 
 #define WMIBM_ZCLAMP_CLAMP 0

@@ -25,6 +25,7 @@ constexpr int kChunk = kThreads * kChunkItems;     // nodes per block
 // ------------------------------------------------------------------------- //
 __device__ __forceinline__ void predicates(double pw, double puv, double pb, bool q[6])
 {
+    // (callers test the owned x-range first)
     q[0] = (pw >= -pb) && (pw <= pb);            // w band:  -phi_b <= phi <= phi_b
     q[1] = (puv >= 0.0) && (puv <= 2.0 * pb);    // uv band: 0 <= phi <= 2 phi_b
     q[2] = pw < -pb;                             // w solid
@@ -33,16 +34,25 @@ __device__ __forceinline__ void predicates(double pw, double puv, double pb, boo
     q[5] = puv <= 0.0;                           // uv body (Eq. 27)
 }
 
+// Whether node p lies in the owned x-range [x0, x1) (x1 == 0: every node is owned).
+__device__ __forceinline__ bool owned(int64_t p, int32_t nx, int32_t x0, int32_t x1)
+{
+    if (x1 == 0) return true;
+    const int32_t i = (int32_t)(p % nx);
+    return i >= x0 && i < x1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_count(const double *__restrict__ phi_uv,
                                                     const double *__restrict__ phi_w, int64_t n, double pb,
-                                                    int32_t *__restrict__ counts, int64_t nblk)
+                                                    int32_t *__restrict__ counts, int64_t nblk, int32_t nx,
+                                                    int32_t x0, int32_t x1)
 {
     __shared__ int warp_tot[6][kThreads / 32];
     int c[6] = {0, 0, 0, 0, 0, 0};
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     for (int it = 0; it < kChunkItems; ++it) {
         int64_t p = base + (int64_t)it * kThreads + threadIdx.x;
-        if (p < n) {
+        if (p < n && owned(p, nx, x0, x1)) {
             bool q[6];
             predicates(phi_w[p], phi_uv[p], pb, q);
             for (int l = 0; l < 6; ++l) c[l] += q[l] ? 1 : 0;
@@ -67,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_count(const double *__restrict__ p
 __global__ void __launch_bounds__(kThreads) k_compact(const double *__restrict__ phi_uv,
                                                       const double *__restrict__ phi_w, int64_t n, double pb,
                                                       const int64_t *__restrict__ offsets, int64_t nblk,
-                                                      Lists lists)
+                                                      Lists lists, int32_t nx, int32_t x0, int32_t x1)
 {
     __shared__ int warp_tot[6][kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const double *__restrict__
     for (int it = 0; it < kChunkItems; ++it) {
         int64_t p = base + (int64_t)it * kThreads + threadIdx.x;
         bool q[6] = {false, false, false, false, false, false};
-        if (p < n) predicates(phi_w[p], phi_uv[p], pb, q);
+        if (p < n && owned(p, nx, x0, x1)) predicates(phi_w[p], phi_uv[p], pb, q);
         unsigned bal[6];
         for (int l = 0; l < 6; ++l) {
             bal[l] = __ballot_sync(0xffffffffu, q[l]);
@@ -373,8 +383,11 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     const int64_t n = (int64_t)g->nx * g->ny * g->nz;
     if (n >= ((int64_t)1 << 31) - 16) return set_error(nullptr, WMIBM_EINVAL, "grid has %lld nodes (>= 2^31)", (long long)n);
 
-    wmibm_opts o = {0.0, 0.0, WMIBM_F32, WMIBM_F32, WMIBM_ZCLAMP_CLAMP};
+    wmibm_opts o = {0.0, 0.0, WMIBM_F32, WMIBM_F32, WMIBM_ZCLAMP_CLAMP, 0, 0};
     if (opts) o = *opts;
+    if (!(o.own_x0 == 0 && o.own_x1 == 0) && !(o.own_x0 >= 0 && o.own_x0 < o.own_x1 && o.own_x1 <= g->nx))
+        return set_error(nullptr, WMIBM_EINVAL, "owned x-range [%d, %d) must lie in [0, nx = %d)", o.own_x0,
+                         o.own_x1, g->nx);
     if (o.zclamp != WMIBM_ZCLAMP_CLAMP && o.zclamp != WMIBM_ZCLAMP_REJECT)
         return set_error(nullptr, WMIBM_EINVAL, "zclamp must be WMIBM_ZCLAMP_CLAMP or WMIBM_ZCLAMP_REJECT");
     const double dz = g->lz / (double)(g->nz - 1);
@@ -429,7 +442,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     TRY(cudaMemcpyAsync(d_phi_w, phi_w, n * sizeof(double), cudaMemcpyHostToDevice, stream), "copy phi_w");
     TRY(cudaMemcpyAsync(d_z0, z0, nz0 * sizeof(double), cudaMemcpyHostToDevice, stream), "copy z0");
 
-    k_count<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_counts, nblk);
+    k_count<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_counts, nblk, g->nx, o.own_x0,
+                                                     o.own_x1);
     TRY(cudaGetLastError(), "k_count launch");
     TRY(cudaMemcpyAsync(counts.data(), d_counts, 6 * nblk * sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
         "copy counts");
@@ -445,7 +459,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     }
     TRY(cudaMemcpyAsync(d_offsets, offsets.data(), 6 * nblk * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
         "copy offsets");
-    k_compact<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_offsets, nblk, h->lists);
+    k_compact<<<(unsigned)nblk, kThreads, 0, stream>>>(d_phi_uv, d_phi_w, n, o.phi_b, d_offsets, nblk, h->lists,
+                                                       g->nx, o.own_x0, o.own_x1);
     TRY(cudaGetLastError(), "k_compact launch");
 
     h->nrec = h->lists.n[0] + h->lists.n[1];

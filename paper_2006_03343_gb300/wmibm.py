@@ -46,7 +46,8 @@ class Grid(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("phi_b", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32), ("zclamp", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("vel_dtype", ctypes.c_int32), ("zclamp", ctypes.c_int32),
+                ("own_x0", ctypes.c_int32), ("own_x1", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -215,10 +216,12 @@ class Handle:
 
     dtype: "f32" or "f64" (stress, force and arithmetic); vel_dtype: None (same as
     dtype) or "bf16" (with f32); zclamp: ZCLAMP_CLAMP (clamp the level of sample
-    points outside the grid and count them) or ZCLAMP_REJECT (fail instead)."""
+    points outside the grid and count them) or ZCLAMP_REJECT (fail instead);
+    own_x: None, or (x0, x1): the handle owns the nodes with x0 <= i < x1 of a slab
+    whose other x-planes are halo (see slab.py)."""
 
     def __init__(self, grid, phi_uv, phi_w, z0, phi_c, phi_b=0.0, dtype="f32", vel_dtype=None, kappa=0.4,
-                 stream=None, zclamp=0):
+                 stream=None, zclamp=0, own_x=None):
         import torch
         L = load()
         nx, ny, nz, lx, ly, lz = grid
@@ -238,7 +241,9 @@ class Handle:
             z0a = np.ascontiguousarray(z0, np.float64)
             is_field = 1
         g = Grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz))
-        o = Opts(float(phi_b), float(kappa), DTYPE_CODES[dtype], DTYPE_CODES[self.vel_dtype], int(zclamp))
+        x0, x1 = own_x if own_x is not None else (0, 0)
+        o = Opts(float(phi_b), float(kappa), DTYPE_CODES[dtype], DTYPE_CODES[self.vel_dtype], int(zclamp), int(x0),
+                 int(x1))
         h = ctypes.c_void_p()
         st = L.wmibm_init(ctypes.byref(h), ctypes.byref(g), phi_uv.ctypes.data, phi_w.ctypes.data,
                           z0a.ctypes.data, is_field, float(phi_c), ctypes.byref(o), _stream_ptr(stream))
