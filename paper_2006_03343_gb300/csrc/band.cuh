@@ -127,15 +127,19 @@ template <typename T, typename V>
 __device__ __forceinline__ void band_gather(const int4 ix, const V *u, const V *v, const V *w, int32_t nx,
                                             int32_t ny, int64_t plane, BandIn<T> &b)
 {
+    // 32-bit index arithmetic: a grid has fewer than 2^31 nodes (checked at init)
+    // and every corner is one of its nodes, so one multiply-add forms each address
     b.idx = ix.x;
-    const int64_t di = (ix.w & 1) ? 1 - nx : 1;
-    const int64_t dj = (ix.w & 2) ? (int64_t)(1 - ny) * nx : nx;
+    const int32_t di = (ix.w & 1) ? 1 - nx : 1;
+    const int32_t dj = (ix.w & 2) ? (1 - ny) * nx : nx;
+    const int32_t dk = (int32_t)plane;
+    const V *const pu = u + ix.y, *const pv = v + ix.y, *const pw = w + ix.z;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int64_t o = ((c & 1) ? di : 0) + ((c & 2) ? dj : 0) + ((c & 4) ? plane : 0);
-        b.cu[c] = load_vel<V, T>(u, ix.y + o);
-        b.cv[c] = load_vel<V, T>(v, ix.y + o);
-        b.cw[c] = load_vel<V, T>(w, ix.z + o);
+        const int32_t o = ((c & 1) ? di : 0) + ((c & 2) ? dj : 0) + ((c & 4) ? dk : 0);
+        b.cu[c] = load_vel<V, T>(pu, o);
+        b.cv[c] = load_vel<V, T>(pv, o);
+        b.cw[c] = load_vel<V, T>(pw, o);
     }
 }
 

@@ -1007,17 +1007,17 @@ __device__ void zero_runs_batch(const KParams<T> &p, int64_t gw, int64_t nwarps,
 // Batch: block b takes a contiguous slice of the concatenated band records
 // (so that it meets few members); a thread walks its records in increasing
 // order, advancing the member linearly, and accumulates the band statistics of
-// the current member in registers, flushed to per-block shared accumulators
-// when the member changes and at the end (warp-reduced when the whole warp
-// holds the same member); blocks flush those to the batch scratch with global
-// atomics.  Warps then zero the solid runs of every member, and the last block
-// converts the scratch into wmibm_band_stats and clears it for the next call.
+// the current member in registers.  When its member changes a lane adds them to
+// the member's FP64 accumulators in the batch scratch with fire-and-forget
+// global reductions; at the end each warp first combines the lanes that hold
+// the same member (one reduction per member and warp).  No shared-memory FP64
+// atomics: on this part their compare-and-swap loops run on the narrow FP64
+// pipe and one contended block held the whole grid back.  Warps then zero the
+// solid runs of every member, and the last block converts the scratch into
+// wmibm_band_stats and clears it for the next call.
 template <typename T, typename VEL>
 __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
 {
-    __shared__ double s_sum[kMaxBatchMembers][2][2];
-    __shared__ unsigned long long s_ext[kMaxBatchMembers][2][2];   // (-min tau_w, max |U_r|) bits
-    __shared__ int s_m0, s_m1;
     __shared__ bool s_last;
     __shared__ uint64_t rbar[2];
     extern __shared__ __align__(128) unsigned char wb_smem[];   // record chunks
@@ -1026,31 +1026,13 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
     const int64_t R = p.rec_total;
     const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
     const bool want_stats = p.stats != nullptr;
-    if (threadIdx.x == 0) {
-        s_m0 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r0) : 0;
-        s_m1 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r1 - 1) : -1;
-    }
-    __syncthreads();
-    const int m0 = s_m0, m1 = s_m1;
-    for (int q = threadIdx.x; q < (m1 - m0 + 1) * 4; q += blockDim.x) {
-        const int mi = q >> 2, bnd = (q >> 1) & 1, c = q & 1;
-        s_sum[mi][bnd][c] = 0.0;
-        s_ext[mi][bnd][c] = 0ull;
-    }
-    __syncthreads();
+    const int m0 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r0) : 0;
 
     T acc[kStatVals];
     stats_identity(acc);
     int nacc = 0;
-    auto flush = [&](int mi) {   // this lane's accumulators into member mi's shared slots
-        atomicAdd(&s_sum[mi - m0][0][0], (double)acc[0]);
-        atomicAdd(&s_sum[mi - m0][0][1], (double)acc[1]);
-        atomicMax(&s_ext[mi - m0][0][0], ordered_bits(-(double)acc[2]));
-        atomicMax(&s_ext[mi - m0][0][1], ordered_bits((double)acc[3]));
-        atomicAdd(&s_sum[mi - m0][1][0], (double)acc[4]);
-        atomicAdd(&s_sum[mi - m0][1][1], (double)acc[5]);
-        atomicMax(&s_ext[mi - m0][1][0], ordered_bits(-(double)acc[6]));
-        atomicMax(&s_ext[mi - m0][1][1], ordered_bits((double)acc[7]));
+    auto flush = [&](int mi) {   // this lane's accumulators into member mi's global slots
+        stats_red(acc, p.bstats + (int64_t)mi * 8);
         stats_identity(acc);
         nacc = 0;
     };
@@ -1139,32 +1121,25 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
     if (threadIdx.x == 0)                                 // after a time-out: let issued copies land
         for (int64_t q = consumed; q < issued; ++q) mbar_drain(&rbar[q & 1], (uint32_t)((q >> 1) & 1));
     if (want_stats) {
+        // one warp reduction per member the warp's lanes hold (0 is the identity of
+        // every statistic: tau_w <= 0, |U_r| >= 0)
         __syncwarp();
-        const int key = nacc ? cm : -1;
-        const unsigned same = __match_any_sync(0xffffffffu, key);
-        if (same == 0xffffffffu) {
-            if (key >= 0) {
-                for (int bnd = 0; bnd < 2; ++bnd) {
-                    acc[4 * bnd + 0] = warp_sum(acc[4 * bnd + 0]);
-                    acc[4 * bnd + 1] = warp_sum(acc[4 * bnd + 1]);
-                    acc[4 * bnd + 2] = warp_min(acc[4 * bnd + 2]);
-                    acc[4 * bnd + 3] = warp_max(acc[4 * bnd + 3]);
-                }
-                if ((threadIdx.x & 31) == 0) flush(cm);
+        const int lane = threadIdx.x & 31;
+        unsigned pending = __ballot_sync(0xffffffffu, nacc != 0);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const int key = __shfl_sync(0xffffffffu, cm, leader);
+            const bool mine = nacc != 0 && cm == key;
+            pending &= ~__ballot_sync(0xffffffffu, mine);
+            T v[kStatVals];
+            for (int s = 0; s < kStatVals; ++s) v[s] = mine ? acc[s] : T(0);
+            for (int bnd = 0; bnd < 2; ++bnd) {
+                v[4 * bnd + 0] = warp_sum(v[4 * bnd + 0]);
+                v[4 * bnd + 1] = warp_sum(v[4 * bnd + 1]);
+                v[4 * bnd + 2] = warp_min(v[4 * bnd + 2]);
+                v[4 * bnd + 3] = warp_max(v[4 * bnd + 3]);
             }
-        } else if (nacc) {
-            flush(cm);
-        }
-    }
-    __syncthreads();
-    if (want_stats) {
-        for (int q = threadIdx.x; q < (m1 - m0 + 1) * 2; q += blockDim.x) {
-            const int mi = q >> 1, bnd = q & 1;
-            double *dst = p.bstats + ((int64_t)(m0 + mi) * 2 + bnd) * 4;
-            atomicAdd(dst + 0, s_sum[mi][bnd][0]);
-            atomicAdd(dst + 1, s_sum[mi][bnd][1]);
-            atomicMax(reinterpret_cast<unsigned long long *>(dst + 2), s_ext[mi][bnd][0]);
-            atomicMax(reinterpret_cast<unsigned long long *>(dst + 3), s_ext[mi][bnd][1]);
+            if (lane == leader) stats_red(v, p.bstats + (int64_t)key * 8);
         }
     }
 
