@@ -739,6 +739,12 @@ def run_ours(args):
                              "a2_force_alone": float(np.mean(parts["force"])),
                              "a3_mask_alone": float(np.mean(parts["mask"])),
                              "a1_a2_a3_one_launch": float(np.mean(parts["step"]))},
+                "a1_bytes": {"algorithmic": h.traffic_bytes(0), "sector_reads": h.traffic_bytes(5),
+                             "sector_writes": h.traffic_bytes(6),
+                             "what": "the wall stage's bytes: per element (records, distinct velocity elements, "
+                                     "run descriptors, band and solid stress writes), and at the memory system's "
+                                     "32-byte sectors (reads include one sector for every stress sector written "
+                                     "only in part)"},
                 "timing": "per step: CUDA events around one graph replay of wall stress + force (a1 + a2, one "
                           "cooperative launch); parts_ms from graphs of each part alone; eager launches: "
                           "%.4f ms/step" % float(np.mean(eager_ms)),

@@ -480,12 +480,20 @@ int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap,
 /*
  * wmibm_traffic_bytes - algorithmic bytes of one call, counted at init:
  *   which = 0: wmibm_wall_stress (band records, each distinct velocity element
- *              its stencils touch, band stress writes, solid index reads and
- *              zero writes); 1: wmibm_force (6 stress reads + 3 force writes per
- *              node); 2: wmibm_mask without grad p; 3: wmibm_mask with grad p;
- *              4: the fused wmibm_wall_stress_force pass (force stream, band
- *              records and velocity elements, band and solid stress writes, run
- *              and row tables).
+ *              its stencils touch, band stress writes, the solid runs'
+ *              descriptors and zero writes); 1: wmibm_force (6 stress reads + 3
+ *              force writes per node); 2: wmibm_mask without grad p; 3:
+ *              wmibm_mask with grad p; 4: the fused wmibm_wall_stress_force pass
+ *              (force stream, band records and velocity elements, band and
+ *              solid stress writes, run and row tables);
+ *           5: wmibm_wall_stress's reads at the 32-byte sector granularity of
+ *              the memory system: the records, every velocity sector its
+ *              stencils touch, the run descriptors, and one sector read for each
+ *              stress sector it writes only in part (the rest of the sector has
+ *              to come from memory);
+ *           6: its writes at sector granularity: every stress sector written.
+ *   Sectors are counted from element 0 of each field, i.e. for fields that
+ *   start on a 32-byte boundary.
  * Returns -1 for a bad argument.
  */
 int64_t wmibm_traffic_bytes(const wmibm_handle *h, int32_t which);

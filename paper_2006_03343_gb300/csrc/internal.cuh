@@ -68,7 +68,7 @@ struct wmibm_handle {
     unsigned int *ticket;       // [4] counters kept at 0 between calls (wall-kernel ticket, fused-step counters)
     double *sacc;               // [8] band-statistics accumulator, kept at 0 between calls
     int64_t partial_blocks;
-    int64_t traffic[5];
+    int64_t traffic[7];
     int64_t nzclamp[2];         // band nodes (w, uv) whose sample point's level was clamped
     uint64_t wait_ns;           // limit of the kernels' bounded waits (WMIBM_WAIT_LIMIT_NS at init; 1 s)
     int hold_release;           // failure-path test: the single launch never releases its dirty stages

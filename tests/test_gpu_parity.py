@@ -202,6 +202,38 @@ def test_traffic_bytes(wm):
         assert h.traffic_bytes(3) > h.traffic_bytes(2) > 0
 
 
+@pytest.mark.parametrize("dtype,es", [("f32", 4), ("f64", 8)])
+def test_sector_traffic(wm, dtype, es):
+    """The wall stage's bytes at 32-byte sector granularity: the written stress
+    sectors recounted from the exported band and solid lists, and the partly
+    written ones inside the sector read count, which lies between the element-level
+    reads and their sector round-up."""
+    case = inputs.cubes(shape=(64, 32, 24))
+    h = wm.Handle.from_case(case, dtype=dtype)
+    per = 32 // es
+    n = case.npoints
+    written = partial = 0
+    for comps, lists in ((2, (wm.LIST_BAND_W, wm.LIST_SOLID_W)), (4, (wm.LIST_BAND_UV, wm.LIST_SOLID_UV))):
+        mask = np.zeros(n + (-n) % per, bool)
+        for l in lists:
+            mask[h.export_list(l)] = True
+        tail = np.arange(mask.size) >= n          # elements past the field's end are not part of any write
+        sec = mask.reshape(-1, per)
+        full = (mask | tail).reshape(-1, per).all(axis=1)
+        touched = sec.any(axis=1)
+        written += comps * int(touched.sum())
+        partial += comps * int((touched & ~full).sum())
+    assert h.traffic_bytes(6) == 32 * written
+    sector_reads = h.traffic_bytes(5)
+    assert sector_reads >= 32 * partial
+    element_reads = h.traffic_bytes(0) - es * sum(
+        c * h.list_size(l) for c, l in ((2, wm.LIST_BAND_W), (4, wm.LIST_BAND_UV), (2, wm.LIST_SOLID_W),
+                                        (4, wm.LIST_SOLID_UV)))
+    # records and run descriptors are in both counts; velocity elements round up to their sectors
+    assert element_reads <= sector_reads - 32 * partial <= per * element_reads
+    h.close()
+
+
 def test_binding_rejects_wrong_dtype(wm):
     case = inputs.ridge(shape=(16, 8, 8))
     h = wm.Handle.from_case(case, dtype="f32")
