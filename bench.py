@@ -743,8 +743,7 @@ def run_ours(args):
                              "sector_writes": h.traffic_bytes(6),
                              "what": "the wall stage's bytes: per element (records, distinct velocity elements, "
                                      "run descriptors, band and solid stress writes), and at the memory system's "
-                                     "32-byte sectors (reads include one sector for every stress sector written "
-                                     "only in part)"},
+                                     "32-byte sectors (reads include one read of every stress sector written)"},
                 "timing": "per step: CUDA events around one graph replay of wall stress + force (a1 + a2, one "
                           "cooperative launch); parts_ms from graphs of each part alone; eager launches: "
                           "%.4f ms/step" % float(np.mean(eager_ms)),
@@ -1087,6 +1086,11 @@ def run_ensemble(args):
                                       "and solid stress writes) + 36 B/pt of the stencil (6 stress reads, 3 forcing "
                                       "writes); the whole batch step"},
             "tuning": tuned, "form": ENSEMBLE_FORMS[form],
+            "wall_bytes": {"algorithmic": sum(h.traffic_bytes(0) for h in handles),
+                           "sector_reads": sum(h.traffic_bytes(5) for h in handles),
+                           "sector_writes": sum(h.traffic_bytes(6) for h in handles),
+                           "what": "every member's wall stage: per element, and at the memory system's 32-byte "
+                                   "sectors (reads include one read of every stress sector written)"},
             "warm_l2": {"ms_per_step": float(np.mean(warm_ms)),
                         "value": points / (float(np.mean(warm_ms)) * 1e-3) / 1e9, "unit": UNIT,
                         "how": "the same graph replays with no L2 flush between steps"},

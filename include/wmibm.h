@@ -488,9 +488,11 @@ int wmibm_export_list(wmibm_handle *h, int32_t which, int32_t *dst, int64_t cap,
  *              solid stress writes, run and row tables);
  *           5: wmibm_wall_stress's reads at the 32-byte sector granularity of
  *              the memory system: the records, every velocity sector its
- *              stencils touch, the run descriptors, and one sector read for each
- *              stress sector it writes only in part (the rest of the sector has
- *              to come from memory);
+ *              stencils touch, the run descriptors, and one read of every stress
+ *              sector it writes (a store that does not cover its whole sector
+ *              has the rest of the sector read from memory, and the stage's
+ *              scattered band stores and unaligned solid runs hardly ever cover
+ *              one whole);
  *           6: its writes at sector granularity: every stress sector written.
  *   Sectors are counted from element 0 of each field, i.e. for fields that
  *   start on a 32-byte boundary.

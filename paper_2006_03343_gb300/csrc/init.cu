@@ -237,32 +237,21 @@ __global__ void __launch_bounds__(kThreads) k_mark_list(const int32_t *list, int
 }
 
 // 32-byte sectors of a field of n elements, `per` elements each (the field
-// starting on a sector boundary): out[0] += sectors holding a marked element,
-// out[1] += those among them that also hold an unmarked one.
+// starting on a sector boundary): *out += sectors holding a marked element.
 __global__ void __launch_bounds__(kThreads) k_count_sectors(const uint8_t *mask, int64_t n, int per,
                                                              unsigned long long *out)
 {
-    unsigned long long touched = 0, partial = 0;
+    unsigned long long touched = 0;
     const int64_t nsec = (n + per - 1) / per;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nsec;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = s * per, b = a + per < n ? a + per : n;
-        int any = 0, all = 1;
-        for (int64_t e = a; e < b; ++e) {
-            any |= mask[e];
-            all &= mask[e];
-        }
+        int any = 0;
+        for (int64_t e = a; e < b; ++e) any |= mask[e];
         touched += any;
-        partial += any & (all ^ 1);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        touched += __shfl_down_sync(0xffffffffu, touched, o);
-        partial += __shfl_down_sync(0xffffffffu, partial, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out, touched);
-        atomicAdd(out + 1, partial);
-    }
+    for (int o = 16; o > 0; o >>= 1) touched += __shfl_down_sync(0xffffffffu, touched, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, touched);
 }
 
 __global__ void __launch_bounds__(kThreads) k_count_marks(const uint8_t *a, const uint8_t *b, int64_t n,
@@ -456,8 +445,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     std::vector<int64_t> offsets(6 * nblk);
     unsigned long long marks[4] = {0, 0, 0, 0};
     // 32-byte sectors: velocity sectors read (uv grid, w grid); stress sectors
-    // written (w grid, uv grid) and how many of those are written only in part
-    unsigned long long sectors[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // written (w grid, uv grid)
+    unsigned long long sectors[4] = {0, 0, 0, 0};
 
     wmibm_handle *h = (wmibm_handle *)host_alloc(sizeof(wmibm_handle));
     if (!h) return set_error(nullptr, WMIBM_ENOMEM, "host allocation failed");
@@ -505,8 +494,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
     h->nrec = h->lists.n[0] + h->lists.n[1];
     // [0, 1]: distinct velocity elements the band stencils read on each grid;
     // [2, 3]: band nodes (w, uv) whose sample point's level is clamped
-    TRY(dev_alloc(&d_marks, 12 * sizeof(unsigned long long)), "cudaMalloc mark counts");
-    TRY(cudaMemsetAsync(d_marks, 0, 12 * sizeof(unsigned long long), stream), "memset mark counts");
+    TRY(dev_alloc(&d_marks, 8 * sizeof(unsigned long long)), "cudaMalloc mark counts");
+    TRY(cudaMemsetAsync(d_marks, 0, 8 * sizeof(unsigned long long), stream), "memset mark counts");
     {
         const size_t rec_size = o.dtype == WMIBM_F64 ? sizeof(RecF64) : sizeof(RecF32);
         TRY(dev_alloc(&h->rec, std::max<int64_t>(h->nrec, 1) * rec_size), "cudaMalloc records");
@@ -547,17 +536,12 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             // the memory system: the velocity sectors the stencils touch, then the
             // stress sectors the wall stage writes (band and solid nodes of a grid)
             const int per_v = 32 / (int)elem_size(o.vel_dtype), per_e = 32 / (int)elem_size(o.dtype);
-            unsigned long long vsec[2][2];
             k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark, n, per_v, d_marks + 4);
             TRY(cudaGetLastError(), "k_count_sectors launch");
-            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark + n, n, per_v, d_marks + 6);
+            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark + n, n, per_v, d_marks + 5);
             TRY(cudaGetLastError(), "k_count_sectors launch");
-            TRY(cudaMemcpyAsync(vsec, d_marks + 4, sizeof(vsec), cudaMemcpyDeviceToHost, stream), "copy sectors");
             TRY(cudaStreamSynchronize(stream), "velocity sectors");
-            sectors[0] = vsec[0][0];
-            sectors[1] = vsec[1][0];
             TRY(cudaMemsetAsync(d_mark, 0, 2 * n, stream), "memset marks");
-            TRY(cudaMemsetAsync(d_marks + 4, 0, 8 * sizeof(unsigned long long), stream), "memset sector counts");
             // lists 0 and 2 (w band, w solid) mark the w grid, lists 1 and 3 the uv grid
             for (int l = 0; l < 4; ++l) {
                 if (h->lists.n[l] == 0) continue;
@@ -566,17 +550,14 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
                     h->lists.p[l], h->lists.n[l], mask);
                 TRY(cudaGetLastError(), "k_mark_list launch");
             }
-            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark + n, n, per_e, d_marks + 4);
+            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark + n, n, per_e, d_marks + 6);
             TRY(cudaGetLastError(), "k_count_sectors launch");
-            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark, n, per_e, d_marks + 6);
+            k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark, n, per_e, d_marks + 7);
             TRY(cudaGetLastError(), "k_count_sectors launch");
-            TRY(cudaMemcpyAsync(vsec, d_marks + 4, sizeof(vsec), cudaMemcpyDeviceToHost, stream), "copy sectors");
+            TRY(cudaMemcpyAsync(sectors, d_marks + 4, sizeof(sectors), cudaMemcpyDeviceToHost, stream),
+                "copy sector counts");
             TRY(cudaMemcpyAsync(marks, d_marks, sizeof(marks), cudaMemcpyDeviceToHost, stream), "copy mark counts");
             TRY(cudaStreamSynchronize(stream), "init kernels");
-            sectors[2] = vsec[0][0];
-            sectors[3] = vsec[1][0];
-            sectors[4] = vsec[0][1];
-            sectors[5] = vsec[1][1];
         }
         h->nzclamp[0] = (int64_t)marks[2];
         h->nzclamp[1] = (int64_t)marks[3];
@@ -660,12 +641,14 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
         const int64_t nruns = h->nruns[0] + h->nruns[1];
         h->traffic[0] = h->nrec * (int64_t)rec_size + (int64_t)(2 * marks[0] + marks[1]) * vs +
                         (2 * L[0] + 4 * L[1]) * es + (int64_t)sizeof(int2) * nruns + (2 * L[2] + 4 * L[3]) * es;
-        // the wall stage at sector granularity: reads (records, velocity sectors, run
-        // descriptors, and the fill of every stress sector written only in part) ...
-        h->traffic[5] = h->nrec * (int64_t)rec_size + 32 * (int64_t)(2 * sectors[0] + sectors[1]) +
-                        (int64_t)sizeof(int2) * nruns + 32 * (int64_t)(2 * sectors[4] + 4 * sectors[5]);
-        // ... and writes (every stress sector written)
+        // the wall stage at sector granularity: writes (every stress sector written) ...
         h->traffic[6] = 32 * (int64_t)(2 * sectors[2] + 4 * sectors[3]);
+        // ... and reads: records, velocity sectors, run descriptors, and each written
+        // stress sector once (a store that does not cover its whole sector makes the
+        // L2 read the sector from memory first; the stage's band stores are scattered
+        // and its solid runs start anywhere, so hardly any store covers a sector whole)
+        h->traffic[5] = h->nrec * (int64_t)rec_size + 32 * (int64_t)(2 * sectors[0] + sectors[1]) +
+                        (int64_t)sizeof(int2) * nruns + h->traffic[6];
         h->traffic[1] = 9 * n * es;
         h->traffic[2] = 4 * (L[4] + L[5]) + (L[4] + 2 * L[5]) * vs;
         h->traffic[3] = h->traffic[2] + (L[4] + 2 * L[5]) * es;
