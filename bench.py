@@ -957,51 +957,71 @@ def run_ensemble(args):
 
     # end to end through the batch API: every member's velocity and stresses in from pinned host memory, the
     # batch step, every member's forcing and statistics out; double-buffered over two batches of the same
-    # members (step s's inputs go in while step s-1 computes and step s-2's results come back)
+    # members (step s's inputs go in while step s-1 computes and step s-2's results come back).  Each field
+    # kind of all members sits in one packed buffer on both sides (the members' fields are views into it),
+    # so a step is 9 host-to-device and 3 device-to-host copies, not one per member and field.
     e2e = None
     if not args.no_e2e:
-        host_in = [[torch.from_numpy(np.ascontiguousarray(x)).to(tdt).pin_memory() for x in (c.u, c.v, c.w)] +
-                   [torch.from_numpy(np.ascontiguousarray(c.tau[k])).to(tdt).pin_memory() for k in inputs.TAU_NAMES]
-                   for c in cases]
-        sets = [(batch, fields, stats)]
-        b2_fields = [fields_of(c, tdt) for c in cases]
-        b2 = wmibm.Batch(handles)
-        if batch.get_tuning():
-            b2.set_tuning(**batch.get_tuning())
-        b2.set_fields(b2_fields)
-        sets.append((b2, b2_fields, b2.new_stats()))
-        host_out = [([[torch.empty(c.shape, dtype=tdt).pin_memory() for _ in range(3)] for c in cases],
+        sizes = [c.npoints for c in cases]
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        n_in = 3 + len(inputs.TAU_NAMES)
+
+        def packed_host(kind_arrays):
+            t = torch.empty(int(offs[-1]), dtype=tdt).pin_memory()
+            for m, a in enumerate(kind_arrays):
+                t[offs[m]:offs[m + 1]] = torch.from_numpy(np.ascontiguousarray(a).ravel()).to(tdt)
+            return t
+
+        host_in = [packed_host([c.u for c in cases]), packed_host([c.v for c in cases]),
+                   packed_host([c.w for c in cases])] + [packed_host([c.tau[k] for c in cases])
+                                                         for k in inputs.TAU_NAMES]
+        sets = []
+        for _ in range(2):
+            dev_in = [torch.empty(int(offs[-1]), dtype=tdt, device=dev) for _ in range(n_in)]
+            dev_out = [torch.empty(int(offs[-1]), dtype=tdt, device=dev) for _ in range(3)]
+            view = lambda t, m: t[offs[m]:offs[m + 1]].view(cases[m].shape)
+            flds = [(view(dev_in[0], m), view(dev_in[1], m), view(dev_in[2], m),
+                     [view(dev_in[3 + q], m) for q in range(len(inputs.TAU_NAMES))],
+                     [view(dev_out[q], m) for q in range(3)]) for m in range(len(cases))]
+            bb = wmibm.Batch(handles)
+            if batch.get_tuning():
+                bb.set_tuning(**batch.get_tuning())
+            bb.set_fields(flds)
+            sets.append((bb, dev_in, dev_out, bb.new_stats()))
+        host_out = [([torch.empty(int(offs[-1]), dtype=tdt).pin_memory() for _ in range(3)],
                      torch.empty(2 * wmibm.STATS_WORDS * len(cases), dtype=torch.float64).pin_memory())
                     for _ in range(2)]
-        h2d = sum(t.numel() * t.element_size() for ins in host_in for t in ins)
-        d2h = sum(t.numel() * t.element_size() for ff in host_out[0][0] for t in ff) + host_out[0][1].numel() * 8
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        d2h = sum(t.numel() * t.element_size() for t in host_out[0][0]) + host_out[0][1].numel() * 8
+        kinds = list(range(n_in))
 
-        def copy_in(b):
-            for ins, fl in zip(host_in, sets[b][1]):
-                for dst, src in zip(list(fl[:3]) + list(fl[3]), ins):
-                    dst.copy_(src, non_blocking=True)
+        def copy_part(q0):
+            def part(b):
+                for q in kinds[q0::3]:
+                    sets[b][1][q].copy_(host_in[q], non_blocking=True)
+            return part
 
         def compute(b):
-            sets[b][0].wall_stress_force(sets[b][2])
+            sets[b][0].wall_stress_force(sets[b][3])
 
         def copy_out(b):
-            for outs, fl in zip(host_out[b][0], sets[b][1]):
-                for dst, src in zip(outs, fl[4]):
-                    dst.copy_(src, non_blocking=True)
-            host_out[b][1].copy_(sets[b][2], non_blocking=True)
+            for dst, src in zip(host_out[b][0], sets[b][2]):
+                dst.copy_(src, non_blocking=True)
+            host_out[b][1].copy_(sets[b][3], non_blocking=True)
 
-        el = pipelined_run(dev, args.steps, [copy_in], compute, copy_out, world)
+        el = pipelined_run(dev, args.steps, [copy_part(0), copy_part(1), copy_part(2)], compute, copy_out, world)
         if world > 1:
             t = torch.tensor([el], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             el = float(t.item())
         e2e = {"value": world * args.steps * points / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
-               "form": "double-buffered over two batches of the same members: step s's inputs copied in on one "
-                       "stream while step s-1 computes on a second and step s-2's forcing and stats come back on "
-                       "a third"}
-        b2.close()
-        del b2_fields, host_in, host_out, sets
+               "form": "double-buffered over two batches of the same members, every field kind of all members in "
+                       "one packed buffer: step s's 9 input kinds copied in on three streams while step s-1 "
+                       "computes and step s-2's 3 forcing kinds and the stats come back on a fourth"}
+        for st in sets:
+            st[0].close()
+        del host_in, host_out, sets
 
     accuracy = None
     if extras:
