@@ -17,7 +17,7 @@
 //   column unit (level k, wy columns): d_y of txy, tyy, tyz, subtracted from f
 // Each unit stages its lines in shared memory, two real lines per complex
 // sequence (z = a + i b; the derivative operator is real, so D z = D a + i D b),
-// runs a radix-8/4/2 Stockham FFT, multiplies by i k / N while loading the first
+// runs a radix-16/8/4/2 Stockham FFT, multiplies by i k / N while loading the first
 // pass of a second forward FFT of the conjugate (IFFT(y) = conj(FFT(conj y))/N),
 // and writes.  Units are dispensed by an atomic ticket in chunks of kc levels:
 // the row units of chunk c, then the column units of chunk c-1.  A column unit
@@ -100,6 +100,20 @@ __device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }       // -i a
 // the stride-R writes of the first Stockham pass over the banks.
 __device__ __forceinline__ int sk(int e) { return e + (e >> 5); }
 
+// log2 of the radix of the Stockham pass that starts at Ns = 2^logns in a
+// transform of N = 2^logn points: as few passes as radix 2^maxlog allows, their
+// radices as even as possible (FP32, radix up to 16: 256 = 16 x 16,
+// 512 = 8 x 8 x 8, 1024 = 16 x 8 x 8; FP64, whose values take twice the
+// registers: radix up to 8).
+__host__ __device__ constexpr int pass_log(int logn, int logns, int maxlog)
+{
+    return logn - logns <= 0 ? 0
+                             : (logn - logns + (logn - logns + maxlog - 1) / maxlog - 1) /
+                                   ((logn - logns + maxlog - 1) / maxlog);
+}
+template <typename T>
+constexpr int kMaxPassLog = sizeof(T) == 4 ? 4 : 3;
+
 // R-point forward DFT in registers, natural order in and out:
 // V[q] = sum_r v[r] exp(-2 pi i r q / R).
 template <typename T, int R>
@@ -131,6 +145,43 @@ struct Dft<T, 4> {
 };
 
 template <typename T>
+struct Dft<T, 16> {
+    // four 4-point DFTs over the stride-4 subsequences, the twiddles
+    // exp(-2 pi i r2 q1 / 16), then four 4-point DFTs across them:
+    // V[q1 + 4 q2] = sum_r2 w4^(r2 q2) w16^(r2 q1) sum_r1 v[4 r1 + r2] w4^(r1 q1)
+    template <typename C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        const T c = T(0.92387953251128675613), s = T(0.38268343236508977173), h = T(0.70710678118654752440);
+        C a[4][4];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+            C x[4] = {v[r2], v[4 + r2], v[8 + r2], v[12 + r2]};
+            Dft<T, 4>::run(x);
+#pragma unroll
+            for (int q1 = 0; q1 < 4; ++q1) a[r2][q1] = x[q1];
+        }
+        const C w1{c, -s}, w2{h, -h}, w3{s, -c}, w6{-h, -h}, w9{-c, s};
+        a[1][1] = cmul(a[1][1], w1);
+        a[1][2] = cmul(a[1][2], w2);
+        a[1][3] = cmul(a[1][3], w3);
+        a[2][1] = cmul(a[2][1], w2);
+        a[2][2] = cmi(a[2][2]);                                       // w16^4 = -i
+        a[2][3] = cmul(a[2][3], w6);
+        a[3][1] = cmul(a[3][1], w3);
+        a[3][2] = cmul(a[3][2], w6);
+        a[3][3] = cmul(a[3][3], w9);
+#pragma unroll
+        for (int q1 = 0; q1 < 4; ++q1) {
+            C y[4] = {a[0][q1], a[1][q1], a[2][q1], a[3][q1]};
+            Dft<T, 4>::run(y);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) v[q1 + 4 * q2] = y[q2];
+        }
+    }
+};
+
+template <typename T>
 struct Dft<T, 8> {
     // even / odd halves by two 4-point DFTs, joined with exp(-2 pi i q / 8)
     template <typename C>
@@ -152,7 +203,7 @@ struct Dft<T, 8> {
     }
 };
 
-// One Stockham pass of radix R = min(8, N/Ns) over S sequences of length
+// One Stockham pass of radix R = 2^pass_log(LOGN, LOGNS, kMaxPassLog<T>) over S sequences of length
 // N = 2^LOGN, from a to b, after passes that reached Ns = 2^LOGNS.  Butterfly j
 // of a sequence reads elements j + r N/R, twiddles them by
 // omega_N^(r jm N/(Ns R)) with jm = j mod Ns, and writes element
@@ -169,7 +220,7 @@ __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict_
                                          const typename Cx<T>::type *__restrict__ tw, const T *__restrict__ kn)
 {
     using C = typename Cx<T>::type;
-    constexpr int LOGR = LOGN - LOGNS >= 3 ? 3 : LOGN - LOGNS;
+    constexpr int LOGR = pass_log(LOGN, LOGNS, kMaxPassLog<T>);
     constexpr int R = 1 << LOGR;
     constexpr int LOGNB = LOGN - LOGR;
     constexpr int NB = 1 << LOGNB;
@@ -210,7 +261,7 @@ struct Passes {
     using C = typename Cx<T>::type;
     __device__ __forceinline__ static C *run(C *a, C *b, int S, int ld, const C *tw, const T *kn)
     {
-        constexpr int LOGR = LOGN - LOGNS >= 3 ? 3 : LOGN - LOGNS;
+        constexpr int LOGR = pass_log(LOGN, LOGNS, kMaxPassLog<T>);
         fft_pass<T, LOGN, LOGNS, PRE>(a, b, S, ld, tw, kn);
         __syncthreads();
         return Passes<T, LOGN, LOGNS + LOGR, false>::run(b, a, S, ld, tw + (((1 << LOGR) - 1) << LOGNS), kn);
@@ -234,7 +285,7 @@ __device__ __forceinline__ void fft_first_pass(const T *__restrict__ P, typename
                                                int logL, int ld)
 {
     using C = typename Cx<T>::type;
-    constexpr int LOGR = LOGN >= 3 ? 3 : LOGN;
+    constexpr int LOGR = pass_log(LOGN, 0, kMaxPassLog<T>);
     constexpr int R = 1 << LOGR;
     constexpr int LOGNB = LOGN - LOGR;
     constexpr int NB = 1 << LOGNB;
@@ -282,7 +333,7 @@ __device__ __forceinline__ typename Cx<T>::type *derive_n(T *P, typename Cx<T>::
                                                           const typename Cx<T>::type *tw, const T *kn)
 {
     using C = typename Cx<T>::type;
-    constexpr int LOGR = LOGN >= 3 ? 3 : LOGN;
+    constexpr int LOGR = pass_log(LOGN, 0, kMaxPassLog<T>);
     C *B = reinterpret_cast<C *>(P);
     const int S = (1 << logL) + (1 << logL) / 2;
     fft_first_pass<T, LOGN, ROWS>(P, A, logL, ld);
@@ -585,7 +636,7 @@ int upload_tables(wmibm_handle *h, SpecState *s, cudaStream_t stream)
         // per-pass twiddles: pass (Ns, R) holds omega_N^(r jm N/(Ns R)) at (r - 1) Ns + jm
         int at = 0;
         for (int logNs = 0, logN = ilog2_exact(N); logNs < logN;) {
-            const int logR = logN - logNs >= 3 ? 3 : logN - logNs;
+            const int logR = pass_log(logN, logNs, kMaxPassLog<T>);
             const int Ns = 1 << logNs, R = 1 << logR;
             for (int r = 1; r < R; ++r)
                 for (int jm = 0; jm < Ns; ++jm) {
