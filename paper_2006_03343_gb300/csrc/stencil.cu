@@ -1855,21 +1855,25 @@ bool stencil_config(const wmibm_handle *h, const void *const tau[6], void *const
     };
     c.rows = h->tuning.rows;
     c.stages = h->tuning.stages;
+    const bool default_shape = c.rows == 0 && c.stages == 0 && h->tuning.consumer_warps == 0;
     if (c.rows == 0) {
-        // default: 2-row strips with at least 3 stages within ~110 KB of shared
-        // memory (two or three blocks per SM); 1-row strips when rows are wide
-        c.rows = (h->ny % 2 == 0 && h->ny >= 4) ? 2 : 1;
-        if (c.rows == 2 && c.stages == 0 && ring_bytes(2, 3) > 110 * 1024) c.rows = 1;
+        // default: the shape the autotuner keeps for the measured grids (nx 256 and
+        // 512): 4-row strips and two stages; narrower strips where the rows do not
+        // divide ny or the rings would not fit
+        c.rows = 4;
+        while (c.rows > 1 && (h->ny % c.rows != 0 || h->ny < c.rows + 2 ||
+                              ring_bytes(c.rows, c.stages > 0 ? c.stages : 2) + 256 > (size_t)kMaxDynSmem))
+            c.rows /= 2;
     }
     if (!(c.rows == 1 || c.rows == 2 || c.rows == 4)) return false;
     if (h->ny % c.rows != 0 || h->ny < c.rows + 2) return false;
-    if (c.stages == 0) {
-        c.stages = 4;
-        while (c.stages > 2 && ring_bytes(c.rows, c.stages) > 110 * 1024) --c.stages;
-    }
+    if (c.stages == 0) c.stages = 2;
     if (c.stages < 2 || c.stages > 8) return false;
     if (ring_bytes(c.rows, c.stages) + 256 > (size_t)kMaxDynSmem) return false;
-    c.consumer_warps = h->tuning.consumer_warps > 0 ? h->tuning.consumer_warps : 4;
+    // default consumers: 4, or 8 when the rings leave room for one block per SM only
+    c.consumer_warps = h->tuning.consumer_warps > 0
+                           ? h->tuning.consumer_warps
+                           : (default_shape && ring_bytes(c.rows, c.stages) + 256 > 113 * 1024 ? 8 : 4);
     c.wall_warps = h->tuning.wall_warps;
     if (1 + c.consumer_warps > 16) return false;
     c.blocks_per_sm = h->tuning.blocks_per_sm;
