@@ -2,7 +2,9 @@
 Eqs. 13-14, vertical differences by Eqs. 15-16) against the FP64 oracle's
 force_spectral on the same seeded stresses: small grids that span several row
 and column units, several level chunks and the edge sizes (2-point lines, the
-longest lines (2048 points FP32, 1024 FP64), nx < ny and nx > ny); the full 512 x 256 x 256 hill grid on
+longest lines (2048 points FP32, 1024 FP64), every radix sequence of the FP32
+passes (16, 16 x 8, 16 x 16, 16 x 8 x 8, 16 x 16 x 8), nx < ny and nx > ny); the
+full 512 x 256 x 256 hill grid on
 sampled levels; graph replay; determinism; and the stage a1 + spectral a2
 against the oracle's wall stress followed by its spectral divergence."""
 import numpy as np
@@ -72,7 +74,8 @@ def test_spectral_force_matches_oracle(wm, oracle_mod, shape, dtype):
 
 
 @pytest.mark.parametrize("shape,dtype", [((512, 256, 12), "f32"), ((512, 256, 8), "f64"), ((2048, 4, 3), "f32"),
-                                         ((8, 2048, 3), "f32"), ((1024, 8, 3), "f64"), ((4, 1024, 3), "f64")])
+                                         ((8, 2048, 3), "f32"), ((1024, 8, 3), "f64"), ((4, 1024, 3), "f64"),
+                                         ((1024, 16, 3), "f32"), ((16, 1024, 3), "f32")])
 def test_spectral_force_several_chunks_and_longest_lines(wm, oracle_mod, shape, dtype):
     """Grids whose level chunks are fewer than the levels (the column units wait on
     row units of earlier chunks) and the longest lines in either direction (2048
