@@ -410,12 +410,31 @@ __device__ __forceinline__ void stage_copies(const SpecParams<T> &p, T *P, int k
     }
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 template <typename T>
 __device__ void stage_unit(const SpecParams<T> &p, T *P, int kind, int level, int idx)
 {
     if (p.v16) stage_copies<T, 16>(p, P, kind, level, idx);
     else stage_copies<T, (int)sizeof(T)>(p, P, kind, level, idx);
     cp_async_commit();
+    // a row unit's epilogue reads the vertical terms of its rows (tzz at k and
+    // k - 1, txz and tyz at k + 1, tyz at k), which no unit has staged yet: start
+    // them towards L2 now, a unit ahead, so that the epilogue waits on L2, not DRAM
+    if (kind == 0 && p.v16 && level < p.nz - 1 && threadIdx.x == 0) {
+        const int64_t plane = (int64_t)p.nx * p.ny;
+        const int64_t base = (int64_t)level * plane + ((int64_t)idx << (p.logrx + p.lognx));
+        const uint32_t bytes = (uint32_t)(sizeof(T) << (p.logrx + p.lognx));
+        prefetch_l2(p.tzz + base, bytes);
+        if (level > 0) prefetch_l2(p.tzz + base - plane, bytes);
+        prefetch_l2(p.tyz + base, bytes);
+        prefetch_l2(p.txz + base + plane, bytes);
+        prefetch_l2(p.tyz + base + plane, bytes);
+    }
 }
 
 // Row unit on level k, rows j0 .. j0 + rx - 1, whose input lines are staged in
