@@ -101,13 +101,16 @@ __device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }       // -i a
 __device__ __forceinline__ int sk(int e) { return e + (e >> 5); }
 
 // log2 of the radix of the Stockham pass that starts at Ns = 2^logns in a
-// transform of N = 2^logn points: as few passes as radix 2^maxlog allows, their
-// radices as even as possible (FP32, radix up to 16: 256 = 16 x 16,
-// 512 = 8 x 8 x 8, 1024 = 16 x 8 x 8; FP64, whose values take twice the
-// registers: radix up to 8).
+// transform of N = 2^logn points: as few passes as radix 2^maxlog allows, the
+// first at the largest radix and the others as even as possible (FP32, radix up
+// to 16: 256 = 16 x 16, 512 = 16 x 8 x 4, 1024 = 16 x 8 x 8; FP64, whose values
+// take twice the registers: radix up to 8).  A first pass of radix 16 keeps the
+// second pass's stride at Ns = 16: with the one-per-32 skew its stores spread
+// two lanes to an 8-byte bank slot, where Ns = 8 (512 = 8 x 8 x 8) put four.
 __host__ __device__ constexpr int pass_log(int logn, int logns, int maxlog)
 {
     return logn - logns <= 0 ? 0
+           : logns == 0      ? (logn < maxlog ? logn : maxlog)
                              : (logn - logns + (logn - logns + maxlog - 1) / maxlog - 1) /
                                    ((logn - logns + maxlog - 1) / maxlog);
 }
