@@ -206,6 +206,28 @@ struct Dft<T, 8> {
     }
 };
 
+// The R outputs of a first-pass butterfly (Ns = 1: element r of the butterfly at
+// out[r]).  With R = 16 the elements of butterfly j start at 16 j + j/2 under the
+// skew, so butterflies j and j + 1 of a half-warp share their 8-byte bank slots:
+// an odd j writes its upper half first, which spreads each store's 16 lanes over
+// 16 slots (FP32, NB >= 16: a half-warp holds 16 butterflies of one sequence).
+template <typename T, int R, int NB, typename C>
+__device__ __forceinline__ void store_first_pass(C *out, const C *v, int j)
+{
+    constexpr bool kRot = sizeof(T) == 4 && R == 16 && NB >= 16;
+    if (kRot) {
+        const bool odd = (j & 1) != 0;
+        C *const lo = out + (odd ? R / 2 : 0), *const hi = out - (odd ? R / 2 : 0);
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) lo[i] = odd ? v[i + R / 2] : v[i];
+#pragma unroll
+        for (int i = R / 2; i < R; ++i) hi[i] = odd ? v[i - R / 2] : v[i];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[r] = v[r];
+    }
+}
+
 // One Stockham pass of radix R = 2^pass_log(LOGN, LOGNS, kMaxPassLog<T>) over S sequences of length
 // N = 2^LOGN, from a to b, after passes that reached Ns = 2^LOGNS.  Butterfly j
 // of a sequence reads elements j + r N/R, twiddles them by
@@ -251,8 +273,12 @@ __device__ __forceinline__ void fft_pass(const typename Cx<T>::type *__restrict_
         }
         Dft<T, R>::run(v);
         C *out = b + s * ld + sk(((j - jm) << LOGR) + jm);
+        if (LOGNS == 0) {
+            store_first_pass<T, R, NB>(out, v, j);
+        } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[r * NS + ((r * NS) >> 5)] = v[r];
+            for (int r = 0; r < R; ++r) out[r * NS + ((r * NS) >> 5)] = v[r];
+        }
     }
 }
 
@@ -326,8 +352,12 @@ __device__ __forceinline__ void fft_first_pass(const T *__restrict__ P, typename
         }
         Dft<T, R>::run(v);
         C *out = b + s * ld + sk(j * R);
+        if (ROWS) {
+            store_first_pass<T, R, NB>(out, v, j);
+        } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[r] = v[r];
+            for (int r = 0; r < R; ++r) out[r] = v[r];
+        }
     }
 }
 
