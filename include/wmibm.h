@@ -301,7 +301,11 @@ typedef struct wmibm_tuning {
                                  wall model in dedicated blocks (one per SM) instead of a share of
                                  every block, 5 single launch with the band records cut into "wall
                                  items" of wall_chunk records, each a stage of the pipeline of the
-                                 block that owns it, spread over the first half of its clean units */
+                                 block that owns it, spread over the first half of its clean units,
+                                 6 single launch with wall_warps extra warps in every block that
+                                 evaluate the block's share of the band records while the producer
+                                 and consumers stream the clean units.  A batch takes 0 (two
+                                 launches, as 3), 3, 5 or 6 */
     int32_t rows;             /* pipeline: rows per strip, 1, 2 or 4 */
     int32_t stages;           /* pipeline: shared-memory stages, 2..8 */
     int32_t consumer_warps;   /* pipeline: warps forming f, 1..12 */
@@ -435,7 +439,10 @@ int wmibm_batch_create(wmibm_batch **out, wmibm_handle *const *members, int32_t 
  * follow any wmibm_batch_set_tuning. */
 int wmibm_batch_set_fields(wmibm_batch *b, const wmibm_member_fields *fields, void *stream);
 
-/* Tile shape of the batch launches (rows, stages, consumer_warps, blocks_per_sm used). */
+/* Tile shape and form of the batch launches (force_path, rows, stages, consumer_warps,
+ * wall_warps, blocks_per_sm, dyn_chunk, wall_grid used).  A batch that is never
+ * tuned (every field 0) takes two launches, 4-row strips, two stages, four
+ * consumer warps and runs of at least 16 units. */
 int wmibm_batch_set_tuning(wmibm_batch *b, const wmibm_tuning *t);
 
 /*

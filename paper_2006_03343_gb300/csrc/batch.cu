@@ -61,8 +61,9 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Tile shape of the batch: the widest members take `rows` x-rows per strip
 // (tuning.rows, default 4); narrower members take proportionally more rows (at
 // most 16, dividing ny) so that every member's stage carries about the same
-// bytes.  The stage slots hold the largest member's stage halves; as many as fit
-// ~110 KB (2..4) unless the tuning sets them.
+// bytes.  The stage slots hold the largest member's stage halves; two unless the
+// tuning sets them (the autotuner's pick on the measured ensembles: three blocks
+// per SM).
 bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out, uint32_t *half_a,
                   uint32_t *half_b)
 {
@@ -88,10 +89,7 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
     }
     auto ring_bytes = [&](int s) { return ((size_t)s * ha + (size_t)(s + 1) * hb) * es; };
     int stages = b->tuning.stages;
-    if (stages == 0) {
-        stages = 4;
-        while (stages > 2 && ring_bytes(stages) > 110 * 1024) --stages;
-    }
+    if (stages == 0) stages = 2;
     if (stages < 2 || stages > 8 || ring_bytes(stages) + 256 > 200 * 1024) return false;
     out->rows = 0;                 // per member
     out->stages = stages;
@@ -99,7 +97,12 @@ bool batch_config(wmibm_batch *b, StencilConfig *out, std::vector<int> *rows_out
     out->wall_warps = b->tuning.wall_warps;
     out->blocks_per_sm = b->tuning.blocks_per_sm;
     out->wall_chunk = b->tuning.wall_chunk;
-    out->dyn_chunk = b->tuning.dyn_chunk;
+    // a batch that was never tuned also takes its units in runs of at least 16 (the
+    // autotuner's pick on the measured ensembles; a fixed share per block left a
+    // spread of about 50 us between the first and the last block)
+    const wmibm_tuning none = {};
+    const bool untuned = memcmp(&b->tuning, &none, sizeof(none)) == 0;
+    out->dyn_chunk = untuned ? 16 : b->tuning.dyn_chunk;
     out->wall_grid = b->tuning.wall_grid;
     if (b->tuning.wall_grid < 0 || b->tuning.wall_grid > 32) return false;
     // one launch (force_path 0 or 6: wall warps; 5: interleaved wall stages) or two launches (3)
@@ -173,7 +176,8 @@ int step_impl(wmibm_batch *b, wmibm_band_stats *stats, int do_mask, cudaStream_t
     p.wait_ns = b->wait_ns;
     p.hold_release = b->hold_release;
     const int wall_blocks = 0;   // one wave of resident blocks
-    const int form = b->tuning.force_path == 0 ? 6 : b->tuning.force_path;
+    // untuned: two launches, the form the autotuner keeps on the measured ensembles
+    const int form = b->tuning.force_path == 0 ? 3 : b->tuning.force_path;
     int st = batch_launch<T, VEL>(b->members[0], (const Member<T> *)b->dev_members, b->count, p, b->cfg, b->max_nx,
                                   wall_blocks, form, stream);
     if (st) return berr(b, st, "%s", b->members[0]->err);
