@@ -1406,7 +1406,7 @@ def run_spectral(args):
                 "spectral_shape": {"rows_per_row_unit": shape[0], "columns_per_column_unit": shape[1],
                                    "levels_per_chunk": shape[2], "smem_bytes": shape[3]},
                 "timing": "per step: CUDA events around one graph replay of wall stress then the spectral forcing",
-                "gpu_launches": 3 * args.steps,      # k_wall, k_stats_emit, k_spectral
+                "gpu_launches": 2 * args.steps,      # k_wall (its last block converts the statistics), k_spectral
                 "device_status": status, "accuracy": accuracy,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line))
@@ -1516,7 +1516,7 @@ def run_sgs(args):
     kms = float(np.mean(parts["sgs"]))
     peak, peak_kind = measured_peak()
     achieved = kbytes / (kms * 1e-3) / 1e9
-    launches = 4                                   # k_sgs, k_wall, k_stats_emit, k_force
+    launches = 3                                   # k_sgs, k_wall (statistics converted by its last block), k_force
 
     e2e = None
     if not args.no_e2e and not args.profile:

@@ -875,11 +875,14 @@ __device__ void zero_runs(const Member<T> &mm, int64_t gw, int64_t nwarps, int l
 
 // Single terrain: the grid shares the band records two per thread and round;
 // band statistics accumulate per thread, are reduced per block and then by the
-// last block.
+// last block (into the caller's scratch), or go to the handle's FP64
+// accumulator, which the last block out converts when the call asks for the
+// statistics (emit_stats) and the stencil launch that follows otherwise.
 template <typename T, typename VEL>
 __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
 {
     __shared__ T red[32][kStatVals];
+    __shared__ bool s_last;
     // let the stencil kernel (next in the stream) launch right away
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     T acc[kStatVals];
@@ -904,20 +907,22 @@ __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     zero_runs(mm, gw, nwarps, threadIdx.x & 31);
     if (p.sacc) {
-        // statistics into the accumulator (a later launch converts them)
+        // statistics into the accumulator
         stats_block_reduce(acc, red);
         if (threadIdx.x == 0) stats_red(acc, p.sacc);
+        if (p.emit_stats && threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
+            if (s_last) {
+                __threadfence();
+                stats_emit(p.sacc, p.stats, mm.nb_w, mm.nb_uv, mm.nzc_w, mm.nzc_uv);
+                *p.ticket = 0u;
+            }
+        }
     } else if (p.stats) {
         stats_block_reduce(acc, red);
         stats_finish(acc, red, p.partials, p.ticket, gridDim.x, p.stats, mm.nb_w, mm.nb_uv, mm.nzc_w, mm.nzc_uv);
     }
-}
-
-// Converts the band-statistics accumulator of the preceding wall launch.
-__global__ void k_stats_emit(double *sacc, wmibm_band_stats *stats, int64_t count_w, int64_t count_uv,
-                             int64_t nzc_w, int64_t nzc_uv)
-{
-    if (threadIdx.x == 0) stats_emit(sacc, stats, count_w, count_uv, nzc_w, nzc_uv);
 }
 
 // One member's wall-model fields, held in registers while a thread walks its
@@ -1779,11 +1784,10 @@ int launch_wall_single(wmibm_handle *h, void *const tau[6], const void *u, const
         if (h->tuning.wall_grid > 0 && h->tuning.wall_grid < wper) wper = h->tuning.wall_grid;
         blocks = (unsigned)std::min<int64_t>((int64_t)wper * h->sm_count, h->partial_blocks);
     }
+    // with the accumulator and emit, the wall kernel's last block converts the statistics
+    p.emit_stats = (p.sacc && emit) ? 1 : 0;
     k_wall<T, VEL><<<blocks, wthreads, 0, stream>>>(p);
-    int st = cuda_status(h, cudaGetLastError(), "k_wall launch");
-    if (st || !p.sacc || !emit) return st;
-    k_stats_emit<<<1, 32, 0, stream>>>(p.sacc, stats, p.one.nb_w, p.one.nb_uv, p.one.nzc_w, p.one.nzc_uv);
-    return cuda_status(h, cudaGetLastError(), "k_stats_emit launch");
+    return cuda_status(h, cudaGetLastError(), "k_wall launch");
 }
 
 }  // namespace
@@ -2004,8 +2008,8 @@ int stencil_step_fused(wmibm_handle *h, void *u, void *v, void *w, void *const t
 }
 
 // The wall model at every band node and the solid zeros (persistent kernel).
-// emit: convert the statistics here (a one-thread launch after the wall kernel);
-// false when the stencil launch that follows converts them.
+// emit: convert the statistics here (the wall kernel's last block); false when
+// the stencil launch that follows converts them.
 int wall_model(wmibm_handle *h, const void *u, const void *v, const void *w, void *const tau[6],
                wmibm_band_stats *stats, const void *logz0, cudaStream_t stream, bool emit)
 {
