@@ -93,8 +93,9 @@ typedef struct wmibm_band_stats {
 typedef struct wmibm_handle wmibm_handle;
 
 /*
- * wmibm_init - one-time set-up for one terrain (Sec. 3.1 and Sec. 3.3: "phi and
- * n are computed only once"; the node classes are identified at start-up).
+ * wmibm_init - one-time set-up for one terrain (Sec. 3.1 and Sec. 3.3: the
+ * distance phi, the normals and the node classes are fixed per geometry, so
+ * they are computed here once).
  *   out      : receives the new handle
  *   g        : grid; nx*ny*nz must be < 2^31
  *   phi_uv   : HOST, nx*ny*nz doubles: signed distance at the uv-nodes (+ fluid, - solid)

@@ -12,7 +12,7 @@ FFT as the library step: a 2-D transform of each z-plane, exactly as the sum ove
 Functions and the passages they follow:
   classify      Sec. 3.3, node classes on the w-grid and the uv-grid
   normals       Sec. 3.1, n = grad(phi)/|grad(phi)| (Eq. 24)
-  interp        Sec. 3.3, "2nd-order accurate interpolation" (trilinear)
+  interp        Sec. 3.3, second-order accurate interpolation (trilinear)
   wall_stress   Sec. 3.3, Eq. 28 and the tensor rotation tau_ij = a_im a_jn tau'_mn
   wall_model_node  the same wall model evaluated at a single node
   force         Eq. 2 / Eq. 18: f = -div(tau) on the staggered grid (Eqs. 15-16)

@@ -25,7 +25,7 @@
  *       the caller passes it.
  *   R2  the velocity sample point lies at distance phi_c from the SURFACE
  *       along n: x_c = x + (phi_c - phi(x)) n (Sec. 3.3).
- *   R3  "2nd-order accurate interpolation" = trilinear interpolation of each
+ *   R3  the second-order accurate interpolation = trilinear interpolation of each
  *       velocity component on its own staggered grid, periodic in x and y,
  *       clamped to the physical levels in z (uv: 0..nz-2, w: 0..nz-1).
  *   R4  grad(phi) by 2nd-order central differences on the node's own grid,

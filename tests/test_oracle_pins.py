@@ -223,7 +223,7 @@ def test_rotation_covariance(oracle_mod):
 # T4: interpolation equals brute-force periodic tent weights
 # --------------------------------------------------------------------------- #
 def test_interp_brute_force(oracle_mod):
-    """Sec. 3.3 '2nd-order accurate interpolation' read as trilinear: the sum over
+    """Sec. 3.3's second-order accurate interpolation read as trilinear: the sum over
     ALL nodes of product tent weights max(0, 1 - |d|/h) (periodic in x, y)."""
     rng = np.random.default_rng(11)
     nx, ny, nz = 8, 8, 8
@@ -405,7 +405,7 @@ def test_force_plane_sums_telescope(oracle_mod):
 @pytest.mark.parametrize("with_gradp", [False, True])
 def test_mask_sets(oracle_mod, with_gradp):
     """Eq. 27: entries with phi <= 0 (on each component's own grid) become
-    3 dt/2 grad p (or 0, Sec. 3.2 'velocity inside the body is always zero');
+    3 dt/2 grad p (or 0 without a pressure gradient: Sec. 3.2 keeps the body at rest);
     all others are untouched."""
     case = inputs.make("ridge", shape=(32, 8, 16), seed=9)
     rng = np.random.default_rng(1)
