@@ -493,7 +493,8 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
 
     h->nrec = h->lists.n[0] + h->lists.n[1];
     // [0, 1]: distinct velocity elements the band stencils read on each grid;
-    // [2, 3]: band nodes (w, uv) whose sample point's level is clamped
+    // [2, 3]: band nodes (w, uv) whose sample point's level is clamped;
+    // [4, 5]: velocity sectors read (uv grid, w grid); [6, 7]: stress sectors written (w grid, uv grid)
     TRY(dev_alloc(&d_marks, 8 * sizeof(unsigned long long)), "cudaMalloc mark counts");
     TRY(cudaMemsetAsync(d_marks, 0, 8 * sizeof(unsigned long long), stream), "memset mark counts");
     {
@@ -540,8 +541,7 @@ extern "C" int wmibm_init(wmibm_handle **out, const wmibm_grid *g, const double 
             TRY(cudaGetLastError(), "k_count_sectors launch");
             k_count_sectors<<<1024, kThreads, 0, stream>>>(d_mark + n, n, per_v, d_marks + 5);
             TRY(cudaGetLastError(), "k_count_sectors launch");
-            TRY(cudaStreamSynchronize(stream), "velocity sectors");
-            TRY(cudaMemsetAsync(d_mark, 0, 2 * n, stream), "memset marks");
+            TRY(cudaMemsetAsync(d_mark, 0, 2 * n, stream), "memset marks");   // stream order: after the counts
             // lists 0 and 2 (w band, w solid) mark the w grid, lists 1 and 3 the uv grid
             for (int l = 0; l < 4; ++l) {
                 if (h->lists.n[l] == 0) continue;
