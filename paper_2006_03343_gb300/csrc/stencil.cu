@@ -838,11 +838,20 @@ __device__ __forceinline__ void store_band(const Member<T> &mm, const BandOut<T>
     }
 }
 
+// Descriptor of solid run t of one member (w-runs first), or an empty run past the end.
+template <typename T>
+__device__ __forceinline__ int2 run_at(const Member<T> &mm, int64_t t)
+{
+    return t < mm.nr_w + mm.nr_uv ? __ldg(t < mm.nr_w ? mm.runs_w + t : mm.runs_uv + (t - mm.nr_w)) : make_int2(0, 0);
+}
+
 // Solid runs of one member, warp-cooperative: warp gw of nwarps takes runs
 // gw, gw + nwarps, ...: lane q fetches the descriptor of the q-th of them, then
-// the warp zeroes them one after the other with coalesced stores.
+// the warp zeroes them one after the other with coalesced stores.  first: the
+// descriptor of this lane's first run, when the caller loaded it early so that
+// its latency overlaps other work.
 template <typename T>
-__device__ void zero_runs(const Member<T> &mm, int64_t gw, int64_t nwarps, int lane)
+__device__ void zero_runs(const Member<T> &mm, int64_t gw, int64_t nwarps, int lane, const int2 *first = nullptr)
 {
     T *const oxx = const_cast<T *>(mm.tau[0]), *const oxy = const_cast<T *>(mm.tau[1]);
     T *const oyy = const_cast<T *>(mm.tau[2]), *const ozz = const_cast<T *>(mm.tau[3]);
@@ -850,8 +859,7 @@ __device__ void zero_runs(const Member<T> &mm, int64_t gw, int64_t nwarps, int l
     const int64_t nruns = mm.nr_w + mm.nr_uv;
     for (int64_t base = gw; base < nruns; base += nwarps * 32) {
         const int64_t t = base + (int64_t)lane * nwarps;
-        int2 run = make_int2(0, 0);
-        if (t < nruns) run = __ldg(t < mm.nr_w ? mm.runs_w + t : mm.runs_uv + (t - mm.nr_w));
+        const int2 run = (first && base == gw) ? *first : run_at(mm, t);
         const int nq = (int)min((int64_t)32, (nruns - base + nwarps - 1) / nwarps);
         for (int q = 0; q < nq; ++q) {
             const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
@@ -891,6 +899,10 @@ __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
     const int64_t nrec = mm.nb_w + mm.nb_uv;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    // this lane's first solid-run descriptor, in flight during the band records
+    const int2 run0 = run_at(mm, gw + (int64_t)(threadIdx.x & 31) * nwarps);
     for (int64_t t0 = tid; t0 < nrec; t0 += 2 * stride) {
         const int64_t t1 = t0 + stride;
         BandOut<T> a, b;
@@ -903,9 +915,7 @@ __global__ void __launch_bounds__(256) k_wall(KParams<T> p)
             stats_add(acc, t1 < mm.nb_w ? 0 : 1, b.tw, b.ur);
         }
     }
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    zero_runs(mm, gw, nwarps, threadIdx.x & 31);
+    zero_runs(mm, gw, nwarps, threadIdx.x & 31, &run0);
     if (p.sacc) {
         // statistics into the accumulator
         stats_block_reduce(acc, red);
@@ -960,78 +970,117 @@ __device__ __forceinline__ void store_regs(const WallRegs<T> &r, const BandOut<T
     store_band(*r.src, o, is_w);
 }
 
-// Solid runs of every member of a batch over the concatenated run space
-// (runs of member m at [run_off, run_off + nr_w + nr_uv), w-runs first); the
-// same warp-cooperative scheme as zero_runs.
-template <typename T>
-__device__ void zero_runs_batch(const KParams<T> &p, int64_t gw, int64_t nwarps, int lane)
+// A batch's member table in the batch wall kernel's shared memory: per member
+// its first band record, record array, first solid run, first uv-run and run
+// arrays; roff and runoff end with the totals (nmembers + 1 entries).
+struct BatchTable {
+    int64_t *roff, *runoff, *uvoff;
+    const void **rec;
+    const int2 **runs_w, **runs_uv;
+};
+
+__device__ __forceinline__ int find_first(const int64_t *first, int n, int64_t g)
 {
-    const int64_t nruns = p.run_total;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Solid runs [lo, hi) of the concatenated run space of a batch (runs of member m
+// at [run_off, run_off + nr_w + nr_uv), w-runs first), zeroed by one warp: each
+// lane loads the descriptors of four batches of 32 consecutive runs at once,
+// then the warp zeroes the runs one after the other with coalesced stores.
+// Consecutive runs mostly share a member, so the stress pointers are rarely
+// reloaded.
+template <typename T>
+__device__ void zero_runs_range(const KParams<T> &p, const BatchTable &mt, int64_t lo, int64_t hi, int lane)
+{
+    constexpr int kDepth = 4;
     int cm = -1;
     T *oxx = nullptr, *oxy = nullptr, *oyy = nullptr, *ozz = nullptr, *oxz = nullptr, *oyz = nullptr;
-    for (int64_t base = gw; base < nruns; base += nwarps * 32) {
-        const int64_t t = base + (int64_t)lane * nwarps;
-        int2 run = make_int2(0, 0);
-        int mrun = 0, wrun = 0;
-        if (t < nruns) {
-            mrun = find_member_at(p, &Member<T>::run_off, t);
-            const Member<T> &mm = p.list[mrun];
-            const int64_t lt = t - mm.run_off;
-            wrun = lt < mm.nr_w;
-            run = __ldg(wrun ? mm.runs_w + lt : mm.runs_uv + (lt - mm.nr_w));
-        }
-        const int nq = (int)min((int64_t)32, (nruns - base + nwarps - 1) / nwarps);
-        for (int q = 0; q < nq; ++q) {
-            const int32_t start = __shfl_sync(0xffffffffu, run.x, q);
-            const int32_t len = __shfl_sync(0xffffffffu, run.y, q);
-            const int m = __shfl_sync(0xffffffffu, mrun, q);
-            const bool is_w = __shfl_sync(0xffffffffu, wrun, q) != 0;
-            if (m != cm) {
-                const Member<T> &mm = p.list[m];
-                oxx = const_cast<T *>(mm.tau[0]); oxy = const_cast<T *>(mm.tau[1]);
-                oyy = const_cast<T *>(mm.tau[2]); ozz = const_cast<T *>(mm.tau[3]);
-                oxz = const_cast<T *>(mm.tau[4]); oyz = const_cast<T *>(mm.tau[5]);
-                cm = m;
+    for (int64_t base = lo; base < hi; base += 32 * kDepth) {
+        int2 run[kDepth];
+        int mrun[kDepth];
+        bool wrun[kDepth];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int64_t t = base + d * 32 + lane;
+            run[d] = make_int2(0, 0);
+            mrun[d] = 0;
+            wrun[d] = false;
+            if (t < hi) {
+                const int m = find_first(mt.runoff, p.nmembers, t);
+                mrun[d] = m;
+                wrun[d] = t < mt.uvoff[m];
+                run[d] = __ldg(wrun[d] ? mt.runs_w[m] + (t - mt.runoff[m]) : mt.runs_uv[m] + (t - mt.uvoff[m]));
             }
-            for (int32_t x = lane; x < len; x += 32) {
-                const int64_t idx = (int64_t)start + x;
-                if (is_w) {
-                    oxz[idx] = T(0);
-                    oyz[idx] = T(0);
-                } else {
-                    oxx[idx] = T(0);
-                    oxy[idx] = T(0);
-                    oyy[idx] = T(0);
-                    ozz[idx] = T(0);
+        }
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            const int64_t b0 = base + d * 32;
+            const int nq = (int)max((int64_t)0, min((int64_t)32, hi - b0));
+            for (int q = 0; q < nq; ++q) {
+                const int32_t start = __shfl_sync(0xffffffffu, run[d].x, q);
+                const int32_t len = __shfl_sync(0xffffffffu, run[d].y, q);
+                const int m = __shfl_sync(0xffffffffu, mrun[d], q);
+                const bool is_w = __shfl_sync(0xffffffffu, (int)wrun[d], q) != 0;
+                if (m != cm) {
+                    const Member<T> &mm = p.list[m];
+                    oxx = const_cast<T *>(mm.tau[0]); oxy = const_cast<T *>(mm.tau[1]);
+                    oyy = const_cast<T *>(mm.tau[2]); ozz = const_cast<T *>(mm.tau[3]);
+                    oxz = const_cast<T *>(mm.tau[4]); oyz = const_cast<T *>(mm.tau[5]);
+                    cm = m;
+                }
+                for (int32_t x = lane; x < len; x += 32) {
+                    const int64_t idx = (int64_t)start + x;
+                    if (is_w) {
+                        oxz[idx] = T(0);
+                        oyz[idx] = T(0);
+                    } else {
+                        oxx[idx] = T(0);
+                        oxy[idx] = T(0);
+                        oyy[idx] = T(0);
+                        ozz[idx] = T(0);
+                    }
                 }
             }
         }
     }
 }
 
-// Batch: block b takes a contiguous slice of the concatenated band records
-// (so that it meets few members); a thread walks its records in increasing
-// order, advancing the member linearly, and accumulates the band statistics of
-// the current member in registers.  When its member changes a lane adds them to
-// the member's FP64 accumulators in the batch scratch with fire-and-forget
-// global reductions; at the end each warp first combines the lanes that hold
-// the same member (one reduction per member and warp).  No shared-memory FP64
-// atomics: on this part their compare-and-swap loops run on the narrow FP64
-// pipe and one contended block held the whole grid back.  Warps then zero the
-// solid runs of every member, and the last block converts the scratch into
-// wmibm_band_stats and clears it for the next call.
+// Batch: a block first copies the member table (record and run offsets and
+// arrays) into shared memory, so that no look-up below waits on a chain of
+// global loads, and starts the copy of its first chunk of records.  While that
+// chunk is on its way, each warp zeroes a contiguous range of the solid runs of
+// all members.  Then the block walks its contiguous slice of the concatenated
+// band records (so that it meets few members); a thread walks its records in
+// increasing order, advancing the member linearly, and accumulates the band
+// statistics of the current member in registers.  When its member changes a
+// lane adds them to the member's FP64 accumulators in the batch scratch with
+// fire-and-forget global reductions; at the end each warp first combines the
+// lanes that hold the same member (one reduction per member and warp).  No
+// shared-memory FP64 atomics: on this part their compare-and-swap loops run on
+// the narrow FP64 pipe and one contended block held the whole grid back.  The
+// last block converts the scratch into wmibm_band_stats and clears it for the
+// next call.
 template <typename T, typename VEL>
 __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
 {
     __shared__ bool s_last;
     __shared__ uint64_t rbar[2];
-    extern __shared__ __align__(128) unsigned char wb_smem[];   // record chunks
+    extern __shared__ __align__(128) unsigned char wb_smem[];   // record chunks, then the member table
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     const int64_t R = p.rec_total;
     const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
     const bool want_stats = p.stats != nullptr;
-    const int m0 = r0 < r1 ? find_member_at(p, &Member<T>::r_off, r0) : 0;
+    const int nm = p.nmembers;
 
     T acc[kStatVals];
     stats_identity(acc);
@@ -1050,6 +1099,29 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
     const int64_t CH = 2 * (int64_t)bd;                  // records per chunk: two per thread
     const int64_t nchunks = (r1 - r0 + CH - 1) / CH;
     Rec *const rbuf = reinterpret_cast<Rec *>(wb_smem);  // [2][CH]
+    // the member table, read from the member list once per block, so that the
+    // look-ups below take no dependent global loads
+    BatchTable mt;
+    mt.roff = reinterpret_cast<int64_t *>(rbuf + 2 * CH);
+    mt.runoff = mt.roff + (nm + 1);
+    mt.uvoff = mt.runoff + (nm + 1);
+    mt.rec = reinterpret_cast<const void **>(mt.uvoff + nm);
+    mt.runs_w = reinterpret_cast<const int2 **>(mt.rec + nm);
+    mt.runs_uv = mt.runs_w + nm;
+    for (int m = threadIdx.x; m <= nm; m += bd) {
+        if (m < nm) {
+            const Member<T> &mm = p.list[m];
+            mt.roff[m] = mm.r_off;
+            mt.runoff[m] = mm.run_off;
+            mt.uvoff[m] = mm.run_off + mm.nr_w;
+            mt.rec[m] = mm.rec;
+            mt.runs_w[m] = mm.runs_w;
+            mt.runs_uv[m] = mm.runs_uv;
+        } else {
+            mt.roff[m] = R;
+            mt.runoff[m] = p.run_total;
+        }
+    }
     if (threadIdx.x == 0) {
         mbar_init(&rbar[0], 1);
         mbar_init(&rbar[1], 1);
@@ -1060,14 +1132,12 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
         const int64_t a = r0 + q * CH, b = min(r1, a + CH);
         Rec *dst = rbuf + (q & 1) * CH;
         mbar_arrive_expect_tx(&rbar[q & 1], (uint32_t)((b - a) * (int64_t)sizeof(Rec)));
-        int m = find_member_at(p, &Member<T>::r_off, a);
-        for (int64_t pos = a; pos < b && m < p.nmembers; ++m) {
-            const Member<T> &mm = p.list[m];
-            const int64_t end = min(b, m + 1 < p.nmembers ? p.list[m + 1].r_off : R);
+        for (int m = find_first(mt.roff, nm, a), pos = 0; pos < b - a && m < nm; ++m) {
+            const int64_t end = min(b, mt.roff[m + 1]) - a;
             if (end > pos)
-                bulk_g2s(dst + (pos - a), reinterpret_cast<const Rec *>(mm.rec) + (pos - mm.r_off),
+                bulk_g2s(dst + pos, reinterpret_cast<const Rec *>(mt.rec[m]) + (a + pos - mt.roff[m]),
                          (uint32_t)((end - pos) * (int64_t)sizeof(Rec)), &rbar[q & 1]);
-            pos = end;
+            pos = (int)end;
         }
     };
     int64_t issued = 0, consumed = 0;                    // thread 0's bookkeeping
@@ -1075,10 +1145,20 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
         issue(0);
         issued = 1;
     }
-    int cm = m0;
+
+    // solid runs of every member (a contiguous range per warp), while the first
+    // chunk of records is on its way
+    {
+        const int64_t nwarps = (int64_t)gridDim.x * (bd / 32);
+        const int64_t gw = (int64_t)blockIdx.x * (bd / 32) + (threadIdx.x >> 5);
+        const int64_t T_ = p.run_total;
+        zero_runs_range(p, mt, T_ * gw / nwarps, T_ * (gw + 1) / nwarps, threadIdx.x & 31);
+    }
+
+    int cm = r0 < r1 ? find_first(mt.roff, nm, r0) : 0;
     WallRegs<T> M;
     load_wall(p.list[cm], M);
-    int64_t r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
+    int64_t r_end = mt.roff[cm + 1];
     for (int64_t q = 0; q < nchunks; ++q) {
         if (threadIdx.x == 0 && q + 1 < nchunks) {       // its buffer was released by the sync below
             issue(q + 1);
@@ -1093,7 +1173,7 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
                 if (want_stats && nacc) flush(cm);
                 do {
                     ++cm;
-                    r_end = cm + 1 < p.nmembers ? p.list[cm + 1].r_off : R;
+                    r_end = mt.roff[cm + 1];
                 } while (g >= r_end);
                 load_wall(p.list[cm], M);
             }
@@ -1147,11 +1227,6 @@ __global__ void __launch_bounds__(256, 2) k_wall_batch(KParams<T> p)
             if (lane == leader) stats_red(v, p.bstats + (int64_t)key * 8);
         }
     }
-
-    // solid runs of every member
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    zero_runs_batch(p, gw, nwarps, threadIdx.x & 31);
 
     if (!want_stats) return;
     __syncthreads();
@@ -2053,14 +2128,17 @@ int batch_launch(wmibm_handle *h0, const Member<T> *dev_members, int nmembers, c
     p.ncons = c.consumer_warps;
     if (form == 5) return launch_stencil_ty<T, VEL, 0, kInterleaved>(h0, p, c, stream, false, max_nx);
     if (form == 6) return launch_stencil_ty<T, VEL, 0, kWarpSpec>(h0, p, c, stream, false, max_nx);
-    // two chunks of 2 x 256 records in shared memory
-    const size_t wsmem = 2 * 2 * 256 * sizeof(typename RecOf<T>::type);
-    static int per_sm = 0;                 // once per instantiation and process
+    // two chunks of 2 x 256 records in shared memory, then the member table
+    // (3 offsets and 3 pointers a member, 8 bytes each, and two end entries)
+    const size_t chunks = 2 * 2 * 256 * sizeof(typename RecOf<T>::type);
+    const size_t wsmem = chunks + (size_t)(6 * nmembers + 2) * 8;
+    const size_t wsmem_max = chunks + (size_t)(6 * kMaxBatchMembers + 2) * 8;
+    static int per_sm = 0;                 // once per instantiation and process (at the largest table)
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_wall_batch<T, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)wsmem);
+                                             (int)wsmem_max);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wall_batch<T, VEL>, 256, wsmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wall_batch<T, VEL>, 256, wsmem_max);
         if (e != cudaSuccess) return cuda_status(h0, e, "batch wall occupancy");
         if (per_sm < 1) per_sm = 1;
     }
