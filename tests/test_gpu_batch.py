@@ -9,7 +9,7 @@ import pytest
 
 from paper_2006_03343_gb300 import inputs
 
-from parity_util import TOL, assert_stats_close, normwise, oracle_step, to_dev, to_host
+from parity_util import TOL, assert_stats_close, normwise, oracle_step, poisoned_tau, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -255,4 +255,53 @@ def test_batch_of_one(wm, oracle_mod, form):
         assert normwise(to_host(fields[0][4][cc]), f_o[cc])[0] <= TOL["f32"], cc
     bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(1, 2)
     assert_stats_close(bstats[0], st_o, "f32")
+    batch.close()
+
+
+def _empty_member(seed):
+    """A member whose wall lies below the floor: no band node, no solid node."""
+    return inputs.flat((24, 16, 10), wall_height=-1.0, lengths=(1.0, 1.0, 1.0), sigma=0.2, seed=seed, dtype="f32")
+
+
+@pytest.mark.parametrize("form", [3, 5, 6])
+@pytest.mark.parametrize("layout", ["mixed", "all_empty"])
+def test_batch_with_empty_members(wm, oracle_mod, form, layout):
+    """Members without band records or solid runs, between members with both (their
+    record and run offsets repeat in the member table) or making up the whole batch
+    (no record and no run at all), leave the fluid stress as it is, report empty
+    statistics, and do not disturb the others: every member matches the oracle."""
+    if layout == "mixed":
+        cases = [_empty_member(11), inputs.ensemble_member(1, shape=(48, 24, 16)), _empty_member(12),
+                 _empty_member(13), inputs.flat((40, 20, 12), wall_height=0.3, sigma=0.2, seed=14, dtype="f32"),
+                 inputs.ensemble_member(2, shape=(32, 16, 20)), _empty_member(15)]
+    else:
+        cases = [_empty_member(21), _empty_member(22), _empty_member(23)]
+    handles = [wm.Handle.from_case(c) for c in cases]
+    batch = wm.Batch(handles)
+    batch.set_tuning(force_path=form)
+    fields = []
+    for c in cases:                       # NaN where the wall model writes, so that a skipped entry shows up
+        u, v, w, _, f = _fields(c, "f32")
+        pt = poisoned_tau(c)
+        fields.append((u, v, w, [to_dev(pt[k], "f32") for k in inputs.TAU_NAMES], f))
+    batch.set_fields(fields)
+    stats = batch.new_stats()
+    for _ in range(2):                    # the second call finds the counters and scratch re-armed
+        batch.wall_stress_force(stats)
+    torch.cuda.synchronize()
+    assert batch.device_status() == wm.OK
+    bstats = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=wm.STATS_DTYPE).reshape(len(cases), 2)
+    for m, c in enumerate(cases):
+        tau_o, f_o, st_o = oracle_step(oracle_mod, c)
+        for k, t in zip(inputs.TAU_NAMES, fields[m][3]):
+            got = to_host(t)
+            assert np.all(np.isfinite(got)), (m, k)
+            assert normwise(got, tau_o[k])[0] <= TOL["f32"], (m, k)
+        for cc in range(3):
+            assert normwise(to_host(fields[m][4][cc]), f_o[cc])[0] <= TOL["f32"], (m, cc)
+        assert_stats_close(bstats[m], st_o, "f32")
+        if float(np.min(c.phi_w)) >= 1.0:          # the members with the wall below the floor
+            for k, t in zip(inputs.TAU_NAMES, fields[m][3]):
+                assert np.array_equal(to_host(t), c.tau[k].astype(np.float32)), (m, k)
+            assert bstats[m][0]["count"] == 0 and bstats[m][1]["count"] == 0
     batch.close()
