@@ -157,3 +157,44 @@ def test_injected_allocation_failure_before_any_gpu_work(lib, monkeypatch):
     assert st != wmibm.ENOMEM
     if st == wmibm.OK:
         lib.wmibm_destroy(h)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The Python mirrors of the header's structs (ctypes Grid, Opts, Tuning,
+    MemberFields and the numpy record of wmibm_band_stats) have the C compiler's
+    size and field offsets, so that a field added to the header without its
+    mirror, or in another order, fails here rather than corrupting a call."""
+    import shutil
+    import subprocess
+    from paper_2006_03343_gb300 import wmibm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"wmibm_grid": wmibm.Grid, "wmibm_opts": wmibm.Opts, "wmibm_tuning": wmibm.Tuning,
+               "wmibm_member_fields": wmibm.MemberFields}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "wmibm.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('    printf("wmibm_band_stats size %zu\\n", sizeof(wmibm_band_stats));')
+    for fname in wmibm.STATS_DTYPE.names:
+        lines.append(f'    printf("wmibm_band_stats {fname} %zu\\n", offsetof(wmibm_band_stats, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        parts = line.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+    assert got[("wmibm_band_stats", "size")] == wmibm.STATS_DTYPE.itemsize
+    for fname in wmibm.STATS_DTYPE.names:
+        assert got[("wmibm_band_stats", fname)] == wmibm.STATS_DTYPE.fields[fname][1], fname
